@@ -1,0 +1,526 @@
+// Brute-force CPU oracle of the batched driving-simulator step.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+// CUDA library is checked against.  Only the test suite, the smoke check and
+// the CPU-baseline leg of the benchmark may load it; the library never does.
+// It shares no code, header, table or constant generator with the CUDA path.
+//
+// Every quantity follows the paper (GPUDrive, arXiv 2408.01584) or, where the
+// paper is silent, the readings written next to the code:
+//   * dynamics: kinematic bicycle model, App. B (the seven equations for
+//     v-dot, v-bar, beta, x-dot, y-dot, theta-dot and the four update lines);
+//   * collision: agents are convex boxes (Sec. 3.2 "Simulator sharp-edges",
+//     "Convex objects only"); the paper's BVH (Sec. 3.1) only prunes pairs,
+//     so the oracle tests every pair;
+//   * off-road: cars and cyclists collide when they drive through a road
+//     edge, pedestrians may cross (Sec. 3.2 "Termination conditions");
+//   * reward 1 on reaching the goal within delta, else 0, with optional
+//     collision penalties (Sec. 3.2 "Rewards");
+//   * termination on goal, optionally on collision; removal after the goal
+//     (Sec. 3.2 "Termination conditions");
+//   * observation: every agent and road point within a fixed radius, in the
+//     agent's relative frame (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1),
+//     truncated to the K / P nearest;
+//   * smooth goal reward (not in the paper): r_s = -(sqrt(d^2 + c^2) - c).
+//
+// Selection is a full std::sort of every candidate by (d^2, index); collision
+// tests every pair and every road-edge segment.  T = double for parity,
+// T = float to measure single-precision rounding.
+//
+// Parity pins live in the test suite (closed forms of App. B, polygon
+// clipping, rigid-motion invariance, brute-force counts); nothing here is
+// pinned against itself.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// flag bits of the per-agent status byte (same meaning as the library's)
+constexpr uint8_t F_DONE = 1, F_GOAL = 2, F_COLLIDED = 4, F_OFFROAD = 8;
+// configuration flag bits
+constexpr uint32_t C_TERM_COLLISION = 1, C_TERM_OFFROAD = 2, C_AUTO_RESET = 4;
+constexpr uint8_t ROAD_EDGE = 1;
+constexpr uint8_t PEDESTRIAN = 2;
+
+struct Config {
+  int k_road, n_partners, episode_len;
+  double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
+  uint32_t flags;
+};
+
+template <typename T>
+struct Box { T cx, cy, ca, sa, hl, hw; };   // centre, heading (cos, sin), half extents
+
+template <typename T>
+struct Env {
+  Config cfg;
+  int W = 0, A = 0, N = 0;
+  std::vector<int32_t> agent_off, road_off;
+  std::vector<T> x, y, th, v;                 // current state
+  std::vector<T> x0, y0, th0, v0;             // initial snapshot (for reset)
+  std::vector<T> len, wid, gx, gy;
+  std::vector<uint8_t> type, flags, flags0;
+  std::vector<T> rx, ry;
+  std::vector<uint8_t> rtype;
+  std::vector<int32_t> rpoly;
+  std::vector<int32_t> t;                     // steps taken in the current episode
+  std::vector<uint8_t> world_done;            // end-of-episode status of the last step
+  // road-edge segments per world: pairs of consecutive ROAD_EDGE points of one polyline
+  std::vector<std::vector<std::pair<int, int>>> segs;
+};
+
+template <typename T>
+T clip(T a, T lo, T hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// ---- App. B: kinematic bicycle model, l_r = 0.5 L, explicit Euler ----------
+template <typename T>
+void bicycle_step(const Config& c, T L, T accel, T steer, T& x, T& y, T& th, T& v) {
+  const T dt = (T)c.dt, vmax = (T)c.v_max;
+  const T vdot = accel;                                               // v-dot = a
+  const T vbar = clip<T>(v + (T)0.5 * vdot * dt, -vmax, vmax);        // mid-step speed
+  const T beta = std::atan((T)0.5 * std::tan(steer));                 // atan(l_r tan(delta) / L)
+  const T xdot = vbar * std::cos(th + beta);
+  const T ydot = vbar * std::sin(th + beta);
+  const T thdot = vbar * std::cos(beta) * std::tan(steer) / L;
+  x = x + xdot * dt;                                                  // uses theta_t
+  y = y + ydot * dt;
+  th = th + thdot * dt;
+  v = clip<T>(v + vdot * dt, -vmax, vmax);
+}
+
+// ---- separating-axis penetration -----------------------------------------
+// Penetration of two intervals [a0,a1] and [b0,b1]: the smaller push that
+// separates them; positive iff they overlap with positive depth.
+template <typename T>
+T interval_pen(T a0, T a1, T b0, T b1) { return std::min(a1 - b0, b1 - a0); }
+
+template <typename T>
+void project_box(const Box<T>& b, T ux, T uy, T& lo, T& hi) {
+  const T c = b.cx * ux + b.cy * uy;
+  const T r = b.hl * std::fabs(ux * b.ca + uy * b.sa) + b.hw * std::fabs(-ux * b.sa + uy * b.ca);
+  lo = c - r;
+  hi = c + r;
+}
+
+// Minimum over the four box axes of the penetration depth: > 0 iff the two
+// oriented rectangles share interior points (touching is not a collision).
+template <typename T>
+T box_box_pen(const Box<T>& p, const Box<T>& q) {
+  const T axes[4][2] = {{p.ca, p.sa}, {-p.sa, p.ca}, {q.ca, q.sa}, {-q.sa, q.ca}};
+  T m = INFINITY;
+  for (auto& u : axes) {
+    T a0, a1, b0, b1;
+    project_box(p, u[0], u[1], a0, a1);
+    project_box(q, u[0], u[1], b0, b1);
+    m = std::min(m, interval_pen(a0, a1, b0, b1));
+  }
+  return m;
+}
+
+// Same for a box and a segment: the two box axes plus the segment normal.
+template <typename T>
+T box_seg_pen(const Box<T>& p, T sx0, T sy0, T sx1, T sy1) {
+  const T ex = sx1 - sx0, ey = sy1 - sy0;
+  const T el = std::sqrt(ex * ex + ey * ey);
+  T axes[3][2] = {{p.ca, p.sa}, {-p.sa, p.ca}, {0, 0}};
+  int na = 2;
+  if (el > 0) { axes[2][0] = -ey / el; axes[2][1] = ex / el; na = 3; }
+  T m = INFINITY;
+  for (int k = 0; k < na; ++k) {
+    const T ux = axes[k][0], uy = axes[k][1];
+    T a0, a1;
+    project_box(p, ux, uy, a0, a1);
+    const T s0 = sx0 * ux + sy0 * uy, s1 = sx1 * ux + sy1 * uy;
+    m = std::min(m, interval_pen(a0, a1, std::min(s0, s1), std::max(s0, s1)));
+  }
+  return m;
+}
+
+template <typename T>
+Box<T> agent_box(const Env<T>& e, int i) {
+  return Box<T>{e.x[i], e.y[i], std::cos(e.th[i]), std::sin(e.th[i]), e.len[i] / 2, e.wid[i] / 2};
+}
+
+template <typename T>
+void reset_world(Env<T>& e, int w) {
+  for (int i = e.agent_off[w]; i < e.agent_off[w + 1]; ++i) {
+    e.x[i] = e.x0[i]; e.y[i] = e.y0[i]; e.th[i] = e.th0[i]; e.v[i] = e.v0[i];
+    e.flags[i] = e.flags0[i];
+  }
+  e.t[w] = 0;
+  e.world_done[w] = 0;
+}
+
+template <typename T>
+bool world_is_done(const Env<T>& e, int w) {
+  const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
+  bool all = a1 > a0;
+  for (int i = a0; i < a1; ++i) all = all && (e.flags[i] & F_DONE);
+  return all || e.t[w] >= e.cfg.episode_len;
+}
+
+// Decisions of one step for world w after the dynamics have moved its active
+// agents: collision, off-road, goal, reward, done, episode end.
+template <typename T>
+void decide_world(Env<T>& e, int w, const std::vector<uint8_t>& active, float* reward, uint8_t* done,
+                  uint8_t* world_done, double* coll_margin, double* off_margin, double* goal_margin,
+                  double* smooth_r) {
+  const Config& c = e.cfg;
+  const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
+  for (int i = a0; i < a1; ++i) {
+    if (!active[i - a0]) {
+      if (reward) reward[i] = 0.f;
+      if (coll_margin) coll_margin[i] = -INFINITY;
+      if (off_margin) off_margin[i] = -INFINITY;
+      if (goal_margin) goal_margin[i] = INFINITY;
+      if (smooth_r) smooth_r[i] = 0.0;
+      continue;
+    }
+    const Box<T> bi = agent_box(e, i);
+    // agent/agent: any other agent active at the start of the step
+    T best = -INFINITY;
+    for (int j = a0; j < a1; ++j) {
+      if (j == i || !active[j - a0]) continue;
+      best = std::max(best, box_box_pen(bi, agent_box(e, j)));
+    }
+    const bool collided = best > 0;
+    // agent/road edge, not for pedestrians
+    T obest = -INFINITY;
+    if (e.type[i] != PEDESTRIAN) {
+      for (auto& s : e.segs[w]) {
+        obest = std::max(obest, box_seg_pen(bi, e.rx[s.first], e.ry[s.first], e.rx[s.second], e.ry[s.second]));
+      }
+    }
+    const bool offroad = obest > 0;
+    const T dx = e.x[i] - e.gx[i], dy = e.y[i] - e.gy[i];
+    const T dg = std::sqrt(dx * dx + dy * dy);
+    const bool at_goal = dg <= (T)c.goal_radius;
+    const bool first_goal = at_goal && !(e.flags[i] & F_GOAL);
+    uint8_t f = e.flags[i] & (uint8_t)~(F_COLLIDED | F_OFFROAD);
+    if (at_goal) f |= F_GOAL;
+    if (collided) f |= F_COLLIDED;
+    if (offroad) f |= F_OFFROAD;
+    if ((f & F_GOAL) || (collided && (c.flags & C_TERM_COLLISION)) || (offroad && (c.flags & C_TERM_OFFROAD)))
+      f |= F_DONE;
+    e.flags[i] = f;
+    if (reward)
+      reward[i] = (float)((first_goal ? 1.0 : 0.0) - (collided ? c.collision_penalty : 0.0) -
+                          (offroad ? c.offroad_penalty : 0.0));
+    if (coll_margin) coll_margin[i] = (double)best;
+    if (off_margin) off_margin[i] = (double)obest;
+    if (goal_margin) goal_margin[i] = (double)dg - c.goal_radius;
+    if (smooth_r) {
+      const double sc = c.smooth_c;
+      smooth_r[i] = -(std::sqrt((double)dx * dx + (double)dy * dy + sc * sc) - sc);
+    }
+  }
+  e.t[w] += 1;
+  e.world_done[w] = world_is_done(e, w) ? 1 : 0;
+  if (done)
+    for (int i = a0; i < a1; ++i) done[i] = (e.flags[i] & F_DONE) ? 1 : 0;
+  if (world_done) world_done[w] = e.world_done[w];
+}
+
+// One full step of every world.  If post_state is given (float [A,4]) the
+// active agents take that state instead of running the dynamics: this lets a
+// test evaluate the decisions on exactly the state another implementation
+// produced.
+template <typename T>
+void step(Env<T>& e, const float* actions, const float* post_state, float* reward, uint8_t* done,
+          uint8_t* world_done, double* cm, double* om, double* gm, double* sr) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int w = 0; w < e.W; ++w) {
+    if ((e.cfg.flags & C_AUTO_RESET) && e.world_done[w]) reset_world(e, w);
+    const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
+    std::vector<uint8_t> active(a1 - a0);
+    for (int i = a0; i < a1; ++i) {
+      active[i - a0] = !(e.flags[i] & F_DONE);
+      if (!active[i - a0]) continue;                       // done agents are frozen
+      if (post_state) {
+        e.x[i] = post_state[4 * i + 0]; e.y[i] = post_state[4 * i + 1];
+        e.th[i] = post_state[4 * i + 2]; e.v[i] = post_state[4 * i + 3];
+      } else {
+        bicycle_step<T>(e.cfg, e.len[i], (T)actions[2 * i], (T)actions[2 * i + 1], e.x[i], e.y[i], e.th[i], e.v[i]);
+      }
+    }
+    decide_world(e, w, active, reward, done, world_done, cm, om, gm, sr);
+  }
+}
+
+// Ego-frame coordinates of point (px, py) seen from agent i: rotate the
+// offset by -theta_i.
+template <typename T>
+void ego_frame(const Env<T>& e, int i, T px, T py, T& xr, T& yr) {
+  const T c = std::cos(e.th[i]), s = std::sin(e.th[i]);
+  const T dx = px - e.x[i], dy = py - e.y[i];
+  xr = c * dx + s * dy;
+  yr = -s * dx + c * dy;
+}
+
+template <typename T>
+void road_feature(const Env<T>& e, int i, int jg, float* f) {
+  T xr, yr;
+  ego_frame(e, i, e.rx[jg], e.ry[jg], xr, yr);
+  f[0] = (float)xr; f[1] = (float)yr; f[2] = (float)e.rtype[jg]; f[3] = 1.f;
+}
+
+template <typename T>
+void partner_feature(const Env<T>& e, int i, int j, float* f) {
+  T xr, yr;
+  ego_frame(e, i, e.x[j], e.y[j], xr, yr);
+  const T dth = e.th[j] - e.th[i];
+  f[0] = (float)xr; f[1] = (float)yr; f[2] = (float)std::cos(dth); f[3] = (float)std::sin(dth);
+  f[4] = (float)e.v[j]; f[5] = (float)e.len[j]; f[6] = (float)e.wid[j]; f[7] = 1.f;
+}
+
+// Observation row of every agent: ego[8], partners[P][8], road[K][4].
+template <typename T>
+void observe(const Env<T>& e, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  const int K = e.cfg.k_road, P = e.cfg.n_partners;
+  const long F = 8 + 8L * P + 4L * K;
+  const T R2 = (T)e.cfg.obs_radius * (T)e.cfg.obs_radius;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int w = 0; w < e.W; ++w) {
+    const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
+    const int r0 = e.road_off[w], r1 = e.road_off[w + 1];
+    std::vector<std::pair<T, int>> cand;
+    for (int i = a0; i < a1; ++i) {
+      float* row = obs + (long)i * F;
+      std::fill(row, row + F, 0.f);
+      if (road_idx) std::fill(road_idx + (long)i * K, road_idx + (long)(i + 1) * K, -1);
+      if (partner_idx) std::fill(partner_idx + (long)i * P, partner_idx + (long)(i + 1) * P, -1);
+      row[5] = (e.flags[i] & F_COLLIDED) ? 1.f : 0.f;
+      row[6] = (e.flags[i] & F_OFFROAD) ? 1.f : 0.f;
+      row[7] = (e.flags[i] & F_GOAL) ? 1.f : 0.f;
+      if (e.flags[i] & F_DONE) continue;                  // removed from the scene
+      T gxr, gyr;
+      ego_frame(e, i, e.gx[i], e.gy[i], gxr, gyr);
+      row[0] = (float)e.v[i]; row[1] = (float)e.len[i]; row[2] = (float)e.wid[i];
+      row[3] = (float)gxr; row[4] = (float)gyr;
+      // partners: every other agent still in the scene within the radius
+      cand.clear();
+      for (int j = a0; j < a1; ++j) {
+        if (j == i || (e.flags[j] & F_DONE)) continue;
+        const T dx = e.x[j] - e.x[i], dy = e.y[j] - e.y[i];
+        const T d2 = dx * dx + dy * dy;
+        if (d2 <= R2) cand.emplace_back(d2, j - a0);
+      }
+      std::sort(cand.begin(), cand.end());
+      for (int k = 0; k < P && k < (int)cand.size(); ++k) {
+        partner_feature(e, i, a0 + cand[k].second, row + 8 + 8 * k);
+        if (partner_idx) partner_idx[(long)i * P + k] = cand[k].second;
+      }
+      // road points within the radius
+      cand.clear();
+      for (int j = r0; j < r1; ++j) {
+        const T dx = e.rx[j] - e.x[i], dy = e.ry[j] - e.y[i];
+        const T d2 = dx * dx + dy * dy;
+        if (d2 <= R2) cand.emplace_back(d2, j - r0);
+      }
+      std::sort(cand.begin(), cand.end());
+      for (int k = 0; k < K && k < (int)cand.size(); ++k) {
+        road_feature(e, i, r0 + cand[k].second, row + 8 + 8 * P + 4 * k);
+        if (road_idx) road_idx[(long)i * K + k] = cand[k].second;
+      }
+    }
+  }
+}
+
+struct Handle {
+  int precision;   // 64 or 32
+  void* env;
+};
+
+template <typename T>
+Env<T>* make_env(const Config* cfg, int W, const int32_t* agent_off, const int32_t* road_off,
+                 const float* x, const float* y, const float* th, const float* v, const float* len,
+                 const float* wid, const float* gx, const float* gy, const uint8_t* atype,
+                 const float* rx, const float* ry, const uint8_t* rtype, const int32_t* rpoly) {
+  auto* e = new Env<T>();
+  e->cfg = *cfg;
+  e->W = W;
+  e->agent_off.assign(agent_off, agent_off + W + 1);
+  e->road_off.assign(road_off, road_off + W + 1);
+  e->A = agent_off[W];
+  e->N = road_off[W];
+  auto cp = [](std::vector<T>& d, const float* s, int n) { d.resize(n); for (int i = 0; i < n; ++i) d[i] = (T)s[i]; };
+  cp(e->x0, x, e->A); cp(e->y0, y, e->A); cp(e->th0, th, e->A); cp(e->v0, v, e->A);
+  cp(e->len, len, e->A); cp(e->wid, wid, e->A); cp(e->gx, gx, e->A); cp(e->gy, gy, e->A);
+  cp(e->rx, rx, e->N); cp(e->ry, ry, e->N);
+  e->type.assign(atype, atype + e->A);
+  e->rtype.assign(rtype, rtype + e->N);
+  e->rpoly.assign(rpoly, rpoly + e->N);
+  e->x = e->x0; e->y = e->y0; e->th = e->th0; e->v = e->v0;
+  e->flags0.assign(e->A, 0);
+  e->flags = e->flags0;
+  e->t.assign(W, 0);
+  e->world_done.assign(W, 0);
+  e->segs.resize(W);
+  for (int w = 0; w < W; ++w)
+    for (int j = road_off[w]; j + 1 < road_off[w + 1]; ++j)
+      if (e->rtype[j] == ROAD_EDGE && e->rtype[j + 1] == ROAD_EDGE && e->rpoly[j] == e->rpoly[j + 1])
+        e->segs[w].emplace_back(j, j + 1);
+  return e;
+}
+
+template <typename T> Env<T>& env_of(Handle* h) { return *static_cast<Env<T>*>(h->env); }
+
+}  // namespace
+
+// ============================ C interface ==================================
+// All arrays are host memory, rows in CSR agent order.  The oracle owns
+// copies of everything it is given.
+extern "C" {
+
+typedef struct or_config {
+  int32_t k_road, n_partners, episode_len;
+  double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
+  uint32_t flags;
+} or_config;
+
+void* or_create(const or_config* cfg, int precision, int32_t W, const int32_t* agent_off, const int32_t* road_off,
+                const float* x, const float* y, const float* th, const float* v, const float* len,
+                const float* wid, const float* gx, const float* gy, const uint8_t* atype, const float* rx,
+                const float* ry, const uint8_t* rtype, const int32_t* rpoly) {
+  Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags};
+  auto* h = new Handle{precision, nullptr};
+  if (precision == 32)
+    h->env = make_env<float>(&c, W, agent_off, road_off, x, y, th, v, len, wid, gx, gy, atype, rx, ry, rtype, rpoly);
+  else
+    h->env = make_env<double>(&c, W, agent_off, road_off, x, y, th, v, len, wid, gx, gy, atype, rx, ry, rtype, rpoly);
+  return h;
+}
+
+void or_destroy(void* hv) {
+  auto* h = static_cast<Handle*>(hv);
+  if (h->precision == 32) delete &env_of<float>(h); else delete &env_of<double>(h);
+  delete h;
+}
+
+#define OR_DISPATCH(h, ...) \
+  do { if ((h)->precision == 32) { auto& e = env_of<float>(h); __VA_ARGS__; } \
+       else { auto& e = env_of<double>(h); __VA_ARGS__; } } while (0)
+
+// Reset the worlds whose mask byte is non-zero (all worlds if mask is NULL).
+void or_reset(void* hv, const uint8_t* mask) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, for (int w = 0; w < e.W; ++w) if (!mask || mask[w]) reset_world(e, w));
+}
+
+// One step.  actions: float [A,2] (accel, steer).  Outputs may be NULL.
+// Margins (double [A]): coll = max over partners of the box/box penetration,
+// off = max over road-edge segments of the box/segment penetration (the flag
+// is set iff the margin is > 0), goal = d_goal - delta; smooth = r_s.
+void or_step(void* hv, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
+             double* coll_margin, double* off_margin, double* goal_margin, double* smooth_r) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, step(e, actions, nullptr, reward, done, world_done, coll_margin, off_margin, goal_margin, smooth_r));
+}
+
+// The same step with the dynamics replaced by a given post-step state
+// (float [A,4]); used to evaluate decisions on another implementation's state.
+void or_step_post(void* hv, const float* post_state, float* reward, uint8_t* done, uint8_t* world_done,
+                  double* coll_margin, double* off_margin, double* goal_margin, double* smooth_r) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, step(e, nullptr, post_state, reward, done, world_done, coll_margin, off_margin, goal_margin, smooth_r));
+}
+
+// Observation rows float [A, 8 + 8P + 4K]; index outputs int32 [A,K] / [A,P]
+// (world-local indices, -1 padding) may be NULL.
+void or_observe(void* hv, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, observe(e, obs, road_idx, partner_idx));
+}
+
+// Feature and exact distance of road point j (world-local) seen by agent i.
+void or_road_point(void* hv, int32_t i, int32_t j, float* feat4, double* dist) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, {
+    int w = int(std::upper_bound(e.agent_off.begin(), e.agent_off.end(), i) - e.agent_off.begin()) - 1;
+    int jg = e.road_off[w] + j;
+    road_feature(e, i, jg, feat4);
+    double dx = (double)e.rx[jg] - (double)e.x[i], dy = (double)e.ry[jg] - (double)e.y[i];
+    *dist = std::sqrt(dx * dx + dy * dy);
+  });
+}
+
+// Feature and exact distance of agent j (world-local) seen by agent i.
+void or_partner(void* hv, int32_t i, int32_t j, float* feat8, double* dist) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, {
+    int w = int(std::upper_bound(e.agent_off.begin(), e.agent_off.end(), i) - e.agent_off.begin()) - 1;
+    int jg = e.agent_off[w] + j;
+    partner_feature(e, i, jg, feat8);
+    double dx = (double)e.x[jg] - (double)e.x[i], dy = (double)e.y[jg] - (double)e.y[i];
+    *dist = std::sqrt(dx * dx + dy * dy);
+  });
+}
+
+// State as double [A,4] = (x, y, theta, v), flags [A], steps taken t [W],
+// end-of-episode status [W].  Any output may be NULL.
+void or_get_state(void* hv, double* state, uint8_t* flags, int32_t* t, uint8_t* world_done) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, {
+    for (int i = 0; i < e.A; ++i) {
+      if (state) { state[4 * i] = e.x[i]; state[4 * i + 1] = e.y[i]; state[4 * i + 2] = e.th[i]; state[4 * i + 3] = e.v[i]; }
+      if (flags) flags[i] = e.flags[i];
+    }
+    for (int w = 0; w < e.W; ++w) { if (t) t[w] = e.t[w]; if (world_done) world_done[w] = e.world_done[w]; }
+  });
+}
+
+// Overwrite the state from float [A,4] (and flags / t when given); the
+// end-of-episode status is re-derived from them.
+void or_set_state(void* hv, const float* state, const uint8_t* flags, const int32_t* t) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, {
+    for (int i = 0; i < e.A; ++i) {
+      if (state) { e.x[i] = state[4 * i]; e.y[i] = state[4 * i + 1]; e.th[i] = state[4 * i + 2]; e.v[i] = state[4 * i + 3]; }
+      if (flags) e.flags[i] = flags[i];
+    }
+    if (t) for (int w = 0; w < e.W; ++w) e.t[w] = t[w];
+    for (int w = 0; w < e.W; ++w) e.world_done[w] = world_is_done(e, w) ? 1 : 0;
+  });
+}
+
+// Bicycle-model step of a flat array of independent agents (no world, no
+// flags): state double [n,4] in place, actions double [n,2], length double [n].
+void or_bicycle(const or_config* cfg, int64_t n, double* state, const double* actions, const double* length) {
+  Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags};
+  for (int64_t i = 0; i < n; ++i)
+    bicycle_step<double>(c, length[i], actions[2 * i], actions[2 * i + 1], state[4 * i], state[4 * i + 1],
+                         state[4 * i + 2], state[4 * i + 3]);
+}
+
+// Penetration depth of two boxes (cx, cy, theta, length, width) and of a box
+// and a segment; > 0 iff they share interior points.
+double or_box_box(const double* p, const double* q) {
+  Box<double> a{p[0], p[1], std::cos(p[2]), std::sin(p[2]), p[3] / 2, p[4] / 2};
+  Box<double> b{q[0], q[1], std::cos(q[2]), std::sin(q[2]), q[3] / 2, q[4] / 2};
+  return box_box_pen(a, b);
+}
+
+double or_box_seg(const double* p, const double* s) {
+  Box<double> a{p[0], p[1], std::cos(p[2]), std::sin(p[2]), p[3] / 2, p[4] / 2};
+  return box_seg_pen(a, s[0], s[1], s[2], s[3]);
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"
