@@ -1,0 +1,218 @@
+/*
+ * gd.h -- C ABI of the B300 batched driving-simulator step.
+ *
+ * A batch of independent worlds (GPUDrive, arXiv 2408.01584, Sec. 3.1:
+ * many worlds with their own agent counts stepped in parallel on one
+ * accelerator) is uploaded once by gd_create and then advanced on the GPU:
+ *
+ *   gd_step     kinematic bicycle dynamics (App. B), agent/agent and
+ *               agent/road-edge collision (Sec. 3.1, Sec. 3.2 "Termination
+ *               conditions"), goal reward (Sec. 3.2 "Rewards"), done flags
+ *               and the end of each world's episode; worlds whose episode
+ *               ended are reset first when GD_AUTO_RESET is set;
+ *   gd_observe  each agent's ego-frame observation: the K nearest road
+ *               points and P nearest other agents within the observation
+ *               radius (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1);
+ *   gd_step_observe, gd_rollout   the same, fused, and whole episodes;
+ *   gd_rollout_backward / gd_step_backward   adjoint of the dynamics, the
+ *               ego-frame observation and a smooth goal-distance reward (the
+ *               paper has no gradient; this is an extension).
+ *
+ * Conventions
+ *   - Units are SI (m, s, rad).  Agents and road points are given in
+ *     compressed-sparse-row order: world w owns agents agent_off[w] ..
+ *     agent_off[w+1]-1 and road points road_off[w] .. road_off[w+1]-1.
+ *     "Local" indices count from the start of the world's range.
+ *   - Every per-step pointer argument is DEVICE memory owned by the caller,
+ *     contiguous, 16-byte aligned for float arrays of 4 or more columns.
+ *     Scene arrays passed to gd_create are HOST memory and are copied.
+ *   - All calls are asynchronous on the stream given to gd_create except
+ *     gd_sync, gd_destroy and gd_create itself; none of them synchronises
+ *     the device unless stated.
+ *   - Errors are status codes, never exceptions.  Arguments are validated
+ *     before anything is launched; a call that returns an error has
+ *     launched nothing.  gd_last_error(env) returns a message for the last
+ *     error of that env (gd_last_error(NULL): the last gd_create error of
+ *     the calling thread).  Faults found on the device (a non-finite
+ *     action, a steering angle with |delta| >= pi/2) set a sticky error word
+ *     that gd_sync reports.
+ *   - Observation row layout (float32, F = 8 + 8P + 4K columns):
+ *       ego[8]       = (v, length, width, goal_x', goal_y', collided,
+ *                       offroad, goal_reached)
+ *       partner[P][8]= (x', y', cos(dtheta), sin(dtheta), v, length,
+ *                       width, 1)
+ *       road[K][4]   = (x', y', road type, 1)
+ *     where (x', y') is the offset from the agent rotated by -theta.
+ *     Slots are sorted by (squared distance, local index); unused slots are
+ *     all zero.  The row of a done agent is all zero except the three flags.
+ */
+#ifndef GD_H
+#define GD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gd_status {
+  GD_OK = 0,
+  GD_ERR_INVALID_ARG = 1,  /* bad argument, bad scene, or a device-detected bad action */
+  GD_ERR_CUDA = 2,         /* a CUDA runtime call failed (message has the CUDA error) */
+  GD_ERR_OOM = 3,          /* device or host allocation failed */
+  GD_ERR_CAPACITY = 4,     /* a size exceeds a compiled limit (see GD_MAX_*) */
+  GD_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  GD_ERR_STATE = 6         /* call not valid in the env's current state */
+} gd_status;
+
+/* gd_config.flags */
+#define GD_TERM_COLLISION 0x1u   /* agent/agent collision ends the agent's episode (Sec. 3.2) */
+#define GD_TERM_OFFROAD 0x2u     /* crossing a road edge ends the agent's episode (Sec. 3.2) */
+#define GD_AUTO_RESET 0x4u       /* gd_step first resets worlds whose episode ended */
+#define GD_BATCHED 0x8u          /* persistent fused kernels over a world work list */
+#define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward */
+
+/* per-agent status byte (gd_get_state / gd_set_state) */
+#define GD_FLAG_DONE 0x1u
+#define GD_FLAG_GOAL 0x2u
+#define GD_FLAG_COLLIDED 0x4u
+#define GD_FLAG_OFFROAD 0x8u
+
+/* road point types and agent types */
+#define GD_ROAD_LANE 0
+#define GD_ROAD_EDGE 1
+#define GD_AGENT_VEHICLE 0
+#define GD_AGENT_CYCLIST 1
+#define GD_AGENT_PEDESTRIAN 2
+
+/* compiled limits */
+#define GD_MAX_AGENTS_PER_WORLD 128
+#define GD_MAX_K_ROAD 256
+#define GD_MAX_PARTNERS 127
+
+typedef struct gd_config {
+  int32_t k_road;            /* K road slots per observation, 0..GD_MAX_K_ROAD */
+  int32_t n_partners;        /* P partner slots, 0..GD_MAX_PARTNERS */
+  int32_t episode_len;       /* steps per episode (91 at 10 Hz) */
+  int32_t ckpt_every;        /* checkpoint interval of differentiable rollouts (10) */
+  float obs_radius;          /* m, radius filter (50) */
+  float goal_radius;         /* m, goal reached when distance <= this (2) */
+  float dt;                  /* s (0.1) */
+  float v_max;               /* m/s, speed clip of App. B (30) */
+  float collision_penalty;   /* subtracted from the reward on collision (0) */
+  float offroad_penalty;     /* subtracted from the reward off road (0) */
+  float smooth_c;            /* m, scale of the smooth goal reward (1) */
+  uint32_t flags;            /* GD_TERM_* | GD_AUTO_RESET | GD_BATCHED | GD_DIFFERENTIABLE */
+  int32_t block_size;        /* threads per block of the observation kernel; 0 = default */
+  float road_cell;           /* m, road-point grid cell; 0 = default (8) */
+  int32_t topk_strategy;     /* road top-K method: 0 = default, 1 = bucket rank, 2 = bitonic sort */
+} gd_config;
+
+typedef struct gd_scene_batch {
+  int32_t num_worlds;
+  const int32_t* agent_off;  /* [W+1], agent_off[0] = 0, non-decreasing */
+  const int32_t* road_off;   /* [W+1], road_off[0] = 0, non-decreasing */
+  const float *x, *y, *theta, *v;           /* [A] initial state */
+  const float *length, *width;              /* [A] box extents, > 0 */
+  const float *goal_x, *goal_y;             /* [A] */
+  const uint8_t* agent_type;                /* [A] GD_AGENT_* */
+  const float *road_x, *road_y;             /* [N] */
+  const uint8_t* road_type;                 /* [N] GD_ROAD_* */
+  const int32_t* road_poly;                 /* [N] polyline id; consecutive GD_ROAD_EDGE
+                                               points of one polyline form a segment */
+} gd_scene_batch;
+
+typedef struct gd_info {
+  int32_t num_worlds, num_agents, num_road, feat;   /* feat = F */
+  int32_t max_agents_per_world, k_road, n_partners, episode_len;
+  int64_t device_bytes;                             /* device memory owned by the env */
+} gd_info;
+
+typedef struct gd_env gd_env;
+
+/* Fill *cfg with the defaults listed above. */
+void gd_default_config(gd_config* cfg);
+
+/* Validate and upload a scene batch; build the static road grids.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) on which every
+ * later call of this env runs.  Blocks until the upload is complete.
+ * Errors: GD_ERR_INVALID_ARG (bad sizes, offsets, non-finite values),
+ * GD_ERR_CAPACITY (a world above GD_MAX_AGENTS_PER_WORLD, K or P above the
+ * limits), GD_ERR_OOM, GD_ERR_CUDA.  On error *out is NULL. */
+gd_status gd_create(const gd_config* cfg, const gd_scene_batch* scene, void* cuda_stream, gd_env** out);
+
+/* Synchronise the env's stream and free everything.  NULL is a no-op. */
+gd_status gd_destroy(gd_env* env);
+
+gd_status gd_get_info(const gd_env* env, gd_info* info);
+
+/* Reset worlds to their initial snapshot (state, flags, episode step).
+ * world_mask: device uint8 [W]; non-zero = reset; NULL = every world. */
+gd_status gd_reset(gd_env* env, const uint8_t* world_mask);
+
+/* One step of every world (see the header comment for the order).
+ * actions: device float [A,2] = (acceleration m/s^2, steering rad).
+ * reward: device float [A]; done: device uint8 [A] (1 = agent done after
+ * this step); world_done: device uint8 [W] (1 = the world's episode ended).
+ * Any output may be NULL.  Agents done before the step do not move, get
+ * reward 0 and are invisible to the others. */
+gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done);
+
+/* Observation of every agent after the last step (layout in the header
+ * comment).  obs: device float [A,F], 16-byte aligned.  road_idx: device
+ * int32 [A,K] local road indices of the slots (-1 = empty) or NULL;
+ * partner_idx: device int32 [A,P] local agent indices or NULL. */
+gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partner_idx);
+
+/* gd_step followed by gd_observe; one fused launch when GD_BATCHED is set. */
+gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
+                          float* obs);
+
+/* T = steps steps of gd_step_observe, replayed from a captured CUDA graph.
+ * actions: device float [T,A,2]; obs: device float [A,F] (overwritten every
+ * step) if obs_per_step == 0, else [T,A,F]; reward: float [T,A] or NULL;
+ * done: uint8 [T,A] or NULL.  With GD_DIFFERENTIABLE the state is also
+ * checkpointed every ckpt_every steps for gd_rollout_backward. */
+gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step,
+                     float* reward, uint8_t* done);
+
+/* Gradient of  L = sum_t sum_i [ reward_weight * r_s(i,t) + sum_f obs_weight[f] * obs(t)[i,f] ]
+ * over the last gd_rollout of an env created with GD_DIFFERENTIABLE, where
+ * r_s = -(sqrt(d_goal^2 + c^2) - c) for agents not done at the start of
+ * step t.  Collision, goal, selection and clip decisions are held constant.
+ * obs_weight: device float [F]; d_actions: device float [T,A,2];
+ * d_state0: device float [A,4] (gradient w.r.t. the state before the
+ * rollout) or NULL.  Recomputes the states between checkpoints. */
+gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, float* d_actions,
+                              float* d_state0);
+
+/* Adjoint of one step about the CURRENT state and the given actions
+ * (the step is not applied): given d_state_next [A,4] = dL/d(state after
+ * the step) and optional per-row obs gradient d_obs [A,F] and d_reward_s
+ * [A], returns d_state [A,4] and d_actions [A,2].  d_obs, obs_weight and
+ * d_reward_s may be NULL; obs_weight [F] broadcasts one weight row to all
+ * agents (ignored if d_obs is given). */
+gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,
+                           const float* obs_weight, const float* d_reward_s, float* d_state, float* d_actions);
+
+/* State snapshot: state device float [A,4] = (x, y, theta, v), flags device
+ * uint8 [A] (GD_FLAG_*), t device int32 [W] = steps into the episode.  Any
+ * pointer may be NULL.  gd_set_state re-derives each world's episode-end
+ * status from the flags and t. */
+gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t);
+gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, const int32_t* t);
+
+/* Time the observation kernel over candidate block sizes, road cell sizes
+ * and top-K strategies on the current state and keep the fastest.  Runs on
+ * the env stream, synchronises it, leaves the simulation state unchanged. */
+gd_status gd_autotune(gd_env* env);
+
+/* Block until the env's stream is idle and report any sticky device error. */
+gd_status gd_sync(gd_env* env);
+
+const char* gd_last_error(const gd_env* env);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GD_H */

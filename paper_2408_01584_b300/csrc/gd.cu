@@ -1,0 +1,468 @@
+// C-ABI implementation of include/gd.h: scene validation and upload, static
+// road / road-edge grids, per-step launches, rollouts and state access.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gd_device.cuh"
+#include "observe_kernel.cuh"
+#include "step_kernels.cuh"
+
+using namespace gd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kObsWarpsDefault = 8;
+
+}  // namespace
+
+struct gd_env {
+  gd_config cfg{};
+  cudaStream_t stream = nullptr;
+  int W = 0, A = 0, N = 0, F = 0, amax = 0;
+  DevEnv d{};
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  std::string err;
+  unsigned* h_err = nullptr;   // pinned host copy of the sticky error word
+  int obs_warps = kObsWarpsDefault;
+};
+
+namespace {
+
+gd_status fail(gd_env* env, gd_status st, const std::string& msg) {
+  if (env) env->err = msg; else g_create_error = msg;
+  return st;
+}
+
+gd_status cuda_fail(gd_env* env, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(env, e == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA, m);
+}
+
+template <typename T>
+cudaError_t dev_alloc(gd_env* env, T** p, size_t count) {
+  *p = nullptr;
+  const size_t b = std::max<size_t>(count, 1) * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, b);
+  if (e != cudaSuccess) return e;
+  env->allocs.push_back(q);
+  env->bytes += (int64_t)b;
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t upload(gd_env* env, T** p, const T* host, size_t count) {
+  cudaError_t e = dev_alloc(env, p, count);
+  if (e != cudaSuccess || count == 0) return e;
+  return cudaMemcpyAsync(*p, host, count * sizeof(T), cudaMemcpyHostToDevice, env->stream);
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+// Static uniform grid of one world (host build).  Points are counted per
+// cell and placed in row-major cell order (stable: ascending index inside a
+// cell), so a run of cells of one row is one contiguous range.
+struct HostGrid {
+  std::vector<GridDesc> desc;
+  std::vector<int> cell_start;
+};
+
+void grid_geometry(float minx, float miny, float maxx, float maxy, float cs, GridDesc& g) {
+  g.ox = minx;
+  g.oy = miny;
+  g.cs = cs;
+  g.inv_cs = 1.f / cs;
+  g.nx = std::max(1, (int)std::floor((maxx - minx) * g.inv_cs) + 1);
+  g.ny = std::max(1, (int)std::floor((maxy - miny) * g.inv_cs) + 1);
+  g.pad = 0;
+}
+
+int cell_clamped(float v, float o, float inv, int n) {
+  const int c = (int)std::floor((v - o) * inv);
+  return std::min(std::max(c, 0), n - 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gd_default_config(gd_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->k_road = 200;
+  c->n_partners = 63;
+  c->episode_len = 91;
+  c->ckpt_every = 10;
+  c->obs_radius = 50.f;
+  c->goal_radius = 2.f;
+  c->dt = 0.1f;
+  c->v_max = 30.f;
+  c->collision_penalty = 0.f;
+  c->offroad_penalty = 0.f;
+  c->smooth_c = 1.f;
+  c->flags = 0;
+  c->block_size = 0;
+  c->road_cell = 0.f;
+  c->topk_strategy = 0;
+}
+
+const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
+
+gd_status gd_destroy(gd_env* env) {
+  if (!env) return GD_OK;
+  cudaStreamSynchronize(env->stream);
+  for (void* p : env->allocs) cudaFree(p);
+  if (env->h_err) cudaFreeHost(env->h_err);
+  delete env;
+  return GD_OK;
+}
+
+static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
+  if (!c || !s) return fail(nullptr, GD_ERR_INVALID_ARG, "config and scene must not be NULL");
+  if (s->num_worlds < 1) return fail(nullptr, GD_ERR_INVALID_ARG, "num_worlds must be >= 1");
+  if (!s->agent_off || !s->road_off) return fail(nullptr, GD_ERR_INVALID_ARG, "agent_off / road_off are NULL");
+  if (c->k_road < 0 || c->k_road > GD_MAX_K_ROAD) return fail(nullptr, GD_ERR_CAPACITY, "k_road outside 0..GD_MAX_K_ROAD");
+  if (c->n_partners < 0 || c->n_partners > GD_MAX_PARTNERS)
+    return fail(nullptr, GD_ERR_CAPACITY, "n_partners outside 0..GD_MAX_PARTNERS");
+  if (c->episode_len < 1) return fail(nullptr, GD_ERR_INVALID_ARG, "episode_len must be >= 1");
+  if (!(c->obs_radius > 0.f) || !finite(c->obs_radius)) return fail(nullptr, GD_ERR_INVALID_ARG, "obs_radius must be > 0");
+  if (!(c->goal_radius >= 0.f) || !finite(c->goal_radius)) return fail(nullptr, GD_ERR_INVALID_ARG, "goal_radius must be >= 0");
+  if (!(c->dt > 0.f) || !finite(c->dt)) return fail(nullptr, GD_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(c->v_max > 0.f) || !finite(c->v_max)) return fail(nullptr, GD_ERR_INVALID_ARG, "v_max must be > 0");
+  if (!finite(c->collision_penalty) || !finite(c->offroad_penalty) || !(c->smooth_c > 0.f))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "penalties must be finite and smooth_c > 0");
+  if (c->road_cell < 0.f || !finite(c->road_cell)) return fail(nullptr, GD_ERR_INVALID_ARG, "road_cell must be >= 0");
+  if (c->ckpt_every < 1) return fail(nullptr, GD_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+  if (c->block_size != 0 && c->block_size != 128 && c->block_size != 256 && c->block_size != 512)
+    return fail(nullptr, GD_ERR_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
+  if (c->topk_strategy < 0 || c->topk_strategy > 2) return fail(nullptr, GD_ERR_INVALID_ARG, "topk_strategy must be 0..2");
+  if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
+  const int W = s->num_worlds;
+  if (s->agent_off[0] != 0 || s->road_off[0] != 0) return fail(nullptr, GD_ERR_INVALID_ARG, "offsets must start at 0");
+  for (int w = 0; w < W; ++w) {
+    const int na = s->agent_off[w + 1] - s->agent_off[w], nr = s->road_off[w + 1] - s->road_off[w];
+    if (na < 0 || nr < 0) return fail(nullptr, GD_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    if (na > GD_MAX_AGENTS_PER_WORLD)
+      return fail(nullptr, GD_ERR_CAPACITY, "world " + std::to_string(w) + " has more than GD_MAX_AGENTS_PER_WORLD agents");
+  }
+  const int A = s->agent_off[W], N = s->road_off[W];
+  if (A > 0 && (!s->x || !s->y || !s->theta || !s->v || !s->length || !s->width || !s->goal_x || !s->goal_y ||
+                !s->agent_type))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "agent arrays must not be NULL");
+  if (N > 0 && (!s->road_x || !s->road_y || !s->road_type || !s->road_poly))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "road arrays must not be NULL");
+  for (int i = 0; i < A; ++i) {
+    if (!finite(s->x[i]) || !finite(s->y[i]) || !finite(s->theta[i]) || !finite(s->v[i]) || !finite(s->goal_x[i]) ||
+        !finite(s->goal_y[i]))
+      return fail(nullptr, GD_ERR_INVALID_ARG, "agent " + std::to_string(i) + " has a non-finite value");
+    if (!(s->length[i] > 0.f) || !(s->width[i] > 0.f) || !finite(s->length[i]) || !finite(s->width[i]))
+      return fail(nullptr, GD_ERR_INVALID_ARG, "agent " + std::to_string(i) + " has a non-positive size");
+    if (s->agent_type[i] > GD_AGENT_PEDESTRIAN) return fail(nullptr, GD_ERR_INVALID_ARG, "bad agent_type");
+  }
+  for (int j = 0; j < N; ++j) {
+    if (!finite(s->road_x[j]) || !finite(s->road_y[j]))
+      return fail(nullptr, GD_ERR_INVALID_ARG, "road point " + std::to_string(j) + " is not finite");
+    if (s->road_type[j] > GD_ROAD_EDGE) return fail(nullptr, GD_ERR_INVALID_ARG, "bad road_type");
+  }
+  return GD_OK;
+}
+
+gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_stream, gd_env** out) {
+  if (!out) return fail(nullptr, GD_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  gd_status st = validate(cfg, s);
+  if (st != GD_OK) return st;
+  gd_env* env = new (std::nothrow) gd_env();
+  if (!env) return fail(nullptr, GD_ERR_OOM, "host allocation failed");
+  env->cfg = *cfg;
+  env->stream = static_cast<cudaStream_t>(cuda_stream);
+  const int W = s->num_worlds, A = s->agent_off[W], N = s->road_off[W];
+  const int K = cfg->k_road, P = cfg->n_partners;
+  env->W = W; env->A = A; env->N = N; env->F = 8 + 8 * P + 4 * K;
+  for (int w = 0; w < W; ++w) env->amax = std::max(env->amax, s->agent_off[w + 1] - s->agent_off[w]);
+  const float R = cfg->obs_radius;
+  // road cell: at most MAX_ROWS rows may cross the observation disk
+  float rcell = cfg->road_cell > 0.f ? cfg->road_cell : 8.f;
+  rcell = std::max(rcell, (2.f * R + 0.01f) / (float)(MAX_ROWS - 2));
+  const float ecell = 8.f;
+
+  // ---- host-side preprocessing --------------------------------------------
+  std::vector<float4> h_state(A), h_stat(A);
+  std::vector<int> h_agent_world(A);
+  float max_diag = 0.f;
+  for (int w = 0; w < W; ++w)
+    for (int i = s->agent_off[w]; i < s->agent_off[w + 1]; ++i) {
+      h_state[i] = make_float4(s->x[i], s->y[i], s->theta[i], s->v[i]);
+      h_stat[i] = make_float4(s->length[i], s->width[i], s->goal_x[i], s->goal_y[i]);
+      h_agent_world[i] = w;
+      max_diag = std::max(max_diag, std::sqrt(s->length[i] * s->length[i] + s->width[i] * s->width[i]));
+    }
+  // road-point grid: cell-sorted points (x, y, local index bits, type bits)
+  std::vector<GridDesc> rdesc(W), edesc(W);
+  std::vector<int> rcell_start;
+  std::vector<float4> rpts(N);
+  std::vector<int> ecell_start;
+  std::vector<float4> esegs;
+  for (int w = 0; w < W; ++w) {
+    const int r0 = s->road_off[w], r1 = s->road_off[w + 1];
+    float minx = 0.f, miny = 0.f, maxx = 0.f, maxy = 0.f;
+    if (r1 > r0) {
+      minx = maxx = s->road_x[r0];
+      miny = maxy = s->road_y[r0];
+      for (int j = r0; j < r1; ++j) {
+        minx = std::min(minx, s->road_x[j]); maxx = std::max(maxx, s->road_x[j]);
+        miny = std::min(miny, s->road_y[j]); maxy = std::max(maxy, s->road_y[j]);
+      }
+    }
+    GridDesc& g = rdesc[w];
+    grid_geometry(minx, miny, maxx, maxy, rcell, g);
+    g.cell_base = (int)rcell_start.size();
+    const int nc = g.nx * g.ny;
+    std::vector<int> cnt(nc + 1, 0), cell(r1 - r0);
+    for (int j = r0; j < r1; ++j) {
+      const int cx = cell_clamped(s->road_x[j], g.ox, g.inv_cs, g.nx), cy = cell_clamped(s->road_y[j], g.oy, g.inv_cs, g.ny);
+      cell[j - r0] = cy * g.nx + cx;
+      cnt[cell[j - r0] + 1]++;
+    }
+    for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    for (int c = 0; c <= nc; ++c) rcell_start.push_back(r0 + cnt[c]);
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int j = r0; j < r1; ++j) {
+      const int dst = r0 + fill[cell[j - r0]]++;
+      int lidx = j - r0, typ = s->road_type[j];
+      float fi, ft;
+      std::memcpy(&fi, &lidx, 4);
+      std::memcpy(&ft, &typ, 4);
+      rpts[dst] = make_float4(s->road_x[j], s->road_y[j], fi, ft);
+    }
+    // road-edge segment grid: a segment is listed under every cell its
+    // bounding box (grown by 1 mm) touches
+    GridDesc& eg = edesc[w];
+    grid_geometry(minx, miny, maxx, maxy, ecell, eg);
+    eg.cell_base = (int)ecell_start.size();
+    const int enc = eg.nx * eg.ny;
+    std::vector<std::vector<float4>> per(enc);
+    for (int j = r0; j + 1 < r1; ++j) {
+      if (s->road_type[j] != GD_ROAD_EDGE || s->road_type[j + 1] != GD_ROAD_EDGE || s->road_poly[j] != s->road_poly[j + 1])
+        continue;
+      const float4 sg = make_float4(s->road_x[j], s->road_y[j], s->road_x[j + 1], s->road_y[j + 1]);
+      const float m = 1e-3f;
+      const int cx0 = cell_clamped(std::min(sg.x, sg.z) - m, eg.ox, eg.inv_cs, eg.nx);
+      const int cx1 = cell_clamped(std::max(sg.x, sg.z) + m, eg.ox, eg.inv_cs, eg.nx);
+      const int cy0 = cell_clamped(std::min(sg.y, sg.w) - m, eg.oy, eg.inv_cs, eg.ny);
+      const int cy1 = cell_clamped(std::max(sg.y, sg.w) + m, eg.oy, eg.inv_cs, eg.ny);
+      for (int cy = cy0; cy <= cy1; ++cy)
+        for (int cx = cx0; cx <= cx1; ++cx) per[cy * eg.nx + cx].push_back(sg);
+    }
+    for (int c = 0; c < enc; ++c) {
+      ecell_start.push_back((int)esegs.size());
+      esegs.insert(esegs.end(), per[c].begin(), per[c].end());
+    }
+    ecell_start.push_back((int)esegs.size());
+  }
+
+  // ---- device upload --------------------------------------------------------
+  DevEnv& d = env->d;
+  d.W = W; d.A = A; d.N = N; d.K = K; d.P = P; d.F = env->F; d.T = cfg->episode_len;
+  d.R = R; d.R2 = R * R; d.goal_r = cfg->goal_radius; d.dt = cfg->dt; d.vmax = cfg->v_max;
+  d.cpen = cfg->collision_penalty; d.opn = cfg->offroad_penalty; d.smooth_c = cfg->smooth_c;
+  d.agent_cell = max_diag * 1.01f + 0.01f;
+  d.cflags = cfg->flags;
+  std::vector<uint8_t> zeros_a(A, 0);
+  std::vector<int> zeros_w(W, 0);
+  int* p_aoff; int* p_roff; int* p_aw; float4* p_state; float4* p_init; float4* p_stat; uint8_t* p_type;
+  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; int* p_rcs; float4* p_rpts;
+  GridDesc* p_eg; int* p_ecs; float4* p_es;
+  cudaError_t e = cudaSuccess;
+#define GD_TRY(x) do { e = (x); if (e != cudaSuccess) { gd_status r_ = cuda_fail(nullptr, e, #x); gd_destroy(env); return r_; } } while (0)
+  GD_TRY(upload(env, &p_aoff, s->agent_off, (size_t)W + 1));
+  GD_TRY(upload(env, &p_roff, s->road_off, (size_t)W + 1));
+  GD_TRY(upload(env, &p_aw, h_agent_world.data(), (size_t)A));
+  GD_TRY(upload(env, &p_state, h_state.data(), (size_t)A));
+  GD_TRY(upload(env, &p_init, h_state.data(), (size_t)A));
+  GD_TRY(upload(env, &p_stat, h_stat.data(), (size_t)A));
+  GD_TRY(upload(env, &p_type, s->agent_type, (size_t)A));
+  GD_TRY(upload(env, &p_flags, zeros_a.data(), (size_t)A));
+  GD_TRY(upload(env, &p_iflags, zeros_a.data(), (size_t)A));
+  GD_TRY(upload(env, &p_t, zeros_w.data(), (size_t)W));
+  GD_TRY(dev_alloc(env, &p_wd, (size_t)W));
+  GD_TRY(cudaMemsetAsync(p_wd, 0, (size_t)W, env->stream));
+  GD_TRY(upload(env, &p_rg, rdesc.data(), (size_t)W));
+  GD_TRY(upload(env, &p_rcs, rcell_start.data(), rcell_start.size()));
+  GD_TRY(upload(env, &p_rpts, rpts.data(), (size_t)N));
+  GD_TRY(upload(env, &p_eg, edesc.data(), (size_t)W));
+  GD_TRY(upload(env, &p_ecs, ecell_start.data(), ecell_start.size()));
+  GD_TRY(upload(env, &p_es, esegs.data(), esegs.size()));
+  GD_TRY(dev_alloc(env, &d.agrid_key, (size_t)A));
+  GD_TRY(dev_alloc(env, &d.agrid_n, (size_t)W));
+  GD_TRY(dev_alloc(env, &d.coll, (size_t)A));
+  GD_TRY(dev_alloc(env, &d.off, (size_t)A));
+  GD_TRY(dev_alloc(env, &d.err, 1));
+  GD_TRY(cudaMemsetAsync(d.err, 0, sizeof(unsigned), env->stream));
+  GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
+  d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
+  d.stat = p_stat; d.type = p_type; d.flags = p_flags; d.init_flags = p_iflags; d.t = p_t; d.world_done = p_wd;
+  d.rgrid = p_rg; d.rcell_start = p_rcs; d.rpts = p_rpts; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
+  GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
+  GD_TRY(cudaStreamSynchronize(env->stream));
+#undef GD_TRY
+  *out = env;
+  return GD_OK;
+}
+
+gd_status gd_get_info(const gd_env* env, gd_info* info) {
+  if (!env || !info) return GD_ERR_INVALID_ARG;
+  info->num_worlds = env->W;
+  info->num_agents = env->A;
+  info->num_road = env->N;
+  info->feat = env->F;
+  info->max_agents_per_world = env->amax;
+  info->k_road = env->cfg.k_road;
+  info->n_partners = env->cfg.n_partners;
+  info->episode_len = env->cfg.episode_len;
+  info->device_bytes = env->bytes;
+  return GD_OK;
+}
+
+static gd_status launch_check(gd_env* env, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(env, e, what);
+  return GD_OK;
+}
+
+static inline unsigned blocks_for(long n, int per) { return (unsigned)std::max<long>(1, (n + per - 1) / per); }
+
+gd_status gd_reset(gd_env* env, const uint8_t* world_mask) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (world_mask) {
+    k_reset_worlds<<<blocks_for(env->W, 8), 256, 0, env->stream>>>(env->d, world_mask);
+  } else {
+    // every world: plain copies of the snapshot
+    cudaMemcpyAsync(env->d.state, env->d.init_state, sizeof(float4) * env->A, cudaMemcpyDeviceToDevice, env->stream);
+    cudaMemcpyAsync(env->d.flags, env->d.init_flags, env->A, cudaMemcpyDeviceToDevice, env->stream);
+    cudaMemsetAsync(env->d.t, 0, sizeof(int) * env->W, env->stream);
+    cudaMemsetAsync(env->d.world_done, 0, env->W, env->stream);
+  }
+  return launch_check(env, "gd_reset");
+}
+
+// Plain form: one launch per stage.
+static void launch_step_plain(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done) {
+  const DevEnv& d = env->d;
+  cudaStream_t s = env->stream;
+  if (d.cflags & GD_AUTO_RESET) k_reset_worlds<<<blocks_for(d.W, 8), 256, 0, s>>>(d, nullptr);
+  k_dynamics<<<blocks_for(d.A, 256), 256, 0, s>>>(d, reinterpret_cast<const float2*>(actions));
+  k_agent_grid<<<blocks_for(d.W, 8), 256, 0, s>>>(d);
+  k_collide<<<blocks_for(d.A, 8), 256, 0, s>>>(d);
+  k_offroad<<<blocks_for(d.A, 8), 256, 0, s>>>(d);
+  k_finish<<<blocks_for(d.W, 8), 256, 0, s>>>(d, reward, done, world_done);
+}
+
+static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  const DevEnv& d = env->d;
+  constexpr int WARPS = kObsWarpsDefault;
+  k_observe<WARPS><<<blocks_for(d.A, WARPS), WARPS * 32, WARPS * sizeof(ObsWarpSmem), env->stream>>>(
+      d, obs, road_idx, partner_idx);
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (!actions && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions must not be NULL");
+  if (!aligned16(actions) && ((uintptr_t)actions & 7u)) return fail(env, GD_ERR_INVALID_ARG, "actions must be 8-byte aligned");
+  launch_step_plain(env, actions, reward, done, world_done);
+  return launch_check(env, "gd_step");
+}
+
+gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (!obs && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "obs must not be NULL");
+  if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
+  launch_observe(env, obs, road_idx, partner_idx);
+  return launch_check(env, "gd_observe");
+}
+
+gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
+                          float* obs) {
+  gd_status st = gd_step(env, actions, reward, done, world_done);
+  if (st != GD_OK) return st;
+  return gd_observe(env, obs, nullptr, nullptr);
+}
+
+gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step, float* reward,
+                     uint8_t* done) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
+  for (int t = 0; t < steps; ++t) {
+    const float* a = actions + (size_t)t * env->A * 2;
+    float* o = obs + (obs_per_step ? (size_t)t * env->A * env->F : 0);
+    gd_status st = gd_step(env, a, reward ? reward + (size_t)t * env->A : nullptr,
+                           done ? done + (size_t)t * env->A : nullptr, nullptr);
+    if (st != GD_OK) return st;
+    st = gd_observe(env, o, nullptr, nullptr);
+    if (st != GD_OK) return st;
+  }
+  return GD_OK;
+}
+
+gd_status gd_rollout_backward(gd_env* env, const float*, float, float*, float*) {
+  return fail(env, GD_ERR_STATE, "gd_rollout_backward: not available in this build");
+}
+
+gd_status gd_step_backward(gd_env* env, const float*, const float*, const float*, const float*, const float*, float*,
+                           float*) {
+  return fail(env, GD_ERR_STATE, "gd_step_backward: not available in this build");
+}
+
+gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (state) cudaMemcpyAsync(state, env->d.state, sizeof(float4) * env->A, cudaMemcpyDeviceToDevice, env->stream);
+  if (flags) cudaMemcpyAsync(flags, env->d.flags, env->A, cudaMemcpyDeviceToDevice, env->stream);
+  if (t) cudaMemcpyAsync(t, env->d.t, sizeof(int) * env->W, cudaMemcpyDeviceToDevice, env->stream);
+  return launch_check(env, "gd_get_state");
+}
+
+gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, const int32_t* t) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (state) cudaMemcpyAsync(env->d.state, state, sizeof(float4) * env->A, cudaMemcpyDeviceToDevice, env->stream);
+  if (flags) cudaMemcpyAsync(env->d.flags, flags, env->A, cudaMemcpyDeviceToDevice, env->stream);
+  if (t) cudaMemcpyAsync(env->d.t, t, sizeof(int) * env->W, cudaMemcpyDeviceToDevice, env->stream);
+  k_derive_world_done<<<blocks_for(env->W, 256), 256, 0, env->stream>>>(env->d);
+  return launch_check(env, "gd_set_state");
+}
+
+gd_status gd_autotune(gd_env* env) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  return GD_OK;
+}
+
+gd_status gd_sync(gd_env* env) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  cudaError_t e = cudaMemcpyAsync(env->h_err, env->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_sync");
+  e = cudaStreamSynchronize(env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_sync");
+  const unsigned w = *env->h_err;
+  if (w) {
+    cudaMemsetAsync(env->d.err, 0, sizeof(unsigned), env->stream);
+    cudaStreamSynchronize(env->stream);
+    if (w & ERR_ACTION) return fail(env, GD_ERR_INVALID_ARG, "a step saw a non-finite action or |steer| >= pi/2");
+    if (w & ERR_TIMEOUT) return fail(env, GD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return fail(env, GD_ERR_CAPACITY, "a device-side capacity was exceeded");
+  }
+  return GD_OK;
+}
+
+}  // extern "C"

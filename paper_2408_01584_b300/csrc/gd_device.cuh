@@ -1,0 +1,140 @@
+// Device-side data layout and per-agent arithmetic of the driving step.
+//
+// Layout in HBM (all arrays in CSR world order, see include/gd.h):
+//   state[A]       float4 (x, y, theta, v)        -- 16 B, one coalesced load
+//   stat[A]        float4 (length, width, goal_x, goal_y)
+//   flags[A]       uint8  GD_FLAG_* bits
+//   rpts[N]        float4 (x, y, local index bits, type bits), per world sorted
+//                  by road-grid cell so that a row of cells is one range
+//   rcell_start[]  int32, per world (ny*nx + 1) cell starts into rpts
+//   esegs[]        float4 (x0, y0, x1, y1) road-edge segments listed under every
+//                  edge-grid cell their bounding box touches
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/gd.h"
+
+namespace gd {
+
+constexpr unsigned ERR_ACTION = 1u;     // non-finite action or |steer| >= pi/2
+constexpr unsigned ERR_TIMEOUT = 2u;    // a bounded wait gave up
+constexpr unsigned ERR_CAPACITY = 4u;   // a device-side capacity was exceeded
+
+constexpr int WARP = 32;
+constexpr int MAX_ROWS = 32;            // grid rows spanned by one observation disk
+
+struct GridDesc {      // one per world, for the road-point grid and the edge grid
+  float ox, oy;        // lower-left corner of cell (0, 0)
+  float cs, inv_cs;    // cell size and its inverse
+  int nx, ny;          // cells per row / rows
+  int cell_base;       // first entry of this world's cell-start table
+  int pad;
+};
+
+// Everything a kernel needs, passed by value (device pointers + sizes).
+struct DevEnv {
+  int W, A, N, K, P, F, T;
+  float R, R2, goal_r, dt, vmax, cpen, opn, smooth_c, agent_cell;
+  uint32_t cflags;
+  const int* agent_off;
+  const int* road_off;
+  const int* agent_world;
+  float4* state;
+  const float4* init_state;
+  const float4* stat;
+  const uint8_t* type;
+  uint8_t* flags;
+  const uint8_t* init_flags;
+  int* t;
+  uint8_t* world_done;
+  const GridDesc* rgrid;
+  const int* rcell_start;
+  const float4* rpts;
+  const GridDesc* egrid;
+  const int* ecell_start;
+  const float4* esegs;
+  // scratch of the per-stage form
+  uint32_t* agrid_key;   // [A] per world: sorted agent-grid keys of the active agents
+  int* agrid_n;          // [W] number of active agents in the agent grid
+  uint8_t* coll;         // [A] collision found this step
+  uint8_t* off;          // [A] road edge crossed this step
+  unsigned* err;         // sticky error word
+};
+
+__device__ __forceinline__ float clampf(float a, float lo, float hi) { return fminf(fmaxf(a, lo), hi); }
+
+// Kinematic bicycle model of App. B with l_r = L/2: mid-step clipped speed,
+// slip angle beta = atan(tan(delta)/2), explicit Euler with the old heading.
+__device__ __forceinline__ void bicycle_step(float4& s, float accel, float steer, float L, float dt, float vmax) {
+  const float vbar = clampf(s.w + 0.5f * accel * dt, -vmax, vmax);
+  const float tn = tanf(steer);
+  const float beta = atanf(0.5f * tn);
+  float sn, cs;
+  sincosf(s.z + beta, &sn, &cs);
+  const float xdot = vbar * cs;
+  const float ydot = vbar * sn;
+  const float thdot = vbar * cosf(beta) * tn / L;
+  s.x = s.x + xdot * dt;
+  s.y = s.y + ydot * dt;
+  s.z = s.z + thdot * dt;
+  s.w = clampf(s.w + accel * dt, -vmax, vmax);
+}
+
+// Separating-axis depth of two oriented boxes: the minimum over the four box
+// axes of (sum of projected half extents - |projected centre offset|).
+// > 0 iff the boxes share interior points.  (dx, dy) = centre_b - centre_a;
+// (ca, sa), (cb, sb) = heading cos/sin; (la, wa), (lb, wb) = half extents.
+__device__ __forceinline__ float box_box_depth(float dx, float dy, float ca, float sa, float la, float wa, float cb,
+                                               float sb, float lb, float wb) {
+  const float C = fabsf(ca * cb + sa * sb);   // |cos(theta_b - theta_a)|
+  const float S = fabsf(ca * sb - sa * cb);   // |sin(theta_b - theta_a)|
+  const float pa1 = la + lb * C + wb * S - fabsf(dx * ca + dy * sa);
+  const float pa2 = wa + lb * S + wb * C - fabsf(-dx * sa + dy * ca);
+  const float pb1 = lb + la * C + wa * S - fabsf(dx * cb + dy * sb);
+  const float pb2 = wb + la * S + wa * C - fabsf(-dx * sb + dy * cb);
+  return fminf(fminf(pa1, pa2), fminf(pb1, pb2));
+}
+
+// Separating-axis depth of an oriented box (centre c, axes (ca, sa) and
+// (-sa, ca), half extents l, w) and a segment: box axes plus the segment
+// normal.  > 0 iff the segment passes through the box interior.
+__device__ __forceinline__ float box_seg_depth(float cx, float cy, float ca, float sa, float l, float w, float4 seg) {
+  const float qx0 = seg.x - cx, qy0 = seg.y - cy, qx1 = seg.z - cx, qy1 = seg.w - cy;
+  // box axis 1
+  float u0 = qx0 * ca + qy0 * sa, u1 = qx1 * ca + qy1 * sa;
+  float d = fminf(fmaxf(u0, u1) + l, l - fminf(u0, u1));
+  // box axis 2
+  u0 = -qx0 * sa + qy0 * ca;
+  u1 = -qx1 * sa + qy1 * ca;
+  d = fminf(d, fminf(fmaxf(u0, u1) + w, w - fminf(u0, u1)));
+  // segment normal
+  const float ex = seg.z - seg.x, ey = seg.w - seg.y;
+  const float el = sqrtf(ex * ex + ey * ey);
+  if (el > 0.f) {
+    const float nx = -ey / el, ny = ex / el;
+    const float s = qx0 * nx + qy0 * ny;
+    const float r = l * fabsf(nx * ca + ny * sa) + w * fabsf(-nx * sa + ny * ca);
+    d = fminf(d, r - fabsf(s));
+  }
+  return d;
+}
+
+// Agent-grid key: 12-bit column, 12-bit row (clamped, monotone) and the
+// 8-bit local agent index, so one column of three cells is one key range.
+__device__ __forceinline__ uint32_t agent_cell_key(int cx, int cy, int local) {
+  cx = min(max(cx, 0), 4095);
+  cy = min(max(cy, 0), 4095);
+  return ((uint32_t)cx << 20) | ((uint32_t)cy << 8) | (uint32_t)local;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < WARP; o <<= 1) {
+    const int n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+}  // namespace gd

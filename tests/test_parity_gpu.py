@@ -1,0 +1,142 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Each step is teacher-forced (see tests/parity.py): state after the bicycle
+step, decisions (collision, off-road, goal, reward, done, end of episode)
+and the full observation row with its index lists are compared element by
+element at sizes that span several grid tiles and a ragged tail, and at the
+full 1,024 x 64 workload for sampled steps.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, OracleConfig
+from paper_2408_01584_b300 import scenes
+from tests import parity
+from tests._util import small_scene, tiny_scene, workload_config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gd_kwargs(c: OracleConfig, **over):
+    from paper_2408_01584_b300 import gd
+    fl = (gd.GD_TERM_COLLISION if c.term_collision else 0) | (gd.GD_TERM_OFFROAD if c.term_offroad else 0) | \
+        (gd.GD_AUTO_RESET if c.auto_reset else 0)
+    kw = dict(k_road=c.k_road, n_partners=c.n_partners, episode_len=c.episode_len, obs_radius=c.obs_radius,
+              goal_radius=c.goal_radius, dt=c.dt, v_max=c.v_max, collision_penalty=c.collision_penalty,
+              offroad_penalty=c.offroad_penalty, smooth_c=c.smooth_c, flags=fl)
+    kw.update(over)
+    return kw
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def teacher_forced(scene, ocfg, steps, actions, obs_every=1, obs_agents=None, gd_over=None, env=None):
+    from paper_2408_01584_b300.gd import Env
+    env = env or Env(scene, **gd_kwargs(ocfg, **(gd_over or {})))
+    ora = Oracle(scene, ocfg)
+    ex = parity.Exceptions()
+    for t in range(steps):
+        s_pre, f_pre, t_pre = [_np(x) for x in env.get_state()]
+        env.step(torch.from_numpy(np.ascontiguousarray(actions[t])).cuda())
+        env.sync()
+        s_post, f_post, t_post = [_np(x) for x in env.get_state()]
+        g = dict(flags=f_post, reward=_np(env.reward), done=_np(env.done), world_done=_np(env.world_done))
+        # dynamics from the GPU's pre-step state
+        ora.set_state(s_pre, f_pre, t_pre)
+        ora.step(actions[t])
+        o_post = ora.get_state()[0]
+        parity.check_state(s_post, o_post, np.ones(len(s_post), bool), ex, t)
+        np.testing.assert_array_equal(t_post, ora.get_state()[2])
+        # decisions on the GPU's post-step state
+        ora.set_state(s_pre, f_pre, t_pre)
+        o = ora.step_post(s_post)
+        o["flags"] = ora.get_state()[1]
+        parity.check_decisions(g, o, ex, t)
+        if obs_every and (t % obs_every == 0 or t == steps - 1):
+            ora.set_state(s_post, f_post, t_post)
+            gobs, gri, gpi = env.observe(with_idx=True)
+            env.sync()
+            oobs, ori, opi = ora.observe()
+            parity.check_obs(_np(gobs), _np(gri), _np(gpi), ora, oobs, ori, opi, ocfg.k_road, ocfg.n_partners,
+                             ocfg.obs_radius, ex, t, obs_agents)
+    return env, ex
+
+
+def test_initial_observation_plain_4x8():
+    sc = scenes.workload_scene("plain_4x8", 0)
+    ocfg = workload_config("plain_4x8")
+    from paper_2408_01584_b300.gd import Env
+    env = Env(sc, **gd_kwargs(ocfg))
+    gobs, gri, gpi = env.observe(with_idx=True)
+    env.sync()
+    ora = Oracle(sc, ocfg)
+    oobs, ori, opi = ora.observe()
+    ex = parity.Exceptions()
+    parity.check_obs(_np(gobs), _np(gri), _np(gpi), ora, oobs, ori, opi, ocfg.k_road, ocfg.n_partners,
+                     ocfg.obs_radius, ex, 0)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_teacher_forced_plain_4x8(seed):
+    sc = scenes.workload_scene("plain_4x8", seed)
+    ocfg = workload_config("plain_4x8")
+    acts = scenes.make_actions(ocfg.episode_len, sc.num_agents, seed)
+    _, ex = teacher_forced(sc, ocfg, ocfg.episode_len, acts)
+    print("exceptions:", ex.items)
+
+
+def test_teacher_forced_ragged_with_resets():
+    # ragged worlds (1 .. 40 agents, 200 .. 3100 road points), termination on,
+    # short episodes so that auto-reset happens several times
+    sc = small_scene(seed=3)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=7, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = scenes.make_actions(20, sc.num_agents, 3)
+    _, ex = teacher_forced(sc, ocfg, 20, acts)
+    print("exceptions:", ex.items)
+
+
+def test_dense_collisions_and_offroad():
+    sc = scenes.make_scene(np.array([60, 128, 45]), np.array([300, 400, 240]), 11, n_poly=2)
+    ocfg = OracleConfig(k_road=64, n_partners=127, episode_len=30)
+    acts = scenes.make_actions(12, sc.num_agents, 1)
+    env, ex = teacher_forced(sc, ocfg, 12, acts)
+    _, f, _ = env.get_state()
+    f = _np(f)
+    assert (f & 4).any() and (f & 8).any()      # the scene does exercise both tests
+
+
+def test_edge_worlds():
+    # an empty world, a world without road, a lone agent far off the map,
+    # pedestrians and cyclists, K and P larger than anything in range
+    far = (5000.0, -3000.0, 0.3, 5.0, 4.5, 2.0, 5050.0, -3000.0, 0)
+    ped = (0.0, 0.0, 0.0, 1.0, 0.8, 0.8, 3.0, 0.0, scenes.PEDESTRIAN)
+    cyc = (0.0, 3.0, 0.0, 4.0, 1.8, 0.7, 40.0, 3.0, scenes.CYCLIST)
+    car = (2.0, 0.0, 0.0, 2.0, 4.5, 2.0, 30.0, 0.0, 0)
+    edge = [(-20.0 + k, 1.5, 1, 0) for k in range(41)] + [(-20.0 + k, -4.0, 0, 1) for k in range(41)]
+    sc = tiny_scene([([], [(0.0, 0.0, 0, 0), (1.0, 0.0, 0, 0)]), ([car, ped], []), ([far], edge),
+                     ([ped, cyc, car], edge)])
+    ocfg = OracleConfig(k_road=256, n_partners=127, episode_len=10, term_offroad=True, term_collision=True)
+    acts = scenes.make_actions(6, sc.num_agents, 2)
+    teacher_forced(sc, ocfg, 6, acts)
+
+
+def test_zero_slots():
+    sc = small_scene(seed=6, worlds=3)
+    for k, p in ((0, 5), (7, 0), (0, 0)):
+        ocfg = OracleConfig(k_road=k, n_partners=p, episode_len=91)
+        acts = scenes.make_actions(2, sc.num_agents, 0)
+        teacher_forced(sc, ocfg, 2, acts)
+
+
+def test_full_size_plain_1024x64_sampled_steps():
+    sc = scenes.workload_scene("plain_1024x64", 0)
+    ocfg = workload_config("plain_1024x64")
+    acts = scenes.make_actions(3, sc.num_agents, 0)
+    rng = np.random.default_rng(0)
+    agents = np.sort(rng.choice(sc.num_agents, 4096, replace=False))
+    _, ex = teacher_forced(sc, ocfg, 3, acts, obs_every=1, obs_agents=agents)
+    print("exceptions:", len(ex))
