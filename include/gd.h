@@ -212,6 +212,38 @@ gd_status gd_sync(gd_env* env);
 
 const char* gd_last_error(const gd_env* env);
 
+/* ---- allocation-free collision query ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: a program whose GPU memory is owned by
+ * another pool allocator (cudaMalloc from this library would fail or escape
+ * that pool's accounting), or a latency-critical loop that cannot take the
+ * synchronisation cudaMalloc / cudaFree may cause.  gd_create allocates, so
+ * such callers use this stateless call instead.
+ *
+ * Computes, for every agent, whether its box overlaps the box of another
+ * active agent of the same world (the test behind GD_FLAG_COLLIDED of
+ * gd_step), through a per-world uniform grid.
+ *   agent_off  HOST int32 [num_worlds+1], CSR offsets (as in gd_scene_batch)
+ *   state      device float [A,4] = (x, y, theta, v), 16-byte aligned
+ *   extent     device float [A,2] = (length, width), 8-byte aligned
+ *   active     device uint8 [A] (0 = not in the scene) or NULL = all active
+ *   cell       grid cell in m; must be >= the largest box diagonal, or
+ *              collisions between boxes more than one cell apart are missed
+ *   collided   device uint8 [A] output: 1 = overlap, 0 = none or inactive
+ * Working memory is one fixed array in the library (GD_NOALLOC_MAX_AGENTS
+ * agents, GD_NOALLOC_MAX_WORLDS worlds; about 1.2 MB held on every GPU that
+ * loads the library until the process exits).  No call allocates.  Larger
+ * inputs return GD_ERR_CAPACITY; bad arguments GD_ERR_INVALID_ARG; the text
+ * is in gd_last_error(NULL).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  Every call reuses the same array
+ * (nothing in it needs to start at zero: each call writes what it reads),
+ * so calls that overlap on the GPU, e.g. on two streams, race. */
+#define GD_NOALLOC_MAX_AGENTS 262144
+#define GD_NOALLOC_MAX_WORLDS 16384
+gd_status gd_collide_noalloc(int32_t num_worlds, const int32_t* agent_off, const float* state, const float* extent,
+                             const uint8_t* active, float cell, uint8_t* collided, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

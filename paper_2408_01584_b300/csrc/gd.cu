@@ -22,6 +22,9 @@ constexpr int kObsWarpsDefault = 8;
 
 }  // namespace
 
+// Message for gd_last_error(NULL) from entry points that have no env.
+void gd_set_thread_error(const std::string& msg) { g_create_error = msg; }
+
 struct gd_env {
   gd_config cfg{};
   cudaStream_t stream = nullptr;

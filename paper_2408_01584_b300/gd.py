@@ -30,7 +30,7 @@ GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD = 1, 2, 4, 8
 # symbols declared in include/gd.h
 SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_reset", "gd_step", "gd_observe",
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
-           "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error")
+           "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc")
 
 
 class GdError(RuntimeError):
@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_sync.argtypes = [vp]
     lib.gd_last_error.argtypes = [vp]
     lib.gd_last_error.restype = C.c_char_p
+    lib.gd_collide_noalloc.argtypes = [i32, vp, vp, vp, vp, f32, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -222,6 +223,18 @@ def gd_sync(env):
 def gd_last_error(env=None) -> str:
     m = load_library().gd_last_error(env)
     return m.decode() if m else ""
+
+
+def gd_collide_noalloc(agent_off, state, extent, active, cell, collided, stream=None):
+    """Allocation-free collision query: agent_off is a HOST int32 array
+    [W+1]; state [A,4], extent [A,2], active [A] (or None) and collided [A]
+    are CUDA tensors.  See include/gd.h for who needs it."""
+    lib = load_library()
+    off = np.ascontiguousarray(agent_off, np.int32)
+    st = lib.gd_collide_noalloc(len(off) - 1, off.ctypes.data_as(C.c_void_p), _ptr(state, align=16),
+                                _ptr(extent, align=8), _ptr(active), float(cell), _ptr(collided),
+                                C.c_void_p(stream or 0))
+    _check(lib, None, st)
 
 
 class Env:
