@@ -9,7 +9,7 @@ synthetic actions.  Inputs are resident in HBM when the timed region starts
 buffers and the copies inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload plain_1024x64] [--form plain|batched]
+                       [--workload plain_1024x64] [--no-cpu-baseline]
 """
 from __future__ import annotations
 
@@ -17,7 +17,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -38,53 +37,93 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """SM clock and throttle-reason sampling (NVML, every 20 ms) during a
+    timed region; the device is matched to the CUDA device by PCI bus id."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
-        self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+    def __init__(self, torch_device):
+        import threading
+        self.dev = torch_device
+        self.samples = []
+        self.stop = threading.Event()
+        self.thread = None
+        self.err = None
+
+    def _handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        p = torch.cuda.get_device_properties(self.dev)
+        bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+
+    def _run(self, nv, h):
+        while not self.stop.is_set():
+            try:
+                self.samples.append((nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
+                                     nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM),
+                                     nv.nvmlDeviceGetCurrentClocksEventReasons(h),
+                                     nv.nvmlDeviceGetPowerUsage(h) / 1000.0))
+            except Exception as e:  # keep timing even if one read fails
+                self.err = repr(e)
+            self.stop.wait(0.02)
+
+    def _smi(self):
+        """Fallback: nvidia-smi every 50 ms for the same PCI bus id."""
+        import subprocess
+        import torch
+        p = torch.cuda.get_device_properties(self.dev)
+        bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        self.proc = subprocess.Popen(["nvidia-smi", f"--id={bus}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                      "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
 
     def __enter__(self):
+        import threading
+        self.proc = None
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.p = None
+            nv, h = self._handle()
+            self.thread = threading.Thread(target=self._run, args=(nv, h), daemon=True)
+            self.thread.start()
+        except Exception as e:
+            self.err = repr(e)
+            try:
+                self._smi()
+            except Exception as e2:
+                self.err += " / " + repr(e2)
         return self
 
     def __exit__(self, *a):
-        if self.p is not None:
-            self.p.terminate()
-            try:
-                self.p.wait(timeout=5)
-            except Exception:
-                self.p.kill()
-            self.f.close()
+        self.stop.set()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        if self.proc is not None:
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=5)
+            bits = (0x8, 0x40, 0x20, 0x4)
+            for line in out.splitlines():
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 7:
+                    continue
+                try:
+                    r = sum(b for b, v in zip(bits, f[3:7]) if v.lower() == "active")
+                    self.samples.append((float(f[0]), float(f[1]), r, float(f[2])))
+                except ValueError:
+                    pass
 
     def summary(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [f"no samples ({self.err})"]}
+        sm = [x[0] for x in self.samples]
+        reasons = sorted({name for x in self.samples for bit, name in self.REASONS.items() if x[2] & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                "reasons": reasons, "samples": len(self.samples),
+                "power_w_max": max(x[3] for x in self.samples),
+                "source": "nvml 20 ms" if self.proc is None else "nvidia-smi 50 ms"}
 
 
 def workload_cfg(name):
@@ -107,7 +146,8 @@ def algorithmic_bytes_per_agent_step(scene, F):
 
 def cpu_baseline(workload, seed, budget_s=12.0):
     """The oracle as it stands, on a bounded sample of the same workload: the
-    first 64 worlds, as many steps (step + observe) as fit in budget_s."""
+    first 64 worlds, stepped (step + observe, episodes repeating the same
+    action sequence) until budget_s of wall-clock has passed."""
     import numpy as np
     from oracle import Oracle, OracleConfig
     from oracle.oracle import num_threads
@@ -121,14 +161,30 @@ def cpu_baseline(workload, seed, budget_s=12.0):
     acts = scenes.make_actions(wl["steps"], sc.num_agents, seed)
     t0 = time.perf_counter()
     steps = 0
-    while steps < wl["steps"] and (time.perf_counter() - t0) < budget_s:
-        o.step(acts[steps])
+    while (time.perf_counter() - t0) < budget_s:
+        o.step(acts[steps % wl["steps"]])
         o.observe()
         steps += 1
     dt = time.perf_counter() - t0
     return {"value": steps * sc.num_agents / dt, "unit": METRIC, "cores": num_threads(), "kind": "oracle",
             "sample": f"first {sc.num_worlds} worlds ({sc.num_agents} agents) of {workload}, {steps} steps of "
-                      f"step+observe, float64 brute force, {dt:.1f} s"}
+                      f"step+observe, float64 brute force, OpenMP over worlds, {dt:.1f} s"}
+
+
+def _time_rollouts(run, n, stream, flush):
+    """Time n calls of run() with CUDA events on `stream`; L2 flushed (256 MB
+    write) before each, outside the timed interval.  Returns ms per call."""
+    import torch
+    ms = []
+    for k in range(n):
+        flush.fill_(float(k))
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        run()
+        s1.record(stream)
+        s1.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    return ms
 
 
 def run_ours(args, rank, world):
@@ -146,95 +202,93 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream(dev)
     cfg = workload_cfg(args.workload)
     with torch.cuda.stream(stream):
-        env = gd.Env(sc, stream=stream, **cfg)
-        A, F = env.A, env.F
+        env_b = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        env_p = gd.Env(sc, stream=stream, **cfg)
+        A, F = env_b.A, env_b.F
         actions_h = torch.from_numpy(scenes.make_actions(T, A, seed=rank)).pin_memory()
         actions = actions_h.to(dev, non_blocking=True)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    n_launch_step = 6 + (1 if cfg["flags"] & gd.GD_AUTO_RESET else 0)
+        reward_d = torch.empty(T, A, dtype=torch.float32, device=dev)
+        done_d = torch.empty(T, A, dtype=torch.uint8, device=dev)
+    n_plain_launch = 6 + (1 if cfg["flags"] & gd.GD_AUTO_RESET else 0) + 1
 
-    def rollout(events=None):
-        # plain form: one launch per stage, driven from the host
-        gd.gd_reset(env.h, None)
+    def batched_rollout():
+        # reset + one CUDA graph of T fused launches (step + observation of every world)
+        gd.gd_reset(env_b.h, None)
+        gd.gd_rollout(env_b.h, T, actions, env_b.obs, False, reward_d, done_d)
+
+    def plain_rollout():
+        # per-stage form: one launch per stage, issued from the host every step
+        gd.gd_reset(env_p.h, None)
         for t in range(T):
-            gd.gd_step(env.h, actions[t], env.reward, env.done, env.world_done)
-            if events is not None:
-                events[t][0].record(stream)
-            gd.gd_observe(env.h, env.obs)
-            if events is not None:
-                events[t][1].record(stream)
+            gd.gd_step(env_p.h, actions[t], env_p.reward, env_p.done, env_p.world_done)
+            gd.gd_observe(env_p.h, env_p.obs)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            rollout()
+            batched_rollout()
+            plain_rollout()
         torch.cuda.synchronize()
-        gd.gd_sync(env.h)
+        gd.gd_sync(env_b.h)
+        gd.gd_sync(env_p.h)
         if world > 1:
             torch.distributed.barrier()
-        ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
-              for _ in range(args.steps)]
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        with Clocks(dev.index) as clk:
-            torch.cuda.synchronize()
-            for k in range(args.steps):
-                flush.fill_(float(k))               # L2 flush between timed rollouts (not timed)
-                starts[k].record(stream)
-                rollout(ev[k])
-                ends[k].record(stream)
-            torch.cuda.synchronize()
-        gd.gd_sync(env.h)
-        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        obs_ms = [a.elapsed_time(b) for row in ev for (a, b) in row]
+        torch.cuda.synchronize()
+        with Clocks(dev) as clk:
+            ms = _time_rollouts(batched_rollout, args.steps, stream, flush)
+        gd.gd_sync(env_b.h)
         total_ms = sum(ms)
         if world > 1:
             t = torch.tensor([total_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
-        # e2e: public rollout call with host buffers, copies inside the timed region
+        plain_ms = _time_rollouts(plain_rollout, max(2, min(args.steps, 5)), stream, flush)
+        gd.gd_sync(env_p.h)
+
+        # e2e: the public rollout call with host buffers; copies in the timed region
         reward_h = torch.empty(T, A, dtype=torch.float32).pin_memory()
         done_h = torch.empty(T, A, dtype=torch.uint8).pin_memory()
-        reward_d = torch.empty(T, A, dtype=torch.float32, device=dev)
-        done_d = torch.empty(T, A, dtype=torch.uint8, device=dev)
-        e2e_ms = []
-        for k in range(max(2, min(args.steps, 5))):
-            flush.fill_(float(k))
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
+
+        def e2e_rollout():
             actions.copy_(actions_h, non_blocking=True)
-            gd.gd_reset(env.h, None)
-            gd.gd_rollout(env.h, T, actions, env.obs, False, reward_d, done_d)
+            gd.gd_reset(env_b.h, None)
+            gd.gd_rollout(env_b.h, T, actions, env_b.obs, False, reward_d, done_d)
             reward_h.copy_(reward_d, non_blocking=True)
             done_h.copy_(done_d, non_blocking=True)
-            s1.record(stream)
-            s1.synchronize()
-            e2e_ms.append(s0.elapsed_time(s1))
-        gd.gd_sync(env.h)
+
+        e2e_ms = _time_rollouts(e2e_rollout, max(2, min(args.steps, 5)), stream, flush)
+        gd.gd_sync(env_b.h)
     agent_steps = T * A * world
     value = agent_steps * args.steps / (total_ms / 1e3)
     bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F)
-    obs_avg_s = statistics.mean(obs_ms) / 1e3
+    launch_s = statistics.mean(ms) / T / 1e3          # one fused launch = one simulator step of every world
     hbm, peak_kind = _peaks()
-    achieved = (bytes_obs + bytes_road) * A / obs_avg_s / 1e9
+    achieved = (bytes_obs + bytes_road) * A / launch_s / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "form": "plain", "worlds": sc.num_worlds, "agents": A,
-                   "road_points": sc.num_road, "k_road": cfg["k_road"], "n_partners": cfg["n_partners"],
-                   "episode_steps": T, "feat": F, "l2": "flushed (256 MB write) before each timed episode; "
-                   f"observation output {A * F * 4 / 1e6:.0f} MB per step > 126 MB L2",
+        "config": {"workload": args.workload, "form": "batched (persistent fused kernel, 91-step CUDA graph)",
+                   "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
+                   "n_partners": cfg["n_partners"], "episode_steps": T, "feat": F,
+                   "step": "one 91-step episode of every world",
+                   "l2": "flushed (256 MB write) before each timed episode; observation output "
+                         f"{A * F * 4 / 1e6:.0f} MB per simulator step > 126 MB L2",
                    "parallelism": f"independent worlds, {world} GPU(s), no collective"},
-        "e2e": {"value": agent_steps * len(e2e_ms) / (sum(e2e_ms) / 1e3) / world * world, "unit": METRIC,
+        "e2e": {"value": agent_steps / world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": METRIC,
                 "h2d_bytes_per_step": int(T * A * 8), "d2h_bytes_per_step": int(T * A * 5)},
-        "gpu_launches": int(args.steps * T * (n_launch_step + 1)),
-        "roofline": {"bound": "hbm", "kernel": "k_observe", "achieved": achieved, "peak": hbm,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+        "gpu_launches": int(args.steps * T),
+        "roofline": {"bound": "hbm", "kernel": "k_world (fused step + observation)", "achieved": achieved,
+                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                      "algorithmic_bytes_per_agent_step": bytes_obs + bytes_road,
-                     "avg_launch_us": obs_avg_s * 1e6, "launches_timed": len(obs_ms)},
+                     "avg_launch_us": launch_s * 1e6, "launches_timed": args.steps * T},
+        "plain": {"value": T * A * len(plain_ms) / (sum(plain_ms) / 1e3), "unit": METRIC,
+                  "ms_per_step": statistics.mean(plain_ms), "launches_per_sim_step": n_plain_launch,
+                  "form": "per-stage launches from the host, no graph"},
         "clocks": clk.summary(),
     }
-    env.close()
+    env_b.close()
+    env_p.close()
     return out
 
 

@@ -11,6 +11,7 @@
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
 #include "step_kernels.cuh"
+#include "world_kernel.cuh"
 
 using namespace gd;
 
@@ -19,6 +20,10 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kObsWarpsDefault = 8;
+constexpr int kWorldWarps = 8;
+
+// Fixed shared memory of the fused kernel besides the road tile.
+constexpr size_t kWorldFixedSmem = 128 + sizeof(FusedAgents) + kWorldWarps * sizeof(ObsWarpSmem);
 
 }  // namespace
 
@@ -35,6 +40,16 @@ struct gd_env {
   std::string err;
   unsigned* h_err = nullptr;   // pinned host copy of the sticky error word
   int obs_warps = kObsWarpsDefault;
+  // batched form
+  int* order = nullptr;        // [W] world order for the work list
+  unsigned* counter = nullptr; // work counter
+  int tile_cap = 0;            // road points per shared-memory tile
+  size_t world_smem = 0;       // dynamic shared memory of k_world
+  int world_grid = 0;          // persistent CTAs
+  // captured rollout graph and the arguments it was captured with
+  cudaGraphExec_t graph = nullptr;
+  const void* g_key[6] = {};
+  int g_steps = -1;
 };
 
 namespace {
@@ -123,6 +138,7 @@ const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g
 gd_status gd_destroy(gd_env* env) {
   if (!env) return GD_OK;
   cudaStreamSynchronize(env->stream);
+  if (env->graph) cudaGraphExecDestroy(env->graph);
   for (void* p : env->allocs) cudaFree(p);
   if (env->h_err) cudaFreeHost(env->h_err);
   delete env;
@@ -157,6 +173,8 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     if (na < 0 || nr < 0) return fail(nullptr, GD_ERR_INVALID_ARG, "offsets must be non-decreasing");
     if (na > GD_MAX_AGENTS_PER_WORLD)
       return fail(nullptr, GD_ERR_CAPACITY, "world " + std::to_string(w) + " has more than GD_MAX_AGENTS_PER_WORLD agents");
+    if (nr > GD_MAX_ROAD_PER_WORLD)
+      return fail(nullptr, GD_ERR_CAPACITY, "world " + std::to_string(w) + " has more than GD_MAX_ROAD_PER_WORLD road points");
   }
   const int A = s->agent_off[W], N = s->road_off[W];
   if (A > 0 && (!s->x || !s->y || !s->theta || !s->v || !s->length || !s->width || !s->goal_x || !s->goal_y ||
@@ -238,7 +256,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       cnt[cell[j - r0] + 1]++;
     }
     for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
-    for (int c = 0; c <= nc; ++c) rcell_start.push_back(r0 + cnt[c]);
+    for (int c = 0; c <= nc; ++c) rcell_start.push_back(cnt[c]);   // relative to the world's first point
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
     for (int j = r0; j < r1; ++j) {
       const int dst = r0 + fill[cell[j - r0]]++;
@@ -318,6 +336,37 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   d.rgrid = p_rg; d.rcell_start = p_rcs; d.rpts = p_rpts; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
   GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
+  // batched form: worlds largest first (agents, then road points), a work
+  // counter, and a road tile sized for two CTAs per SM when every world fits,
+  // else one CTA per SM with the largest tile
+  {
+    std::vector<int> order(W);
+    for (int w = 0; w < W; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+      const long cp = (long)(s->agent_off[p + 1] - s->agent_off[p]) * 65536 + (s->road_off[p + 1] - s->road_off[p]);
+      const long cq = (long)(s->agent_off[q + 1] - s->agent_off[q]) * 65536 + (s->road_off[q + 1] - s->road_off[q]);
+      return cp > cq;
+    });
+    GD_TRY(upload(env, &env->order, order.data(), (size_t)W));
+    GD_TRY(dev_alloc(env, &env->counter, 1));
+    int dev = 0, smem_sm = 0, smem_blk = 0, nsm = 0;
+    GD_TRY(cudaGetDevice(&dev));
+    GD_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int max_nr = 0;
+    for (int w = 0; w < W; ++w) max_nr = std::max(max_nr, s->road_off[w + 1] - s->road_off[w]);
+    const long two = ((long)smem_sm / 2 - 2048 - (long)kWorldFixedSmem) / 16;   // points per tile, 2 CTAs/SM
+    const long one = ((long)smem_blk - 1024 - (long)kWorldFixedSmem) / 16;      // 1 CTA/SM
+    long cap = (max_nr <= two) ? std::max(max_nr, 1) : one;
+    cap = std::max(1L, std::min(cap, (long)GD_MAX_ROAD_PER_WORLD));
+    env->tile_cap = (int)cap;
+    env->world_smem = kWorldFixedSmem + (size_t)cap * 16;
+    GD_TRY(cudaFuncSetAttribute(k_world<kWorldWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem));
+    int per_sm = 0;
+    GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<kWorldWarps>, kWorldWarps * 32, env->world_smem));
+    env->world_grid = std::max(1, std::min(W, std::max(per_sm, 1) * nsm));
+  }
   GD_TRY(cudaStreamSynchronize(env->stream));
 #undef GD_TRY
   *out = env;
@@ -379,13 +428,40 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
       d, obs, road_idx, partner_idx);
 }
 
+// Batched form: one persistent fused launch (work counter cleared first).
+static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
+                         float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
+                         cudaStream_t stream = nullptr) {
+  if (!stream) stream = env->stream;
+  FusedArgs a;
+  a.actions = reinterpret_cast<const float2*>(actions);
+  a.reward = reward;
+  a.done = done;
+  a.world_done = world_done;
+  a.obs = obs;
+  a.road_idx = road_idx;
+  a.partner_idx = partner_idx;
+  a.counter = env->counter;
+  a.order = env->order;
+  a.tile_cap = env->tile_cap;
+  a.do_step = do_step;
+  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
+  k_world<kWorldWarps><<<env->world_grid, kWorldWarps * 32, env->world_smem, stream>>>(env->d, a);
+}
+
+static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) != 0; }
+
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done) {
   if (!env) return GD_ERR_INVALID_ARG;
   if (!actions && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions must not be NULL");
   if (!aligned16(actions) && ((uintptr_t)actions & 7u)) return fail(env, GD_ERR_INVALID_ARG, "actions must be 8-byte aligned");
-  launch_step_plain(env, actions, reward, done, world_done);
+  if (batched(env)) {
+    if (env->A > 0 || env->W > 0) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1);
+  } else {
+    launch_step_plain(env, actions, reward, done, world_done);
+  }
   return launch_check(env, "gd_step");
 }
 
@@ -393,12 +469,21 @@ gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partne
   if (!env) return GD_ERR_INVALID_ARG;
   if (!obs && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "obs must not be NULL");
   if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
-  launch_observe(env, obs, road_idx, partner_idx);
+  if (env->A == 0) return GD_OK;
+  if (batched(env)) launch_world(env, nullptr, nullptr, nullptr, nullptr, obs, road_idx, partner_idx, 0);
+  else launch_observe(env, obs, road_idx, partner_idx);
   return launch_check(env, "gd_observe");
 }
 
 gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                           float* obs) {
+  if (env && batched(env)) {
+    if (!actions && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions must not be NULL");
+    if (!obs && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "obs must not be NULL");
+    if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
+    launch_world(env, actions, reward, done, world_done, obs, nullptr, nullptr, 1);
+    return launch_check(env, "gd_step_observe");
+  }
   gd_status st = gd_step(env, actions, reward, done, world_done);
   if (st != GD_OK) return st;
   return gd_observe(env, obs, nullptr, nullptr);
@@ -408,15 +493,58 @@ gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* ob
                      uint8_t* done) {
   if (!env) return GD_ERR_INVALID_ARG;
   if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
-  for (int t = 0; t < steps; ++t) {
-    const float* a = actions + (size_t)t * env->A * 2;
-    float* o = obs + (obs_per_step ? (size_t)t * env->A * env->F : 0);
-    gd_status st = gd_step(env, a, reward ? reward + (size_t)t * env->A : nullptr,
-                           done ? done + (size_t)t * env->A : nullptr, nullptr);
-    if (st != GD_OK) return st;
-    st = gd_observe(env, o, nullptr, nullptr);
-    if (st != GD_OK) return st;
+  if (steps == 0 || env->A == 0) return GD_OK;
+  if (!actions || !obs) return fail(env, GD_ERR_INVALID_ARG, "actions and obs must not be NULL");
+  if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
+  const size_t A = (size_t)env->A;
+  if (!batched(env)) {
+    // per-stage form: launches issued from the host, one step at a time
+    for (int t = 0; t < steps; ++t) {
+      gd_status st = gd_step(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                             done ? done + (size_t)t * A : nullptr, nullptr);
+      if (st != GD_OK) return st;
+      st = gd_observe(env, obs + (obs_per_step ? (size_t)t * A * env->F : 0), nullptr, nullptr);
+      if (st != GD_OK) return st;
+    }
+    return GD_OK;
   }
+  // batched form: the whole rollout is one CUDA graph (T fused launches),
+  // captured on a private stream and re-used while the arguments are the same
+  const void* key[6] = {actions, obs, reward, done, (const void*)(intptr_t)(obs_per_step != 0), nullptr};
+  bool same = env->graph && env->g_steps == steps;
+  for (int k = 0; k < 6 && same; ++k) same = env->g_key[k] == key[k];
+  if (!same) {
+    if (env->graph) {
+      cudaGraphExecDestroy(env->graph);
+      env->graph = nullptr;
+    }
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout: capture stream");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_fail(env, e, "gd_rollout: begin capture");
+    }
+    for (int t = 0; t < steps; ++t)
+      launch_world(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                   done ? done + (size_t)t * A : nullptr, nullptr, obs + (obs_per_step ? (size_t)t * A * env->F : 0),
+                   nullptr, nullptr, 1, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout: end capture");
+    e = cudaGraphInstantiate(&env->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      env->graph = nullptr;
+      return cuda_fail(env, e, "gd_rollout: instantiate");
+    }
+    for (int k = 0; k < 6; ++k) env->g_key[k] = key[k];
+    env->g_steps = steps;
+  }
+  cudaError_t e = cudaGraphLaunch(env->graph, env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout: graph launch");
   return GD_OK;
 }
 

@@ -1,0 +1,293 @@
+// Fused per-world kernel (the batched form): one persistent launch runs the
+// whole step -- masked reset, bicycle dynamics (App. B), agent grid and
+// box collision, road-edge test, goal / reward / done (Sec. 3.2) -- and the
+// observation of every world, taking worlds from a work list with an
+// atomic counter (no grid-wide synchronisation).
+//
+// Per world the CTA keeps the agents in shared memory and copies the
+// world's cell-sorted road points into a shared-memory tile with one
+// cp.async.bulk (TMA) copy, issued first so that it overlaps the step
+// stages.  Worlds whose road does not fit the tile read it from global
+// memory instead.  The mbarrier wait is bounded: after ~2 s the CTA sets
+// ERR_TIMEOUT, waits once more (bounded) for its copy and leaves; other
+// CTAs keep draining the work list.
+#pragma once
+#include "gd_device.cuh"
+#include "observe_kernel.cuh"
+
+namespace gd {
+
+struct FusedArgs {
+  const float2* actions;     // [A] (step) or nullptr
+  float* reward;             // [A] or nullptr
+  uint8_t* done;             // [A] or nullptr
+  uint8_t* world_done;       // [W] or nullptr
+  float* obs;                // [A,F] or nullptr (no observation)
+  int32_t* road_idx;         // [A,K] or nullptr
+  int32_t* partner_idx;      // [A,P] or nullptr
+  unsigned* counter;         // work counter, zero at launch
+  const int* order;          // [W] world order (largest first)
+  int tile_cap;              // road points that fit the tile
+  int do_step;
+};
+
+struct FusedAgents {
+  float4 st[GD_MAX_AGENTS_PER_WORLD];
+  float4 sc[GD_MAX_AGENTS_PER_WORLD];
+  uint32_t key[GD_MAX_AGENTS_PER_WORLD];     // sorted grid keys of the active agents
+  uint8_t fl[GD_MAX_AGENTS_PER_WORLD];
+  uint8_t ty[GD_MAX_AGENTS_PER_WORLD];
+  uint8_t coll[GD_MAX_AGENTS_PER_WORLD];
+  uint8_t offr[GD_MAX_AGENTS_PER_WORLD];
+};
+
+// ---- TMA bulk copy + mbarrier (inline PTX) --------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity` of the barrier: true when it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 4000000000ll) return false;    // ~2 s at 2 GHz
+  }
+  return true;
+}
+
+// 1-D bulk copy global -> this CTA's shared memory; completion is reported
+// to the mbarrier as transferred bytes.  dst, src 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Dynamic shared memory: [mbarrier, 128 B][tile float4 x tile_cap][FusedAgents][ObsWarpSmem x WARPS]
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wsm);
+  float4* tile = reinterpret_cast<float4*>(wsm + 128);
+  FusedAgents& ag = *reinterpret_cast<FusedAgents*>(wsm + 128 + (size_t)a.tile_cap * sizeof(float4));
+  ObsWarpSmem* wsmem = reinterpret_cast<ObsWarpSmem*>(reinterpret_cast<unsigned char*>(&ag) + sizeof(FusedAgents));
+  __shared__ int s_w;
+  __shared__ int s_nact;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  ObsWarpSmem& osm = wsmem[wid];
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    s_abort = 0;
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  const bool observe = a.obs != nullptr;
+  for (;;) {
+    if (tid == 0) s_w = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int k = s_w;
+    if (k >= e.W) break;
+    const int w = a.order[k];
+    const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0;
+    const int r0 = e.road_off[w], nr = e.road_off[w + 1] - r0;
+    const bool use_tile = observe && nr > 0 && nr <= a.tile_cap;
+    if (use_tile && tid == 0) {
+      fence_proxy_async_smem();     // earlier generic reads of the tile before the async write
+      mbar_arrive_expect_tx(bar, (unsigned)nr * 16u);
+      tma_load_1d(tile, e.rpts + r0, (unsigned)nr * 16u, bar);
+    }
+    const GridDesc g = e.rgrid[w];
+    if (a.do_step) {
+      const bool reset = (e.cflags & GD_AUTO_RESET) && e.world_done[w];
+      const float inv = 1.f / e.agent_cell;
+      bool act = false;
+      uint32_t key = 0;
+      if (tid < n) {
+        const int i = a0 + tid;
+        float4 s = reset ? e.init_state[i] : e.state[i];
+        uint8_t f = reset ? e.init_flags[i] : e.flags[i];
+        if (!(f & GD_FLAG_DONE)) {
+          const float2 u = a.actions[i];
+          if (!isfinite(u.x) || !isfinite(u.y) || fabsf(u.y) >= 1.5707963f) {
+            atomicOr(e.err, ERR_ACTION);
+          } else {
+            bicycle_step(s, u.x, u.y, e.stat[i].x, e.dt, e.vmax);
+          }
+          act = true;
+          key = agent_cell_key((int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f),
+                               (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f), tid);
+        }
+        ag.st[tid] = s;
+        ag.sc[tid] = e.stat[i];
+        ag.fl[tid] = f;
+        ag.ty[tid] = e.type[i];
+        ag.key[tid] = key;
+      }
+      const int nact = __syncthreads_count(act);
+      // agent grid: rank of each active key among the active keys
+      uint32_t rank = 0;
+      if (act)
+        for (int q = 0; q < n; ++q) rank += (!(ag.fl[q] & GD_FLAG_DONE)) && ag.key[q] < key;
+      __syncthreads();
+      if (act) ag.key[rank] = key;
+      if (tid == 0) s_nact = nact;
+      __syncthreads();
+      // collision and road edge: warp per agent, ballot-OR over candidates
+      for (int li = wid; li < n; li += WARPS) {
+        if (ag.fl[li] & GD_FLAG_DONE) continue;
+        const float4 s = ag.st[li];
+        const float4 sc = ag.sc[li];
+        float sa, ca;
+        sincosf(s.z, &sa, &ca);
+        const int cx = (int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f);
+        const int cy = (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f);
+        bool hit = false;
+        for (int dcx = -1; dcx <= 1; ++dcx) {
+          const int c = cx + dcx;
+          if (c < 0 || c > 4095) continue;
+          const uint32_t lo = agent_cell_key(c, max(cy - 1, 0), 0), hi = agent_cell_key(c, min(cy + 1, 4095), 255);
+          int b = 0, en = s_nact;
+          {  // lower bound of lo
+            int l = 0, h = s_nact;
+            while (l < h) { const int m = (l + h) >> 1; if (ag.key[m] < lo) l = m + 1; else h = m; }
+            b = l;
+          }
+          {  // upper bound of hi
+            int l = b, h = s_nact;
+            while (l < h) { const int m = (l + h) >> 1; if (ag.key[m] <= hi) l = m + 1; else h = m; }
+            en = l;
+          }
+          for (int q = b + lane; q < en; q += WARP) {
+            const int j = (int)(ag.key[q] & 0xffu);
+            if (j == li) continue;
+            const float4 sj = ag.st[j];
+            const float4 tj = ag.sc[j];
+            float sb, cb;
+            sincosf(sj.z, &sb, &cb);
+            hit |= box_box_depth(sj.x - s.x, sj.y - s.y, ca, sa, 0.5f * sc.x, 0.5f * sc.y, cb, sb, 0.5f * tj.x,
+                                 0.5f * tj.y) > 0.f;
+          }
+        }
+        hit = __any_sync(0xffffffffu, hit);
+        bool off = false;
+        if (ag.ty[li] != GD_AGENT_PEDESTRIAN) {
+          const GridDesc eg = e.egrid[w];
+          const float hl = 0.5f * sc.x, hw = 0.5f * sc.y;
+          const float ex = hl * fabsf(ca) + hw * fabsf(sa) + 1e-3f, ey = hl * fabsf(sa) + hw * fabsf(ca) + 1e-3f;
+          const int cx0 = (int)clampf(floorf((s.x - ex - eg.ox) * eg.inv_cs), 0.f, (float)(eg.nx - 1));
+          const int cx1 = (int)clampf(floorf((s.x + ex - eg.ox) * eg.inv_cs), -1.f, (float)(eg.nx - 1));
+          const int cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
+          const int cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
+          for (int row = cy0; row <= cy1 && cx0 <= cx1; ++row) {
+            const int sb = __ldg(e.ecell_start + eg.cell_base + row * eg.nx + cx0);
+            const int se = __ldg(e.ecell_start + eg.cell_base + row * eg.nx + cx1 + 1);
+            for (int q = sb + lane; q < se; q += WARP) off |= box_seg_depth(s.x, s.y, ca, sa, hl, hw, e.esegs[q]) > 0.f;
+          }
+          off = __any_sync(0xffffffffu, off);
+        }
+        if (lane == 0) {
+          ag.coll[li] = hit ? 1 : 0;
+          ag.offr[li] = off ? 1 : 0;
+        }
+      }
+      __syncthreads();
+      // goal, reward, flags, done
+      bool dn = true;
+      if (tid < n) {
+        const int i = a0 + tid;
+        uint8_t f = ag.fl[tid];
+        float r = 0.f;
+        if (!(f & GD_FLAG_DONE)) {
+          const float4 s = ag.st[tid];
+          const float4 sc = ag.sc[tid];
+          const float dx = s.x - sc.z, dy = s.y - sc.w;
+          const bool at_goal = sqrtf(dx * dx + dy * dy) <= e.goal_r;
+          const bool coll = ag.coll[tid] != 0, offr = ag.offr[tid] != 0;
+          const bool first = at_goal && !(f & GD_FLAG_GOAL);
+          f &= (uint8_t)~(GD_FLAG_COLLIDED | GD_FLAG_OFFROAD);
+          if (at_goal) f |= GD_FLAG_GOAL;
+          if (coll) f |= GD_FLAG_COLLIDED;
+          if (offr) f |= GD_FLAG_OFFROAD;
+          if ((f & GD_FLAG_GOAL) || (coll && (e.cflags & GD_TERM_COLLISION)) || (offr && (e.cflags & GD_TERM_OFFROAD)))
+            f |= GD_FLAG_DONE;
+          r = (first ? 1.f : 0.f) - (coll ? e.cpen : 0.f) - (offr ? e.opn : 0.f);
+        }
+        ag.fl[tid] = f;
+        e.state[i] = ag.st[tid];
+        e.flags[i] = f;
+        if (a.reward) a.reward[i] = r;
+        if (a.done) a.done[i] = (f & GD_FLAG_DONE) ? 1 : 0;
+        dn = (f & GD_FLAG_DONE) != 0;
+      }
+      const int all_done = __syncthreads_and(dn);
+      if (tid == 0) {
+        const int t = (reset ? 0 : e.t[w]) + 1;
+        e.t[w] = t;
+        const uint8_t wd = ((n > 0 && all_done) || t >= e.T) ? 1 : 0;
+        e.world_done[w] = wd;
+        if (a.world_done) a.world_done[w] = wd;
+      }
+    } else if (observe && tid < n) {
+      ag.st[tid] = e.state[a0 + tid];
+      ag.sc[tid] = e.stat[a0 + tid];
+      ag.fl[tid] = e.flags[a0 + tid];
+    }
+    if (observe) {
+      if (use_tile) {
+        // every thread waits for the tile (bounded)
+        const bool ok = mbar_wait_bounded(bar, phase);
+        if (!ok) s_abort = 1;
+        phase ^= 1u;
+      }
+      __syncthreads();
+      if (s_abort) {
+        if (tid == 0) {
+          atomicOr(e.err, ERR_TIMEOUT);
+          mbar_wait_bounded(bar, phase ^ 1u);   // give the copy one more bounded chance to land
+        }
+        __syncthreads();
+        return;
+      }
+      WorldView v;
+      v.state = ag.st;
+      v.stat = ag.sc;
+      v.flags = ag.fl;
+      v.n = n;
+      v.pts = use_tile ? tile : e.rpts + r0;
+      v.g = g;
+      v.cell_start = e.rcell_start + g.cell_base;
+      for (int li = wid; li < n; li += WARPS) {
+        const int i = a0 + li;
+        observe_agent(e, v, li, a.obs + (size_t)i * e.F, a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr,
+                      a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr, osm, lane);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gd

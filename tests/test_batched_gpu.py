@@ -1,0 +1,110 @@
+"""GPU parity of the batched form (GD_BATCHED: persistent fused per-world
+kernel with the road tile in shared memory, whole rollouts as one CUDA
+graph) against the oracle, and bitwise equality with the per-stage form.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleConfig
+from paper_2408_01584_b300 import scenes
+from tests._util import small_scene, workload_config
+from tests.test_parity_gpu import _np, gd_kwargs, teacher_forced
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _batched(ocfg, **over):
+    from paper_2408_01584_b300 import gd
+    kw = gd_kwargs(ocfg, **over)
+    kw["flags"] |= gd.GD_BATCHED
+    return kw
+
+
+def test_batched_teacher_forced_ragged_with_resets():
+    sc = small_scene(seed=3)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=7, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = scenes.make_actions(20, sc.num_agents, 3)
+    from paper_2408_01584_b300.gd import Env
+    env = Env(sc, **_batched(ocfg))
+    _, ex = teacher_forced(sc, ocfg, 20, acts, env=env)
+    print("exceptions:", ex.items)
+
+
+def test_batched_teacher_forced_uneven_subset():
+    # 48 worlds of the uneven workload: 1..128 agents, 500..20,000 road points
+    # (large worlds exceed the shared-memory tile and read road from global memory)
+    sc = scenes.workload_scene("uneven_4096", 0).subset(0, 48)
+    ocfg = workload_config("uneven_4096")
+    acts = scenes.make_actions(4, sc.num_agents, 0)
+    from paper_2408_01584_b300.gd import Env
+    env = Env(sc, **_batched(ocfg))
+    rng = np.random.default_rng(1)
+    agents = np.sort(rng.choice(sc.num_agents, min(600, sc.num_agents), replace=False))
+    _, ex = teacher_forced(sc, ocfg, 4, acts, env=env, obs_agents=agents)
+    print("exceptions:", len(ex))
+
+
+def _rollout(sc, kw, acts, mode):
+    """Run a rollout; returns per-step (state, flags, reward, done, obs)."""
+    from paper_2408_01584_b300 import gd
+    env = gd.Env(sc, **kw)
+    T = acts.shape[0]
+    a = torch.from_numpy(acts).cuda().contiguous()
+    out = []
+    if mode == "graph":
+        obs = torch.zeros(T, env.A, env.F, device="cuda")
+        rew = torch.zeros(T, env.A, device="cuda")
+        dn = torch.zeros(T, env.A, dtype=torch.uint8, device="cuda")
+        gd.gd_rollout(env.h, T, a, obs, True, rew, dn)
+        env.sync()
+        s, f, _ = env.get_state()
+        return dict(obs=_np(obs), reward=_np(rew), done=_np(dn), state=_np(s), flags=_np(f))
+    obs_all, rew_all, dn_all = [], [], []
+    for t in range(T):
+        if mode == "fused":
+            gd.gd_step_observe(env.h, a[t], env.reward, env.done, env.world_done, env.obs)
+        else:
+            env.step(a[t])
+            env.observe()
+        env.sync()
+        obs_all.append(_np(env.obs).copy())
+        rew_all.append(_np(env.reward).copy())
+        dn_all.append(_np(env.done).copy())
+    s, f, _ = env.get_state()
+    return dict(obs=np.stack(obs_all), reward=np.stack(rew_all), done=np.stack(dn_all), state=_np(s), flags=_np(f))
+
+
+@pytest.mark.parametrize("mode", ["stepwise", "fused", "graph"])
+def test_batched_bitwise_equals_plain(mode):
+    sc = small_scene(seed=9)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = scenes.make_actions(12, sc.num_agents, 9)
+    plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
+    bat = _rollout(sc, _batched(ocfg), acts, mode)
+    for k in plain:
+        np.testing.assert_array_equal(plain[k], bat[k], err_msg=k)
+
+
+def test_graph_rollout_replay_and_full_size_agreement():
+    # full 1,024 x 64 workload, 5 steps: graph replay (twice, after a reset)
+    # equals the per-stage form bit for bit
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("plain_1024x64", 0)
+    ocfg = workload_config("plain_1024x64")
+    acts = scenes.make_actions(5, sc.num_agents, 0)
+    plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
+    env = gd.Env(sc, **_batched(ocfg))
+    a = torch.from_numpy(acts).cuda().contiguous()
+    obs = torch.zeros(env.A, env.F, device="cuda")
+    rew = torch.zeros(5, env.A, device="cuda")
+    for rep in range(2):
+        gd.gd_reset(env.h, None)
+        gd.gd_rollout(env.h, 5, a, obs, False, rew, None)
+        env.sync()
+        np.testing.assert_array_equal(_np(obs), plain["obs"][-1])
+        np.testing.assert_array_equal(_np(rew), plain["reward"])
+        s, f, _ = env.get_state()
+        np.testing.assert_array_equal(_np(s), plain["state"])
