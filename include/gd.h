@@ -89,7 +89,7 @@ typedef enum gd_status {
 #define GD_MAX_AGENTS_PER_WORLD 128
 #define GD_MAX_K_ROAD 256
 #define GD_MAX_PARTNERS 127
-#define GD_MAX_ROAD_PER_WORLD 65535
+#define GD_MAX_ROAD_PER_WORLD 32767
 
 typedef struct gd_config {
   int32_t k_road;            /* K road slots per observation, 0..GD_MAX_K_ROAD */

@@ -43,7 +43,7 @@ struct gd_env {
   // batched form
   int* order = nullptr;        // [W] world order for the work list
   unsigned* counter = nullptr; // work counter
-  int tile_cap = 0;            // road points per shared-memory tile
+  int tile_cap = 0;            // bytes of the shared-memory road tile
   size_t world_smem = 0;       // dynamic shared memory of k_world
   int world_grid = 0;          // persistent CTAs
   // captured rollout graph and the arguments it was captured with
@@ -228,10 +228,17 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       h_agent_world[i] = w;
       max_diag = std::max(max_diag, std::sqrt(s->length[i] * s->length[i] + s->width[i] * s->width[i]));
     }
-  // road-point grid: cell-sorted points (x, y, local index bits, type bits)
+  // road arena: per world one 16-byte aligned block of cell-sorted points,
+  // road_pad(N_w) float2 (x, y) then road_pad(N_w) uint16 (index | type << 15)
   std::vector<GridDesc> rdesc(W), edesc(W);
   std::vector<int> rcell_start;
-  std::vector<float4> rpts(N);
+  std::vector<long long> arena_off(W);
+  size_t arena_bytes = 0;
+  for (int w = 0; w < W; ++w) {
+    arena_off[w] = (long long)(arena_bytes / 16);
+    arena_bytes += road_block_bytes(s->road_off[w + 1] - s->road_off[w]);
+  }
+  std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
   std::vector<int> ecell_start;
   std::vector<float4> esegs;
   for (int w = 0; w < W; ++w) {
@@ -258,13 +265,12 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
     for (int c = 0; c <= nc; ++c) rcell_start.push_back(cnt[c]);   // relative to the world's first point
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    float2* bxy = reinterpret_cast<float2*>(arena.data() + (size_t)arena_off[w] * 16);
+    uint16_t* bmeta = reinterpret_cast<uint16_t*>(bxy + road_pad(r1 - r0));
     for (int j = r0; j < r1; ++j) {
-      const int dst = r0 + fill[cell[j - r0]]++;
-      int lidx = j - r0, typ = s->road_type[j];
-      float fi, ft;
-      std::memcpy(&fi, &lidx, 4);
-      std::memcpy(&ft, &typ, 4);
-      rpts[dst] = make_float4(s->road_x[j], s->road_y[j], fi, ft);
+      const int dst = fill[cell[j - r0]]++;
+      bxy[dst] = make_float2(s->road_x[j], s->road_y[j]);
+      bmeta[dst] = (uint16_t)((j - r0) | (s->road_type[j] << 15));
     }
     // road-edge segment grid: a segment is listed under every cell its
     // bounding box (grown by 1 mm) touches
@@ -302,7 +308,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   std::vector<uint8_t> zeros_a(A, 0);
   std::vector<int> zeros_w(W, 0);
   int* p_aoff; int* p_roff; int* p_aw; float4* p_state; float4* p_init; float4* p_stat; uint8_t* p_type;
-  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; int* p_rcs; float4* p_rpts;
+  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; int* p_rcs; unsigned char* p_arena;
+  long long* p_aroff;
   GridDesc* p_eg; int* p_ecs; float4* p_es;
   cudaError_t e = cudaSuccess;
 #define GD_TRY(x) do { e = (x); if (e != cudaSuccess) { gd_status r_ = cuda_fail(nullptr, e, #x); gd_destroy(env); return r_; } } while (0)
@@ -320,7 +327,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(cudaMemsetAsync(p_wd, 0, (size_t)W, env->stream));
   GD_TRY(upload(env, &p_rg, rdesc.data(), (size_t)W));
   GD_TRY(upload(env, &p_rcs, rcell_start.data(), rcell_start.size()));
-  GD_TRY(upload(env, &p_rpts, rpts.data(), (size_t)N));
+  GD_TRY(upload(env, &p_arena, arena.data(), arena.size()));
+  GD_TRY(upload(env, &p_aroff, arena_off.data(), (size_t)W));
   GD_TRY(upload(env, &p_eg, edesc.data(), (size_t)W));
   GD_TRY(upload(env, &p_ecs, ecell_start.data(), ecell_start.size()));
   GD_TRY(upload(env, &p_es, esegs.data(), esegs.size()));
@@ -333,7 +341,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
   d.stat = p_stat; d.type = p_type; d.flags = p_flags; d.init_flags = p_iflags; d.t = p_t; d.world_done = p_wd;
-  d.rgrid = p_rg; d.rcell_start = p_rcs; d.rpts = p_rpts; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
+  d.rgrid = p_rg; d.rcell_start = p_rcs; d.arena = p_arena; d.arena_off = p_aroff; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
   GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
   // batched form: worlds largest first (agents, then road points), a work
@@ -354,14 +362,13 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    int max_nr = 0;
-    for (int w = 0; w < W; ++w) max_nr = std::max(max_nr, s->road_off[w + 1] - s->road_off[w]);
-    const long two = ((long)smem_sm / 2 - 2048 - (long)kWorldFixedSmem) / 16;   // points per tile, 2 CTAs/SM
-    const long one = ((long)smem_blk - 1024 - (long)kWorldFixedSmem) / 16;      // 1 CTA/SM
-    long cap = (max_nr <= two) ? std::max(max_nr, 1) : one;
-    cap = std::max(1L, std::min(cap, (long)GD_MAX_ROAD_PER_WORLD));
+    size_t max_block = 16;
+    for (int w = 0; w < W; ++w) max_block = std::max(max_block, road_block_bytes(s->road_off[w + 1] - s->road_off[w]));
+    const long two = ((long)smem_sm / 2 - 2048 - (long)kWorldFixedSmem) & ~15L;   // tile bytes, 2 CTAs/SM
+    const long one = ((long)smem_blk - 1024 - (long)kWorldFixedSmem) & ~15L;      // 1 CTA/SM
+    const long cap = ((long)max_block <= two) ? (long)max_block : one;
     env->tile_cap = (int)cap;
-    env->world_smem = kWorldFixedSmem + (size_t)cap * 16;
+    env->world_smem = kWorldFixedSmem + (size_t)cap;
     GD_TRY(cudaFuncSetAttribute(k_world<kWorldWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem));
     int per_sm = 0;
     GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<kWorldWarps>, kWorldWarps * 32, env->world_smem));
@@ -443,7 +450,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.partner_idx = partner_idx;
   a.counter = env->counter;
   a.order = env->order;
-  a.tile_cap = env->tile_cap;
+  a.tile_bytes = env->tile_cap;
   a.do_step = do_step;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
   k_world<kWorldWarps><<<env->world_grid, kWorldWarps * 32, env->world_smem, stream>>>(env->d, a);

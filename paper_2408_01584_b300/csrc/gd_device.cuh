@@ -4,9 +4,11 @@
 //   state[A]       float4 (x, y, theta, v)        -- 16 B, one coalesced load
 //   stat[A]        float4 (length, width, goal_x, goal_y)
 //   flags[A]       uint8  GD_FLAG_* bits
-//   rpts[N]        float4 (x, y, local index bits, type bits), per world sorted
-//                  by road-grid cell so that a row of cells is one range
-//   rcell_start[]  int32, per world (ny*nx + 1) cell starts into rpts
+//   arena          per world one 16-byte aligned block: road_pad(N_w) float2
+//                  (x, y) then road_pad(N_w) uint16 (local index | type << 15),
+//                  both sorted by road-grid cell so that a row of cells is one
+//                  range; arena_off[w] is the block's offset in 16-byte units
+//   rcell_start[]  int32, per world (ny*nx + 1) cell starts, relative to the block
 //   esegs[]        float4 (x0, y0, x1, y1) road-edge segments listed under every
 //                  edge-grid cell their bounding box touches
 #pragma once
@@ -22,6 +24,10 @@ constexpr unsigned ERR_TIMEOUT = 2u;    // a bounded wait gave up
 constexpr unsigned ERR_CAPACITY = 4u;   // a device-side capacity was exceeded
 
 constexpr int WARP = 32;
+
+// Points of a world's road block, padded so the block is a multiple of 16 B.
+__host__ __device__ __forceinline__ int road_pad(int nr) { return (nr + 7) & ~7; }
+__host__ __device__ __forceinline__ size_t road_block_bytes(int nr) { return (size_t)road_pad(nr) * 10; }
 constexpr int MAX_ROWS = 32;            // grid rows spanned by one observation disk
 
 struct GridDesc {      // one per world, for the road-point grid and the edge grid
@@ -50,7 +56,8 @@ struct DevEnv {
   uint8_t* world_done;
   const GridDesc* rgrid;
   const int* rcell_start;
-  const float4* rpts;
+  const unsigned char* arena;
+  const long long* arena_off;
   const GridDesc* egrid;
   const int* ecell_start;
   const float4* esegs;
@@ -66,20 +73,27 @@ __device__ __forceinline__ float clampf(float a, float lo, float hi) { return fm
 
 // Kinematic bicycle model of App. B with l_r = L/2: mid-step clipped speed,
 // slip angle beta = atan(tan(delta)/2), explicit Euler with the old heading.
+// Every rounding step is spelled out (fmaf / __fmul_rn), so all kernels that
+// inline this produce bit-identical states.
 __device__ __forceinline__ void bicycle_step(float4& s, float accel, float steer, float L, float dt, float vmax) {
-  const float vbar = clampf(s.w + 0.5f * accel * dt, -vmax, vmax);
+  const float vbar = clampf(fmaf(__fmul_rn(0.5f, accel), dt, s.w), -vmax, vmax);
   const float tn = tanf(steer);
-  const float beta = atanf(0.5f * tn);
+  const float beta = atanf(__fmul_rn(0.5f, tn));
   float sn, cs;
-  sincosf(s.z + beta, &sn, &cs);
-  const float xdot = vbar * cs;
-  const float ydot = vbar * sn;
-  const float thdot = vbar * cosf(beta) * tn / L;
-  s.x = s.x + xdot * dt;
-  s.y = s.y + ydot * dt;
-  s.z = s.z + thdot * dt;
-  s.w = clampf(s.w + accel * dt, -vmax, vmax);
+  sincosf(__fadd_rn(s.z, beta), &sn, &cs);
+  const float xdot = __fmul_rn(vbar, cs);
+  const float ydot = __fmul_rn(vbar, sn);
+  const float thdot = __fdiv_rn(__fmul_rn(__fmul_rn(vbar, cosf(beta)), tn), L);
+  s.x = fmaf(xdot, dt, s.x);
+  s.y = fmaf(ydot, dt, s.y);
+  s.z = fmaf(thdot, dt, s.z);
+  s.w = clampf(fmaf(accel, dt, s.w), -vmax, vmax);
 }
+
+// Ego-frame rotation by -theta of the offset (dx, dy), given c = cos theta,
+// s = sin theta, with a fixed rounding sequence.
+__device__ __forceinline__ float rot_x(float c, float s, float dx, float dy) { return fmaf(c, dx, __fmul_rn(s, dy)); }
+__device__ __forceinline__ float rot_y(float c, float s, float dx, float dy) { return fmaf(c, dy, -__fmul_rn(s, dx)); }
 
 // Separating-axis depth of two oriented boxes: the minimum over the four box
 // axes of (sum of projected half extents - |projected centre offset|).
@@ -87,12 +101,12 @@ __device__ __forceinline__ void bicycle_step(float4& s, float accel, float steer
 // (ca, sa), (cb, sb) = heading cos/sin; (la, wa), (lb, wb) = half extents.
 __device__ __forceinline__ float box_box_depth(float dx, float dy, float ca, float sa, float la, float wa, float cb,
                                                float sb, float lb, float wb) {
-  const float C = fabsf(ca * cb + sa * sb);   // |cos(theta_b - theta_a)|
-  const float S = fabsf(ca * sb - sa * cb);   // |sin(theta_b - theta_a)|
-  const float pa1 = la + lb * C + wb * S - fabsf(dx * ca + dy * sa);
-  const float pa2 = wa + lb * S + wb * C - fabsf(-dx * sa + dy * ca);
-  const float pb1 = lb + la * C + wa * S - fabsf(dx * cb + dy * sb);
-  const float pb2 = wb + la * S + wa * C - fabsf(-dx * sb + dy * cb);
+  const float C = fabsf(fmaf(ca, cb, __fmul_rn(sa, sb)));   // |cos(theta_b - theta_a)|
+  const float S = fabsf(fmaf(ca, sb, -__fmul_rn(sa, cb)));  // |sin(theta_b - theta_a)|
+  const float pa1 = __fadd_rn(la, fmaf(lb, C, __fmul_rn(wb, S))) - fabsf(rot_x(ca, sa, dx, dy));
+  const float pa2 = __fadd_rn(wa, fmaf(lb, S, __fmul_rn(wb, C))) - fabsf(rot_y(ca, sa, dx, dy));
+  const float pb1 = __fadd_rn(lb, fmaf(la, C, __fmul_rn(wa, S))) - fabsf(rot_x(cb, sb, dx, dy));
+  const float pb2 = __fadd_rn(wb, fmaf(la, S, __fmul_rn(wa, C))) - fabsf(rot_y(cb, sb, dx, dy));
   return fminf(fminf(pa1, pa2), fminf(pb1, pb2));
 }
 
@@ -102,19 +116,19 @@ __device__ __forceinline__ float box_box_depth(float dx, float dy, float ca, flo
 __device__ __forceinline__ float box_seg_depth(float cx, float cy, float ca, float sa, float l, float w, float4 seg) {
   const float qx0 = seg.x - cx, qy0 = seg.y - cy, qx1 = seg.z - cx, qy1 = seg.w - cy;
   // box axis 1
-  float u0 = qx0 * ca + qy0 * sa, u1 = qx1 * ca + qy1 * sa;
+  float u0 = rot_x(ca, sa, qx0, qy0), u1 = rot_x(ca, sa, qx1, qy1);
   float d = fminf(fmaxf(u0, u1) + l, l - fminf(u0, u1));
   // box axis 2
-  u0 = -qx0 * sa + qy0 * ca;
-  u1 = -qx1 * sa + qy1 * ca;
+  u0 = rot_y(ca, sa, qx0, qy0);
+  u1 = rot_y(ca, sa, qx1, qy1);
   d = fminf(d, fminf(fmaxf(u0, u1) + w, w - fminf(u0, u1)));
   // segment normal
   const float ex = seg.z - seg.x, ey = seg.w - seg.y;
-  const float el = sqrtf(ex * ex + ey * ey);
+  const float el = sqrtf(fmaf(ex, ex, __fmul_rn(ey, ey)));
   if (el > 0.f) {
     const float nx = -ey / el, ny = ex / el;
-    const float s = qx0 * nx + qy0 * ny;
-    const float r = l * fabsf(nx * ca + ny * sa) + w * fabsf(-nx * sa + ny * ca);
+    const float s = fmaf(qx0, nx, __fmul_rn(qy0, ny));
+    const float r = fmaf(l, fabsf(fmaf(nx, ca, __fmul_rn(ny, sa))), __fmul_rn(w, fabsf(fmaf(ny, ca, -__fmul_rn(nx, sa)))));
     d = fminf(d, r - fabsf(s));
   }
   return d;

@@ -6,18 +6,22 @@
 // One warp per agent.  Road candidates come from the rows of the world's
 // road grid that meet the observation disk; each row is clipped to the
 // disk's chord, so one row is one contiguous range of cell-sorted points and
-// the warp walks all rows as one flat list.  The points are read from a
-// pointer that is either the world's tile in shared memory (fused kernel)
-// or global memory (per-stage kernel).
+// the warp walks all rows as one flat list.  A world's road is one block of
+// the road arena: x, y as float2 for every point, then one 16-bit word per
+// point (local index | type << 15), both in cell order.  The block is read
+// from the world's shared-memory tile (fused kernel) or from global memory.
 //
 // Top-K selection ("bucket rank"): d^2 in [0, R^2] is split into NB equal
-// buckets (equal-area annuli).  Pass 1 counts candidates per bucket; an
+// buckets (equal-area annuli).  Pass 1 walks the rows, counts in-radius
+// points per bucket and keeps their positions in a compact list.  An
 // exclusive scan gives each bucket's first rank and the bucket b* holding
-// rank K.  Pass 2 scatters the keys of buckets <= b* to their bucket's slice
-// of shared memory; the rank of a key is its bucket's first rank plus the
-// number of smaller keys in its bucket.  If buckets <= b* do not fit, the
-// exact K-th key is found by bisection over the key space and only keys up
-// to it are kept.  Every rank is exact: the output equals a full sort.
+// rank K.  Pass 2 walks the compact list and scatters the keys of buckets
+// <= b* into their bucket's slice of shared memory; the rank of a key is its
+// bucket's first rank plus the number of smaller keys in its bucket.  If
+// buckets <= b* do not fit, the exact K-th key is found by bisection over
+// the key space and only keys up to it are kept; if the compact list
+// overflows, pass 2 walks the rows again.  Every rank is exact: the output
+// equals a full sort.
 //
 // Key = (d^2 bits << 32) | (local index << 16) | (position in the world's
 // cell-sorted points): d^2 >= 0 so its bits order like the value, the local
@@ -28,17 +32,19 @@
 
 namespace gd {
 
-constexpr int OBS_NB = 128;        // d^2 buckets
+constexpr int OBS_NB = 256;        // d^2 buckets
 constexpr int OBS_CAP = 384;       // keys kept per warp (>= GD_MAX_K_ROAD)
+constexpr int OBS_CAND = 1024;     // compact list of in-radius positions
 static_assert(OBS_CAP >= GD_MAX_K_ROAD, "selection capacity must hold K keys");
 
 struct ObsWarpSmem {
-  unsigned off[OBS_NB + 1];        // first rank of each bucket
   unsigned cur[OBS_NB];            // histogram, then scatter cursor
+  unsigned short off[OBS_NB + 2];  // first rank of each bucket
   union {
     unsigned long long keys[OBS_CAP];                     // road keys, bucket order
     unsigned long long pkeys[GD_MAX_AGENTS_PER_WORLD];    // partner keys
   } u;
+  unsigned short cand[OBS_CAND];   // positions of the in-radius points (pass 1)
   unsigned short sel[GD_MAX_K_ROAD];                      // road: position of rank r
   unsigned char psel[GD_MAX_PARTNERS + 1];                // partner: local index of rank r
   unsigned row_start[MAX_ROWS];
@@ -50,10 +56,12 @@ struct ObsWarpSmem {
 struct WorldView {
   const float4* state;     // [n] agents of the world
   const float4* stat;      // [n]
+  const float2* cs;        // [n] (cos theta, sin theta) of the agents, or nullptr: computed here
   const uint8_t* flags;    // [n]
   int n;                   // agents in the world
-  const float4* pts;       // [nr] cell-sorted road points (x, y, idx bits, type bits)
-  const int* cell_start;   // world's cell-start table (global), ny*nx + 1 entries, relative to pts
+  const float2* xy;        // [nr] cell-sorted road points
+  const uint16_t* meta;    // [nr] local index | type << 15
+  const int* cell_start;   // world's cell-start table (global), ny*nx + 1 entries
   GridDesc g;
 };
 
@@ -91,9 +99,9 @@ __device__ __forceinline__ int road_rows(const WorldView& v, float R, float R2, 
       const int cx0 = (int)clampf(floorf((ex - hw - g.ox) * g.inv_cs), 0.f, (float)g.nx);
       const int cx1 = (int)clampf(floorf((ex + hw - g.ox) * g.inv_cs), -1.f, (float)(g.nx - 1));
       if (cx0 <= cx1) {
-        const int* cs = v.cell_start + row * g.nx;
-        start = (unsigned)__ldg(cs + cx0);
-        len = __ldg(cs + cx1 + 1) - (int)start;
+        const int* cst = v.cell_start + row * g.nx;
+        start = (unsigned)__ldg(cst + cx0);
+        len = __ldg(cst + cx1 + 1) - (int)start;
       }
     }
   }
@@ -104,19 +112,25 @@ __device__ __forceinline__ int road_rows(const WorldView& v, float R, float R2, 
   return __shfl_sync(0xffffffffu, incl, 31);
 }
 
-// Walk the flat candidate list; fn(pos) is called for each candidate point.
+// Warp-uniform walk of the flat candidate list: fn(pos, valid) is called
+// by every lane in every round (valid = this lane has a candidate), so fn
+// may use warp collectives.
 template <typename Fn>
-__device__ __forceinline__ void for_each_candidate(const ObsWarpSmem& sm, int nrows, int total, int lane, Fn&& fn) {
+__device__ __forceinline__ void walk_rows(const ObsWarpSmem& sm, int nrows, int total, int lane, Fn&& fn) {
   int r = 0;
   unsigned rs = sm.row_start[0], re = nrows > 1 ? sm.row_excl[1] : 0xffffffffu, rx = 0;
-  for (int f = lane; f < total; f += WARP) {
-    while ((unsigned)f >= re) {
-      ++r;
-      rs = sm.row_start[r];
-      rx = sm.row_excl[r];
-      re = (r + 1 < nrows) ? sm.row_excl[r + 1] : 0xffffffffu;
+  for (int f0 = 0; f0 < total; f0 += WARP) {
+    const int f = f0 + lane;
+    const bool valid = f < total;
+    if (valid) {
+      while ((unsigned)f >= re) {
+        ++r;
+        rs = sm.row_start[r];
+        rx = sm.row_excl[r];
+        re = (r + 1 < nrows) ? sm.row_excl[r + 1] : 0xffffffffu;
+      }
     }
-    fn(rs + ((unsigned)f - rx));
+    fn(valid ? rs + ((unsigned)f - rx) : 0u, valid);
   }
 }
 
@@ -127,17 +141,28 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
                                              int32_t* __restrict__ ridx) {
   if (K == 0) return;
   const float binv = (float)OBS_NB / R2;
-  const float4* __restrict__ pts = v.pts;
+  const float2* __restrict__ xy = v.xy;
+  const uint16_t* __restrict__ meta = v.meta;
   int nrows;
   const int total = road_rows(v, R, R2, ex, ey, sm, lane, nrows);
 
-  // pass 1: histogram of d^2 buckets
+  // pass 1: histogram of d^2 buckets + compact list of in-radius positions
   for (int b = lane; b < OBS_NB; b += WARP) sm.cur[b] = 0;
   __syncwarp();
-  for_each_candidate(sm, nrows, total, lane, [&](unsigned p) {
-    const float4 q = pts[p];
-    const float d2 = dist2(q.x - ex, q.y - ey);
-    if (d2 <= R2) atomicAdd(&sm.cur[bucket_of(d2, binv)], 1u);
+  int n_in = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  walk_rows(sm, nrows, total, lane, [&](unsigned p, bool valid) {
+    bool in = false;
+    if (valid) {
+      const float2 q = xy[p];
+      const float d2 = dist2(q.x - ex, q.y - ey);
+      in = d2 <= R2;
+      if (in) atomicAdd(&sm.cur[bucket_of(d2, binv)], 1u);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    const int slot = n_in + __popc(m & lt);
+    if (in && slot < OBS_CAND) sm.cand[slot] = (unsigned short)p;
+    n_in += __popc(m);
   });
   __syncwarp();
   // exclusive scan: lane owns OBS_NB/32 consecutive buckets
@@ -150,33 +175,46 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
     mine += (int)cnt[k];
   }
   const int incl = warp_incl_scan(mine, lane);
-  const int n_in = __shfl_sync(0xffffffffu, incl, 31);
   const int n_sel = min(K, n_in);
+  int bstar = OBS_NB - 1;    // bucket holding rank n_sel - 1
   {
     unsigned run = (unsigned)(incl - mine);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      sm.off[lane * PER + k] = run;
-      sm.cur[lane * PER + k] = run;     // scatter cursor
-      run += cnt[k];
-    }
-    if (lane == WARP - 1) sm.off[OBS_NB] = run;
-  }
-  // bucket holding rank n_sel - 1 (the last selected key)
-  int bstar = OBS_NB - 1;
-  if (n_in > K) {
     int cand = OBS_NB;
-    unsigned run = (unsigned)(incl - mine);
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
+      sm.off[lane * PER + k] = (unsigned short)run;
+      sm.cur[lane * PER + k] = run;     // scatter cursor
       if ((int)run < K && (int)(run + cnt[k]) >= K) cand = min(cand, lane * PER + k);
       run += cnt[k];
     }
+    if (lane == WARP - 1) sm.off[OBS_NB] = (unsigned short)run;
+    if (n_in > K) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
-    bstar = cand;
+      for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
+      bstar = cand;
+    }
   }
   __syncwarp();
+  const bool compact = n_in <= OBS_CAND;
+  // Calls fn(p, d2) for every in-radius point, from the compact list when
+  // it holds them all, else by walking the rows again.
+  auto for_each_in_radius = [&](auto&& fn) {
+    if (compact) {
+      for (int k = lane; k < n_in; k += WARP) {
+        const unsigned p = sm.cand[k];
+        const float2 q = xy[p];
+        fn(p, dist2(q.x - ex, q.y - ey));
+      }
+    } else {
+      walk_rows(sm, nrows, total, lane, [&](unsigned p, bool valid) {
+        if (valid) {
+          const float2 q = xy[p];
+          const float d2 = dist2(q.x - ex, q.y - ey);
+          if (d2 <= R2) fn(p, d2);
+        }
+      });
+    }
+  };
   const int keep = (int)sm.off[bstar + 1];   // keys in buckets <= b*
   unsigned long long tau = ~0ull;             // keep keys <= tau in bucket b*
   if (keep > OBS_CAP) {
@@ -186,31 +224,25 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
     while (lo < hi) {
       const unsigned long long mid = lo + ((hi - lo) >> 1);
       unsigned cntle = 0;
-      for_each_candidate(sm, nrows, total, lane, [&](unsigned p) {
-        const float4 q = pts[p];
-        const float d2 = dist2(q.x - ex, q.y - ey);
-        if (d2 <= R2 && bucket_of(d2, binv) == bstar && road_key(d2, __float_as_uint(q.z), p) <= mid) ++cntle;
+      for_each_in_radius([&](unsigned p, float d2) {
+        if (bucket_of(d2, binv) == bstar && road_key(d2, meta[p] & 0x7fffu, p) <= mid) ++cntle;
       });
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cntle += __shfl_xor_sync(0xffffffffu, cntle, o);
       if (cntle >= need) hi = mid; else lo = mid + 1;
     }
     tau = lo;
-    if (lane == 0) sm.off[bstar + 1] = (unsigned)n_sel;
+    if (lane == 0) sm.off[bstar + 1] = (unsigned short)n_sel;
     __syncwarp();
   }
   // pass 2: scatter keys of buckets <= b* into their bucket slices
-  for_each_candidate(sm, nrows, total, lane, [&](unsigned p) {
-    const float4 q = pts[p];
-    const float d2 = dist2(q.x - ex, q.y - ey);
-    if (d2 <= R2) {
-      const int b = bucket_of(d2, binv);
-      if (b <= bstar) {
-        const unsigned long long key = road_key(d2, __float_as_uint(q.z), p);
-        if (b < bstar || key <= tau) {
-          const unsigned slot = atomicAdd(&sm.cur[b], 1u);
-          if (slot < (unsigned)OBS_CAP) sm.u.keys[slot] = key;
-        }
+  for_each_in_radius([&](unsigned p, float d2) {
+    const int b = bucket_of(d2, binv);
+    if (b <= bstar) {
+      const unsigned long long key = road_key(d2, meta[p] & 0x7fffu, p);
+      if (b < bstar || key <= tau) {
+        const unsigned slot = atomicAdd(&sm.cur[b], 1u);
+        if (slot < (unsigned)OBS_CAP) sm.u.keys[slot] = key;
       }
     }
   });
@@ -231,10 +263,12 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
     int idx = -1;
     if (r < n_sel) {
-      const float4 q = pts[sm.sel[r]];
+      const unsigned p = sm.sel[r];
+      const float2 q = xy[p];
+      const unsigned mt = meta[p];
       const float dx = q.x - ex, dy = q.y - ey;
-      o = make_float4(c * dx + s * dy, -s * dx + c * dy, (float)__float_as_int(q.w), 1.f);
-      idx = __float_as_int(q.z);
+      o = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), (float)(mt >> 15), 1.f);
+      idx = (int)(mt & 0x7fffu);
     }
     __stcs(out4 + r, o);
     if (ridx) ridx[r] = idx;
@@ -242,11 +276,14 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
 }
 
 // Partner part: other agents of the world still in the scene within R.
+// The relative heading uses cos/sin of the difference from the two agents'
+// own cos/sin: cos(tj - ti) = cj ci + sj si, sin(tj - ti) = sj ci - cj si.
 __device__ __forceinline__ void observe_partners(const WorldView& v, int li, int P, float R2, float ex, float ey,
-                                                 float th, float c, float s, ObsWarpSmem& sm, int lane,
+                                                 float c, float s, ObsWarpSmem& sm, int lane,
                                                  float4* __restrict__ out4, int32_t* __restrict__ pidx) {
   if (P == 0) return;
   int n = 0;
+  const unsigned lt = (1u << lane) - 1u;
   for (int j0 = 0; j0 < v.n; j0 += WARP) {
     const int j = j0 + lane;
     bool ok = false;
@@ -258,7 +295,7 @@ __device__ __forceinline__ void observe_partners(const WorldView& v, int li, int
       key = partner_key(d2, (unsigned)j);
     }
     const unsigned m = __ballot_sync(0xffffffffu, ok);
-    if (ok) sm.u.pkeys[n + __popc(m & ((1u << lane) - 1u))] = key;
+    if (ok) sm.u.pkeys[n + __popc(m & lt)] = key;
     n += __popc(m);
   }
   __syncwarp();
@@ -277,10 +314,10 @@ __device__ __forceinline__ void observe_partners(const WorldView& v, int li, int
       idx = (int)sm.psel[r];
       const float4 q = v.state[idx];
       const float4 st = v.stat[idx];
+      float2 cj;
+      if (v.cs) cj = v.cs[idx]; else sincosf(q.z, &cj.y, &cj.x);
       const float dx = q.x - ex, dy = q.y - ey;
-      float sd, cd;
-      sincosf(q.z - th, &sd, &cd);
-      o0 = make_float4(c * dx + s * dy, -s * dx + c * dy, cd, sd);
+      o0 = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), rot_x(c, s, cj.x, cj.y), rot_y(c, s, cj.x, cj.y));
       o1 = make_float4(q.w, st.x, st.y, 1.f);
     }
     __stcs(out4 + 2 * r, o0);
@@ -312,15 +349,27 @@ __device__ __forceinline__ void observe_agent(const DevEnv& e, const WorldView& 
   }
   const float4 st = v.state[li];
   const float4 sc = v.stat[li];
-  float s, c;
-  sincosf(st.z, &s, &c);
+  float c, s;
+  if (v.cs) {
+    c = v.cs[li].x;
+    s = v.cs[li].y;
+  } else {
+    sincosf(st.z, &s, &c);
+  }
   if (lane == 0) {
     const float gx = sc.z - st.x, gy = sc.w - st.y;
-    __stcs(row + 0, make_float4(st.w, sc.x, sc.y, c * gx + s * gy));
-    __stcs(row + 1, make_float4(-s * gx + c * gy, fc, fo, fg));
+    __stcs(row + 0, make_float4(st.w, sc.x, sc.y, rot_x(c, s, gx, gy)));
+    __stcs(row + 1, make_float4(rot_y(c, s, gx, gy), fc, fo, fg));
   }
-  observe_partners(v, li, e.P, e.R2, st.x, st.y, st.z, c, s, sm, lane, row + 2, pidx);
+  observe_partners(v, li, e.P, e.R2, st.x, st.y, c, s, sm, lane, row + 2, pidx);
   observe_road(v, e.K, e.R, e.R2, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx);
+}
+
+// Road block of world w in the arena: (xy, meta) pointers for `base`
+// (global arena or a shared-memory copy of the block).
+__device__ __forceinline__ void road_block(const unsigned char* base, int nr, const float2*& xy, const uint16_t*& meta) {
+  xy = reinterpret_cast<const float2*>(base);
+  meta = reinterpret_cast<const uint16_t*>(base + (size_t)road_pad(nr) * sizeof(float2));
 }
 
 // Per-stage form: one warp per agent over the whole batch, everything read
@@ -336,13 +385,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   if (i >= e.A) return;
   ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[wib];
   const int w = e.agent_world[i];
-  const int a0 = e.agent_off[w], r0 = e.road_off[w];
+  const int a0 = e.agent_off[w];
   WorldView v;
   v.state = e.state + a0;
   v.stat = e.stat + a0;
+  v.cs = nullptr;
   v.flags = e.flags + a0;
   v.n = e.agent_off[w + 1] - a0;
-  v.pts = e.rpts + r0;
+  road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v.xy, v.meta);
   v.g = e.rgrid[w];
   v.cell_start = e.rcell_start + v.g.cell_base;
   observe_agent(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,

@@ -201,7 +201,7 @@ __global__ void k_finish(DevEnv e, float* __restrict__ reward, uint8_t* __restri
       const float4 s = e.state[i];
       const float4 st = e.stat[i];
       const float dx = s.x - st.z, dy = s.y - st.w;
-      const bool at_goal = sqrtf(dx * dx + dy * dy) <= e.goal_r;
+      const bool at_goal = sqrtf(fmaf(dx, dx, __fmul_rn(dy, dy))) <= e.goal_r;
       const bool coll = e.coll[i] != 0, offr = e.off[i] != 0;
       const bool first = at_goal && !(f & GD_FLAG_GOAL);
       f &= (uint8_t)~(GD_FLAG_COLLIDED | GD_FLAG_OFFROAD);

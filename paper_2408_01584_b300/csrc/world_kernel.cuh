@@ -27,13 +27,14 @@ struct FusedArgs {
   int32_t* partner_idx;      // [A,P] or nullptr
   unsigned* counter;         // work counter, zero at launch
   const int* order;          // [W] world order (largest first)
-  int tile_cap;              // road points that fit the tile
+  int tile_bytes;            // bytes of the shared-memory road tile
   int do_step;
 };
 
 struct FusedAgents {
   float4 st[GD_MAX_AGENTS_PER_WORLD];
   float4 sc[GD_MAX_AGENTS_PER_WORLD];
+  float2 cs[GD_MAX_AGENTS_PER_WORLD];        // (cos theta, sin theta) after the step
   uint32_t key[GD_MAX_AGENTS_PER_WORLD];     // sorted grid keys of the active agents
   uint8_t fl[GD_MAX_AGENTS_PER_WORLD];
   uint8_t ty[GD_MAX_AGENTS_PER_WORLD];
@@ -86,17 +87,18 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Dynamic shared memory: [mbarrier, 128 B][tile float4 x tile_cap][FusedAgents][ObsWarpSmem x WARPS]
+// Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents][ObsWarpSmem x WARPS]
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(wsm);
-  float4* tile = reinterpret_cast<float4*>(wsm + 128);
-  FusedAgents& ag = *reinterpret_cast<FusedAgents*>(wsm + 128 + (size_t)a.tile_cap * sizeof(float4));
+  unsigned char* tile = wsm + 128;
+  FusedAgents& ag = *reinterpret_cast<FusedAgents*>(wsm + 128 + (size_t)a.tile_bytes);
   ObsWarpSmem* wsmem = reinterpret_cast<ObsWarpSmem*>(reinterpret_cast<unsigned char*>(&ag) + sizeof(FusedAgents));
   __shared__ int s_w;
   __shared__ int s_nact;
   __shared__ int s_abort;
+  __shared__ int s_next;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   ObsWarpSmem& osm = wsmem[wid];
   if (tid == 0) {
@@ -113,13 +115,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
     if (k >= e.W) break;
     const int w = a.order[k];
     const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0;
-    const int r0 = e.road_off[w], nr = e.road_off[w + 1] - r0;
-    const bool use_tile = observe && nr > 0 && nr <= a.tile_cap;
+    const int nr = e.road_off[w + 1] - e.road_off[w];
+    const unsigned block = (unsigned)road_block_bytes(nr);
+    const unsigned char* gblock = e.arena + (size_t)e.arena_off[w] * 16;
+    const bool use_tile = observe && nr > 0 && block <= (unsigned)a.tile_bytes;
     if (use_tile && tid == 0) {
       fence_proxy_async_smem();     // earlier generic reads of the tile before the async write
-      mbar_arrive_expect_tx(bar, (unsigned)nr * 16u);
-      tma_load_1d(tile, e.rpts + r0, (unsigned)nr * 16u, bar);
+      mbar_arrive_expect_tx(bar, block);
+      tma_load_1d(tile, gblock, block, bar);
     }
+    if (tid == 0) s_next = WARPS;
     const GridDesc g = e.rgrid[w];
     if (a.do_step) {
       const bool reset = (e.cflags & GD_AUTO_RESET) && e.world_done[w];
@@ -142,6 +147,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
                                (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f), tid);
         }
         ag.st[tid] = s;
+        float sn, cn;
+        sincosf(s.z, &sn, &cn);
+        ag.cs[tid] = make_float2(cn, sn);
         ag.sc[tid] = e.stat[i];
         ag.fl[tid] = f;
         ag.ty[tid] = e.type[i];
@@ -161,33 +169,35 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
         if (ag.fl[li] & GD_FLAG_DONE) continue;
         const float4 s = ag.st[li];
         const float4 sc = ag.sc[li];
-        float sa, ca;
-        sincosf(s.z, &sa, &ca);
+        const float ca = ag.cs[li].x, sa = ag.cs[li].y;
         const int cx = (int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f);
         const int cy = (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f);
-        bool hit = false;
-        for (int dcx = -1; dcx <= 1; ++dcx) {
-          const int c = cx + dcx;
-          if (c < 0 || c > 4095) continue;
-          const uint32_t lo = agent_cell_key(c, max(cy - 1, 0), 0), hi = agent_cell_key(c, min(cy + 1, 4095), 255);
-          int b = 0, en = s_nact;
-          {  // lower bound of lo
+        // lanes 0..5 bound the three neighbouring columns in parallel:
+        // lane 2k / 2k+1 = lower / upper bound of column cx - 1 + k
+        int bound = 0;
+        if (lane < 6) {
+          const int c = cx - 1 + (lane >> 1);
+          if (c >= 0 && c <= 4095) {
+            const bool upper = lane & 1;
+            const uint32_t v = upper ? agent_cell_key(c, min(cy + 1, 4095), 255) : agent_cell_key(c, max(cy - 1, 0), 0);
             int l = 0, h = s_nact;
-            while (l < h) { const int m = (l + h) >> 1; if (ag.key[m] < lo) l = m + 1; else h = m; }
-            b = l;
+            while (l < h) {
+              const int m = (l + h) >> 1;
+              if (upper ? (ag.key[m] <= v) : (ag.key[m] < v)) l = m + 1; else h = m;
+            }
+            bound = l;
           }
-          {  // upper bound of hi
-            int l = b, h = s_nact;
-            while (l < h) { const int m = (l + h) >> 1; if (ag.key[m] <= hi) l = m + 1; else h = m; }
-            en = l;
-          }
+        }
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int b = __shfl_sync(0xffffffffu, bound, 2 * k), en = __shfl_sync(0xffffffffu, bound, 2 * k + 1);
           for (int q = b + lane; q < en; q += WARP) {
             const int j = (int)(ag.key[q] & 0xffu);
             if (j == li) continue;
             const float4 sj = ag.st[j];
             const float4 tj = ag.sc[j];
-            float sb, cb;
-            sincosf(sj.z, &sb, &cb);
+            const float cb = ag.cs[j].x, sb = ag.cs[j].y;
             hit |= box_box_depth(sj.x - s.x, sj.y - s.y, ca, sa, 0.5f * sc.x, 0.5f * sc.y, cb, sb, 0.5f * tj.x,
                                  0.5f * tj.y) > 0.f;
           }
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
           const float4 s = ag.st[tid];
           const float4 sc = ag.sc[tid];
           const float dx = s.x - sc.z, dy = s.y - sc.w;
-          const bool at_goal = sqrtf(dx * dx + dy * dy) <= e.goal_r;
+          const bool at_goal = sqrtf(fmaf(dx, dx, __fmul_rn(dy, dy))) <= e.goal_r;
           const bool coll = ag.coll[tid] != 0, offr = ag.offr[tid] != 0;
           const bool first = at_goal && !(f & GD_FLAG_GOAL);
           f &= (uint8_t)~(GD_FLAG_COLLIDED | GD_FLAG_OFFROAD);
@@ -252,7 +262,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
         if (a.world_done) a.world_done[w] = wd;
       }
     } else if (observe && tid < n) {
-      ag.st[tid] = e.state[a0 + tid];
+      const float4 s = e.state[a0 + tid];
+      ag.st[tid] = s;
+      float sn, cn;
+      sincosf(s.z, &sn, &cn);
+      ag.cs[tid] = make_float2(cn, sn);
       ag.sc[tid] = e.stat[a0 + tid];
       ag.fl[tid] = e.flags[a0 + tid];
     }
@@ -275,15 +289,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
       WorldView v;
       v.state = ag.st;
       v.stat = ag.sc;
+      v.cs = ag.cs;
       v.flags = ag.fl;
       v.n = n;
-      v.pts = use_tile ? tile : e.rpts + r0;
+      road_block(use_tile ? tile : gblock, nr, v.xy, v.meta);
       v.g = g;
       v.cell_start = e.rcell_start + g.cell_base;
-      for (int li = wid; li < n; li += WARPS) {
+      // warps take the world's agents one at a time (first WARPS statically)
+      for (int li = wid; li < n;) {
         const int i = a0 + li;
         observe_agent(e, v, li, a.obs + (size_t)i * e.F, a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr,
                       a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr, osm, lane);
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&s_next, 1);
+        li = __shfl_sync(0xffffffffu, nx, 0);
       }
     }
     __syncthreads();
