@@ -177,22 +177,39 @@ gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint
 gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step,
                      float* reward, uint8_t* done);
 
-/* Gradient of  L = sum_t sum_i [ reward_weight * r_s(i,t) + sum_f obs_weight[f] * obs(t)[i,f] ]
- * over the last gd_rollout of an env created with GD_DIFFERENTIABLE, where
- * r_s = -(sqrt(d_goal^2 + c^2) - c) for agents not done at the start of
- * step t.  Collision, goal, selection and clip decisions are held constant.
- * obs_weight: device float [F]; d_actions: device float [T,A,2];
- * d_state0: device float [A,4] (gradient w.r.t. the state before the
- * rollout) or NULL.  Recomputes the states between checkpoints. */
-gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, float* d_actions,
-                              float* d_state0);
+/* Differentiable rollout (an extension; the paper has no gradient).  Runs
+ * `steps` fused steps from the current state, like gd_rollout, and writes
+ * the per-step objective terms
+ *   ell[t,i] = sum_f obs_weight[f] * obs(t)[i,f] + reward_weight * r_s(t,i)
+ * where obs(t) is the observation after step t and r_s = -(sqrt(d_goal^2 +
+ * c^2) - c), c = smooth_c, for agents in the scene at the start of step t
+ * (0 otherwise).  The state is checkpointed every ckpt_every steps for
+ * gd_rollout_backward; `actions` must stay unchanged until then.
+ * Requires GD_DIFFERENTIABLE; steps <= episode_len.
+ *   actions: device float [T,A,2]; obs_weight: device float [F], 16-byte
+ *   aligned; ell: device float [T,A]; obs: device float [A,F] overwritten
+ *   every step, or NULL (an internal buffer is used). */
+gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
+                               float reward_weight, float* ell, float* obs);
+
+/* Gradient of  L = sum_{t,i} d_ell[t,i] * ell[t,i]  (d_ell = NULL: all ones)
+ * for the last gd_rollout_objective, w.r.t. its actions and its initial
+ * state.  Collision, goal, done, selection and clip decisions are held
+ * constant.  Recomputes the states between checkpoints; the env's current
+ * state is not changed.  obs_weight / reward_weight must be the values used
+ * in the forward call.
+ *   d_ell: device float [T,A] or NULL; d_actions: device float [T,A,2];
+ *   d_state0: device float [A,4] or NULL. */
+gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                              float* d_actions, float* d_state0);
 
 /* Adjoint of one step about the CURRENT state and the given actions
- * (the step is not applied): given d_state_next [A,4] = dL/d(state after
- * the step) and optional per-row obs gradient d_obs [A,F] and d_reward_s
- * [A], returns d_state [A,4] and d_actions [A,2].  d_obs, obs_weight and
- * d_reward_s may be NULL; obs_weight [F] broadcasts one weight row to all
- * agents (ignored if d_obs is given). */
+ * (the step is not applied; requires GD_DIFFERENTIABLE): given
+ * d_state_next [A,4] = dL/d(state after the step) (NULL = zero), the
+ * gradient of L w.r.t. the observation after the step, d_obs [A,F] (or one
+ * row obs_weight [F] for every agent; both NULL = no observation term), and
+ * d_reward_s [A] = dL/d r_s (NULL = none), returns d_state [A,4] =
+ * dL/d(state before the step) and d_actions [A,2].  All device pointers. */
 gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,
                            const float* obs_weight, const float* d_reward_s, float* d_state, float* d_actions);
 

@@ -265,25 +265,26 @@ void ego_frame(const Env<T>& e, int i, T px, T py, T& xr, T& yr) {
   yr = -s * dx + c * dy;
 }
 
-template <typename T>
-void road_feature(const Env<T>& e, int i, int jg, float* f) {
+template <typename T, typename O>
+void road_feature(const Env<T>& e, int i, int jg, O* f) {
   T xr, yr;
   ego_frame(e, i, e.rx[jg], e.ry[jg], xr, yr);
-  f[0] = (float)xr; f[1] = (float)yr; f[2] = (float)e.rtype[jg]; f[3] = 1.f;
+  f[0] = (O)xr; f[1] = (O)yr; f[2] = (O)e.rtype[jg]; f[3] = 1;
 }
 
-template <typename T>
-void partner_feature(const Env<T>& e, int i, int j, float* f) {
+template <typename T, typename O>
+void partner_feature(const Env<T>& e, int i, int j, O* f) {
   T xr, yr;
   ego_frame(e, i, e.x[j], e.y[j], xr, yr);
   const T dth = e.th[j] - e.th[i];
-  f[0] = (float)xr; f[1] = (float)yr; f[2] = (float)std::cos(dth); f[3] = (float)std::sin(dth);
-  f[4] = (float)e.v[j]; f[5] = (float)e.len[j]; f[6] = (float)e.wid[j]; f[7] = 1.f;
+  f[0] = (O)xr; f[1] = (O)yr; f[2] = (O)std::cos(dth); f[3] = (O)std::sin(dth);
+  f[4] = (O)e.v[j]; f[5] = (O)e.len[j]; f[6] = (O)e.wid[j]; f[7] = 1;
 }
 
-// Observation row of every agent: ego[8], partners[P][8], road[K][4].
-template <typename T>
-void observe(const Env<T>& e, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+// Observation row of every agent: ego[8], partners[P][8], road[K][4],
+// written as O (float for the library's layout, double for derivatives).
+template <typename T, typename O>
+void observe(const Env<T>& e, O* obs, int32_t* road_idx, int32_t* partner_idx) {
   const int K = e.cfg.k_road, P = e.cfg.n_partners;
   const long F = 8 + 8L * P + 4L * K;
   const T R2 = (T)e.cfg.obs_radius * (T)e.cfg.obs_radius;
@@ -293,18 +294,18 @@ void observe(const Env<T>& e, float* obs, int32_t* road_idx, int32_t* partner_id
     const int r0 = e.road_off[w], r1 = e.road_off[w + 1];
     std::vector<std::pair<T, int>> cand;
     for (int i = a0; i < a1; ++i) {
-      float* row = obs + (long)i * F;
-      std::fill(row, row + F, 0.f);
+      O* row = obs + (long)i * F;
+      std::fill(row, row + F, (O)0);
       if (road_idx) std::fill(road_idx + (long)i * K, road_idx + (long)(i + 1) * K, -1);
       if (partner_idx) std::fill(partner_idx + (long)i * P, partner_idx + (long)(i + 1) * P, -1);
-      row[5] = (e.flags[i] & F_COLLIDED) ? 1.f : 0.f;
-      row[6] = (e.flags[i] & F_OFFROAD) ? 1.f : 0.f;
-      row[7] = (e.flags[i] & F_GOAL) ? 1.f : 0.f;
+      row[5] = (e.flags[i] & F_COLLIDED) ? 1 : 0;
+      row[6] = (e.flags[i] & F_OFFROAD) ? 1 : 0;
+      row[7] = (e.flags[i] & F_GOAL) ? 1 : 0;
       if (e.flags[i] & F_DONE) continue;                  // removed from the scene
       T gxr, gyr;
       ego_frame(e, i, e.gx[i], e.gy[i], gxr, gyr);
-      row[0] = (float)e.v[i]; row[1] = (float)e.len[i]; row[2] = (float)e.wid[i];
-      row[3] = (float)gxr; row[4] = (float)gyr;
+      row[0] = (O)e.v[i]; row[1] = (O)e.len[i]; row[2] = (O)e.wid[i];
+      row[3] = (O)gxr; row[4] = (O)gyr;
       // partners: every other agent still in the scene within the radius
       cand.clear();
       for (int j = a0; j < a1; ++j) {
@@ -437,6 +438,12 @@ void or_step_post(void* hv, const float* post_state, float* reward, uint8_t* don
 // Observation rows float [A, 8 + 8P + 4K]; index outputs int32 [A,K] / [A,P]
 // (world-local indices, -1 padding) may be NULL.
 void or_observe(void* hv, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, observe(e, obs, road_idx, partner_idx));
+}
+
+// The same rows in double precision (for derivative checks).
+void or_observe64(void* hv, double* obs, int32_t* road_idx, int32_t* partner_idx) {
   auto* h = static_cast<Handle*>(hv);
   OR_DISPATCH(h, observe(e, obs, road_idx, partner_idx));
 }

@@ -53,6 +53,7 @@ def load_oracle():
         lib.or_step.argtypes = [vp] * 9
         lib.or_step_post.argtypes = [vp] * 9
         lib.or_observe.argtypes = [vp] * 4
+        lib.or_observe64.argtypes = [vp] * 4
         lib.or_road_point.argtypes = [vp, i32, i32, vp, vp]
         lib.or_partner.argtypes = [vp, i32, i32, vp, vp]
         lib.or_get_state.argtypes = [vp] * 5
@@ -154,6 +155,15 @@ class Oracle:
         ridx = np.zeros((self.A, cfg.k_road), np.int32)
         pidx = np.zeros((self.A, cfg.n_partners), np.int32)
         self.lib.or_observe(self.h, _p(obs), _p(ridx), _p(pidx))
+        return obs, ridx, pidx
+
+    def observe64(self):
+        """Observation rows in float64 (same layout) with the index lists."""
+        cfg = self.cfg
+        obs = np.zeros((self.A, cfg.feat), np.float64)
+        ridx = np.zeros((self.A, cfg.k_road), np.int32)
+        pidx = np.zeros((self.A, cfg.n_partners), np.int32)
+        self.lib.or_observe64(self.h, _p(obs), _p(ridx), _p(pidx))
         return obs, ridx, pidx
 
     def road_point(self, i: int, j: int):

@@ -12,6 +12,7 @@
 #include "observe_kernel.cuh"
 #include "step_kernels.cuh"
 #include "world_kernel.cuh"
+#include "adjoint_kernel.cuh"
 
 using namespace gd;
 
@@ -22,8 +23,9 @@ thread_local std::string g_create_error;
 constexpr int kObsWarpsDefault = 8;
 constexpr int kWorldWarps = 8;
 
-// Fixed shared memory of the fused kernel besides the road tile.
+// Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t kWorldFixedSmem = 128 + sizeof(FusedAgents) + kWorldWarps * sizeof(ObsWarpSmem);
+constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kWorldWarps * sizeof(ObsWarpSmem);
 
 }  // namespace
 
@@ -50,6 +52,23 @@ struct gd_env {
   cudaGraphExec_t graph = nullptr;
   const void* g_key[6] = {};
   int g_steps = -1;
+  // differentiable rollouts: checkpoints every C steps, one recompute segment
+  int C = 0, n_ckpt = 0;
+  float4* ckS = nullptr;        // [n_ckpt][A]
+  uint8_t* ckF = nullptr;       // [n_ckpt][A]
+  int* ckT = nullptr;           // [n_ckpt][W]
+  uint8_t* ckWD = nullptr;      // [n_ckpt][W]
+  float4* segS = nullptr;       // [C+1][A] states of the segment being differentiated
+  uint8_t* segF = nullptr;      // [C+1][A]
+  int* segT = nullptr;          // [W]
+  uint8_t* segWD = nullptr;     // [W]
+  float4* lam = nullptr;        // [A] adjoint of the state
+  float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
+  int adj_tile = 0;
+  size_t adj_smem = 0;
+  int adj_grid = 0;
+  const float* diff_actions = nullptr;   // actions of the last objective rollout
+  int diff_steps = 0;
 };
 
 namespace {
@@ -374,6 +393,34 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<kWorldWarps>, kWorldWarps * 32, env->world_smem));
     env->world_grid = std::max(1, std::min(W, std::max(per_sm, 1) * nsm));
   }
+  if (cfg->flags & GD_DIFFERENTIABLE) {
+    env->C = cfg->ckpt_every;
+    env->n_ckpt = (cfg->episode_len + env->C - 1) / env->C;
+    GD_TRY(dev_alloc(env, &env->ckS, (size_t)env->n_ckpt * A));
+    GD_TRY(dev_alloc(env, &env->ckF, (size_t)env->n_ckpt * A));
+    GD_TRY(dev_alloc(env, &env->ckT, (size_t)env->n_ckpt * W));
+    GD_TRY(dev_alloc(env, &env->ckWD, (size_t)env->n_ckpt * W));
+    GD_TRY(dev_alloc(env, &env->segS, (size_t)(env->C + 1) * A));
+    GD_TRY(dev_alloc(env, &env->segF, (size_t)(env->C + 1) * A));
+    GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
+    GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
+    GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
+    int dev = 0, smem_sm = 0, smem_blk = 0, nsm = 0;
+    GD_TRY(cudaGetDevice(&dev));
+    GD_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    size_t max_block = 16;
+    for (int w = 0; w < W; ++w) max_block = std::max(max_block, road_block_bytes(s->road_off[w + 1] - s->road_off[w]));
+    const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
+    const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
+    env->adj_tile = (int)(((long)max_block <= two) ? (long)max_block : one);
+    env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
+    GD_TRY(cudaFuncSetAttribute(k_adjoint<kWorldWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->adj_smem));
+    int per_sm = 0;
+    GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<kWorldWarps>, kWorldWarps * 32, env->adj_smem));
+    env->adj_grid = std::max(1, std::min(W, std::max(per_sm, 1) * nsm));
+  }
   GD_TRY(cudaStreamSynchronize(env->stream));
 #undef GD_TRY
   *out = env;
@@ -438,8 +485,10 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
 // Batched form: one persistent fused launch (work counter cleared first).
 static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
-                         cudaStream_t stream = nullptr) {
+                         cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
+                         float reward_w = 0.f, float* ell = nullptr) {
   if (!stream) stream = env->stream;
+  if (!dv) dv = &env->d;
   FusedArgs a;
   a.actions = reinterpret_cast<const float2*>(actions);
   a.reward = reward;
@@ -452,8 +501,11 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.order = env->order;
   a.tile_bytes = env->tile_cap;
   a.do_step = do_step;
+  a.obs_w = obs_w;
+  a.reward_w = reward_w;
+  a.ell = ell;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
-  k_world<kWorldWarps><<<env->world_grid, kWorldWarps * 32, env->world_smem, stream>>>(env->d, a);
+  k_world<kWorldWarps><<<env->world_grid, kWorldWarps * 32, env->world_smem, stream>>>(*dv, a);
 }
 
 static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) != 0; }
@@ -555,13 +607,143 @@ gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* ob
   return GD_OK;
 }
 
-gd_status gd_rollout_backward(gd_env* env, const float*, float, float*, float*) {
-  return fail(env, GD_ERR_STATE, "gd_rollout_backward: not available in this build");
+// ---- differentiable rollouts ------------------------------------------------
+
+static gd_status need_diff(gd_env* env, const char* what) {
+  if (!(env->cfg.flags & GD_DIFFERENTIABLE))
+    return fail(env, GD_ERR_STATE, std::string(what) + ": the env was not created with GD_DIFFERENTIABLE");
+  return GD_OK;
 }
 
-gd_status gd_step_backward(gd_env* env, const float*, const float*, const float*, const float*, const float*, float*,
-                           float*) {
-  return fail(env, GD_ERR_STATE, "gd_step_backward: not available in this build");
+// Copy (state, flags, t, episode-end status) between the env and a slot.
+static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t* dWD, const float4* sS,
+                          const uint8_t* sF, const int* sT, const uint8_t* sWD) {
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  cudaMemcpyAsync(dS, sS, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  cudaMemcpyAsync(dF, sF, A, cudaMemcpyDeviceToDevice, env->stream);
+  if (dT) cudaMemcpyAsync(dT, sT, sizeof(int) * W, cudaMemcpyDeviceToDevice, env->stream);
+  if (dWD) cudaMemcpyAsync(dWD, sWD, W, cudaMemcpyDeviceToDevice, env->stream);
+}
+
+gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
+                               float reward_weight, float* ell, float* obs) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_diff(env, "gd_rollout_objective");
+  if (st != GD_OK) return st;
+  if (steps < 1 || steps > env->n_ckpt * env->C)
+    return fail(env, GD_ERR_INVALID_ARG, "steps must be in 1..episode_len");
+  if (!actions || !obs_weight || !ell) return fail(env, GD_ERR_INVALID_ARG, "actions, obs_weight and ell must not be NULL");
+  if (!aligned16(obs_weight) || (obs && !aligned16(obs)))
+    return fail(env, GD_ERR_INVALID_ARG, "obs_weight and obs must be 16-byte aligned");
+  if (!obs) {
+    if (!env->obs_scratch) {
+      cudaError_t e = dev_alloc(env, &env->obs_scratch, (size_t)env->A * env->F);
+      if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_objective: observation scratch");
+    }
+    obs = env->obs_scratch;
+  }
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  const DevEnv& d = env->d;
+  for (int t = 0; t < steps; ++t) {
+    if (t % env->C == 0) {
+      const int c = t / env->C;
+      copy_snapshot(env, env->ckS + c * A, env->ckF + c * A, env->ckT + c * W, env->ckWD + c * W, d.state, d.flags, d.t,
+                    d.world_done);
+    }
+    launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, nullptr, nullptr,
+                 obs_weight, reward_weight, ell + (size_t)t * A);
+  }
+  env->diff_actions = actions;
+  env->diff_steps = steps;
+  return launch_check(env, "gd_rollout_objective");
+}
+
+static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, const float4* post, const uint8_t* fpost,
+                           const float* actions, const float* obs_w, long long stride, const float* row_scale,
+                           const float* rew_w, float reward_w, float* d_actions) {
+  AdjArgs a;
+  a.pre = pre;
+  a.fpre = fpre;
+  a.post = post;
+  a.fpost = fpost;
+  a.actions = reinterpret_cast<const float2*>(actions);
+  a.obs_w = obs_w;
+  a.obs_w_stride = stride;
+  a.row_scale = row_scale;
+  a.rew_w = rew_w;
+  a.reward_w = reward_w;
+  a.lam = env->lam;
+  a.d_actions = reinterpret_cast<float2*>(d_actions);
+  a.counter = env->counter;
+  a.order = env->order;
+  a.tile_bytes = env->adj_tile;
+  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), env->stream);
+  k_adjoint<kWorldWarps><<<env->adj_grid, kWorldWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
+}
+
+// Recompute `len` steps of the segment starting from segS[0] / segF[0] /
+// segT / segWD, leaving the state after step k in segS[k+1] / segF[k+1].
+static void recompute_segment(gd_env* env, const float* actions0, int len) {
+  const size_t A = (size_t)env->A;
+  DevEnv dv = env->d;
+  dv.t = env->segT;
+  dv.world_done = env->segWD;
+  for (int k = 0; k < len; ++k) {
+    cudaMemcpyAsync(env->segS + (k + 1) * A, env->segS + k * A, sizeof(float4) * A, cudaMemcpyDeviceToDevice,
+                    env->stream);
+    cudaMemcpyAsync(env->segF + (k + 1) * A, env->segF + k * A, A, cudaMemcpyDeviceToDevice, env->stream);
+    dv.state = env->segS + (k + 1) * A;
+    dv.flags = env->segF + (k + 1) * A;
+    launch_world(env, actions0 + (size_t)k * A * 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, nullptr,
+                 &dv);
+  }
+}
+
+gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                              float* d_actions, float* d_state0) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_diff(env, "gd_rollout_backward");
+  if (st != GD_OK) return st;
+  if (env->diff_steps < 1) return fail(env, GD_ERR_STATE, "gd_rollout_backward: no gd_rollout_objective to differentiate");
+  if (!obs_weight || !d_actions) return fail(env, GD_ERR_INVALID_ARG, "obs_weight and d_actions must not be NULL");
+  if (!aligned16(obs_weight)) return fail(env, GD_ERR_INVALID_ARG, "obs_weight must be 16-byte aligned");
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  const int T = env->diff_steps, C = env->C;
+  cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
+  for (int seg = (T - 1) / C; seg >= 0; --seg) {
+    const int t0 = seg * C, len = std::min(C, T - t0);
+    copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->ckS + seg * A, env->ckF + seg * A,
+                  env->ckT + seg * W, env->ckWD + seg * W);
+    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len);
+    for (int k = len - 1; k >= 0; --k) {
+      const int t = t0 + k;
+      launch_adjoint(env, env->segS + k * A, env->segF + k * A, env->segS + (k + 1) * A, env->segF + (k + 1) * A,
+                     env->diff_actions + (size_t)t * A * 2, obs_weight, 0, d_ell ? d_ell + (size_t)t * A : nullptr,
+                     nullptr, reward_weight, d_actions + (size_t)t * A * 2);
+    }
+  }
+  if (d_state0) cudaMemcpyAsync(d_state0, env->lam, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  return launch_check(env, "gd_rollout_backward");
+}
+
+gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,
+                           const float* obs_weight, const float* d_reward_s, float* d_state, float* d_actions) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_diff(env, "gd_step_backward");
+  if (st != GD_OK) return st;
+  if (!actions || !d_state || !d_actions) return fail(env, GD_ERR_INVALID_ARG, "actions, d_state and d_actions must not be NULL");
+  const float* w = d_obs ? d_obs : obs_weight;
+  if (w && !aligned16(w)) return fail(env, GD_ERR_INVALID_ARG, "d_obs / obs_weight must be 16-byte aligned");
+  const size_t A = (size_t)env->A;
+  copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->d.state, env->d.flags, env->d.t,
+                env->d.world_done);
+  recompute_segment(env, actions, 1);
+  if (d_state_next) cudaMemcpyAsync(env->lam, d_state_next, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  else cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
+  launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, actions, w, d_obs ? env->F : 0, nullptr,
+                 d_reward_s, 0.f, d_actions);
+  cudaMemcpyAsync(d_state, env->lam, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  return launch_check(env, "gd_step_backward");
 }
 
 gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t) {

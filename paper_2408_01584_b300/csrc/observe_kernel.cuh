@@ -134,12 +134,11 @@ __device__ __forceinline__ void walk_rows(const ObsWarpSmem& sm, int nrows, int 
   }
 }
 
-// Road part of one observation row: K float4 slots at out4 and the optional
-// local indices.
-__device__ __forceinline__ void observe_road(const WorldView& v, int K, float R, float R2, float ex, float ey, float c,
-                                             float s, ObsWarpSmem& sm, int lane, float4* __restrict__ out4,
-                                             int32_t* __restrict__ ridx) {
-  if (K == 0) return;
+// Road selection of one agent at (ex, ey): the positions of the n_sel <= K
+// nearest in-radius points, in rank order, land in sm.sel; returns n_sel.
+__device__ __forceinline__ int select_road(const WorldView& v, int K, float R, float R2, float ex, float ey,
+                                           ObsWarpSmem& sm, int lane) {
+  if (K == 0) return 0;
   const float binv = (float)OBS_NB / R2;
   const float2* __restrict__ xy = v.xy;
   const uint16_t* __restrict__ meta = v.meta;
@@ -258,6 +257,18 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
     if (r < n_sel) sm.sel[r] = (unsigned short)(key & 0xffffu);
   }
   __syncwarp();
+  return n_sel;
+}
+
+// Road part of one observation row: K float4 slots at out4 (local indices
+// to ridx if given).  With LOSS, each lane also adds w . features of its
+// slots to acc (w = the row's weights for these slots, 4 per slot).
+template <bool LOSS>
+__device__ __forceinline__ void write_road(const WorldView& v, int K, int n_sel, float ex, float ey, float c, float s,
+                                           const ObsWarpSmem& sm, int lane, float4* __restrict__ out4,
+                                           int32_t* __restrict__ ridx, const float* __restrict__ w, float& acc) {
+  const float2* __restrict__ xy = v.xy;
+  const uint16_t* __restrict__ meta = v.meta;
   // write K slots, coalesced, streaming (evict-first) stores
   for (int r = lane; r < K; r += WARP) {
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -272,16 +283,20 @@ __device__ __forceinline__ void observe_road(const WorldView& v, int K, float R,
     }
     __stcs(out4 + r, o);
     if (ridx) ridx[r] = idx;
+    if (LOSS) {
+      const float4 wr = __ldg(reinterpret_cast<const float4*>(w) + r);
+      acc = fmaf(wr.x, o.x, fmaf(wr.y, o.y, fmaf(wr.z, o.z, fmaf(wr.w, o.w, acc))));
+    }
   }
 }
 
 // Partner part: other agents of the world still in the scene within R.
 // The relative heading uses cos/sin of the difference from the two agents'
 // own cos/sin: cos(tj - ti) = cj ci + sj si, sin(tj - ti) = sj ci - cj si.
-__device__ __forceinline__ void observe_partners(const WorldView& v, int li, int P, float R2, float ex, float ey,
-                                                 float c, float s, ObsWarpSmem& sm, int lane,
-                                                 float4* __restrict__ out4, int32_t* __restrict__ pidx) {
-  if (P == 0) return;
+// Selection: local indices of the n_sel <= P nearest land in sm.psel.
+__device__ __forceinline__ int select_partners(const WorldView& v, int li, int P, float R2, float ex, float ey,
+                                               ObsWarpSmem& sm, int lane) {
+  if (P == 0) return 0;
   int n = 0;
   const unsigned lt = (1u << lane) - 1u;
   for (int j0 = 0; j0 < v.n; j0 += WARP) {
@@ -307,6 +322,13 @@ __device__ __forceinline__ void observe_partners(const WorldView& v, int li, int
     if (r < n_sel) sm.psel[r] = (unsigned char)(key & 0xffu);
   }
   __syncwarp();
+  return n_sel;
+}
+
+template <bool LOSS>
+__device__ __forceinline__ void write_partners(const WorldView& v, int P, int n_sel, float ex, float ey, float c,
+                                               float s, const ObsWarpSmem& sm, int lane, float4* __restrict__ out4,
+                                               int32_t* __restrict__ pidx, const float* __restrict__ w, float& acc) {
   for (int r = lane; r < P; r += WARP) {
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
     int idx = -1;
@@ -323,18 +345,27 @@ __device__ __forceinline__ void observe_partners(const WorldView& v, int li, int
     __stcs(out4 + 2 * r, o0);
     __stcs(out4 + 2 * r + 1, o1);
     if (pidx) pidx[r] = idx;
+    if (LOSS) {
+      const float4 w0 = __ldg(reinterpret_cast<const float4*>(w) + 2 * r);
+      const float4 w1 = __ldg(reinterpret_cast<const float4*>(w) + 2 * r + 1);
+      acc = fmaf(w0.x, o0.x, fmaf(w0.y, o0.y, fmaf(w0.z, o0.z, fmaf(w0.w, o0.w, acc))));
+      acc = fmaf(w1.x, o1.x, fmaf(w1.y, o1.y, fmaf(w1.z, o1.z, fmaf(w1.w, o1.w, acc))));
+    }
   }
-  __syncwarp();
 }
 
 // One full observation row of local agent li of the world in view v.
-__device__ __forceinline__ void observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
-                                              int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
-                                              ObsWarpSmem& sm, int lane) {
+// With LOSS, returns (to every lane) w . row for the weight row w (F
+// floats); otherwise returns 0.
+template <bool LOSS>
+__device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
+                                               int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
+                                               ObsWarpSmem& sm, int lane, const float* __restrict__ w = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
               fg = (f & GD_FLAG_GOAL) ? 1.f : 0.f;
+  float acc = 0.f;
   if (f & GD_FLAG_DONE) {
     // removed from the scene: all-zero row except the three flags
     const int n4 = e.F >> 2;
@@ -345,24 +376,39 @@ __device__ __forceinline__ void observe_agent(const DevEnv& e, const WorldView& 
     }
     if (ridx) for (int k = lane; k < e.K; k += WARP) ridx[k] = -1;
     if (pidx) for (int k = lane; k < e.P; k += WARP) pidx[k] = -1;
-    return;
-  }
-  const float4 st = v.state[li];
-  const float4 sc = v.stat[li];
-  float c, s;
-  if (v.cs) {
-    c = v.cs[li].x;
-    s = v.cs[li].y;
+    if (LOSS && lane == 0) acc = fmaf(__ldg(w + 5), fc, fmaf(__ldg(w + 6), fo, __fmul_rn(__ldg(w + 7), fg)));
   } else {
-    sincosf(st.z, &s, &c);
+    const float4 st = v.state[li];
+    const float4 sc = v.stat[li];
+    float c, s;
+    if (v.cs) {
+      c = v.cs[li].x;
+      s = v.cs[li].y;
+    } else {
+      sincosf(st.z, &s, &c);
+    }
+    if (lane == 0) {
+      const float gx = sc.z - st.x, gy = sc.w - st.y;
+      const float4 o0 = make_float4(st.w, sc.x, sc.y, rot_x(c, s, gx, gy));
+      const float4 o1 = make_float4(rot_y(c, s, gx, gy), fc, fo, fg);
+      __stcs(row + 0, o0);
+      __stcs(row + 1, o1);
+      if (LOSS) {
+        acc = fmaf(__ldg(w + 0), o0.x, fmaf(__ldg(w + 1), o0.y, fmaf(__ldg(w + 2), o0.z, __fmul_rn(__ldg(w + 3), o0.w))));
+        acc = fmaf(__ldg(w + 4), o1.x, fmaf(__ldg(w + 5), o1.y, fmaf(__ldg(w + 6), o1.z, fmaf(__ldg(w + 7), o1.w, acc))));
+      }
+    }
+    const int np = select_partners(v, li, e.P, e.R2, st.x, st.y, sm, lane);
+    write_partners<LOSS>(v, e.P, np, st.x, st.y, c, s, sm, lane, row + 2, pidx, LOSS ? w + 8 : nullptr, acc);
+    const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane);
+    write_road<LOSS>(v, e.K, nroad, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx,
+                     LOSS ? w + 8 + 8 * e.P : nullptr, acc);
   }
-  if (lane == 0) {
-    const float gx = sc.z - st.x, gy = sc.w - st.y;
-    __stcs(row + 0, make_float4(st.w, sc.x, sc.y, rot_x(c, s, gx, gy)));
-    __stcs(row + 1, make_float4(rot_y(c, s, gx, gy), fc, fo, fg));
+  if (LOSS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   }
-  observe_partners(v, li, e.P, e.R2, st.x, st.y, c, s, sm, lane, row + 2, pidx);
-  observe_road(v, e.K, e.R, e.R2, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx);
+  return acc;
 }
 
 // Road block of world w in the arena: (xy, meta) pointers for `base`
@@ -395,7 +441,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v.xy, v.meta);
   v.g = e.rgrid[w];
   v.cell_start = e.rcell_start + v.g.cell_base;
-  observe_agent(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
+  observe_agent<false>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
                 partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane);
 }
 

@@ -29,6 +29,11 @@ struct FusedArgs {
   const int* order;          // [W] world order (largest first)
   int tile_bytes;            // bytes of the shared-memory road tile
   int do_step;
+  // objective terms ell[i] = obs_w . obs row + reward_w * r_s (agents in the
+  // scene at the start of the step), written when ell != nullptr
+  const float* obs_w;        // [F], 16-byte aligned
+  float reward_w;
+  float* ell;                // [A] or nullptr
 };
 
 struct FusedAgents {
@@ -40,6 +45,7 @@ struct FusedAgents {
   uint8_t ty[GD_MAX_AGENTS_PER_WORLD];
   uint8_t coll[GD_MAX_AGENTS_PER_WORLD];
   uint8_t offr[GD_MAX_AGENTS_PER_WORLD];
+  uint8_t act0[GD_MAX_AGENTS_PER_WORLD];     // in the scene at the start of the step
 };
 
 // ---- TMA bulk copy + mbarrier (inline PTX) --------------------------------
@@ -135,6 +141,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
         const int i = a0 + tid;
         float4 s = reset ? e.init_state[i] : e.state[i];
         uint8_t f = reset ? e.init_flags[i] : e.flags[i];
+        ag.act0[tid] = !(f & GD_FLAG_DONE);
         if (!(f & GD_FLAG_DONE)) {
           const float2 u = a.actions[i];
           if (!isfinite(u.x) || !isfinite(u.y) || fabsf(u.y) >= 1.5707963f) {
@@ -298,8 +305,23 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
       // warps take the world's agents one at a time (first WARPS statically)
       for (int li = wid; li < n;) {
         const int i = a0 + li;
-        observe_agent(e, v, li, a.obs + (size_t)i * e.F, a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr,
-                      a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr, osm, lane);
+        float* orow = a.obs + (size_t)i * e.F;
+        int32_t* ridx = a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr;
+        int32_t* pidx = a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr;
+        if (a.ell) {
+          const float dot = observe_agent<true>(e, v, li, orow, ridx, pidx, osm, lane, a.obs_w);
+          if (lane == 0) {
+            float rs = 0.f;
+            if (a.do_step && ag.act0[li]) {
+              const float4 st = ag.st[li], sc = ag.sc[li];
+              const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
+              rs = c - sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));
+            }
+            a.ell[i] = fmaf(a.reward_w, rs, dot);
+          }
+        } else {
+          observe_agent<false>(e, v, li, orow, ridx, pidx, osm, lane);
+        }
         int nx = 0;
         if (lane == 0) nx = atomicAdd(&s_next, 1);
         li = __shfl_sync(0xffffffffu, nx, 0);

@@ -30,7 +30,8 @@ GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD = 1, 2, 4, 8
 # symbols declared in include/gd.h
 SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_reset", "gd_step", "gd_observe",
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
-           "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc")
+           "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
+           "gd_rollout_objective")
 
 
 class GdError(RuntimeError):
@@ -83,7 +84,8 @@ def load_library(path: str = LIB_PATH):
     lib.gd_observe.argtypes = [vp, vp, vp, vp]
     lib.gd_step_observe.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.gd_rollout.argtypes = [vp, i32, vp, vp, i32, vp, vp]
-    lib.gd_rollout_backward.argtypes = [vp, vp, f32, vp, vp]
+    lib.gd_rollout_backward.argtypes = [vp, vp, f32, vp, vp, vp]
+    lib.gd_rollout_objective.argtypes = [vp, i32, vp, vp, f32, vp, vp]
     lib.gd_step_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gd_get_state.argtypes = [vp, vp, vp, vp]
     lib.gd_set_state.argtypes = [vp, vp, vp, vp]
@@ -188,10 +190,16 @@ def gd_rollout(env, steps, actions, obs, obs_per_step=False, reward=None, done=N
                                     _ptr(reward), _ptr(done)))
 
 
-def gd_rollout_backward(env, obs_weight, reward_weight, d_actions, d_state0=None):
+def gd_rollout_objective(env, steps, actions, obs_weight, reward_weight, ell, obs=None):
     lib = load_library()
-    _check(lib, env, lib.gd_rollout_backward(env, _ptr(obs_weight), float(reward_weight), _ptr(d_actions),
-                                             _ptr(d_state0)))
+    _check(lib, env, lib.gd_rollout_objective(env, int(steps), _ptr(actions), _ptr(obs_weight, align=16),
+                                              float(reward_weight), _ptr(ell), _ptr(obs, align=16)))
+
+
+def gd_rollout_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0=None):
+    lib = load_library()
+    _check(lib, env, lib.gd_rollout_backward(env, _ptr(obs_weight, align=16), float(reward_weight), _ptr(d_ell),
+                                             _ptr(d_actions), _ptr(d_state0)))
 
 
 def gd_step_backward(env, actions, d_state_next, d_obs, obs_weight, d_reward_s, d_state, d_actions):
