@@ -187,6 +187,94 @@ def _time_rollouts(run, n, stream, flush):
     return ms
 
 
+def active_agent_steps(done, agent_off):
+    """Agent-steps of agents still in the scene at the start of each step
+    (the controlled-agent analogue of Sec. 4.1): after gd_reset every agent
+    is in; an agent done after step t-1 is out at step t unless its whole
+    world was done (the world then restarts from its snapshot)."""
+    import numpy as np
+    T, A = done.shape
+    world = np.repeat(np.arange(len(agent_off) - 1), np.diff(agent_off))
+    total = A
+    for t in range(1, T):
+        d = done[t - 1].astype(bool)
+        n_out = np.bincount(world, weights=d, minlength=len(agent_off) - 1)
+        all_done = (n_out == np.diff(agent_off)) & (np.diff(agent_off) > 0)
+        total += int((~d | all_done[world]).sum())
+    return total
+
+
+def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
+    """Batched rollouts (fused kernel, CUDA graph) of another workload."""
+    import torch
+    from paper_2408_01584_b300 import gd, scenes
+    wl = scenes.WORKLOADS[workload]
+    T = wl["steps"]
+    sc = scenes.workload_scene(workload, seed)
+    cfg = workload_cfg(workload)
+    with torch.cuda.stream(stream):
+        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        A = env.A
+        actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
+        rew = torch.empty(T, A, device=dev)
+        done = torch.empty(T, A, dtype=torch.uint8, device=dev)
+
+        def run():
+            gd.gd_reset(env.h, None)
+            gd.gd_rollout(env.h, T, actions, env.obs, False, rew, done)
+
+        for _ in range(warmup):
+            run()
+        ms = _time_rollouts(run, steps, stream, flush)
+        gd.gd_sync(env.h)
+    act = active_agent_steps(done.cpu().numpy(), sc.agent_off)
+    out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
+           "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
+           "active_agent_steps_per_s": act * steps / (sum(ms) / 1e3)}
+    env.close()
+    return out
+
+
+def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
+    """Differentiable rollouts: objective forward (checkpoints every 10
+    steps) + adjoint backward over the whole episode."""
+    import numpy as np
+    import torch
+    from paper_2408_01584_b300 import gd, scenes
+    wl = scenes.WORKLOADS[workload]
+    T = wl["steps"]
+    sc = scenes.workload_scene(workload, seed)
+    cfg = workload_cfg(workload)
+    with torch.cuda.stream(stream):
+        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_DIFFERENTIABLE))
+        A, F = env.A, env.F
+        actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
+        w = torch.from_numpy(np.random.default_rng(seed).uniform(0, 1, F).astype(np.float32)).to(dev)
+        ell = torch.empty(T, A, device=dev)
+        d_act = torch.empty(T, A, 2, device=dev)
+        d_s0 = torch.empty(A, 4, device=dev)
+
+        def fwd():
+            gd.gd_reset(env.h, None)
+            gd.gd_rollout_objective(env.h, T, actions, w, 1.0, ell, env.obs)
+
+        def fwdbwd():
+            fwd()
+            gd.gd_rollout_backward(env.h, w, 1.0, None, d_act, d_s0)
+
+        for _ in range(warmup):
+            fwdbwd()
+        ms_f = _time_rollouts(fwd, steps, stream, flush)
+        ms = _time_rollouts(fwdbwd, steps, stream, flush)
+        gd.gd_sync(env.h)
+    out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
+           "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC + " (forward+backward)",
+           "ms_per_episode": statistics.mean(ms), "forward_only_ms_per_episode": statistics.mean(ms_f),
+           "ckpt_every": 10}
+    env.close()
+    return out
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -282,6 +370,8 @@ def run_ours(args, rank, world):
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
                      "algorithmic_bytes_per_agent_step": bytes_obs + bytes_road,
                      "avg_launch_us": launch_s * 1e6, "launches_timed": args.steps * T},
+        "active_agent_steps_per_s": active_agent_steps(done_d.cpu().numpy(), sc.agent_off) * args.steps
+        / (total_ms / 1e3),
         "plain": {"value": T * A * len(plain_ms) / (sum(plain_ms) / 1e3), "unit": METRIC,
                   "ms_per_step": statistics.mean(plain_ms), "launches_per_sim_step": n_plain_launch,
                   "form": "per-stage launches from the host, no graph"},
@@ -289,6 +379,12 @@ def run_ours(args, rank, world):
     }
     env_b.close()
     env_p.close()
+    del env_b, env_p
+    if args.extras and world == 1:
+        torch.cuda.empty_cache()
+        out["workloads"] = [bench_batched_forward("uneven_4096", 3, 1, dev, stream, flush),
+                            bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush),
+                            bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush)]
     return out
 
 
@@ -300,6 +396,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain_1024x64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the uneven, differentiable and forward+backward workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
