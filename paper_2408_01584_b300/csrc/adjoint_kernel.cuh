@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
     const int w = a.order[k];
     const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0;
     const int nr = e.road_off[w + 1] - e.road_off[w];
-    const unsigned block = (unsigned)road_block_bytes(nr);
+    const GridDesc g = e.rgrid[w];
+    const unsigned block = (unsigned)g.block_bytes;
     const unsigned char* gblock = e.arena + (size_t)e.arena_off[w] * 16;
     const bool use_tile = obs_term && nr > 0 && block <= (unsigned)a.tile_bytes;
     if (use_tile && tid == 0) {
@@ -148,9 +149,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
       v.cs = ag.cs;
       v.flags = ag.fl;
       v.n = n;
-      road_block(use_tile ? tile : gblock, nr, v.xy, v.meta);
-      v.g = e.rgrid[w];
-      v.cell_start = e.rcell_start + v.g.cell_base;
+      road_block(use_tile ? tile : gblock, nr, v);
+      v.g = g;
       for (int li = wid; li < n;) {
         if (!(ag.fl[li] & GD_FLAG_DONE)) {
           const int i = a0 + li;

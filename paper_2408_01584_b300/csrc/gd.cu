@@ -120,7 +120,8 @@ void grid_geometry(float minx, float miny, float maxx, float maxy, float cs, Gri
   g.inv_cs = 1.f / cs;
   g.nx = std::max(1, (int)std::floor((maxx - minx) * g.inv_cs) + 1);
   g.ny = std::max(1, (int)std::floor((maxy - miny) * g.inv_cs) + 1);
-  g.pad = 0;
+  g.seg_max = 0.f;
+  g.block_bytes = 0;
 }
 
 int cell_clamped(float v, float o, float inv, int n) {
@@ -248,18 +249,13 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       max_diag = std::max(max_diag, std::sqrt(s->length[i] * s->length[i] + s->width[i] * s->width[i]));
     }
   // road arena: per world one 16-byte aligned block of cell-sorted points,
-  // road_pad(N_w) float2 (x, y) then road_pad(N_w) uint16 (index | type << 15)
+  // road_pad(N_w) float2 (x, y), road_pad(N_w) uint16 (index | type << 15),
+  // road_pad(N_w) uint16 next-point-of-the-edge-segment, then the uint16
+  // cell starts of the world's road grid
   std::vector<GridDesc> rdesc(W), edesc(W);
-  std::vector<int> rcell_start;
+  std::vector<float4> bbox(W);
   std::vector<long long> arena_off(W);
   size_t arena_bytes = 0;
-  for (int w = 0; w < W; ++w) {
-    arena_off[w] = (long long)(arena_bytes / 16);
-    arena_bytes += road_block_bytes(s->road_off[w + 1] - s->road_off[w]);
-  }
-  std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
-  std::vector<int> ecell_start;
-  std::vector<float4> esegs;
   for (int w = 0; w < W; ++w) {
     const int r0 = s->road_off[w], r1 = s->road_off[w + 1];
     float minx = 0.f, miny = 0.f, maxx = 0.f, maxy = 0.f;
@@ -271,9 +267,20 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
         miny = std::min(miny, s->road_y[j]); maxy = std::max(maxy, s->road_y[j]);
       }
     }
+    bbox[w] = make_float4(minx, miny, maxx, maxy);
+    grid_geometry(minx, miny, maxx, maxy, rcell, rdesc[w]);
+    rdesc[w].cell_base = 0;
+    rdesc[w].block_bytes = road_block_bytes(r1 - r0, rdesc[w].nx * rdesc[w].ny);
+    arena_off[w] = (long long)(arena_bytes / 16);
+    arena_bytes += (size_t)rdesc[w].block_bytes;
+  }
+  std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
+  std::vector<int> ecell_start;
+  std::vector<float4> esegs;
+  for (int w = 0; w < W; ++w) {
+    const int r0 = s->road_off[w], r1 = s->road_off[w + 1];
+    const float minx = bbox[w].x, miny = bbox[w].y, maxx = bbox[w].z, maxy = bbox[w].w;
     GridDesc& g = rdesc[w];
-    grid_geometry(minx, miny, maxx, maxy, rcell, g);
-    g.cell_base = (int)rcell_start.size();
     const int nc = g.nx * g.ny;
     std::vector<int> cnt(nc + 1, 0), cell(r1 - r0);
     for (int j = r0; j < r1; ++j) {
@@ -282,15 +289,28 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       cnt[cell[j - r0] + 1]++;
     }
     for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
-    for (int c = 0; c <= nc; ++c) rcell_start.push_back(cnt[c]);   // relative to the world's first point
+    uint16_t* bcells = reinterpret_cast<uint16_t*>(arena.data() + (size_t)arena_off[w] * 16 + (size_t)road_pad(r1 - r0) * 12);
+    for (int c = 0; c <= nc; ++c) bcells[c] = (uint16_t)cnt[c];   // positions within the block
     std::vector<int> fill(cnt.begin(), cnt.end() - 1);
     float2* bxy = reinterpret_cast<float2*>(arena.data() + (size_t)arena_off[w] * 16);
     uint16_t* bmeta = reinterpret_cast<uint16_t*>(bxy + road_pad(r1 - r0));
+    uint16_t* bnext = bmeta + road_pad(r1 - r0);
+    std::vector<int> pos(r1 - r0);
     for (int j = r0; j < r1; ++j) {
       const int dst = fill[cell[j - r0]]++;
+      pos[j - r0] = dst;
       bxy[dst] = make_float2(s->road_x[j], s->road_y[j]);
       bmeta[dst] = (uint16_t)((j - r0) | (s->road_type[j] << 15));
     }
+    // road-edge segments: consecutive ROAD_EDGE points of one polyline
+    float seg_max = 0.f;
+    for (int j = r0; j < r1; ++j) {
+      const bool seg = j + 1 < r1 && s->road_type[j] == GD_ROAD_EDGE && s->road_type[j + 1] == GD_ROAD_EDGE &&
+                       s->road_poly[j] == s->road_poly[j + 1];
+      bnext[pos[j - r0]] = seg ? (uint16_t)pos[j + 1 - r0] : NO_SEGMENT;
+      if (seg) seg_max = std::max(seg_max, std::hypot(s->road_x[j + 1] - s->road_x[j], s->road_y[j + 1] - s->road_y[j]));
+    }
+    g.seg_max = seg_max;
     // road-edge segment grid: a segment is listed under every cell its
     // bounding box (grown by 1 mm) touches
     GridDesc& eg = edesc[w];
@@ -327,7 +347,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   std::vector<uint8_t> zeros_a(A, 0);
   std::vector<int> zeros_w(W, 0);
   int* p_aoff; int* p_roff; int* p_aw; float4* p_state; float4* p_init; float4* p_stat; uint8_t* p_type;
-  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; int* p_rcs; unsigned char* p_arena;
+  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; unsigned char* p_arena;
   long long* p_aroff;
   GridDesc* p_eg; int* p_ecs; float4* p_es;
   cudaError_t e = cudaSuccess;
@@ -345,7 +365,6 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(dev_alloc(env, &p_wd, (size_t)W));
   GD_TRY(cudaMemsetAsync(p_wd, 0, (size_t)W, env->stream));
   GD_TRY(upload(env, &p_rg, rdesc.data(), (size_t)W));
-  GD_TRY(upload(env, &p_rcs, rcell_start.data(), rcell_start.size()));
   GD_TRY(upload(env, &p_arena, arena.data(), arena.size()));
   GD_TRY(upload(env, &p_aroff, arena_off.data(), (size_t)W));
   GD_TRY(upload(env, &p_eg, edesc.data(), (size_t)W));
@@ -360,7 +379,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
   d.stat = p_stat; d.type = p_type; d.flags = p_flags; d.init_flags = p_iflags; d.t = p_t; d.world_done = p_wd;
-  d.rgrid = p_rg; d.rcell_start = p_rcs; d.arena = p_arena; d.arena_off = p_aroff; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
+  d.rgrid = p_rg; d.arena = p_arena; d.arena_off = p_aroff; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
   GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
   // batched form: worlds largest first (agents, then road points), a work
@@ -382,7 +401,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     size_t max_block = 16;
-    for (int w = 0; w < W; ++w) max_block = std::max(max_block, road_block_bytes(s->road_off[w + 1] - s->road_off[w]));
+    for (int w = 0; w < W; ++w) max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
     const long two = ((long)smem_sm / 2 - 2048 - (long)kWorldFixedSmem) & ~15L;   // tile bytes, 2 CTAs/SM
     const long one = ((long)smem_blk - 1024 - (long)kWorldFixedSmem) & ~15L;      // 1 CTA/SM
     const long cap = ((long)max_block <= two) ? (long)max_block : one;
@@ -411,7 +430,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     size_t max_block = 16;
-    for (int w = 0; w < W; ++w) max_block = std::max(max_block, road_block_bytes(s->road_off[w + 1] - s->road_off[w]));
+    for (int w = 0; w < W; ++w) max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
     const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
     const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
     env->adj_tile = (int)(((long)max_block <= two) ? (long)max_block : one);

@@ -5,10 +5,12 @@
 //   stat[A]        float4 (length, width, goal_x, goal_y)
 //   flags[A]       uint8  GD_FLAG_* bits
 //   arena          per world one 16-byte aligned block: road_pad(N_w) float2
-//                  (x, y) then road_pad(N_w) uint16 (local index | type << 15),
-//                  both sorted by road-grid cell so that a row of cells is one
-//                  range; arena_off[w] is the block's offset in 16-byte units
-//   rcell_start[]  int32, per world (ny*nx + 1) cell starts, relative to the block
+//                  (x, y), road_pad(N_w) uint16 (local index | type << 15),
+//                  road_pad(N_w) uint16 "next" (block position of the next point
+//                  when the two form a road-edge segment, else 0xffff), all
+//                  sorted by road-grid cell so that a row of cells is one range,
+//                  then the (ny*nx + 1) uint16 cell starts; arena_off[w] is the
+//                  block's offset in 16-byte units, rgrid[w].block_bytes its size
 //   esegs[]        float4 (x0, y0, x1, y1) road-edge segments listed under every
 //                  edge-grid cell their bounding box touches
 #pragma once
@@ -27,15 +29,20 @@ constexpr int WARP = 32;
 
 // Points of a world's road block, padded so the block is a multiple of 16 B.
 __host__ __device__ __forceinline__ int road_pad(int nr) { return (nr + 7) & ~7; }
-__host__ __device__ __forceinline__ size_t road_block_bytes(int nr) { return (size_t)road_pad(nr) * 10; }
+// Bytes of a world's road block: points (12 B each, padded) + cell starts.
+__host__ __device__ __forceinline__ int road_block_bytes(int nr, int ncells) {
+  return road_pad(nr) * 12 + ((2 * (ncells + 1) + 15) & ~15);
+}
+constexpr unsigned short NO_SEGMENT = 0xffff;
 constexpr int MAX_ROWS = 32;            // grid rows spanned by one observation disk
 
 struct GridDesc {      // one per world, for the road-point grid and the edge grid
   float ox, oy;        // lower-left corner of cell (0, 0)
   float cs, inv_cs;    // cell size and its inverse
   int nx, ny;          // cells per row / rows
-  int cell_base;       // first entry of this world's cell-start table
-  int pad;
+  int cell_base;       // edge grid: first entry of this world's cell-start table
+  float seg_max;       // road grid: longest road-edge segment of the world (m)
+  int block_bytes;     // road grid: bytes of the world's road block in the arena
 };
 
 // Everything a kernel needs, passed by value (device pointers + sizes).
@@ -55,7 +62,6 @@ struct DevEnv {
   int* t;
   uint8_t* world_done;
   const GridDesc* rgrid;
-  const int* rcell_start;
   const unsigned char* arena;
   const long long* arena_off;
   const GridDesc* egrid;

@@ -33,8 +33,8 @@
 namespace gd {
 
 constexpr int OBS_NB = 256;        // d^2 buckets
-constexpr int OBS_CAP = 384;       // keys kept per warp (>= GD_MAX_K_ROAD)
-constexpr int OBS_CAND = 1024;     // compact list of in-radius positions
+constexpr int OBS_CAP = 288;       // keys kept per warp (>= GD_MAX_K_ROAD)
+constexpr int OBS_CAND = 768;      // compact list of in-radius positions
 static_assert(OBS_CAP >= GD_MAX_K_ROAD, "selection capacity must hold K keys");
 
 struct ObsWarpSmem {
@@ -61,7 +61,8 @@ struct WorldView {
   int n;                   // agents in the world
   const float2* xy;        // [nr] cell-sorted road points
   const uint16_t* meta;    // [nr] local index | type << 15
-  const int* cell_start;   // world's cell-start table (global), ny*nx + 1 entries
+  const uint16_t* next;    // [nr] position of the edge segment's second point, or NO_SEGMENT
+  const uint16_t* cell_start;  // ny*nx + 1 cell starts (block positions)
   GridDesc g;
 };
 
@@ -99,9 +100,9 @@ __device__ __forceinline__ int road_rows(const WorldView& v, float R, float R2, 
       const int cx0 = (int)clampf(floorf((ex - hw - g.ox) * g.inv_cs), 0.f, (float)g.nx);
       const int cx1 = (int)clampf(floorf((ex + hw - g.ox) * g.inv_cs), -1.f, (float)(g.nx - 1));
       if (cx0 <= cx1) {
-        const int* cst = v.cell_start + row * g.nx;
-        start = (unsigned)__ldg(cst + cx0);
-        len = __ldg(cst + cx1 + 1) - (int)start;
+        const uint16_t* cst = v.cell_start + row * g.nx;
+        start = cst[cx0];
+        len = (int)cst[cx1 + 1] - (int)start;
       }
     }
   }
@@ -145,24 +146,58 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   int nrows;
   const int total = road_rows(v, R, R2, ex, ey, sm, lane, nrows);
 
-  // pass 1: histogram of d^2 buckets + compact list of in-radius positions
+  // pass 1: histogram of d^2 buckets + compact list of in-radius positions.
+  // Lane l walks the contiguous chunk [l*chunk, (l+1)*chunk) of the flat
+  // candidate list, four candidates per round: the four loads are
+  // independent, and lanes sit far apart in the disk so their histogram
+  // atomics rarely hit the same bucket.
   for (int b = lane; b < OBS_NB; b += WARP) sm.cur[b] = 0;
   __syncwarp();
   int n_in = 0;
   const unsigned lt = (1u << lane) - 1u;
-  walk_rows(sm, nrows, total, lane, [&](unsigned p, bool valid) {
-    bool in = false;
-    if (valid) {
-      const float2 q = xy[p];
-      const float d2 = dist2(q.x - ex, q.y - ey);
-      in = d2 <= R2;
-      if (in) atomicAdd(&sm.cur[bucket_of(d2, binv)], 1u);
+  {
+    constexpr int U = 4;
+    // odd chunk: lane l reads 8-byte points 8*chunk bytes after lane l-1,
+    // which puts the 16 lanes of each 64-bit shared-memory phase on 16
+    // different bank pairs
+    const int chunk = ((total + WARP - 1) / WARP) | 1;
+    const int fbeg = lane * chunk, fend = min(fbeg + chunk, total);
+    int r = 0;
+    while (r + 1 < nrows && (int)sm.row_excl[r + 1] <= fbeg) ++r;
+    unsigned rs = sm.row_start[r], rx = sm.row_excl[r];
+    unsigned re = (r + 1 < nrows) ? sm.row_excl[r + 1] : 0xffffffffu;
+    for (int j = 0; j < chunk; j += U) {
+      unsigned pu[U];
+      bool vu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int f = fbeg + j + u;
+        vu[u] = f < fend;
+        if (vu[u]) {
+          while ((unsigned)f >= re) {
+            ++r;
+            rs = sm.row_start[r];
+            rx = sm.row_excl[r];
+            re = (r + 1 < nrows) ? sm.row_excl[r + 1] : 0xffffffffu;
+          }
+        }
+        pu[u] = vu[u] ? rs + ((unsigned)f - rx) : 0u;
+      }
+      float2 qu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) qu[u] = xy[pu[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float d2 = dist2(qu[u].x - ex, qu[u].y - ey);
+        const bool in = vu[u] && d2 <= R2;
+        if (in) atomicAdd(&sm.cur[bucket_of(d2, binv)], 1u);
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        const int slot = n_in + __popc(m & lt);
+        if (in && slot < OBS_CAND) sm.cand[slot] = (unsigned short)pu[u];
+        n_in += __popc(m);
+      }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    const int slot = n_in + __popc(m & lt);
-    if (in && slot < OBS_CAND) sm.cand[slot] = (unsigned short)p;
-    n_in += __popc(m);
-  });
+  }
   __syncwarp();
   // exclusive scan: lane owns OBS_NB/32 consecutive buckets
   constexpr int PER = OBS_NB / WARP;
@@ -199,10 +234,17 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   // it holds them all, else by walking the rows again.
   auto for_each_in_radius = [&](auto&& fn) {
     if (compact) {
-      for (int k = lane; k < n_in; k += WARP) {
-        const unsigned p = sm.cand[k];
-        const float2 q = xy[p];
-        fn(p, dist2(q.x - ex, q.y - ey));
+      constexpr int U = 4;
+      for (int k0 = lane; k0 < n_in; k0 += U * WARP) {
+        unsigned pu[U];
+        float2 qu[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) pu[u] = (k0 + u * WARP < n_in) ? sm.cand[k0 + u * WARP] : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) qu[u] = xy[pu[u]];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + u * WARP < n_in) fn(pu[u], dist2(qu[u].x - ex, qu[u].y - ey));
       }
     } else {
       walk_rows(sm, nrows, total, lane, [&](unsigned p, bool valid) {
@@ -252,8 +294,9 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     const unsigned long long key = sm.u.keys[k];
     const int b = bucket_of(__uint_as_float((unsigned)(key >> 32)), binv);
     const int lo = (int)sm.off[b], hi = min((int)sm.off[b + 1], OBS_CAP);
-    int r = lo;
-    for (int q = lo; q < hi; ++q) r += sm.u.keys[q] < key;
+    int r = lo, q = lo;
+    for (; q + 1 < hi; q += 2) r += (int)(sm.u.keys[q] < key) + (int)(sm.u.keys[q + 1] < key);
+    if (q < hi) r += sm.u.keys[q] < key;
     if (r < n_sel) sm.sel[r] = (unsigned short)(key & 0xffffu);
   }
   __syncwarp();
@@ -411,11 +454,43 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
   return acc;
 }
 
-// Road block of world w in the arena: (xy, meta) pointers for `base`
-// (global arena or a shared-memory copy of the block).
-__device__ __forceinline__ void road_block(const unsigned char* base, int nr, const float2*& xy, const uint16_t*& meta) {
-  xy = reinterpret_cast<const float2*>(base);
-  meta = reinterpret_cast<const uint16_t*>(base + (size_t)road_pad(nr) * sizeof(float2));
+// Road block of world w in the arena: (xy, meta, next, cell_start)
+// pointers for `base` (global arena or a shared-memory copy of the block).
+__device__ __forceinline__ void road_block(const unsigned char* base, int nr, WorldView& v) {
+  v.xy = reinterpret_cast<const float2*>(base);
+  v.meta = reinterpret_cast<const uint16_t*>(base + (size_t)road_pad(nr) * sizeof(float2));
+  v.next = v.meta + road_pad(nr);
+  v.cell_start = v.next + road_pad(nr);
+}
+
+// Road-edge crossing (Sec. 3.2 "Termination conditions") of a box, from the
+// world's road block: a segment that meets the box has its first point
+// within (box circumradius + longest segment) of the box centre, so the
+// grid cells under that square hold every candidate.  Warp per agent, lanes
+// over the candidate points, ballot-OR of the separating-axis tests.
+__device__ __forceinline__ bool offroad_from_block(const WorldView& v, float cx, float cy, float ca, float sa, float hl,
+                                                   float hw, int lane) {
+  const GridDesc& g = v.g;
+  const float rq = sqrtf(fmaf(hl, hl, hw * hw)) + g.seg_max + 1e-3f;
+  const int cx0 = (int)clampf(floorf((cx - rq - g.ox) * g.inv_cs), 0.f, (float)g.nx);
+  const int cx1 = (int)clampf(floorf((cx + rq - g.ox) * g.inv_cs), -1.f, (float)(g.nx - 1));
+  const int cy0 = (int)clampf(floorf((cy - rq - g.oy) * g.inv_cs), 0.f, (float)g.ny);
+  const int cy1 = (int)clampf(floorf((cy + rq - g.oy) * g.inv_cs), -1.f, (float)(g.ny - 1));
+  bool hit = false;
+  if (cx0 <= cx1) {
+    for (int row = cy0; row <= cy1; ++row) {
+      const uint16_t* cst = v.cell_start + row * g.nx;
+      const int b = cst[cx0], en = cst[cx1 + 1];
+      for (int q = b + lane; q < en; q += WARP) {
+        const unsigned nx = v.next[q];
+        if (nx != NO_SEGMENT) {
+          const float2 p0 = v.xy[q], p1 = v.xy[nx];
+          hit |= box_seg_depth(cx, cy, ca, sa, hl, hw, make_float4(p0.x, p0.y, p1.x, p1.y)) > 0.f;
+        }
+      }
+    }
+  }
+  return __any_sync(0xffffffffu, hit);
 }
 
 // Per-stage form: one warp per agent over the whole batch, everything read
@@ -438,9 +513,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   v.cs = nullptr;
   v.flags = e.flags + a0;
   v.n = e.agent_off[w + 1] - a0;
-  road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v.xy, v.meta);
+  road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
-  v.cell_start = e.rcell_start + v.g.cell_base;
   observe_agent<false>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
                 partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane);
 }

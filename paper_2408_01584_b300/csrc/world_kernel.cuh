@@ -122,16 +122,43 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
     const int w = a.order[k];
     const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0;
     const int nr = e.road_off[w + 1] - e.road_off[w];
-    const unsigned block = (unsigned)road_block_bytes(nr);
+    const GridDesc g = e.rgrid[w];
+    const unsigned block = (unsigned)g.block_bytes;
     const unsigned char* gblock = e.arena + (size_t)e.arena_off[w] * 16;
-    const bool use_tile = observe && nr > 0 && block <= (unsigned)a.tile_bytes;
+    const bool use_tile = nr > 0 && block <= (unsigned)a.tile_bytes;
     if (use_tile && tid == 0) {
       fence_proxy_async_smem();     // earlier generic reads of the tile before the async write
       mbar_arrive_expect_tx(bar, block);
       tma_load_1d(tile, gblock, block, bar);
     }
     if (tid == 0) s_next = WARPS;
-    const GridDesc g = e.rgrid[w];
+    WorldView v;
+    v.state = ag.st;
+    v.stat = ag.sc;
+    v.cs = ag.cs;
+    v.flags = ag.fl;
+    v.n = n;
+    road_block(use_tile ? tile : gblock, nr, v);
+    v.g = g;
+    bool tile_ready = !use_tile;
+    // every thread waits for the tile (bounded); false = give up this CTA
+    auto wait_tile = [&]() -> bool {
+      if (!tile_ready) {
+        if (!mbar_wait_bounded(bar, phase)) s_abort = 1;
+        phase ^= 1u;
+        tile_ready = true;
+      }
+      __syncthreads();
+      if (s_abort) {
+        if (tid == 0) {
+          atomicOr(e.err, ERR_TIMEOUT);
+          mbar_wait_bounded(bar, phase ^ 1u);   // give the copy one more bounded chance to land
+        }
+        __syncthreads();
+        return false;
+      }
+      return true;
+    };
     if (a.do_step) {
       const bool reset = (e.cflags & GD_AUTO_RESET) && e.world_done[w];
       const float inv = 1.f / e.agent_cell;
@@ -210,26 +237,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
           }
         }
         hit = __any_sync(0xffffffffu, hit);
-        bool off = false;
-        if (ag.ty[li] != GD_AGENT_PEDESTRIAN) {
-          const GridDesc eg = e.egrid[w];
-          const float hl = 0.5f * sc.x, hw = 0.5f * sc.y;
-          const float ex = hl * fabsf(ca) + hw * fabsf(sa) + 1e-3f, ey = hl * fabsf(sa) + hw * fabsf(ca) + 1e-3f;
-          const int cx0 = (int)clampf(floorf((s.x - ex - eg.ox) * eg.inv_cs), 0.f, (float)(eg.nx - 1));
-          const int cx1 = (int)clampf(floorf((s.x + ex - eg.ox) * eg.inv_cs), -1.f, (float)(eg.nx - 1));
-          const int cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
-          const int cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
-          for (int row = cy0; row <= cy1 && cx0 <= cx1; ++row) {
-            const int sb = __ldg(e.ecell_start + eg.cell_base + row * eg.nx + cx0);
-            const int se = __ldg(e.ecell_start + eg.cell_base + row * eg.nx + cx1 + 1);
-            for (int q = sb + lane; q < se; q += WARP) off |= box_seg_depth(s.x, s.y, ca, sa, hl, hw, e.esegs[q]) > 0.f;
-          }
-          off = __any_sync(0xffffffffu, off);
+        if (lane == 0) ag.coll[li] = hit ? 1 : 0;
+      }
+      // road edges, from the world's road block (shared-memory tile): warp
+      // per agent, ballot-OR over the candidate segments
+      if (!wait_tile()) return;
+      for (int li = wid; li < n; li += WARPS) {
+        if ((ag.fl[li] & GD_FLAG_DONE) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
+          if (lane == 0) ag.offr[li] = 0;
+          continue;
         }
-        if (lane == 0) {
-          ag.coll[li] = hit ? 1 : 0;
-          ag.offr[li] = off ? 1 : 0;
-        }
+        const float4 s = ag.st[li];
+        const float4 sc = ag.sc[li];
+        const bool off = offroad_from_block(v, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane);
+        if (lane == 0) ag.offr[li] = off ? 1 : 0;
       }
       __syncthreads();
       // goal, reward, flags, done
@@ -278,30 +299,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
       ag.fl[tid] = e.flags[a0 + tid];
     }
     if (observe) {
-      if (use_tile) {
-        // every thread waits for the tile (bounded)
-        const bool ok = mbar_wait_bounded(bar, phase);
-        if (!ok) s_abort = 1;
-        phase ^= 1u;
-      }
-      __syncthreads();
-      if (s_abort) {
-        if (tid == 0) {
-          atomicOr(e.err, ERR_TIMEOUT);
-          mbar_wait_bounded(bar, phase ^ 1u);   // give the copy one more bounded chance to land
-        }
-        __syncthreads();
-        return;
-      }
-      WorldView v;
-      v.state = ag.st;
-      v.stat = ag.sc;
-      v.cs = ag.cs;
-      v.flags = ag.fl;
-      v.n = n;
-      road_block(use_tile ? tile : gblock, nr, v.xy, v.meta);
-      v.g = g;
-      v.cell_start = e.rcell_start + g.cell_base;
+      if (!wait_tile()) return;
       // warps take the world's agents one at a time (first WARPS statically)
       for (int li = wid; li < n;) {
         const int i = a0 + li;
