@@ -214,6 +214,8 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
     cfg = workload_cfg(workload)
     with torch.cuda.stream(stream):
         env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        gd.gd_autotune(env.h)
+        info = gd.gd_get_info(env.h)
         A = env.A
         actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
         rew = torch.empty(T, A, device=dev)
@@ -230,7 +232,9 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
     act = active_agent_steps(done.cpu().numpy(), sc.agent_off)
     out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
-           "active_agent_steps_per_s": act * steps / (sum(ms) / 1e3)}
+           "active_agent_steps_per_s": act * steps / (sum(ms) / 1e3),
+           "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
+                         "topk_strategy": info.topk_strategy}}
     env.close()
     return out
 
@@ -313,6 +317,10 @@ def run_ours(args, rank, world):
             gd.gd_observe(env_p.h, env_p.obs)
 
     with torch.cuda.stream(stream):
+        gd.gd_autotune(env_b.h)
+        info = gd.gd_get_info(env_b.h)
+        tuned = {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
+                 "topk_strategy": {1: "bucket rank", 2: "bitonic sort"}[info.topk_strategy]}
         for _ in range(args.warmup):
             batched_rollout()
             plain_rollout()
@@ -357,6 +365,7 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "form": "batched (persistent fused kernel, 91-step CUDA graph)",
+                   "autotuned": tuned,
                    "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
                    "n_partners": cfg["n_partners"], "episode_steps": T, "feat": F,
                    "step": "one 91-step episode of every world",

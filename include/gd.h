@@ -127,6 +127,9 @@ typedef struct gd_info {
   int32_t num_worlds, num_agents, num_road, feat;   /* feat = F */
   int32_t max_agents_per_world, k_road, n_partners, episode_len;
   int64_t device_bytes;                             /* device memory owned by the env */
+  int32_t block_size;                               /* fused-kernel threads per block in use */
+  float road_cell;                                  /* road grid cell in use (m) */
+  int32_t topk_strategy;                            /* road top-K method in use */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -220,9 +223,14 @@ gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_sta
 gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t);
 gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, const int32_t* t);
 
-/* Time the observation kernel over candidate block sizes, road cell sizes
- * and top-K strategies on the current state and keep the fastest.  Runs on
- * the env stream, synchronises it, leaves the simulation state unchanged. */
+/* Autotuner of the fused (batched) kernel: times one step + observation
+ * from the current state for every road grid cell in {6, 8, 12} m, CTA size
+ * in {128, 256, 512} threads and top-K strategy in {1 bucket rank, 2 bitonic
+ * sort when at most 256 points are in range}, and keeps the fastest
+ * (reported by gd_get_info).  Every combination gives the same results.
+ * Synchronises the env's stream; the simulation state is unchanged
+ * afterwards.  A captured gd_rollout graph is dropped and re-captured on the
+ * next call. */
 gd_status gd_autotune(gd_env* env);
 
 /* Block until the env's stream is idle and report any sticky device error. */

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
             gt += fmaf(wa.x, yp, -__fmul_rn(wa.y, xp)) + fmaf(wa.z, sd, -__fmul_rn(wa.w, cd));
           }
           // road points
-          const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane);
+          const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
           const float* wroad = wrow + 8 + 8 * e.P;
           for (int r = lane; r < nroad; r += WARP) {
             const float2 q = v.xy[sm.sel[r]];

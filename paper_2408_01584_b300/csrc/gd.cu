@@ -21,11 +21,12 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr int kObsWarpsDefault = 8;
-constexpr int kWorldWarps = 8;
+constexpr int kWorldWarps = 8;    // default CTA size of the fused kernel (warps); 4 and 16 also built
+constexpr int kAdjWarps = 8;
 
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
-constexpr size_t kWorldFixedSmem = 128 + sizeof(FusedAgents) + kWorldWarps * sizeof(ObsWarpSmem);
-constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kWorldWarps * sizeof(ObsWarpSmem);
+constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
+constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(ObsWarpSmem);
 
 }  // namespace
 
@@ -48,6 +49,15 @@ struct gd_env {
   int tile_cap = 0;            // bytes of the shared-memory road tile
   size_t world_smem = 0;       // dynamic shared memory of k_world
   int world_grid = 0;          // persistent CTAs
+  int warps = kWorldWarps;     // CTA size of k_world (4, 8 or 16 warps)
+  float road_cell = 8.f;       // road grid cell (m)
+  size_t max_block = 16;       // largest road block (bytes)
+  // host copy of the road, to rebuild the road blocks for another cell size
+  std::vector<int> h_road_off;
+  std::vector<float> h_rx, h_ry;
+  std::vector<uint8_t> h_rtype;
+  std::vector<int32_t> h_rpoly;
+  std::vector<float4> h_bbox;
   // captured rollout graph and the arguments it was captured with
   cudaGraphExec_t graph = nullptr;
   const void* g_key[6] = {};
@@ -127,6 +137,148 @@ void grid_geometry(float minx, float miny, float maxx, float maxy, float cs, Gri
 int cell_clamped(float v, float o, float inv, int n) {
   const int c = (int)std::floor((v - o) * inv);
   return std::min(std::max(c, 0), n - 1);
+}
+
+
+// ---- road blocks and kernel shapes (built at create, rebuilt by the tuner) ---
+
+static void dev_free(gd_env* env, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < env->allocs.size(); ++k)
+    if (env->allocs[k] == p) {
+      env->allocs.erase(env->allocs.begin() + (long)k);
+      break;
+    }
+  cudaFree(p);
+}
+
+template <int WARPS>
+static cudaError_t shape_world(gd_env* env, size_t max_block, int smem_sm, int smem_blk, int nsm) {
+  const long fixed = (long)world_fixed_smem(WARPS);
+  const long two = ((long)smem_sm / 2 - 2048 - fixed) & ~15L;   // tile bytes, 2 CTAs/SM
+  const long one = ((long)smem_blk - 1024 - fixed) & ~15L;      // 1 CTA/SM
+  const long cap = ((long)max_block <= two) ? (long)max_block : one;
+  env->tile_cap = (int)std::max(16L, cap);
+  env->world_smem = (size_t)fixed + (size_t)env->tile_cap;
+  cudaError_t e = cudaFuncSetAttribute(k_world<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<WARPS>, WARPS * 32, env->world_smem);
+  if (e != cudaSuccess) return e;
+  env->world_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
+  return cudaSuccess;
+}
+
+// Tile sizes, shared memory and grid of the fused (and adjoint) kernel for
+// the current road blocks and CTA size.
+static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
+  int dev = 0, smem_sm = 0, smem_blk = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  switch (env->warps) {
+    case 4: e = shape_world<4>(env, max_block, smem_sm, smem_blk, nsm); break;
+    case 16: e = shape_world<16>(env, max_block, smem_sm, smem_blk, nsm); break;
+    default: env->warps = 8; e = shape_world<8>(env, max_block, smem_sm, smem_blk, nsm); break;
+  }
+  if (e != cudaSuccess) return e;
+  if (env->cfg.flags & GD_DIFFERENTIABLE) {
+    const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
+    const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
+    env->adj_tile = (int)std::max(16L, ((long)max_block <= two) ? (long)max_block : one);
+    env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
+    e = cudaFuncSetAttribute(k_adjoint<kAdjWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->adj_smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<kAdjWarps>, kAdjWarps * 32, env->adj_smem);
+    if (e != cudaSuccess) return e;
+    env->adj_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
+  }
+  return cudaSuccess;
+}
+
+// Road arena for grid cell `cell` (m): per world one 16-byte aligned block of
+// cell-sorted points, road_pad(N_w) float2 (x, y), road_pad(N_w) uint16
+// (index | type << 15), road_pad(N_w) uint16 next-point-of-the-edge-segment,
+// then the uint16 cell starts of the world's road grid.  Replaces any
+// earlier arena; synchronises the env's stream.
+static cudaError_t build_road(gd_env* env, float cell) {
+  const int W = env->W;
+  const std::vector<int>& off = env->h_road_off;
+  std::vector<GridDesc> rdesc(W);
+  std::vector<long long> arena_off(W);
+  size_t arena_bytes = 0, max_block = 16;
+  for (int w = 0; w < W; ++w) {
+    const float4 bb = env->h_bbox[w];
+    grid_geometry(bb.x, bb.y, bb.z, bb.w, cell, rdesc[w]);
+    rdesc[w].cell_base = 0;
+    rdesc[w].block_bytes = road_block_bytes(off[w + 1] - off[w], rdesc[w].nx * rdesc[w].ny);
+    arena_off[w] = (long long)(arena_bytes / 16);
+    arena_bytes += (size_t)rdesc[w].block_bytes;
+    max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
+  }
+  std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
+  for (int w = 0; w < W; ++w) {
+    const int r0 = off[w], r1 = off[w + 1], nr = r1 - r0;
+    GridDesc& g = rdesc[w];
+    const int nc = g.nx * g.ny;
+    std::vector<int> cnt(nc + 1, 0), cellid(nr), pos(nr);
+    for (int j = r0; j < r1; ++j) {
+      const int cx = cell_clamped(env->h_rx[j], g.ox, g.inv_cs, g.nx), cy = cell_clamped(env->h_ry[j], g.oy, g.inv_cs, g.ny);
+      cellid[j - r0] = cy * g.nx + cx;
+      cnt[cellid[j - r0] + 1]++;
+    }
+    for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    unsigned char* blk = arena.data() + (size_t)arena_off[w] * 16;
+    float2* bxy = reinterpret_cast<float2*>(blk);
+    uint16_t* bmeta = reinterpret_cast<uint16_t*>(bxy + road_pad(nr));
+    uint16_t* bnext = bmeta + road_pad(nr);
+    uint16_t* bcells = bnext + road_pad(nr);
+    for (int c = 0; c <= nc; ++c) bcells[c] = (uint16_t)cnt[c];   // positions within the block
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int j = r0; j < r1; ++j) {
+      const int dst = fill[cellid[j - r0]]++;
+      pos[j - r0] = dst;
+      bxy[dst] = make_float2(env->h_rx[j], env->h_ry[j]);
+      bmeta[dst] = (uint16_t)((j - r0) | (env->h_rtype[j] << 15));
+    }
+    // road-edge segments: consecutive ROAD_EDGE points of one polyline
+    float seg_max = 0.f;
+    for (int j = r0; j < r1; ++j) {
+      const bool seg = j + 1 < r1 && env->h_rtype[j] == GD_ROAD_EDGE && env->h_rtype[j + 1] == GD_ROAD_EDGE &&
+                       env->h_rpoly[j] == env->h_rpoly[j + 1];
+      bnext[pos[j - r0]] = seg ? (uint16_t)pos[j + 1 - r0] : NO_SEGMENT;
+      if (seg) seg_max = std::max(seg_max, std::hypot(env->h_rx[j + 1] - env->h_rx[j], env->h_ry[j + 1] - env->h_ry[j]));
+    }
+    g.seg_max = seg_max;
+  }
+  cudaError_t e = cudaStreamSynchronize(env->stream);
+  if (e != cudaSuccess) return e;
+  dev_free(env, const_cast<GridDesc*>(env->d.rgrid));
+  dev_free(env, const_cast<unsigned char*>(env->d.arena));
+  dev_free(env, const_cast<long long*>(env->d.arena_off));
+  env->d.rgrid = nullptr;
+  env->d.arena = nullptr;
+  env->d.arena_off = nullptr;
+  GridDesc* p_rg;
+  unsigned char* p_arena;
+  long long* p_aroff;
+  if ((e = upload(env, &p_rg, rdesc.data(), (size_t)W)) != cudaSuccess) return e;
+  env->d.rgrid = p_rg;
+  if ((e = upload(env, &p_arena, arena.data(), arena.size())) != cudaSuccess) return e;
+  env->d.arena = p_arena;
+  if ((e = upload(env, &p_aroff, arena_off.data(), (size_t)W)) != cudaSuccess) return e;
+  env->d.arena_off = p_aroff;
+  env->road_cell = cell;
+  env->max_block = max_block;
+  if ((e = shape_kernels(env, max_block)) != cudaSuccess) return e;
+  if (env->graph) {
+    cudaGraphExecDestroy(env->graph);
+    env->graph = nullptr;
+  }
+  return cudaStreamSynchronize(env->stream);
 }
 
 }  // namespace
@@ -248,14 +400,17 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       h_agent_world[i] = w;
       max_diag = std::max(max_diag, std::sqrt(s->length[i] * s->length[i] + s->width[i] * s->width[i]));
     }
-  // road arena: per world one 16-byte aligned block of cell-sorted points,
-  // road_pad(N_w) float2 (x, y), road_pad(N_w) uint16 (index | type << 15),
-  // road_pad(N_w) uint16 next-point-of-the-edge-segment, then the uint16
-  // cell starts of the world's road grid
-  std::vector<GridDesc> rdesc(W), edesc(W);
-  std::vector<float4> bbox(W);
-  std::vector<long long> arena_off(W);
-  size_t arena_bytes = 0;
+  // keep the road on the host (the tuner rebuilds the road blocks) and
+  // build the edge-segment grid of the per-stage form
+  env->h_road_off.assign(s->road_off, s->road_off + W + 1);
+  env->h_rx.assign(s->road_x, s->road_x + N);
+  env->h_ry.assign(s->road_y, s->road_y + N);
+  env->h_rtype.assign(s->road_type, s->road_type + N);
+  env->h_rpoly.assign(s->road_poly, s->road_poly + N);
+  env->h_bbox.resize(W);
+  std::vector<GridDesc> edesc(W);
+  std::vector<int> ecell_start;
+  std::vector<float4> esegs;
   for (int w = 0; w < W; ++w) {
     const int r0 = s->road_off[w], r1 = s->road_off[w + 1];
     float minx = 0.f, miny = 0.f, maxx = 0.f, maxy = 0.f;
@@ -267,50 +422,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
         miny = std::min(miny, s->road_y[j]); maxy = std::max(maxy, s->road_y[j]);
       }
     }
-    bbox[w] = make_float4(minx, miny, maxx, maxy);
-    grid_geometry(minx, miny, maxx, maxy, rcell, rdesc[w]);
-    rdesc[w].cell_base = 0;
-    rdesc[w].block_bytes = road_block_bytes(r1 - r0, rdesc[w].nx * rdesc[w].ny);
-    arena_off[w] = (long long)(arena_bytes / 16);
-    arena_bytes += (size_t)rdesc[w].block_bytes;
-  }
-  std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
-  std::vector<int> ecell_start;
-  std::vector<float4> esegs;
-  for (int w = 0; w < W; ++w) {
-    const int r0 = s->road_off[w], r1 = s->road_off[w + 1];
-    const float minx = bbox[w].x, miny = bbox[w].y, maxx = bbox[w].z, maxy = bbox[w].w;
-    GridDesc& g = rdesc[w];
-    const int nc = g.nx * g.ny;
-    std::vector<int> cnt(nc + 1, 0), cell(r1 - r0);
-    for (int j = r0; j < r1; ++j) {
-      const int cx = cell_clamped(s->road_x[j], g.ox, g.inv_cs, g.nx), cy = cell_clamped(s->road_y[j], g.oy, g.inv_cs, g.ny);
-      cell[j - r0] = cy * g.nx + cx;
-      cnt[cell[j - r0] + 1]++;
-    }
-    for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
-    uint16_t* bcells = reinterpret_cast<uint16_t*>(arena.data() + (size_t)arena_off[w] * 16 + (size_t)road_pad(r1 - r0) * 12);
-    for (int c = 0; c <= nc; ++c) bcells[c] = (uint16_t)cnt[c];   // positions within the block
-    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-    float2* bxy = reinterpret_cast<float2*>(arena.data() + (size_t)arena_off[w] * 16);
-    uint16_t* bmeta = reinterpret_cast<uint16_t*>(bxy + road_pad(r1 - r0));
-    uint16_t* bnext = bmeta + road_pad(r1 - r0);
-    std::vector<int> pos(r1 - r0);
-    for (int j = r0; j < r1; ++j) {
-      const int dst = fill[cell[j - r0]]++;
-      pos[j - r0] = dst;
-      bxy[dst] = make_float2(s->road_x[j], s->road_y[j]);
-      bmeta[dst] = (uint16_t)((j - r0) | (s->road_type[j] << 15));
-    }
-    // road-edge segments: consecutive ROAD_EDGE points of one polyline
-    float seg_max = 0.f;
-    for (int j = r0; j < r1; ++j) {
-      const bool seg = j + 1 < r1 && s->road_type[j] == GD_ROAD_EDGE && s->road_type[j + 1] == GD_ROAD_EDGE &&
-                       s->road_poly[j] == s->road_poly[j + 1];
-      bnext[pos[j - r0]] = seg ? (uint16_t)pos[j + 1 - r0] : NO_SEGMENT;
-      if (seg) seg_max = std::max(seg_max, std::hypot(s->road_x[j + 1] - s->road_x[j], s->road_y[j + 1] - s->road_y[j]));
-    }
-    g.seg_max = seg_max;
+    env->h_bbox[w] = make_float4(minx, miny, maxx, maxy);
     // road-edge segment grid: a segment is listed under every cell its
     // bounding box (grown by 1 mm) touches
     GridDesc& eg = edesc[w];
@@ -347,8 +459,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   std::vector<uint8_t> zeros_a(A, 0);
   std::vector<int> zeros_w(W, 0);
   int* p_aoff; int* p_roff; int* p_aw; float4* p_state; float4* p_init; float4* p_stat; uint8_t* p_type;
-  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd; GridDesc* p_rg; unsigned char* p_arena;
-  long long* p_aroff;
+  uint8_t* p_flags; uint8_t* p_iflags; int* p_t; uint8_t* p_wd;
   GridDesc* p_eg; int* p_ecs; float4* p_es;
   cudaError_t e = cudaSuccess;
 #define GD_TRY(x) do { e = (x); if (e != cudaSuccess) { gd_status r_ = cuda_fail(nullptr, e, #x); gd_destroy(env); return r_; } } while (0)
@@ -364,9 +475,6 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(upload(env, &p_t, zeros_w.data(), (size_t)W));
   GD_TRY(dev_alloc(env, &p_wd, (size_t)W));
   GD_TRY(cudaMemsetAsync(p_wd, 0, (size_t)W, env->stream));
-  GD_TRY(upload(env, &p_rg, rdesc.data(), (size_t)W));
-  GD_TRY(upload(env, &p_arena, arena.data(), arena.size()));
-  GD_TRY(upload(env, &p_aroff, arena_off.data(), (size_t)W));
   GD_TRY(upload(env, &p_eg, edesc.data(), (size_t)W));
   GD_TRY(upload(env, &p_ecs, ecell_start.data(), ecell_start.size()));
   GD_TRY(upload(env, &p_es, esegs.data(), esegs.size()));
@@ -379,7 +487,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
   d.stat = p_stat; d.type = p_type; d.flags = p_flags; d.init_flags = p_iflags; d.t = p_t; d.world_done = p_wd;
-  d.rgrid = p_rg; d.arena = p_arena; d.arena_off = p_aroff; d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
+  d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
   GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
   // batched form: worlds largest first (agents, then road points), a work
@@ -395,22 +503,6 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     });
     GD_TRY(upload(env, &env->order, order.data(), (size_t)W));
     GD_TRY(dev_alloc(env, &env->counter, 1));
-    int dev = 0, smem_sm = 0, smem_blk = 0, nsm = 0;
-    GD_TRY(cudaGetDevice(&dev));
-    GD_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    size_t max_block = 16;
-    for (int w = 0; w < W; ++w) max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
-    const long two = ((long)smem_sm / 2 - 2048 - (long)kWorldFixedSmem) & ~15L;   // tile bytes, 2 CTAs/SM
-    const long one = ((long)smem_blk - 1024 - (long)kWorldFixedSmem) & ~15L;      // 1 CTA/SM
-    const long cap = ((long)max_block <= two) ? (long)max_block : one;
-    env->tile_cap = (int)cap;
-    env->world_smem = kWorldFixedSmem + (size_t)cap;
-    GD_TRY(cudaFuncSetAttribute(k_world<kWorldWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem));
-    int per_sm = 0;
-    GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<kWorldWarps>, kWorldWarps * 32, env->world_smem));
-    env->world_grid = std::max(1, std::min(W, std::max(per_sm, 1) * nsm));
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
     env->C = cfg->ckpt_every;
@@ -424,22 +516,10 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
     GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
-    int dev = 0, smem_sm = 0, smem_blk = 0, nsm = 0;
-    GD_TRY(cudaGetDevice(&dev));
-    GD_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-    GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    size_t max_block = 16;
-    for (int w = 0; w < W; ++w) max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
-    const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
-    const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
-    env->adj_tile = (int)(((long)max_block <= two) ? (long)max_block : one);
-    env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
-    GD_TRY(cudaFuncSetAttribute(k_adjoint<kWorldWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->adj_smem));
-    int per_sm = 0;
-    GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<kWorldWarps>, kWorldWarps * 32, env->adj_smem));
-    env->adj_grid = std::max(1, std::min(W, std::max(per_sm, 1) * nsm));
   }
+  if (cfg->block_size) env->warps = cfg->block_size / 32;
+  env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
+  GD_TRY(build_road(env, rcell));
   GD_TRY(cudaStreamSynchronize(env->stream));
 #undef GD_TRY
   *out = env;
@@ -457,6 +537,9 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->n_partners = env->cfg.n_partners;
   info->episode_len = env->cfg.episode_len;
   info->device_bytes = env->bytes;
+  info->block_size = env->warps * 32;
+  info->road_cell = env->road_cell;
+  info->topk_strategy = env->d.topk;
   return GD_OK;
 }
 
@@ -524,7 +607,11 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
-  k_world<kWorldWarps><<<env->world_grid, kWorldWarps * 32, env->world_smem, stream>>>(*dv, a);
+  switch (env->warps) {
+    case 4: k_world<4><<<env->world_grid, 4 * 32, env->world_smem, stream>>>(*dv, a); break;
+    case 16: k_world<16><<<env->world_grid, 16 * 32, env->world_smem, stream>>>(*dv, a); break;
+    default: k_world<8><<<env->world_grid, 8 * 32, env->world_smem, stream>>>(*dv, a); break;
+  }
 }
 
 static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) != 0; }
@@ -697,7 +784,7 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
   a.order = env->order;
   a.tile_bytes = env->adj_tile;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), env->stream);
-  k_adjoint<kWorldWarps><<<env->adj_grid, kWorldWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
+  k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
 }
 
 // Recompute `len` steps of the segment starting from segS[0] / segF[0] /
@@ -782,9 +869,85 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
   return launch_check(env, "gd_set_state");
 }
 
+// Time the fused step + observation on the env's current state for each
+// (road cell, CTA size, top-K strategy) and keep the fastest; the state is
+// saved first and restored after every trial and at the end.
 gd_status gd_autotune(gd_env* env) {
   if (!env) return GD_ERR_INVALID_ARG;
-  return GD_OK;
+  if (env->A == 0) return GD_OK;
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  float4* sS = nullptr;
+  uint8_t* sF = nullptr;
+  int* sT = nullptr;
+  uint8_t* sWD = nullptr;
+  float* act = nullptr;
+  cudaError_t e = dev_alloc(env, &sS, A);
+  if (e == cudaSuccess) e = dev_alloc(env, &sF, A);
+  if (e == cudaSuccess) e = dev_alloc(env, &sT, W);
+  if (e == cudaSuccess) e = dev_alloc(env, &sWD, W);
+  if (e == cudaSuccess) e = dev_alloc(env, &act, 2 * A);
+  if (e == cudaSuccess && !env->obs_scratch) e = dev_alloc(env, &env->obs_scratch, A * (size_t)env->F);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto cleanup = [&]() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(env, sS); dev_free(env, sF); dev_free(env, sT); dev_free(env, sWD); dev_free(env, act);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(env, e, "gd_autotune: scratch");
+  }
+  DevEnv& d = env->d;
+  copy_snapshot(env, sS, sF, sT, sWD, d.state, d.flags, d.t, d.world_done);
+  cudaMemsetAsync(act, 0, sizeof(float) * 2 * A, env->stream);
+  const float min_cell = (2.f * env->cfg.obs_radius + 0.01f) / (float)(MAX_ROWS - 2);
+  const float cells[] = {6.f, 8.f, 12.f};
+  const int warps[] = {4, 8, 16};
+  float best_ms = INFINITY, best_cell = env->road_cell;
+  int best_w = env->warps, best_st = d.topk;
+  for (float c : cells) {
+    const float cell = std::max(c, min_cell);
+    if ((e = build_road(env, cell)) != cudaSuccess) break;
+    for (int wp : warps) {
+      env->warps = wp;
+      if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
+      for (int st = 1; st <= 2; ++st) {
+        d.topk = st;
+        float ms = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {
+          copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
+          cudaEventRecord(e0, env->stream);
+          launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
+          cudaEventRecord(e1, env->stream);
+          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          if (rep > 0) ms = std::min(ms, t);
+        }
+        if (e != cudaSuccess) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_cell = cell;
+          best_w = wp;
+          best_st = st;
+        }
+      }
+      if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) {
+    env->warps = best_w;
+    d.topk = best_st;
+    e = build_road(env, best_cell);
+  }
+  copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_autotune");
+  return launch_check(env, "gd_autotune");
 }
 
 gd_status gd_sync(gd_env* env) {

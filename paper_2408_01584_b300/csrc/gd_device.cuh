@@ -49,6 +49,7 @@ struct GridDesc {      // one per world, for the road-point grid and the edge gr
 struct DevEnv {
   int W, A, N, K, P, F, T;
   float R, R2, goal_r, dt, vmax, cpen, opn, smooth_c, agent_cell;
+  int topk;              // road top-K: 1 = bucket rank, 2 = bitonic sort when <= 256 points are in range
   uint32_t cflags;
   const int* agent_off;
   const int* road_off;

@@ -35,7 +35,9 @@ namespace gd {
 constexpr int OBS_NB = 256;        // d^2 buckets
 constexpr int OBS_CAP = 288;       // keys kept per warp (>= GD_MAX_K_ROAD)
 constexpr int OBS_CAND = 768;      // compact list of in-radius positions
+constexpr int BITONIC_MAX = 256;   // strategy 2 sorts at most this many keys
 static_assert(OBS_CAP >= GD_MAX_K_ROAD, "selection capacity must hold K keys");
+static_assert(OBS_CAP >= BITONIC_MAX && OBS_CAND >= BITONIC_MAX, "bitonic keys must fit");
 
 struct ObsWarpSmem {
   unsigned cur[OBS_NB];            // histogram, then scatter cursor
@@ -138,7 +140,7 @@ __device__ __forceinline__ void walk_rows(const ObsWarpSmem& sm, int nrows, int 
 // Road selection of one agent at (ex, ey): the positions of the n_sel <= K
 // nearest in-radius points, in rank order, land in sm.sel; returns n_sel.
 __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, float R2, float ex, float ey,
-                                           ObsWarpSmem& sm, int lane) {
+                                           ObsWarpSmem& sm, int lane, int strategy = 1) {
   if (K == 0) return 0;
   const float binv = (float)OBS_NB / R2;
   const float2* __restrict__ xy = v.xy;
@@ -230,6 +232,38 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   }
   __syncwarp();
   const bool compact = n_in <= OBS_CAND;
+  if (strategy == 2 && n_in <= BITONIC_MAX) {
+    // strategy 2: bitonic sort of all in-radius keys (padded to a power of
+    // two with ~0), ascending; the first n_sel are the selection
+    int m = 1;
+    while (m < n_in) m <<= 1;
+    for (int k = lane; k < m; k += WARP) {
+      unsigned long long key = ~0ull;
+      if (k < n_in) {
+        const unsigned p = sm.cand[k];
+        const float2 q = xy[p];
+        key = road_key(dist2(q.x - ex, q.y - ey), meta[p] & 0x7fffu, p);
+      }
+      sm.u.keys[k] = key;
+    }
+    __syncwarp();
+    for (int size = 2; size <= m; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = lane; t < (m >> 1); t += WARP) {
+          const int i = (t / stride) * (2 * stride) + (t % stride), j = i + stride;
+          const unsigned long long x = sm.u.keys[i], y = sm.u.keys[j];
+          if ((x > y) == ((i & size) == 0)) {
+            sm.u.keys[i] = y;
+            sm.u.keys[j] = x;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int r = lane; r < n_sel; r += WARP) sm.sel[r] = (unsigned short)(sm.u.keys[r] & 0xffffu);
+    __syncwarp();
+    return n_sel;
+  }
   // Calls fn(p, d2) for every in-radius point, from the compact list when
   // it holds them all, else by walking the rows again.
   auto for_each_in_radius = [&](auto&& fn) {
@@ -443,7 +477,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     }
     const int np = select_partners(v, li, e.P, e.R2, st.x, st.y, sm, lane);
     write_partners<LOSS>(v, e.P, np, st.x, st.y, c, s, sm, lane, row + 2, pidx, LOSS ? w + 8 : nullptr, acc);
-    const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane);
+    const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
     write_road<LOSS>(v, e.K, nroad, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx,
                      LOSS ? w + 8 + 8 * e.P : nullptr, acc);
   }

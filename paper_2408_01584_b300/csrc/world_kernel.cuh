@@ -95,7 +95,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 // Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents][ObsWarpSmem x WARPS]
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(wsm);
   unsigned char* tile = wsm + 128;
@@ -132,14 +132,18 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
       tma_load_1d(tile, gblock, block, bar);
     }
     if (tid == 0) s_next = WARPS;
-    WorldView v;
-    v.state = ag.st;
-    v.stat = ag.sc;
-    v.cs = ag.cs;
-    v.flags = ag.fl;
-    v.n = n;
-    road_block(use_tile ? tile : gblock, nr, v);
-    v.g = g;
+    // Two views of the world: one on the shared-memory tile, one on the
+    // global road block.  Each use site picks one with a uniform branch, so
+    // the shared path compiles to shared-memory accesses.
+    WorldView vt, vg;
+    vt.state = vg.state = ag.st;
+    vt.stat = vg.stat = ag.sc;
+    vt.cs = vg.cs = ag.cs;
+    vt.flags = vg.flags = ag.fl;
+    vt.n = vg.n = n;
+    vt.g = vg.g = g;
+    road_block(tile, nr, vt);
+    road_block(gblock, nr, vg);
     bool tile_ready = !use_tile;
     // every thread waits for the tile (bounded); false = give up this CTA
     auto wait_tile = [&]() -> bool {
@@ -249,7 +253,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
         }
         const float4 s = ag.st[li];
         const float4 sc = ag.sc[li];
-        const bool off = offroad_from_block(v, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane);
+        const bool off = use_tile
+                             ? offroad_from_block(vt, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane)
+                             : offroad_from_block(vg, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane);
         if (lane == 0) ag.offr[li] = off ? 1 : 0;
       }
       __syncthreads();
@@ -307,7 +313,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
         int32_t* ridx = a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr;
         int32_t* pidx = a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr;
         if (a.ell) {
-          const float dot = observe_agent<true>(e, v, li, orow, ridx, pidx, osm, lane, a.obs_w);
+          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, a.obs_w)
+                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, a.obs_w);
           if (lane == 0) {
             float rs = 0.f;
             if (a.do_step && ag.act0[li]) {
@@ -317,8 +324,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_world(DevEnv e, FusedArgs a) {
             }
             a.ell[i] = fmaf(a.reward_w, rs, dot);
           }
+        } else if (use_tile) {
+          observe_agent<false>(e, vt, li, orow, ridx, pidx, osm, lane);
         } else {
-          observe_agent<false>(e, v, li, orow, ridx, pidx, osm, lane);
+          observe_agent<false>(e, vg, li, orow, ridx, pidx, osm, lane);
         }
         int nx = 0;
         if (lane == 0) nx = atomicAdd(&s_next, 1);

@@ -59,7 +59,8 @@ class gd_scene_batch(C.Structure):
 class gd_info(C.Structure):
     _fields_ = [("num_worlds", C.c_int32), ("num_agents", C.c_int32), ("num_road", C.c_int32),
                 ("feat", C.c_int32), ("max_agents_per_world", C.c_int32), ("k_road", C.c_int32),
-                ("n_partners", C.c_int32), ("episode_len", C.c_int32), ("device_bytes", C.c_int64)]
+                ("n_partners", C.c_int32), ("episode_len", C.c_int32), ("device_bytes", C.c_int64),
+                ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32)]
 
 
 _lib = None

@@ -108,3 +108,41 @@ def test_graph_rollout_replay_and_full_size_agreement():
         np.testing.assert_array_equal(_np(rew), plain["reward"])
         s, f, _ = env.get_state()
         np.testing.assert_array_equal(_np(s), plain["state"])
+
+
+@pytest.mark.parametrize("cell,block,topk", [(6.0, 128, 2), (8.0, 512, 1), (12.0, 256, 2), (10.0, 512, 2)])
+def test_tuning_choices_do_not_change_results(cell, block, topk):
+    # road grid cell, CTA size and top-K strategy are performance choices only
+    sc = small_scene(seed=12)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = scenes.make_actions(10, sc.num_agents, 12)
+    plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
+    bat = _rollout(sc, _batched(ocfg, road_cell=cell, block_size=block, topk_strategy=topk), acts, "fused")
+    for k in plain:
+        np.testing.assert_array_equal(plain[k], bat[k], err_msg=k)
+
+
+def test_autotune_then_rollout_matches_plain():
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("plain_4x8", 1)
+    ocfg = workload_config("plain_4x8")
+    acts = scenes.make_actions(ocfg.episode_len, sc.num_agents, 1)
+    plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
+    env = gd.Env(sc, **_batched(ocfg))
+    before = [_np(x).copy() for x in env.get_state()]
+    gd.gd_autotune(env.h)
+    after = [_np(x) for x in env.get_state()]
+    for b, a in zip(before, after):
+        np.testing.assert_array_equal(b, a)           # the tuner leaves the state as it was
+    info = gd.gd_get_info(env.h)
+    assert info.block_size in (128, 256, 512) and info.topk_strategy in (1, 2) and info.road_cell >= 3.3
+    a = torch.from_numpy(acts).cuda().contiguous()
+    obs = torch.zeros(ocfg.episode_len, env.A, env.F, device="cuda")
+    rew = torch.zeros(ocfg.episode_len, env.A, device="cuda")
+    dn = torch.zeros(ocfg.episode_len, env.A, dtype=torch.uint8, device="cuda")
+    gd.gd_rollout(env.h, ocfg.episode_len, a, obs, True, rew, dn)
+    env.sync()
+    np.testing.assert_array_equal(_np(obs), plain["obs"])
+    np.testing.assert_array_equal(_np(rew), plain["reward"])
+    print("autotuned:", info.block_size, info.road_cell, info.topk_strategy)
