@@ -194,6 +194,19 @@ def cpu_baseline(workload, seed, budget_s=12.0):
                       f"step+observe, float64 brute force, OpenMP over worlds, {dt:.1f} s"}
 
 
+def whole_job_rate(units_per_rank, local_ms, world, device):
+    """Max time over ranks (ms) and whole-job throughput: the units every
+    rank processed divided by that time (weak scaling, no data exchange)."""
+    t = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return t, units_per_rank * world / (t / 1e3)
+
+
 def _time_rollouts(run, n, stream, flush):
     """Time n calls of run() with CUDA events on `stream`; L2 flushed (256 MB
     write) before each, outside the timed interval.  Returns ms per call."""
@@ -385,11 +398,7 @@ def run_ours(args, rank, world):
         with Clocks(dev) as clk:
             ms = _time_rollouts(batched_rollout, args.steps, stream, flush)
         gd.gd_sync(env_b.h)
-        total_ms = sum(ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms, _ = whole_job_rate(T * A * args.steps, sum(ms), world, dev)
         plain_ms = _time_rollouts(plain_rollout, max(2, min(args.steps, 5)), stream, flush)
         gd.gd_sync(env_p.h)
 

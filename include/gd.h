@@ -233,7 +233,15 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * next call. */
 gd_status gd_autotune(gd_env* env);
 
-/* Block until the env's stream is idle and report any sticky device error. */
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * block that waits, bounded by about wait_us microseconds (1..1,000,000),
+ * on a barrier phase nothing completes, and records the timeout in the
+ * env's sticky error word exactly as the fused kernel's bounded copy waits
+ * do; the next gd_sync returns GD_ERR_TIMEOUT.  No GPU fault is involved. */
+gd_status gd_selftest_timeout(gd_env* env, int32_t wait_us);
+
+/* Block until the env's stream is idle and report any sticky device error
+ * (and clear it). */
 gd_status gd_sync(gd_env* env);
 
 const char* gd_last_error(const gd_env* env);

@@ -950,6 +950,33 @@ gd_status gd_autotune(gd_env* env) {
   return launch_check(env, "gd_autotune");
 }
 
+// Failure-detection self-test: one CTA waits on an mbarrier phase that
+// nothing completes, for at most ~wait_us microseconds of its own clock, then
+// records ERR_TIMEOUT in the env's sticky error word and returns.  No copy
+// is in flight, so leaving the barrier pending is harmless.
+__global__ void k_selftest_wait(unsigned* err, long long limit_cycles) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const long long t0 = clock64();
+  bool done = false;
+  while (!(done = mbar_try_wait(&bar, 0))) {
+    if (clock64() - t0 > limit_cycles) break;
+  }
+  if (!done && threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+}
+
+gd_status gd_selftest_timeout(gd_env* env, int32_t wait_us) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (wait_us < 1 || wait_us > 1000000) return fail(env, GD_ERR_INVALID_ARG, "wait_us must be in 1..1000000");
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  const long long cycles = (long long)std::max(khz, 1000000) * wait_us / 1000;
+  k_selftest_wait<<<1, 32, 0, env->stream>>>(env->d.err, cycles);
+  return launch_check(env, "gd_selftest_timeout");
+}
+
 gd_status gd_sync(gd_env* env) {
   if (!env) return GD_ERR_INVALID_ARG;
   cudaError_t e = cudaMemcpyAsync(env->h_err, env->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, env->stream);

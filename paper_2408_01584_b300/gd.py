@@ -31,7 +31,7 @@ GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD = 1, 2, 4, 8
 SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_reset", "gd_step", "gd_observe",
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
-           "gd_rollout_objective")
+           "gd_rollout_objective", "gd_selftest_timeout")
 
 
 class GdError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_rollout.argtypes = [vp, i32, vp, vp, i32, vp, vp]
     lib.gd_rollout_backward.argtypes = [vp, vp, f32, vp, vp, vp]
     lib.gd_rollout_objective.argtypes = [vp, i32, vp, vp, f32, vp, vp]
+    lib.gd_selftest_timeout.argtypes = [vp, i32]
     lib.gd_step_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gd_get_state.argtypes = [vp, vp, vp, vp]
     lib.gd_set_state.argtypes = [vp, vp, vp, vp]
@@ -222,6 +223,11 @@ def gd_set_state(env, state=None, flags=None, t=None):
 def gd_autotune(env):
     lib = load_library()
     _check(lib, env, lib.gd_autotune(env))
+
+
+def gd_selftest_timeout(env, wait_us):
+    lib = load_library()
+    _check(lib, env, lib.gd_selftest_timeout(env, int(wait_us)))
 
 
 def gd_sync(env):
