@@ -21,10 +21,15 @@
 //   * observation: every agent and road point within a fixed radius, in the
 //     agent's relative frame (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1),
 //     truncated to the K / P nearest;
-//   * smooth goal reward (not in the paper): r_s = -(sqrt(d^2 + c^2) - c).
+//   * smooth goal reward (not in the paper): r_s = -(sqrt(d^2 + c^2) - c);
+//   * LiDAR / view cone: rays cast from the agent over the other agents'
+//     boxes and the road edges, in a full circle or a cone turned by a head
+//     rotation (Sec. 3.2 "Sensor modalities"; 3000 rays, 360 or 120 degrees
+//     in Fig. 1).
 //
 // Selection is a full std::sort of every candidate by (d^2, index); collision
-// tests every pair and every road-edge segment.  T = double for parity,
+// tests every pair and every road-edge segment; every LiDAR ray is tested
+// against every box and every road-edge segment of its world.  T = double for parity,
 // T = float to measure single-precision rounding.
 //
 // Parity pins live in the test suite (closed forms of App. B, polygon
@@ -335,6 +340,131 @@ void observe(const Env<T>& e, O* obs, int32_t* road_idx, int32_t* partner_idx) {
   }
 }
 
+// ---- LiDAR / view cone (Sec. 3.2 "Sensor modalities") ---------------------
+// Readings where the paper is silent:
+//   * ray k of n leaves the agent's centre at angle
+//       phi_k = theta + head - fov/2 + (k + 1/2) fov / n,
+//     fov = 2 pi for the LiDAR, a smaller cone for the human-like view;
+//     head is the head-rotation action (rad, relative to the heading);
+//   * rays stop at the first point, 0 <= t <= R (the observation radius),
+//     that lies in the closed box of another agent still in the scene or on
+//     a road-edge segment (lane centre lines are markings, not obstacles);
+//   * depth = that t and class 1 (agent) or 2 (road edge), agent first at
+//     equal t; nothing met: depth R, class 0;  an agent that is done sees
+//     nothing (depth 0, class 0).
+// Per ray the oracle also reports how fragile the result is: a candidate
+// whose hit/miss decision is within `band` metres of flipping (near a
+// segment end, a box corner, t = 0 or t = R) at a distance not beyond the
+// nearest hit, or an agent hit and an edge hit within `band` of each other,
+// marks the ray fragile; sens = |d depth / d phi| of the nearest hit.
+
+// Ray p + t u, 0 <= t <= R, against the closed box b (slab method in the
+// box frame).  Returns true on a hit (t = 0 when p is inside); `tc` is the
+// hit distance (or where the near-miss would hit), `margin` the metres by
+// which the hit/miss decision could flip (hit: the smallest slack of its
+// conditions; miss: the largest violation) and `sens` = |dt/dphi|.
+template <typename T>
+bool ray_box(T px, T py, T ux, T uy, T R, const Box<T>& b, T& tc, T& margin, T& sens) {
+  const T dx = px - b.cx, dy = py - b.cy;
+  const T o[2] = {b.ca * dx + b.sa * dy, -b.sa * dx + b.ca * dy};
+  const T v[2] = {b.ca * ux + b.sa * uy, -b.sa * ux + b.ca * uy};
+  const T h[2] = {b.hl, b.hw};
+  T lo = -INFINITY, hi = INFINITY;
+  int near_axis = -1;
+  sens = 0;
+  for (int a = 0; a < 2; ++a) {
+    if (v[a] == 0) {
+      if (std::fabs(o[a]) > h[a]) { tc = INFINITY; margin = std::fabs(o[a]) - h[a]; return false; }
+      continue;
+    }
+    T t1 = (-h[a] - o[a]) / v[a], t2 = (h[a] - o[a]) / v[a];
+    if (t1 > t2) std::swap(t1, t2);
+    if (t1 > lo) { lo = t1; near_axis = a; }
+    hi = std::min(hi, t2);
+  }
+  tc = std::max(lo, (T)0);
+  const bool hit = lo <= hi && hi >= 0 && tc <= R;
+  if (hit) {
+    margin = std::min(hi - lo, R - tc);
+    if (lo < 0) margin = std::min(margin, hi);
+    if (lo > 0 && near_axis >= 0) sens = lo * std::fabs(v[1 - near_axis] / v[near_axis]);
+  } else {
+    margin = std::max(std::max(lo - hi, -hi), tc - R);
+  }
+  return hit;
+}
+
+// Ray p + t u, 0 <= t <= R, against the segment a-b: p + t u = a + s (b - a)
+// by Cramer's rule; a hit needs 0 <= s <= 1.  Outputs as for ray_box.
+template <typename T>
+bool ray_seg(T px, T py, T ux, T uy, T R, T ax, T ay, T bx, T by, T& tc, T& margin, T& sens) {
+  const T dx = bx - ax, dy = by - ay;
+  const T wx = ax - px, wy = ay - py;
+  const T den = ux * dy - uy * dx;
+  if (den == 0) { tc = INFINITY; margin = INFINITY; sens = 0; return false; }
+  const T t = (wx * dy - wy * dx) / den;
+  const T s = (wx * uy - wy * ux) / den;
+  const T len = std::sqrt(dx * dx + dy * dy);
+  tc = t;
+  sens = std::fabs(t * (ux * dx + uy * dy) / den);
+  const bool hit = s >= 0 && s <= 1 && t >= 0 && t <= R;
+  if (hit)
+    margin = std::min(std::min(s * len, (1 - s) * len), std::min(t, R - t));
+  else
+    margin = std::max(std::max(-s * len, (s - 1) * len), std::max(-t, t - R));
+  return hit;
+}
+
+template <typename T>
+void lidar(const Env<T>& e, int n, double fov, const float* head, const int32_t* sel, int nsel, double band,
+           double* depth, uint8_t* cls, uint8_t* fragile, double* sens_out) {
+  const T R = (T)e.cfg.obs_radius;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int q = 0; q < nsel; ++q) {
+    const int i = sel ? sel[q] : q;
+    const int w = int(std::upper_bound(e.agent_off.begin(), e.agent_off.end(), i) - e.agent_off.begin()) - 1;
+    const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
+    for (int k = 0; k < n; ++k) {
+      const long o = (long)q * n + k;
+      depth[o] = 0; cls[o] = 0; fragile[o] = 0; sens_out[o] = 0;
+    }
+    if (e.flags[i] & F_DONE) continue;
+    const T px = e.x[i], py = e.y[i];
+    for (int k = 0; k < n; ++k) {
+      const T phi = e.th[i] + (T)(head ? head[i] : 0.f) + (T)(-fov / 2 + (k + 0.5) * fov / n);
+      const T ux = std::cos(phi), uy = std::sin(phi);
+      // nearest hit of each class, then the winner
+      T best[3] = {R, INFINITY, INFINITY}, bsens[3] = {0, 0, 0};
+      T close_t = INFINITY;     // nearest candidate whose decision is within the band
+      for (int j = a0; j < a1; ++j) {
+        if (j == i || (e.flags[j] & F_DONE)) continue;
+        T t, m, sn;
+        const bool hit = ray_box(px, py, ux, uy, R, agent_box(e, j), t, m, sn);
+        if (m < (T)band + (T)1e-6 * sn) close_t = std::min(close_t, t);
+        if (hit && t < best[1]) { best[1] = t; bsens[1] = sn; }
+      }
+      for (auto& sg : e.segs[w]) {
+        T t, m, sn;
+        const bool hit = ray_seg(px, py, ux, uy, R, e.rx[sg.first], e.ry[sg.first], e.rx[sg.second],
+                                 e.ry[sg.second], t, m, sn);
+        if (m < (T)band + (T)1e-6 * sn) close_t = std::min(close_t, t);
+        if (hit && t < best[2]) { best[2] = t; bsens[2] = sn; }
+      }
+      int c = 0;
+      T d = R;
+      if (best[1] <= R && best[1] <= best[2]) { c = 1; d = best[1]; }
+      else if (best[2] <= R) { c = 2; d = best[2]; }
+      bool frag = best[1] <= R && best[2] <= R && std::fabs(best[1] - best[2]) <= (T)band;
+      frag = frag || close_t <= d + (T)band;
+      const long o = (long)q * n + k;
+      depth[o] = (double)d;
+      cls[o] = (uint8_t)c;
+      fragile[o] = frag ? 1 : 0;
+      sens_out[o] = (double)bsens[c];
+    }
+  }
+}
+
 struct Handle {
   int precision;   // 64 or 32
   void* env;
@@ -520,6 +650,16 @@ double or_box_box(const double* p, const double* q) {
 double or_box_seg(const double* p, const double* s) {
   Box<double> a{p[0], p[1], std::cos(p[2]), std::sin(p[2]), p[3] / 2, p[4] / 2};
   return box_seg_pen(a, s[0], s[1], s[2], s[3]);
+}
+
+// LiDAR / view-cone scan (readings above lidar()) of the agents listed in
+// sel (int32 [nsel], global indices; NULL = all agents, nsel = A): n rays
+// over fov radians about theta + head[i] (head float [A] or NULL = 0).
+// Outputs [nsel, n]: depth double, cls uint8, fragile uint8, sens double.
+void or_lidar(void* hv, int32_t n, double fov, const float* head, const int32_t* sel, int32_t nsel, double band,
+              double* depth, uint8_t* cls, uint8_t* fragile, double* sens) {
+  auto* h = static_cast<Handle*>(hv);
+  OR_DISPATCH(h, lidar(e, n, fov, head, sel, nsel, band, depth, cls, fragile, sens));
 }
 
 int or_num_threads(void) {

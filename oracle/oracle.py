@@ -63,6 +63,7 @@ def load_oracle():
         lib.or_box_box.argtypes = [vp, vp]
         lib.or_box_seg.restype = C.c_double
         lib.or_box_seg.argtypes = [vp, vp]
+        lib.or_lidar.argtypes = [vp, i32, C.c_double, vp, vp, i32, C.c_double, vp, vp, vp, vp]
         lib.or_num_threads.restype = C.c_int
         _lib = lib
     return _lib
@@ -165,6 +166,21 @@ class Oracle:
         pidx = np.zeros((self.A, cfg.n_partners), np.int32)
         self.lib.or_observe64(self.h, _p(obs), _p(ridx), _p(pidx))
         return obs, ridx, pidx
+
+    def lidar(self, n_rays: int, fov: float = 2 * np.pi, head=None, agents=None, band: float = 2e-4):
+        """LiDAR / view-cone scan (readings in oracle.cpp, above lidar()):
+        for the agents `agents` (global indices; None = all) returns
+        depth float64 [n, n_rays], cls uint8 (0 none, 1 agent, 2 road edge),
+        fragile uint8 (1 = a decision within `band` m of flipping) and
+        sens = |d depth / d ray angle|."""
+        sel = None if agents is None else _c(agents, np.int32)
+        n = self.A if sel is None else len(sel)
+        hd = None if head is None else _c(head, np.float32).reshape(self.A)
+        out = dict(depth=np.zeros((n, n_rays)), cls=np.zeros((n, n_rays), np.uint8),
+                   fragile=np.zeros((n, n_rays), np.uint8), sens=np.zeros((n, n_rays)))
+        self.lib.or_lidar(self.h, int(n_rays), float(fov), _p(hd), _p(sel), n, float(band),
+                          _p(out["depth"]), _p(out["cls"]), _p(out["fragile"]), _p(out["sens"]))
+        return out
 
     def road_point(self, i: int, j: int):
         f = np.zeros(4, np.float32)
