@@ -14,6 +14,10 @@
  *               points and P nearest other agents within the observation
  *               radius (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1);
  *   gd_step_observe, gd_rollout   the same, fused, and whole episodes;
+ *   gd_observe_lidar, gd_step_observe_lidar, gd_rollout_lidar   the LiDAR
+ *               and view-cone observations (Sec. 3.2 "Sensor modalities":
+ *               rays cast against bounding boxes and road edges, all around
+ *               or in a cone turned by a head-rotation action);
  *   gd_rollout_backward / gd_step_backward   adjoint of the dynamics, the
  *               ego-frame observation and a smooth goal-distance reward (the
  *               paper has no gradient; this is an extension).
@@ -90,6 +94,7 @@ typedef enum gd_status {
 #define GD_MAX_K_ROAD 256
 #define GD_MAX_PARTNERS 127
 #define GD_MAX_ROAD_PER_WORLD 32767
+#define GD_MAX_LIDAR_RAYS 8192
 
 typedef struct gd_config {
   int32_t k_road;            /* K road slots per observation, 0..GD_MAX_K_ROAD */
@@ -107,6 +112,10 @@ typedef struct gd_config {
   int32_t block_size;        /* threads per block of the observation kernel; 0 = default */
   float road_cell;           /* m, road-point grid cell; 0 = default (8) */
   int32_t topk_strategy;     /* road top-K method: 0 = default, 1 = bucket rank, 2 = bitonic sort */
+  int32_t lidar_rays;        /* rays per agent of the LiDAR observation, 0..GD_MAX_LIDAR_RAYS;
+                                0 = LiDAR not enabled (default); 3000 in Fig. 1 */
+  float lidar_fov;           /* rad, width of the ray fan, in [1e-3, 2 pi]: 2 pi = LiDAR (default),
+                                2 pi / 3 = the 120-degree view cone of Fig. 1 */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -130,6 +139,9 @@ typedef struct gd_info {
   int32_t block_size;                               /* fused-kernel threads per block in use */
   float road_cell;                                  /* road grid cell in use (m) */
   int32_t topk_strategy;                            /* road top-K method in use */
+  int32_t lidar_rays;                               /* rays per agent (0 = LiDAR not enabled) */
+  float lidar_fov;                                  /* rad */
+  int32_t lidar_block_size;                         /* fused LiDAR kernel threads per block in use */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -180,6 +192,43 @@ gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint
 gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step,
                      float* reward, uint8_t* done);
 
+/* LiDAR / view-cone observation of every agent after the last step
+ * (Sec. 3.2 "Sensor modalities"; Fig. 1: 3000 rays over 360 degrees, or
+ * over a 120-degree cone).  Requires lidar_rays > 0 at gd_create.  With
+ * n = lidar_rays and fov = lidar_fov, ray k of agent i leaves the agent's
+ * centre at angle
+ *     theta_i + head[i] - fov/2 + (k + 1/2) fov / n
+ * and stops at the first point at distance 0 <= t <= obs_radius that lies
+ * in the closed box of another agent still in the scene (not done) or on a
+ * road-edge segment (consecutive GD_ROAD_EDGE points of one polyline; lane
+ * centre lines do not block rays).  The ray reports depth = t and class 1
+ * (agent) or 2 (road edge), the agent at equal t; a ray that meets nothing
+ * reports depth = obs_radius, class 0.  An agent inside another box sees
+ * depth 0 on every ray.  Rows of done agents are all zero.  Depths are
+ * float32 (the lowest mantissa bit may be cleared: one unit in the last
+ * place).
+ *   head:  device float [A] head rotation (rad, relative to the heading) or
+ *          NULL = 0; 4-byte aligned
+ *   depth: device float [A, n] (m); 4-byte aligned (16 for the fastest
+ *          stores when n is a multiple of 4)
+ *   cls:   device uint8 [A, n] or NULL
+ * Errors: GD_ERR_STATE if the env has no LiDAR, GD_ERR_INVALID_ARG for NULL
+ * or misaligned pointers. */
+gd_status gd_observe_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls);
+
+/* gd_step followed by gd_observe_lidar; one fused launch when GD_BATCHED is
+ * set.  Arguments as for gd_step and gd_observe_lidar. */
+gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* head, float* reward, uint8_t* done,
+                                uint8_t* world_done, float* depth, uint8_t* cls);
+
+/* T = steps steps of gd_step_observe_lidar (a captured CUDA graph when
+ * GD_BATCHED is set).  actions: device float [T,A,2]; head: device float
+ * [T,A] or NULL; depth / cls: [A,n] overwritten every step if
+ * obs_per_step == 0, else [T,A,n] (cls may be NULL); reward: float [T,A]
+ * or NULL; done: uint8 [T,A] or NULL. */
+gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, const float* head, float* depth,
+                           uint8_t* cls, int32_t obs_per_step, float* reward, uint8_t* done);
+
 /* Differentiable rollout (an extension; the paper has no gradient).  Runs
  * `steps` fused steps from the current state, like gd_rollout, and writes
  * the per-step objective terms
@@ -227,7 +276,9 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * from the current state for every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads and top-K strategy in {1 bucket rank, 2 bitonic
  * sort when at most 256 points are in range}, and keeps the fastest
- * (reported by gd_get_info).  Every combination gives the same results.
+ * (reported by gd_get_info).  With LiDAR enabled it then times the fused
+ * step + LiDAR scan with 128 and 256 threads per block and keeps the faster
+ * (a scratch of A * lidar_rays * 5 bytes is held during the call).  Every combination gives the same results.
  * Synchronises the env's stream; the simulation state is unchanged
  * afterwards.  A captured gd_rollout graph is dropped and re-captured on the
  * next call. */

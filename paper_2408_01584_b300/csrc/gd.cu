@@ -12,6 +12,7 @@
 #include "observe_kernel.cuh"
 #include "step_kernels.cuh"
 #include "world_kernel.cuh"
+#include "lidar_kernel.cuh"
 #include "adjoint_kernel.cuh"
 
 using namespace gd;
@@ -27,6 +28,8 @@ constexpr int kAdjWarps = 8;
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
 constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(ObsWarpSmem);
+// Fixed shared memory of the fused LiDAR kernel besides the road tile.
+inline size_t lidar_fixed_smem(int warps, int n) { return 128 + sizeof(FusedAgents) + warps * lidar_warp_bytes(n); }
 
 }  // namespace
 
@@ -79,6 +82,18 @@ struct gd_env {
   int adj_grid = 0;
   const float* diff_actions = nullptr;   // actions of the last objective rollout
   int diff_steps = 0;
+  // LiDAR / view cone
+  int lidar_n = 0;              // rays per agent (0 = not enabled)
+  LidarFan fan{};
+  float2* ray_dirs = nullptr;   // [n] (cos, sin) of the ray angles in the sensor frame
+  int lidar_obs_warps = 8;      // per-stage k_lidar CTA size (warps)
+  int lw_warps = 8;             // fused LiDAR kernel CTA size (4 or 8 warps)
+  int lw_tile = 0;              // its road tile (bytes)
+  size_t lw_smem = 0;
+  int lw_grid = 0;
+  cudaGraphExec_t lgraph = nullptr;   // captured LiDAR rollout
+  const void* lg_key[8] = {};
+  int lg_steps = -1;
 };
 
 namespace {
@@ -169,6 +184,24 @@ static cudaError_t shape_world(gd_env* env, size_t max_block, int smem_sm, int s
   return cudaSuccess;
 }
 
+template <int WARPS>
+static cudaError_t shape_world_lidar(gd_env* env, size_t max_block, int smem_sm, int smem_blk, int nsm) {
+  const long fixed = (long)lidar_fixed_smem(WARPS, env->lidar_n);
+  const long two = ((long)smem_sm / 2 - 2048 - fixed) & ~15L;
+  const long one = ((long)smem_blk - 1024 - fixed) & ~15L;
+  const long cap = ((long)max_block <= two) ? (long)max_block : std::min<long>(one, (long)max_block);
+  env->lw_tile = (int)std::max(16L, cap);
+  env->lw_smem = (size_t)fixed + (size_t)env->lw_tile;
+  cudaError_t e = cudaFuncSetAttribute(k_world<WARPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)env->lw_smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<WARPS, true>, WARPS * 32, env->lw_smem);
+  if (e != cudaSuccess) return e;
+  env->lw_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
+  return cudaSuccess;
+}
+
 // Tile sizes, shared memory and grid of the fused (and adjoint) kernel for
 // the current road blocks and CTA size.
 static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
@@ -184,6 +217,13 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     default: env->warps = 8; e = shape_world<8>(env, max_block, smem_sm, smem_blk, nsm); break;
   }
   if (e != cudaSuccess) return e;
+  if (env->lidar_n > 0) {
+    // the tile shrinks first; if even a 16-byte tile does not fit, fewer warps
+    if (env->lw_warps == 8 && lidar_fixed_smem(8, env->lidar_n) + 16 + 1024 > (size_t)smem_blk) env->lw_warps = 4;
+    e = env->lw_warps == 4 ? shape_world_lidar<4>(env, max_block, smem_sm, smem_blk, nsm)
+                           : shape_world_lidar<8>(env, max_block, smem_sm, smem_blk, nsm);
+    if (e != cudaSuccess) return e;
+  }
   if (env->cfg.flags & GD_DIFFERENTIABLE) {
     const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
     const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
@@ -278,6 +318,10 @@ static cudaError_t build_road(gd_env* env, float cell) {
     cudaGraphExecDestroy(env->graph);
     env->graph = nullptr;
   }
+  if (env->lgraph) {
+    cudaGraphExecDestroy(env->lgraph);
+    env->lgraph = nullptr;
+  }
   return cudaStreamSynchronize(env->stream);
 }
 
@@ -303,6 +347,8 @@ void gd_default_config(gd_config* c) {
   c->block_size = 0;
   c->road_cell = 0.f;
   c->topk_strategy = 0;
+  c->lidar_rays = 0;
+  c->lidar_fov = 6.28318530717958647692f;
 }
 
 const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
@@ -311,11 +357,14 @@ gd_status gd_destroy(gd_env* env) {
   if (!env) return GD_OK;
   cudaStreamSynchronize(env->stream);
   if (env->graph) cudaGraphExecDestroy(env->graph);
+  if (env->lgraph) cudaGraphExecDestroy(env->lgraph);
   for (void* p : env->allocs) cudaFree(p);
   if (env->h_err) cudaFreeHost(env->h_err);
   delete env;
   return GD_OK;
 }
+
+static inline unsigned blocks_for_host(long n, int per) { return (unsigned)std::max<long>(1, (n + per - 1) / per); }
 
 static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
   if (!c || !s) return fail(nullptr, GD_ERR_INVALID_ARG, "config and scene must not be NULL");
@@ -336,6 +385,10 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
   if (c->block_size != 0 && c->block_size != 128 && c->block_size != 256 && c->block_size != 512)
     return fail(nullptr, GD_ERR_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
   if (c->topk_strategy < 0 || c->topk_strategy > 2) return fail(nullptr, GD_ERR_INVALID_ARG, "topk_strategy must be 0..2");
+  if (c->lidar_rays < 0 || c->lidar_rays > GD_MAX_LIDAR_RAYS)
+    return fail(nullptr, GD_ERR_CAPACITY, "lidar_rays outside 0..GD_MAX_LIDAR_RAYS");
+  if (!(c->lidar_fov >= 1e-3f) || !(c->lidar_fov <= 6.2831855f))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_fov must be in [1e-3, 2 pi]");
   if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
   const int W = s->num_worlds;
@@ -519,6 +572,26 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
   env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
+  if (cfg->lidar_rays > 0) {
+    const int n = cfg->lidar_rays;
+    const double fov = (double)cfg->lidar_fov;
+    env->lidar_n = n;
+    env->fan.n = n;
+    env->fan.b0 = (float)(-0.5 * fov + 0.5 * fov / n);
+    env->fan.inv_step = (float)(n / fov);
+    env->fan.wrap_steps = (float)(6.283185307179586 * n / fov);
+    GD_TRY(dev_alloc(env, &env->ray_dirs, (size_t)n));
+    k_lidar_dirs<<<blocks_for_host(n, 256), 256, 0, env->stream>>>(env->ray_dirs, n, fov);
+    GD_TRY(cudaGetLastError());
+    int dev = 0, smem_blk = 0;
+    GD_TRY(cudaGetDevice(&dev));
+    GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    env->lidar_obs_warps = (8 * lidar_warp_bytes(n) <= (size_t)smem_blk) ? 8 : 4;
+    if (env->lidar_obs_warps == 8)
+      GD_TRY(cudaFuncSetAttribute(k_lidar<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * lidar_warp_bytes(n))));
+    else
+      GD_TRY(cudaFuncSetAttribute(k_lidar<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * lidar_warp_bytes(n))));
+  }
   GD_TRY(build_road(env, rcell));
   GD_TRY(cudaStreamSynchronize(env->stream));
 #undef GD_TRY
@@ -540,6 +613,9 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->block_size = env->warps * 32;
   info->road_cell = env->road_cell;
   info->topk_strategy = env->d.topk;
+  info->lidar_rays = env->lidar_n;
+  info->lidar_fov = env->cfg.lidar_fov;
+  info->lidar_block_size = env->lw_warps * 32;
   return GD_OK;
 }
 
@@ -591,7 +667,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          float reward_w = 0.f, float* ell = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
-  FusedArgs a;
+  FusedArgs a{};
   a.actions = reinterpret_cast<const float2*>(actions);
   a.reward = reward;
   a.done = done;
@@ -612,6 +688,50 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
     case 16: k_world<16><<<env->world_grid, 16 * 32, env->world_smem, stream>>>(*dv, a); break;
     default: k_world<8><<<env->world_grid, 8 * 32, env->world_smem, stream>>>(*dv, a); break;
   }
+}
+
+static LidarArgs lidar_args(const gd_env* env, const float* head, float* depth, uint8_t* cls) {
+  LidarArgs la{};
+  la.head = head;
+  la.depth = depth;
+  la.cls = cls;
+  la.dirs = env->ray_dirs;
+  la.fan = env->fan;
+  la.warp_bytes = (int)lidar_warp_bytes(env->lidar_n);
+  return la;
+}
+
+// Per-stage LiDAR scan: one warp per agent, everything from global memory.
+static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls) {
+  const LidarArgs la = lidar_args(env, head, depth, cls);
+  const size_t wb = (size_t)la.warp_bytes;
+  if (env->lidar_obs_warps == 8)
+    k_lidar<8><<<blocks_for(env->A, 8), 8 * 32, 8 * wb, env->stream>>>(env->d, la);
+  else
+    k_lidar<4><<<blocks_for(env->A, 4), 4 * 32, 4 * wb, env->stream>>>(env->d, la);
+}
+
+// Fused LiDAR form: one persistent launch of the step (if do_step) and the
+// LiDAR scan of every world.
+static void launch_world_lidar(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
+                               const float* head, float* depth, uint8_t* cls, int do_step,
+                               cudaStream_t stream = nullptr) {
+  if (!stream) stream = env->stream;
+  FusedArgs a{};
+  a.actions = reinterpret_cast<const float2*>(actions);
+  a.reward = reward;
+  a.done = done;
+  a.world_done = world_done;
+  a.counter = env->counter;
+  a.order = env->order;
+  a.tile_bytes = env->lw_tile;
+  a.do_step = do_step;
+  a.lidar = lidar_args(env, head, depth, cls);
+  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
+  if (env->lw_warps == 4)
+    k_world<4, true><<<env->lw_grid, 4 * 32, env->lw_smem, stream>>>(env->d, a);
+  else
+    k_world<8, true><<<env->lw_grid, 8 * 32, env->lw_smem, stream>>>(env->d, a);
 }
 
 static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) != 0; }
@@ -710,6 +830,107 @@ gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* ob
   }
   cudaError_t e = cudaGraphLaunch(env->graph, env->stream);
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout: graph launch");
+  return GD_OK;
+}
+
+// ---- LiDAR / view cone -------------------------------------------------------
+
+static gd_status need_lidar(gd_env* env, const char* what) {
+  if (env->lidar_n <= 0) return fail(env, GD_ERR_STATE, std::string(what) + ": the env was created with lidar_rays = 0");
+  return GD_OK;
+}
+
+static bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
+
+gd_status gd_observe_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_lidar(env, "gd_observe_lidar");
+  if (st != GD_OK) return st;
+  if (!depth && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "depth must not be NULL");
+  if (!aligned4(depth) || !aligned4(head)) return fail(env, GD_ERR_INVALID_ARG, "depth and head must be 4-byte aligned");
+  if (env->A == 0) return GD_OK;
+  if (batched(env)) launch_world_lidar(env, nullptr, nullptr, nullptr, nullptr, head, depth, cls, 0);
+  else launch_lidar(env, head, depth, cls);
+  return launch_check(env, "gd_observe_lidar");
+}
+
+gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* head, float* reward, uint8_t* done,
+                                uint8_t* world_done, float* depth, uint8_t* cls) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (batched(env)) {
+    gd_status st = need_lidar(env, "gd_step_observe_lidar");
+    if (st != GD_OK) return st;
+    if ((!actions || !depth) && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions and depth must not be NULL");
+    if (((uintptr_t)actions & 7u) || !aligned4(depth) || !aligned4(head))
+      return fail(env, GD_ERR_INVALID_ARG, "actions must be 8-byte, depth and head 4-byte aligned");
+    launch_world_lidar(env, actions, reward, done, world_done, head, depth, cls, 1);
+    return launch_check(env, "gd_step_observe_lidar");
+  }
+  gd_status st = need_lidar(env, "gd_step_observe_lidar");
+  if (st != GD_OK) return st;
+  st = gd_step(env, actions, reward, done, world_done);
+  if (st != GD_OK) return st;
+  return gd_observe_lidar(env, head, depth, cls);
+}
+
+gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, const float* head, float* depth,
+                           uint8_t* cls, int32_t obs_per_step, float* reward, uint8_t* done) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_lidar(env, "gd_rollout_lidar");
+  if (st != GD_OK) return st;
+  if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
+  if (steps == 0 || env->A == 0) return GD_OK;
+  if (!actions || !depth) return fail(env, GD_ERR_INVALID_ARG, "actions and depth must not be NULL");
+  if (((uintptr_t)actions & 7u) || !aligned4(depth) || !aligned4(head))
+    return fail(env, GD_ERR_INVALID_ARG, "actions must be 8-byte, depth and head 4-byte aligned");
+  const size_t A = (size_t)env->A, n = (size_t)env->lidar_n;
+  auto dstep = [&](int t) { return depth + (obs_per_step ? (size_t)t * A * n : 0); };
+  auto cstep = [&](int t) { return cls ? cls + (obs_per_step ? (size_t)t * A * n : 0) : nullptr; };
+  auto hstep = [&](int t) { return head ? head + (size_t)t * A : nullptr; };
+  if (!batched(env)) {
+    for (int t = 0; t < steps; ++t) {
+      st = gd_step(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                   done ? done + (size_t)t * A : nullptr, nullptr);
+      if (st != GD_OK) return st;
+      st = gd_observe_lidar(env, hstep(t), dstep(t), cstep(t));
+      if (st != GD_OK) return st;
+    }
+    return GD_OK;
+  }
+  const void* key[8] = {actions, head, depth, cls, reward, done, (const void*)(intptr_t)(obs_per_step != 0), nullptr};
+  bool same = env->lgraph && env->lg_steps == steps;
+  for (int k = 0; k < 8 && same; ++k) same = env->lg_key[k] == key[k];
+  if (!same) {
+    if (env->lgraph) {
+      cudaGraphExecDestroy(env->lgraph);
+      env->lgraph = nullptr;
+    }
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_lidar: capture stream");
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_fail(env, e, "gd_rollout_lidar: begin capture");
+    }
+    for (int t = 0; t < steps; ++t)
+      launch_world_lidar(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                         done ? done + (size_t)t * A : nullptr, nullptr, hstep(t), dstep(t), cstep(t), 1, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_lidar: end capture");
+    e = cudaGraphInstantiate(&env->lgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      env->lgraph = nullptr;
+      return cuda_fail(env, e, "gd_rollout_lidar: instantiate");
+    }
+    for (int k = 0; k < 8; ++k) env->lg_key[k] = key[k];
+    env->lg_steps = steps;
+  }
+  cudaError_t e = cudaGraphLaunch(env->lgraph, env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_lidar: graph launch");
   return GD_OK;
 }
 
@@ -942,6 +1163,41 @@ gd_status gd_autotune(gd_env* env) {
     env->warps = best_w;
     d.topk = best_st;
     e = build_road(env, best_cell);
+  }
+  // fused LiDAR kernel: CTA size, on the chosen road grid
+  if (e == cudaSuccess && env->lidar_n > 0) {
+    float* ldepth = nullptr;
+    uint8_t* lcls = nullptr;
+    e = dev_alloc(env, &ldepth, A * (size_t)env->lidar_n);
+    if (e == cudaSuccess) e = dev_alloc(env, &lcls, A * (size_t)env->lidar_n);
+    float lbest = INFINITY;
+    int lbest_w = env->lw_warps;
+    for (int wp : {4, 8}) {
+      if (e != cudaSuccess) break;
+      env->lw_warps = wp;
+      if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
+      if (env->lw_warps != wp) continue;       // 8 warps do not fit with this many rays
+      float ms = INFINITY;
+      for (int rep = 0; rep < 3; ++rep) {
+        copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
+        cudaEventRecord(e0, env->stream);
+        launch_world_lidar(env, act, nullptr, nullptr, nullptr, nullptr, ldepth, lcls, 1);
+        cudaEventRecord(e1, env->stream);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms = std::min(ms, t);
+      }
+      if (e == cudaSuccess && ms < lbest) {
+        lbest = ms;
+        lbest_w = wp;
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
+    dev_free(env, ldepth);
+    dev_free(env, lcls);
+    env->lw_warps = lbest_w;
+    if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
   copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
   if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);

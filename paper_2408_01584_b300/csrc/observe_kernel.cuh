@@ -115,11 +115,12 @@ __device__ __forceinline__ int road_rows(const WorldView& v, float R, float R2, 
   return __shfl_sync(0xffffffffu, incl, 31);
 }
 
-// Warp-uniform walk of the flat candidate list: fn(pos, valid) is called
-// by every lane in every round (valid = this lane has a candidate), so fn
-// may use warp collectives.
-template <typename Fn>
-__device__ __forceinline__ void walk_rows(const ObsWarpSmem& sm, int nrows, int total, int lane, Fn&& fn) {
+// Warp-uniform walk of the flat candidate list of the rows published in
+// sm.row_start / sm.row_excl: fn(pos, valid) is called by every lane in
+// every round (valid = this lane has a candidate), so fn may use warp
+// collectives.
+template <typename SM, typename Fn>
+__device__ __forceinline__ void walk_rows(const SM& sm, int nrows, int total, int lane, Fn&& fn) {
   int r = 0;
   unsigned rs = sm.row_start[0], re = nrows > 1 ? sm.row_excl[1] : 0xffffffffu, rx = 0;
   for (int f0 = 0; f0 < total; f0 += WARP) {

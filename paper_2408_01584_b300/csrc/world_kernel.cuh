@@ -14,6 +14,7 @@
 #pragma once
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
+#include "lidar_kernel.cuh"
 
 namespace gd {
 
@@ -34,6 +35,7 @@ struct FusedArgs {
   const float* obs_w;        // [F], 16-byte aligned
   float reward_w;
   float* ell;                // [A] or nullptr
+  LidarArgs lidar;           // LiDAR observation (k_world<W, true>); lidar.depth == nullptr: none
 };
 
 struct FusedAgents {
@@ -93,27 +95,32 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
 
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents][ObsWarpSmem x WARPS]
-template <int WARPS>
+// Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents]
+// then per warp an ObsWarpSmem (radial observation) or LidarWarpHead + one
+// key per ray (LIDAR).
+template <int WARPS, bool LIDAR = false>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(wsm);
   unsigned char* tile = wsm + 128;
   FusedAgents& ag = *reinterpret_cast<FusedAgents*>(wsm + 128 + (size_t)a.tile_bytes);
-  ObsWarpSmem* wsmem = reinterpret_cast<ObsWarpSmem*>(reinterpret_cast<unsigned char*>(&ag) + sizeof(FusedAgents));
+  unsigned char* warp_base = reinterpret_cast<unsigned char*>(&ag) + sizeof(FusedAgents);
   __shared__ int s_w;
   __shared__ int s_nact;
   __shared__ int s_abort;
   __shared__ int s_next;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  ObsWarpSmem& osm = wsmem[wid];
+  ObsWarpSmem& osm = reinterpret_cast<ObsWarpSmem*>(warp_base)[wid];
+  unsigned char* lbase = warp_base + (size_t)wid * (size_t)a.lidar.warp_bytes;
+  LidarWarpHead& lh = *reinterpret_cast<LidarWarpHead*>(lbase);
+  unsigned* lkeys = reinterpret_cast<unsigned*>(lbase + sizeof(LidarWarpHead));
   if (tid == 0) {
     mbar_init(bar, 1);
     s_abort = 0;
   }
   __syncthreads();
   unsigned phase = 0;
-  const bool observe = a.obs != nullptr;
+  const bool observe = LIDAR ? a.lidar.depth != nullptr : a.obs != nullptr;
   for (;;) {
     if (tid == 0) s_w = (int)atomicAdd(a.counter, 1u);
     __syncthreads();
@@ -309,6 +316,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
       // warps take the world's agents one at a time (first WARPS statically)
       for (int li = wid; li < n;) {
         const int i = a0 + li;
+        if constexpr (LIDAR) {
+          const LidarArgs& la = a.lidar;
+          const size_t ro = (size_t)i * la.fan.n;
+          const float hd = la.head ? la.head[i] : 0.f;
+          if (use_tile) lidar_agent(vt, li, e.R, hd, la, la.depth + ro, la.cls ? la.cls + ro : nullptr, lh, lkeys, lane);
+          else lidar_agent(vg, li, e.R, hd, la, la.depth + ro, la.cls ? la.cls + ro : nullptr, lh, lkeys, lane);
+          int nx = 0;
+          if (lane == 0) nx = atomicAdd(&s_next, 1);
+          li = __shfl_sync(0xffffffffu, nx, 0);
+          continue;
+        }
         float* orow = a.obs + (size_t)i * e.F;
         int32_t* ridx = a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr;
         int32_t* pidx = a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr;

@@ -31,7 +31,11 @@ GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD = 1, 2, 4, 8
 SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_reset", "gd_step", "gd_observe",
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
-           "gd_rollout_objective", "gd_selftest_timeout")
+           "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
+           "gd_rollout_lidar")
+
+GD_MAX_LIDAR_RAYS = 8192
+LIDAR_NONE, LIDAR_AGENT, LIDAR_ROAD_EDGE = 0, 1, 2
 
 
 class GdError(RuntimeError):
@@ -45,7 +49,8 @@ class gd_config(C.Structure):
                 ("ckpt_every", C.c_int32), ("obs_radius", C.c_float), ("goal_radius", C.c_float),
                 ("dt", C.c_float), ("v_max", C.c_float), ("collision_penalty", C.c_float),
                 ("offroad_penalty", C.c_float), ("smooth_c", C.c_float), ("flags", C.c_uint32),
-                ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32)]
+                ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
+                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float)]
 
 
 class gd_scene_batch(C.Structure):
@@ -60,7 +65,8 @@ class gd_info(C.Structure):
     _fields_ = [("num_worlds", C.c_int32), ("num_agents", C.c_int32), ("num_road", C.c_int32),
                 ("feat", C.c_int32), ("max_agents_per_world", C.c_int32), ("k_road", C.c_int32),
                 ("n_partners", C.c_int32), ("episode_len", C.c_int32), ("device_bytes", C.c_int64),
-                ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32)]
+                ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
+                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32)]
 
 
 _lib = None
@@ -96,6 +102,9 @@ def load_library(path: str = LIB_PATH):
     lib.gd_last_error.argtypes = [vp]
     lib.gd_last_error.restype = C.c_char_p
     lib.gd_collide_noalloc.argtypes = [i32, vp, vp, vp, vp, f32, vp, vp]
+    lib.gd_observe_lidar.argtypes = [vp, vp, vp, vp]
+    lib.gd_step_observe_lidar.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.gd_rollout_lidar.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -192,6 +201,24 @@ def gd_rollout(env, steps, actions, obs, obs_per_step=False, reward=None, done=N
                                     _ptr(reward), _ptr(done)))
 
 
+def gd_observe_lidar(env, head, depth, cls=None):
+    lib = load_library()
+    _check(lib, env, lib.gd_observe_lidar(env, _ptr(head, align=4), _ptr(depth, align=4), _ptr(cls)))
+
+
+def gd_step_observe_lidar(env, actions, head, reward, done, world_done, depth, cls=None):
+    lib = load_library()
+    _check(lib, env, lib.gd_step_observe_lidar(env, _ptr(actions, align=8), _ptr(head, align=4), _ptr(reward),
+                                               _ptr(done), _ptr(world_done), _ptr(depth, align=4), _ptr(cls)))
+
+
+def gd_rollout_lidar(env, steps, actions, head, depth, cls=None, obs_per_step=False, reward=None, done=None):
+    lib = load_library()
+    _check(lib, env, lib.gd_rollout_lidar(env, int(steps), _ptr(actions, align=8), _ptr(head, align=4),
+                                          _ptr(depth, align=4), _ptr(cls), int(bool(obs_per_step)), _ptr(reward),
+                                          _ptr(done)))
+
+
 def gd_rollout_objective(env, steps, actions, obs_weight, reward_weight, ell, obs=None):
     lib = load_library()
     _check(lib, env, lib.gd_rollout_objective(env, int(steps), _ptr(actions), _ptr(obs_weight, align=16),
@@ -271,6 +298,10 @@ class Env:
         self.done = torch.zeros(self.A, dtype=torch.uint8, device=dev)
         self.world_done = torch.zeros(self.W, dtype=torch.uint8, device=dev)
         self.obs = torch.zeros(self.A, self.F, dtype=torch.float32, device=dev)
+        self.n_rays = info.lidar_rays
+        if self.n_rays:
+            self.depth = torch.zeros(self.A, self.n_rays, dtype=torch.float32, device=dev)
+            self.cls = torch.zeros(self.A, self.n_rays, dtype=torch.uint8, device=dev)
         self.device = dev
 
     def close(self):
@@ -295,6 +326,11 @@ class Env:
             pi = t.empty(self.A, self.P, dtype=t.int32, device=self.device)
         gd_observe(self.h, self.obs, ri, pi)
         return self.obs, ri, pi
+
+    def lidar(self, head=None):
+        """LiDAR / view-cone scan after the last step: (depth [A, n], cls [A, n])."""
+        gd_observe_lidar(self.h, head, self.depth, self.cls)
+        return self.depth, self.cls
 
     def get_state(self):
         t = self.torch

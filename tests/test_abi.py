@@ -66,6 +66,7 @@ def test_default_config(lib):
     c = gd.gd_default_config()
     assert (c.k_road, c.n_partners, c.episode_len, c.ckpt_every) == (200, 63, 91, 10)
     assert abs(c.obs_radius - 50) < 1e-6 and abs(c.goal_radius - 2) < 1e-6 and abs(c.dt - 0.1) < 1e-7
+    assert c.lidar_rays == 0 and abs(c.lidar_fov - 2 * np.pi) < 1e-6
 
 
 def _expect(status, fn, *a):
@@ -85,6 +86,10 @@ def test_rejects_bad_arguments_before_any_launch(lib):
     _expect(INV, gd.gd_create, gd.gd_default_config(dt=-0.1), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(block_size=96), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(flags=gd.GD_DIFFERENTIABLE | gd.GD_AUTO_RESET), sc)
+    _expect(CAP, gd.gd_create, gd.gd_default_config(lidar_rays=gd.GD_MAX_LIDAR_RAYS + 1), sc)
+    _expect(CAP, gd.gd_create, gd.gd_default_config(lidar_rays=-1), sc)
+    _expect(INV, gd.gd_create, gd.gd_default_config(lidar_rays=100, lidar_fov=1e-4), sc)
+    _expect(INV, gd.gd_create, gd.gd_default_config(lidar_rays=100, lidar_fov=7.0), sc)
     big = scenes.make_scene(np.array([129]), np.array([500]), 0)
     _expect(CAP, gd.gd_create, gd.gd_default_config(), big)
     bad = scenes.workload_scene("plain_4x8", 0)
