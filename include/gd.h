@@ -116,6 +116,12 @@ typedef struct gd_config {
                                 0 = LiDAR not enabled (default); 3000 in Fig. 1 */
   float lidar_fov;           /* rad, width of the ray fan, in [1e-3, 2 pi]: 2 pi = LiDAR (default),
                                 2 pi / 3 = the 120-degree view cone of Fig. 1 */
+  int32_t lidar_block_size;  /* threads per block of the fused LiDAR kernel: 0 = default (256),
+                                128, 256 or 384 */
+  int32_t lidar_no_tile;     /* 1: the fused LiDAR kernel reads the road from global memory
+                                instead of a shared-memory tile (more warps per SM); default 0 */
+  int32_t lidar_split;       /* 1: with GD_BATCHED the step and the LiDAR scan are two launches
+                                (the scan over all agents at once); default 0 = one fused launch */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -142,6 +148,8 @@ typedef struct gd_info {
   int32_t lidar_rays;                               /* rays per agent (0 = LiDAR not enabled) */
   float lidar_fov;                                  /* rad */
   int32_t lidar_block_size;                         /* fused LiDAR kernel threads per block in use */
+  int32_t lidar_road_tile;                          /* 1: it copies each world's road into shared memory */
+  int32_t lidar_split;                              /* 1: step and LiDAR scan are two launches */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -277,8 +285,10 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * in {128, 256, 512} threads and top-K strategy in {1 bucket rank, 2 bitonic
  * sort when at most 256 points are in range}, and keeps the fastest
  * (reported by gd_get_info).  With LiDAR enabled it then times the fused
- * step + LiDAR scan with 128 and 256 threads per block and keeps the faster
- * (a scratch of A * lidar_rays * 5 bytes is held during the call).  Every combination gives the same results.
+ * step + LiDAR scan with 128, 256 and 384 threads per block, each with and
+ * without the shared-memory road tile, and the split form (step, then a
+ * scan over all agents), and keeps the fastest (a scratch of
+ * A * lidar_rays * 5 bytes is held during the call).  Every combination gives the same results.
  * Synchronises the env's stream; the simulation state is unchanged
  * afterwards.  A captured gd_rollout graph is dropped and re-captured on the
  * next call. */

@@ -29,7 +29,9 @@ constexpr int kAdjWarps = 8;
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
 constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(ObsWarpSmem);
 // Fixed shared memory of the fused LiDAR kernel besides the road tile.
-inline size_t lidar_fixed_smem(int warps, int n) { return 128 + sizeof(FusedAgents) + warps * lidar_warp_bytes(n); }
+inline size_t lidar_fixed_smem(int warps, int n) {
+  return 128 + sizeof(FusedAgents) + warps * lidar_warp_bytes(n) + lidar_dirs_bytes(n);
+}
 
 }  // namespace
 
@@ -86,8 +88,12 @@ struct gd_env {
   int lidar_n = 0;              // rays per agent (0 = not enabled)
   LidarFan fan{};
   float2* ray_dirs = nullptr;   // [n] (cos, sin) of the ray angles in the sensor frame
-  int lidar_obs_warps = 8;      // per-stage k_lidar CTA size (warps)
-  int lw_warps = 8;             // fused LiDAR kernel CTA size (4 or 8 warps)
+  int lidar_obs_warps = 12;     // stand-alone k_lidar CTA size (warps: 12, 8 or 4)
+  int lo_grid = 0;              // its persistent CTAs
+  unsigned* lcounter = nullptr; // its agent counter
+  int lw_split = 0;             // batched form: 1 = k_world step + k_lidar, 0 = one fused k_world
+  int lw_warps = 8;             // fused LiDAR kernel CTA size (4, 8 or 12 warps)
+  int lw_notile = 0;            // 1: no shared-memory road tile (more warps per SM)
   int lw_tile = 0;              // its road tile (bytes)
   size_t lw_smem = 0;
   int lw_grid = 0;
@@ -190,7 +196,8 @@ static cudaError_t shape_world_lidar(gd_env* env, size_t max_block, int smem_sm,
   const long two = ((long)smem_sm / 2 - 2048 - fixed) & ~15L;
   const long one = ((long)smem_blk - 1024 - fixed) & ~15L;
   const long cap = ((long)max_block <= two) ? (long)max_block : std::min<long>(one, (long)max_block);
-  env->lw_tile = (int)std::max(16L, cap);
+  // without a tile every world reads its road from global memory (L1/L2)
+  env->lw_tile = env->lw_notile ? 16 : (int)std::max(16L, cap);
   env->lw_smem = (size_t)fixed + (size_t)env->lw_tile;
   cudaError_t e = cudaFuncSetAttribute(k_world<WARPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)env->lw_smem);
@@ -219,9 +226,13 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
   if (e != cudaSuccess) return e;
   if (env->lidar_n > 0) {
     // the tile shrinks first; if even a 16-byte tile does not fit, fewer warps
-    if (env->lw_warps == 8 && lidar_fixed_smem(8, env->lidar_n) + 16 + 1024 > (size_t)smem_blk) env->lw_warps = 4;
-    e = env->lw_warps == 4 ? shape_world_lidar<4>(env, max_block, smem_sm, smem_blk, nsm)
-                           : shape_world_lidar<8>(env, max_block, smem_sm, smem_blk, nsm);
+    while (env->lw_warps > 4 && lidar_fixed_smem(env->lw_warps, env->lidar_n) + 16 + 1024 > (size_t)smem_blk)
+      env->lw_warps -= 4;
+    switch (env->lw_warps) {
+      case 4: e = shape_world_lidar<4>(env, max_block, smem_sm, smem_blk, nsm); break;
+      case 12: e = shape_world_lidar<12>(env, max_block, smem_sm, smem_blk, nsm); break;
+      default: env->lw_warps = 8; e = shape_world_lidar<8>(env, max_block, smem_sm, smem_blk, nsm); break;
+    }
     if (e != cudaSuccess) return e;
   }
   if (env->cfg.flags & GD_DIFFERENTIABLE) {
@@ -253,13 +264,14 @@ static cudaError_t build_road(gd_env* env, float cell) {
   for (int w = 0; w < W; ++w) {
     const float4 bb = env->h_bbox[w];
     grid_geometry(bb.x, bb.y, bb.z, bb.w, cell, rdesc[w]);
-    rdesc[w].cell_base = 0;
     rdesc[w].block_bytes = road_block_bytes(off[w + 1] - off[w], rdesc[w].nx * rdesc[w].ny);
     arena_off[w] = (long long)(arena_bytes / 16);
     arena_bytes += (size_t)rdesc[w].block_bytes;
     max_block = std::max(max_block, (size_t)rdesc[w].block_bytes);
   }
   std::vector<unsigned char> arena(std::max<size_t>(arena_bytes, 16), 0);
+  std::vector<float4> lsegs;
+  std::vector<int> lcell;
   for (int w = 0; w < W; ++w) {
     const int r0 = off[w], r1 = off[w + 1], nr = r1 - r0;
     GridDesc& g = rdesc[w];
@@ -285,6 +297,20 @@ static cudaError_t build_road(gd_env* env, float cell) {
       bmeta[dst] = (uint16_t)((j - r0) | (env->h_rtype[j] << 15));
     }
     // road-edge segments: consecutive ROAD_EDGE points of one polyline
+    // (next links inside the block, and the LiDAR list by first-point cell)
+    std::vector<int> scnt(nc + 1, 0);
+    for (int j = r0; j + 1 < r1; ++j)
+      if (env->h_rtype[j] == GD_ROAD_EDGE && env->h_rtype[j + 1] == GD_ROAD_EDGE && env->h_rpoly[j] == env->h_rpoly[j + 1])
+        scnt[cellid[j - r0] + 1]++;
+    for (int c = 0; c < nc; ++c) scnt[c + 1] += scnt[c];
+    g.cell_base = (int)lcell.size();
+    const int sbase = (int)lsegs.size();
+    for (int c = 0; c <= nc; ++c) lcell.push_back(sbase + scnt[c]);
+    lsegs.resize((size_t)sbase + scnt[nc]);
+    for (int j = r0; j + 1 < r1; ++j)
+      if (env->h_rtype[j] == GD_ROAD_EDGE && env->h_rtype[j + 1] == GD_ROAD_EDGE && env->h_rpoly[j] == env->h_rpoly[j + 1])
+        lsegs[(size_t)sbase + scnt[cellid[j - r0]]++] =
+            make_float4(env->h_rx[j], env->h_ry[j], env->h_rx[j + 1], env->h_ry[j + 1]);
     float seg_max = 0.f;
     for (int j = r0; j < r1; ++j) {
       const bool seg = j + 1 < r1 && env->h_rtype[j] == GD_ROAD_EDGE && env->h_rtype[j + 1] == GD_ROAD_EDGE &&
@@ -298,6 +324,10 @@ static cudaError_t build_road(gd_env* env, float cell) {
   if (e != cudaSuccess) return e;
   dev_free(env, const_cast<GridDesc*>(env->d.rgrid));
   dev_free(env, const_cast<unsigned char*>(env->d.arena));
+  dev_free(env, const_cast<float4*>(env->d.lsegs));
+  dev_free(env, const_cast<int*>(env->d.lcell));
+  env->d.lsegs = nullptr;
+  env->d.lcell = nullptr;
   dev_free(env, const_cast<long long*>(env->d.arena_off));
   env->d.rgrid = nullptr;
   env->d.arena = nullptr;
@@ -311,6 +341,12 @@ static cudaError_t build_road(gd_env* env, float cell) {
   env->d.arena = p_arena;
   if ((e = upload(env, &p_aroff, arena_off.data(), (size_t)W)) != cudaSuccess) return e;
   env->d.arena_off = p_aroff;
+  float4* p_ls;
+  int* p_lc;
+  if ((e = upload(env, &p_ls, lsegs.data(), lsegs.size())) != cudaSuccess) return e;
+  env->d.lsegs = p_ls;
+  if ((e = upload(env, &p_lc, lcell.data(), lcell.size())) != cudaSuccess) return e;
+  env->d.lcell = p_lc;
   env->road_cell = cell;
   env->max_block = max_block;
   if ((e = shape_kernels(env, max_block)) != cudaSuccess) return e;
@@ -389,6 +425,11 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     return fail(nullptr, GD_ERR_CAPACITY, "lidar_rays outside 0..GD_MAX_LIDAR_RAYS");
   if (!(c->lidar_fov >= 1e-3f) || !(c->lidar_fov <= 6.2831855f))
     return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_fov must be in [1e-3, 2 pi]");
+  if (c->lidar_block_size != 0 && c->lidar_block_size != 128 && c->lidar_block_size != 256 &&
+      c->lidar_block_size != 384)
+    return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_block_size must be 0, 128, 256 or 384");
+  if (c->lidar_no_tile != 0 && c->lidar_no_tile != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_no_tile must be 0 or 1");
+  if (c->lidar_split != 0 && c->lidar_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_split must be 0 or 1");
   if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
   const int W = s->num_worlds;
@@ -576,6 +617,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     const int n = cfg->lidar_rays;
     const double fov = (double)cfg->lidar_fov;
     env->lidar_n = n;
+    if (cfg->lidar_block_size) env->lw_warps = cfg->lidar_block_size / 32;
+    env->lw_notile = cfg->lidar_no_tile;
     env->fan.n = n;
     env->fan.b0 = (float)(-0.5 * fov + 0.5 * fov / n);
     env->fan.inv_step = (float)(n / fov);
@@ -586,11 +629,30 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     int dev = 0, smem_blk = 0;
     GD_TRY(cudaGetDevice(&dev));
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    env->lidar_obs_warps = (8 * lidar_warp_bytes(n) <= (size_t)smem_blk) ? 8 : 4;
-    if (env->lidar_obs_warps == 8)
-      GD_TRY(cudaFuncSetAttribute(k_lidar<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * lidar_warp_bytes(n))));
-    else
-      GD_TRY(cudaFuncSetAttribute(k_lidar<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4 * lidar_warp_bytes(n))));
+    env->lw_split = cfg->lidar_split;
+    GD_TRY(dev_alloc(env, &env->lcounter, 1));
+    // stand-alone scan: the most warps whose shared memory fits one CTA
+    int wp = 12;
+    while (wp > 4 && wp * lidar_warp_bytes(n) + lidar_dirs_bytes(n) + 1024 > (size_t)smem_blk) wp -= 4;
+    env->lidar_obs_warps = wp;
+    const size_t ls = wp * lidar_warp_bytes(n) + lidar_dirs_bytes(n);
+    int per_sm = 0, nsm = 0;
+    GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    switch (wp) {
+      case 12:
+        GD_TRY(cudaFuncSetAttribute(k_lidar<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<12>, 12 * 32, ls));
+        break;
+      case 8:
+        GD_TRY(cudaFuncSetAttribute(k_lidar<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<8>, 8 * 32, ls));
+        break;
+      default:
+        GD_TRY(cudaFuncSetAttribute(k_lidar<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<4>, 4 * 32, ls));
+        break;
+    }
+    env->lo_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (A + wp - 1) / wp));
   }
   GD_TRY(build_road(env, rcell));
   GD_TRY(cudaStreamSynchronize(env->stream));
@@ -616,6 +678,8 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->lidar_rays = env->lidar_n;
   info->lidar_fov = env->cfg.lidar_fov;
   info->lidar_block_size = env->lw_warps * 32;
+  info->lidar_road_tile = env->lw_notile ? 0 : 1;
+  info->lidar_split = env->lw_split;
   return GD_OK;
 }
 
@@ -696,19 +760,26 @@ static LidarArgs lidar_args(const gd_env* env, const float* head, float* depth, 
   la.depth = depth;
   la.cls = cls;
   la.dirs = env->ray_dirs;
+  la.lsegs = env->d.lsegs;
+  la.lcell = env->d.lcell;
   la.fan = env->fan;
   la.warp_bytes = (int)lidar_warp_bytes(env->lidar_n);
   return la;
 }
 
-// Per-stage LiDAR scan: one warp per agent, everything from global memory.
-static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls) {
+// Stand-alone LiDAR scan of every agent: persistent CTAs, warps take agents
+// from a counter (cleared first); the scene is read from global memory.
+static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls, cudaStream_t stream = nullptr) {
+  if (!stream) stream = env->stream;
   const LidarArgs la = lidar_args(env, head, depth, cls);
-  const size_t wb = (size_t)la.warp_bytes;
-  if (env->lidar_obs_warps == 8)
-    k_lidar<8><<<blocks_for(env->A, 8), 8 * 32, 8 * wb, env->stream>>>(env->d, la);
-  else
-    k_lidar<4><<<blocks_for(env->A, 4), 4 * 32, 4 * wb, env->stream>>>(env->d, la);
+  const int wp = env->lidar_obs_warps;
+  const size_t smem = wp * (size_t)la.warp_bytes + lidar_dirs_bytes(env->lidar_n);
+  cudaMemsetAsync(env->lcounter, 0, sizeof(unsigned), stream);
+  switch (wp) {
+    case 12: k_lidar<12><<<env->lo_grid, 12 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
+    case 8: k_lidar<8><<<env->lo_grid, 8 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
+    default: k_lidar<4><<<env->lo_grid, 4 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
+  }
 }
 
 // Fused LiDAR form: one persistent launch of the step (if do_step) and the
@@ -717,6 +788,12 @@ static void launch_world_lidar(gd_env* env, const float* actions, float* reward,
                                const float* head, float* depth, uint8_t* cls, int do_step,
                                cudaStream_t stream = nullptr) {
   if (!stream) stream = env->stream;
+  if (env->lw_split) {
+    // split form: the fused step without observation, then the stand-alone scan
+    if (do_step) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream);
+    launch_lidar(env, head, depth, cls, stream);
+    return;
+  }
   FusedArgs a{};
   a.actions = reinterpret_cast<const float2*>(actions);
   a.reward = reward;
@@ -728,10 +805,11 @@ static void launch_world_lidar(gd_env* env, const float* actions, float* reward,
   a.do_step = do_step;
   a.lidar = lidar_args(env, head, depth, cls);
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
-  if (env->lw_warps == 4)
-    k_world<4, true><<<env->lw_grid, 4 * 32, env->lw_smem, stream>>>(env->d, a);
-  else
-    k_world<8, true><<<env->lw_grid, 8 * 32, env->lw_smem, stream>>>(env->d, a);
+  switch (env->lw_warps) {
+    case 4: k_world<4, true><<<env->lw_grid, 4 * 32, env->lw_smem, stream>>>(env->d, a); break;
+    case 12: k_world<12, true><<<env->lw_grid, 12 * 32, env->lw_smem, stream>>>(env->d, a); break;
+    default: k_world<8, true><<<env->lw_grid, 8 * 32, env->lw_smem, stream>>>(env->d, a); break;
+  }
 }
 
 static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) != 0; }
@@ -1171,12 +1249,17 @@ gd_status gd_autotune(gd_env* env) {
     e = dev_alloc(env, &ldepth, A * (size_t)env->lidar_n);
     if (e == cudaSuccess) e = dev_alloc(env, &lcls, A * (size_t)env->lidar_n);
     float lbest = INFINITY;
-    int lbest_w = env->lw_warps;
-    for (int wp : {4, 8}) {
+    int lbest_w = env->lw_warps, lbest_nt = env->lw_notile, lbest_sp = env->lw_split;
+    for (int cfg = 0; cfg < 7; ++cfg) {
       if (e != cudaSuccess) break;
+      // trials 0..5: fused kernel, 4 / 8 / 12 warps, with and without the
+      // road tile; trial 6: step and stand-alone scan as two launches
+      const int wp = cfg < 6 ? 4 * (1 + cfg / 2) : 8;
       env->lw_warps = wp;
+      env->lw_notile = cfg & 1;
+      env->lw_split = cfg == 6;
       if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
-      if (env->lw_warps != wp) continue;       // 8 warps do not fit with this many rays
+      if (env->lw_warps != wp) continue;       // this many warps do not fit with this many rays
       float ms = INFINITY;
       for (int rep = 0; rep < 3; ++rep) {
         copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
@@ -1191,12 +1274,16 @@ gd_status gd_autotune(gd_env* env) {
       if (e == cudaSuccess && ms < lbest) {
         lbest = ms;
         lbest_w = wp;
+        lbest_nt = env->lw_notile;
+        lbest_sp = env->lw_split;
       }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
     dev_free(env, ldepth);
     dev_free(env, lcls);
     env->lw_warps = lbest_w;
+    env->lw_notile = lbest_nt;
+    env->lw_split = lbest_sp;
     if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
   copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);

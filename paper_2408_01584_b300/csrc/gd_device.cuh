@@ -13,6 +13,10 @@
 //                  block's offset in 16-byte units, rgrid[w].block_bytes its size
 //   esegs[]        float4 (x0, y0, x1, y1) road-edge segments listed under every
 //                  edge-grid cell their bounding box touches
+//   lsegs[]        float4 (x0, y0, x1, y1) road-edge segments of each world, each
+//                  listed once, under the road-grid cell of its first point, in
+//                  cell order; lcell[rgrid[w].cell_base + c] = first segment of
+//                  cell c of world w (ny*nx + 1 entries per world)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -40,7 +44,8 @@ struct GridDesc {      // one per world, for the road-point grid and the edge gr
   float ox, oy;        // lower-left corner of cell (0, 0)
   float cs, inv_cs;    // cell size and its inverse
   int nx, ny;          // cells per row / rows
-  int cell_base;       // edge grid: first entry of this world's cell-start table
+  int cell_base;       // edge grid: first entry of this world's cell-start table;
+                       // road grid: first entry of the world's table in lcell
   float seg_max;       // road grid: longest road-edge segment of the world (m)
   int block_bytes;     // road grid: bytes of the world's road block in the arena
 };
@@ -68,6 +73,8 @@ struct DevEnv {
   const GridDesc* egrid;
   const int* ecell_start;
   const float4* esegs;
+  const float4* lsegs;   // road-edge segments by road-grid cell of the first point (LiDAR)
+  const int* lcell;      // their cell starts
   // scratch of the per-stage form
   uint32_t* agrid_key;   // [A] per world: sorted agent-grid keys of the active agents
   int* agrid_n;          // [W] number of active agents in the agent grid

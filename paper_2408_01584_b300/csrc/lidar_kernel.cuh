@@ -44,7 +44,7 @@ struct LidarWarpHead {
   float4 ga[LIDAR_ITEMS];        // segment: (w', d') in the sensor frame; box: (o, cos psi, sin psi)
   float2 gb[LIDAR_ITEMS];        // segment: (cross(w', d'), 0); box: half extents
   unsigned range[LIDAR_ITEMS];   // first ray | ray count << 16
-  unsigned pre[LIDAR_ITEMS];     // exclusive prefix of the ray counts
+  int kofs[LIDAR_ITEMS];         // first pair index of the item (during a drain)
   unsigned row_start[MAX_ROWS];
   unsigned row_excl[MAX_ROWS];
 };
@@ -53,6 +53,13 @@ static_assert(sizeof(LidarWarpHead) % 16 == 0, "per-warp key array must stay 16-
 // Shared memory of one warp: the head and one key per ray (rounded up to 4).
 __host__ __device__ __forceinline__ size_t lidar_warp_bytes(int n) {
   return sizeof(LidarWarpHead) + 16 * (size_t)((n + 3) / 4);
+}
+// Shared memory of the CTA's copy of the ray directions (float2 per ray).
+__host__ __device__ __forceinline__ size_t lidar_dirs_bytes(int n) { return 16 * (size_t)((n + 1) / 2); }
+
+// Copy the ray directions into shared memory (whole CTA; caller syncs).
+__device__ __forceinline__ void lidar_stage_dirs(float2* dst, const float2* __restrict__ src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
 // The ray fan in the sensor frame (x axis = heading turned by the head angle).
@@ -68,6 +75,8 @@ struct LidarArgs {
   float* depth;            // [A, n] or nullptr (no LiDAR output)
   uint8_t* cls;            // [A, n] or nullptr
   const float2* dirs;      // [n] (cos, sin) of each ray's angle in the sensor frame
+  const float4* lsegs;     // road-edge segments by road-grid cell of the first point
+  const int* lcell;        // their cell starts (world w: from rgrid[w].cell_base)
   LidarFan fan;
   int warp_bytes;          // lidar_warp_bytes(n)
 };
@@ -82,6 +91,12 @@ __device__ __forceinline__ int arc_ranges(const LidarFan& f, float lo, float hi,
   }
   int m = 0;
   const float a0 = (lo - LIDAR_PAD - f.b0) * f.inv_step, b0 = (hi + LIDAR_PAD - f.b0) * f.inv_step;
+  if (a0 > 0.f && b0 < (float)(f.n - 1)) {
+    // inside the fan: the copies one turn away cannot reach it
+    const int k0 = (int)ceilf(a0) - 1, k1 = (int)floorf(b0) + 1;
+    r0 = (unsigned)k0 | ((unsigned)(k1 - k0 + 1) << 16);
+    return 1;
+  }
 #pragma unroll
   for (int sft = -1; sft <= 1; ++sft) {
     const float a = fmaf((float)sft, f.wrap_steps, a0), b = fmaf((float)sft, f.wrap_steps, b0);
@@ -97,14 +112,18 @@ __device__ __forceinline__ int arc_ranges(const LidarFan& f, float lo, float hi,
 
 // Ray test of a segment item: p + t u = a + s (b - a) in the sensor frame,
 // w' = a - p, d' = b - a, C = cross(w', d'); hit iff 0 <= s <= 1, 0 <= t <= R.
+// With den = cross(u, d'), s = cross(w', u) / den and t = C / den: both
+// conditions are tested on the numerators after flipping their signs by
+// den's, and the one division happens for the depth.
 __device__ __forceinline__ bool ray_seg_item(float4 g, float C, float cb, float sb, float R, float& t) {
   const float den = fmaf(cb, g.w, -__fmul_rn(sb, g.z));     // cross(u, d')
   const float sn = fmaf(g.x, sb, -__fmul_rn(g.y, cb));      // cross(w', u)
-  bool hit = den > 0.f ? (sn >= 0.f && sn <= den) : (den < 0.f && sn <= 0.f && sn >= den);
-  t = __fdiv_rn(C, den);
-  hit = hit && t >= 0.f && t <= R;
-  t = fabsf(t);
-  return hit;
+  const unsigned sgn = __float_as_uint(den) & 0x80000000u;
+  const float ad = fabsf(den);
+  const float sp = __uint_as_float(__float_as_uint(sn) ^ sgn);
+  const float cp = __uint_as_float(__float_as_uint(C) ^ sgn);
+  t = fminf(fabsf(__fdividef(cp, ad)), R);                   // about 2 ulp; |den| <= segment length
+  return ad > 0.f && sp >= 0.f && sp <= ad && cp >= 0.f && cp <= __fmul_rn(R, ad);
 }
 
 // Ray test of a box item (slab method in the box frame): o = ray origin in
@@ -119,8 +138,7 @@ __device__ __forceinline__ bool ray_box_item(float4 g, float2 h, float cb, float
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
     if (v[a] != 0.f) {
-      const float inv = __frcp_rn(v[a]);
-      const float t1 = __fmul_rn(-hh[a] - o[a], inv), t2 = __fmul_rn(hh[a] - o[a], inv);
+      const float t1 = __fdividef(-hh[a] - o[a], v[a]), t2 = __fdividef(hh[a] - o[a], v[a]);
       lo = fmaxf(lo, fminf(t1, t2));
       hi = fminf(hi, fmaxf(t1, t2));
     } else {
@@ -131,8 +149,60 @@ __device__ __forceinline__ bool ray_box_item(float4 g, float2 h, float cb, float
   return ok && lo <= hi && hi >= 0.f && t <= R;
 }
 
-// Drain the item queue: every (item, ray) pair is tested once, one pair
-// per lane per round, and the hits are folded into the per-ray keys.
+// Position of a lane in the pair sequence of a drain: the item `it` of pair
+// q, the first pair of the next item, the ray index of pair q and the
+// item's geometry.
+struct LidarCursor {
+  unsigned q, end, next;
+  int it, k;
+  float4 g;
+  float2 gb;
+};
+
+__device__ __forceinline__ void cursor_load(LidarCursor& c, const LidarWarpHead& h, int n_items, unsigned total) {
+  c.next = c.it + 1 < n_items ? (unsigned)h.kofs[c.it + 1] : total;
+  c.g = h.ga[c.it];
+  c.gb = h.gb[c.it];
+}
+
+__device__ __forceinline__ void cursor_start(LidarCursor& c, const LidarWarpHead& h, int n_items, unsigned total,
+                                             unsigned q, unsigned end) {
+  c.q = q;
+  c.end = end;
+  int lo = 0, hi = n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((unsigned)h.kofs[mid] <= q) lo = mid; else hi = mid - 1;
+  }
+  c.it = lo;
+  c.k = (int)(h.range[lo] & 0xffffu) + (int)(q - (unsigned)h.kofs[lo]);
+  cursor_load(c, h, n_items, total);
+}
+
+template <bool SEG>
+__device__ __forceinline__ void cursor_test(LidarCursor& c, const LidarWarpHead& h, unsigned* keys, int n_items,
+                                            unsigned total, const float2* __restrict__ dirs, float R) {
+  if (c.q < c.end) {
+    if (c.q == c.next) {
+      ++c.it;
+      c.k = (int)(h.range[c.it] & 0xffffu);
+      cursor_load(c, h, n_items, total);
+    }
+    const float2 u = dirs[c.k];
+    float t;
+    const bool hit = SEG ? ray_seg_item(c.g, c.gb.x, u.x, u.y, R, t) : ray_box_item(c.g, c.gb, u.x, u.y, R, t);
+    if (hit) atomicMin(&keys[c.k], (__float_as_uint(t) & ~1u) | (SEG ? 1u : 0u));
+    ++c.q;
+    ++c.k;
+  }
+}
+
+// Drain the item queue: every (item, ray) pair is tested once and the hits
+// are folded into the per-ray keys.  The pairs, numbered by a prefix sum of
+// the range lengths, are cut into 64 contiguous blocks, two per lane: a lane
+// finds the item of each block's first pair by bisection and then walks both
+// blocks forward side by side (two independent dependency chains), so an
+// item's geometry stays in registers while its rays are tested.
 template <bool SEG>
 __device__ __forceinline__ void lidar_drain(LidarWarpHead& h, unsigned* keys, int n_items,
                                             const float2* __restrict__ dirs, float R, int lane) {
@@ -148,25 +218,21 @@ __device__ __forceinline__ void lidar_drain(LidarWarpHead& h, unsigned* keys, in
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int it = 3 * lane + r;
-    if (it < n_items) h.pre[it] = ex;
+    if (it < n_items) h.kofs[it] = (int)ex;     // first pair index of the item
     ex += c[r];
   }
   const unsigned total = (unsigned)__shfl_sync(0xffffffffu, incl, 31);
   __syncwarp();
-  for (unsigned q0 = 0; q0 < total; q0 += WARP) {
-    const unsigned q = q0 + lane;
-    if (q < total) {
-      int lo = 0, hi = n_items - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (h.pre[mid] <= q) lo = mid; else hi = mid - 1;
-      }
-      const int k = (int)(h.range[lo] & 0xffffu) + (int)(q - h.pre[lo]);
-      const float2 u = dirs[k];
-      float t;
-      const bool hit = SEG ? ray_seg_item(h.ga[lo], h.gb[lo].x, u.x, u.y, R, t)
-                           : ray_box_item(h.ga[lo], h.gb[lo], u.x, u.y, R, t);
-      if (hit) atomicMin(&keys[k], (__float_as_uint(t) & ~1u) | (SEG ? 1u : 0u));
+  const unsigned per = (total + 2 * WARP - 1) / (2 * WARP);
+  const unsigned q0 = min(2u * lane * per, total), q1 = min(q0 + per, total), q2 = min(q1 + per, total);
+  if (q0 < q2) {
+    LidarCursor a, b;
+    cursor_start(a, h, n_items, total, q0, q1);
+    if (q1 < q2) cursor_start(b, h, n_items, total, q1, q2);
+    else b = a, b.q = b.end = q2;
+    for (unsigned j = 0; j < per; ++j) {
+      cursor_test<SEG>(a, h, keys, n_items, total, dirs, R);
+      cursor_test<SEG>(b, h, keys, n_items, total, dirs, R);
     }
   }
   __syncwarp();
@@ -193,11 +259,13 @@ __device__ __forceinline__ int lidar_push(LidarWarpHead& h, int nq, int m, unsig
 }
 
 // Rows [row0, row0 + 32) of the grid rows that meet the disk of radius Rr
-// about (ex, ey), each clipped to the disk's chord: published in
+// about (ex, ey), each clipped to the disk's chord, as ranges of the world's
+// road-edge segment list (cell starts `lcell` of the world): published in
 // h.row_start / h.row_excl like road_rows.  Returns the candidate count of
 // the chunk; nrows = rows in it; rows_total = rows of the whole disk.
-__device__ __forceinline__ int lidar_rows(const WorldView& v, float Rr, float ex, float ey, int row0,
-                                          LidarWarpHead& h, int lane, int& nrows, int& rows_total) {
+__device__ __forceinline__ int lidar_rows(const WorldView& v, const int* __restrict__ lcell, float Rr, float ex,
+                                          float ey, int row0, LidarWarpHead& h, int lane, int& nrows,
+                                          int& rows_total) {
   const GridDesc& g = v.g;
   const float margin = 1e-3f;
   const int cy0 = (int)clampf(floorf((ey - Rr - margin - g.oy) * g.inv_cs), 0.f, (float)g.ny);
@@ -215,9 +283,9 @@ __device__ __forceinline__ int lidar_rows(const WorldView& v, float Rr, float ex
       const int cx0 = (int)clampf(floorf((ex - hw - g.ox) * g.inv_cs), 0.f, (float)g.nx);
       const int cx1 = (int)clampf(floorf((ex + hw - g.ox) * g.inv_cs), -1.f, (float)(g.nx - 1));
       if (cx0 <= cx1) {
-        const uint16_t* cst = v.cell_start + row * g.nx;
-        start = cst[cx0];
-        len = (int)cst[cx1 + 1] - (int)start;
+        const int* cst = lcell + g.cell_base + row * g.nx;
+        start = (unsigned)cst[cx0];
+        len = cst[cx1 + 1] - cst[cx0];
       }
     }
   }
@@ -328,20 +396,26 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
         bool full = fabsf(ox) <= hl + LIDAR_NEAR_FULL && fabsf(oy) <= hw + LIDAR_NEAR_FULL;
         float lo = 0.f, hi = 0.f;
         if (!full) {
-          // box centre and axes in the sensor frame
+          // corner directions in the sensor frame; the box subtends less
+          // than pi, so offsets from corner 0 need no wrap beyond one turn
           const float c1 = rot_x(cs, ss, -qx, -qy), c2 = rot_y(cs, ss, -qx, -qy);
-          const float gc = atan2f(c2, c1);
-          float dmin = 0.f, dmax = 0.f;
+          float g0 = 0.f, dmin = 0.f, dmax = 0.f;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const float u = (k & 1) ? hl : -hl, w = (k & 2) ? hw : -hw;
             const float p1 = c1 + fmaf(u, cp, __fmul_rn(w, sp)), p2 = c2 + fmaf(w, cp, -__fmul_rn(u, sp));
-            const float dl = atan2f(fmaf(c1, p2, -__fmul_rn(c2, p1)), fmaf(c1, p1, __fmul_rn(c2, p2)));
-            dmin = fminf(dmin, dl);
-            dmax = fmaxf(dmax, dl);
+            const float gk = atan2f(p2, p1);
+            if (k == 0) {
+              g0 = gk;
+            } else {
+              float dl = gk - g0;
+              dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
+              dmin = fminf(dmin, dl);
+              dmax = fmaxf(dmax, dl);
+            }
           }
-          lo = gc + dmin;
-          hi = gc + dmax;
+          lo = g0 + dmin;
+          hi = g0 + dmax;
           full = hi - lo >= LIDAR_PI - 0.01f;
         }
         m = arc_ranges(la.fan, lo, hi, full, r0, r1);
@@ -361,18 +435,17 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
   int rows_total = 1;
   for (int row0 = 0; row0 < rows_total; row0 += MAX_ROWS) {
     int nrows = 0;
-    const int total = lidar_rows(v, Rr, ex, ey, row0, h, lane, nrows, rows_total);
+    const int total = lidar_rows(v, la.lcell, Rr, ex, ey, row0, h, lane, nrows, rows_total);
     walk_rows(h, nrows, total, lane, [&](unsigned p, bool valid) {
       int m = 0;
       unsigned r0 = 0, r1 = 0;
       float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
       float2 gb = make_float2(0.f, 0.f);
-      const unsigned nx = valid ? (unsigned)v.next[p] : (unsigned)NO_SEGMENT;
-      if (nx != NO_SEGMENT) {
-        const float2 a = v.xy[p], b = v.xy[nx];
-        const float wx = a.x - ex, wy = a.y - ey, dx = b.x - a.x, dy = b.y - a.y;
+      if (valid) {
+        const float4 sg = la.lsegs[p];
+        const float wx = sg.x - ex, wy = sg.y - ey, dx = sg.z - sg.x, dy = sg.w - sg.y;
         const float dd = dist2(dx, dy);
-        const float tp = dd > 0.f ? clampf(-fmaf(wx, dx, __fmul_rn(wy, dy)) / dd, 0.f, 1.f) : 0.f;
+        const float tp = dd > 0.f ? clampf(__fdividef(-fmaf(wx, dx, __fmul_rn(wy, dy)), dd), 0.f, 1.f) : 0.f;
         const float dist = sqrtf(dist2(fmaf(tp, dx, wx), fmaf(tp, dy, wy)));
         if (dist <= R + 1e-3f) {
           const float w1 = rot_x(cs, ss, wx, wy), w2 = rot_y(cs, ss, wx, wy);
@@ -382,13 +455,12 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
           bool full = dist < LIDAR_NEAR_FULL;
           float lo = 0.f, hi = 0.f;
           if (!full) {
-            const float m1 = fmaf(0.5f, d1, w1), m2 = fmaf(0.5f, d2, w2);   // midpoint
-            const float gm = atan2f(m2, m1);
-            const float b1 = w1 + d1, b2 = w2 + d2;
-            const float da = atan2f(fmaf(m1, w2, -__fmul_rn(m2, w1)), fmaf(m1, w1, __fmul_rn(m2, w2)));
-            const float db = atan2f(fmaf(m1, b2, -__fmul_rn(m2, b1)), fmaf(m1, b1, __fmul_rn(m2, b2)));
-            lo = gm + fminf(da, db);
-            hi = gm + fmaxf(da, db);
+            // end point directions; the short way between them is the arc
+            const float ga0 = atan2f(w2, w1), gb0 = atan2f(w2 + d2, w1 + d1);
+            float dl = gb0 - ga0;
+            dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
+            lo = dl >= 0.f ? ga0 : gb0;
+            hi = lo + fabsf(dl);
             full = hi - lo >= LIDAR_PI - 0.01f;
           }
           m = arc_ranges(la.fan, lo, hi, full, r0, r1);
@@ -405,30 +477,41 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
   lidar_write(keys, n, R, false, drow, crow, lane);
 }
 
-// Per-stage form: one warp per agent over the whole batch, everything read
-// from global memory.  Dynamic shared memory: WARPS * warp_bytes.
+// Stand-alone scan of every agent (the per-stage form, and the second
+// launch of the split batched form): persistent CTAs, each warp takes the
+// next agent from a global counter, so no warp waits for another.  The
+// scene is read from global memory.  Dynamic shared memory: WARPS *
+// warp_bytes, then the ray directions.
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_lidar(DevEnv e, LidarArgs la) {
+__global__ void __launch_bounds__(WARPS * 32, 1) k_lidar(DevEnv e, LidarArgs la, unsigned* counter) {
   extern __shared__ __align__(16) unsigned char lidar_smem_raw[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * WARPS + wib;
-  if (i >= e.A) return;
+  float2* sdirs = reinterpret_cast<float2*>(lidar_smem_raw + (size_t)WARPS * la.warp_bytes);
+  lidar_stage_dirs(sdirs, la.dirs, la.fan.n);
+  __syncthreads();
+  la.dirs = sdirs;
   unsigned char* base = lidar_smem_raw + (size_t)wib * la.warp_bytes;
   LidarWarpHead& h = *reinterpret_cast<LidarWarpHead*>(base);
   unsigned* keys = reinterpret_cast<unsigned*>(base + sizeof(LidarWarpHead));
-  const int w = e.agent_world[i];
-  const int a0 = e.agent_off[w];
-  WorldView v;
-  v.state = e.state + a0;
-  v.stat = e.stat + a0;
-  v.cs = nullptr;
-  v.flags = e.flags + a0;
-  v.n = e.agent_off[w + 1] - a0;
-  road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
-  v.g = e.rgrid[w];
-  lidar_agent(v, i - a0, e.R, la.head ? la.head[i] : 0.f, la, la.depth + (size_t)i * la.fan.n,
-              la.cls ? la.cls + (size_t)i * la.fan.n : nullptr, h, keys, lane);
+  for (;;) {
+    int i = 0;
+    if (lane == 0) i = (int)atomicAdd(counter, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= e.A) break;
+    const int w = e.agent_world[i];
+    const int a0 = e.agent_off[w];
+    WorldView v;
+    v.state = e.state + a0;
+    v.stat = e.stat + a0;
+    v.cs = nullptr;
+    v.flags = e.flags + a0;
+    v.n = e.agent_off[w + 1] - a0;
+    road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
+    v.g = e.rgrid[w];
+    lidar_agent(v, i - a0, e.R, la.head ? la.head[i] : 0.f, la, la.depth + (size_t)i * la.fan.n,
+                la.cls ? la.cls + (size_t)i * la.fan.n : nullptr, h, keys, lane);
+  }
 }
 
 // Ray directions of the fan in the sensor frame, (cos, sin) of

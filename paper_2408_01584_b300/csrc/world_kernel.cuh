@@ -97,7 +97,7 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 
 // Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents]
 // then per warp an ObsWarpSmem (radial observation) or LidarWarpHead + one
-// key per ray (LIDAR).
+// key per ray followed by the CTA's copy of the ray directions (LIDAR).
 template <int WARPS, bool LIDAR = false>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
@@ -114,6 +114,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
   unsigned char* lbase = warp_base + (size_t)wid * (size_t)a.lidar.warp_bytes;
   LidarWarpHead& lh = *reinterpret_cast<LidarWarpHead*>(lbase);
   unsigned* lkeys = reinterpret_cast<unsigned*>(lbase + sizeof(LidarWarpHead));
+  LidarArgs lar = a.lidar;
+  if constexpr (LIDAR) {
+    float2* sdirs = reinterpret_cast<float2*>(warp_base + (size_t)WARPS * (size_t)a.lidar.warp_bytes);
+    lidar_stage_dirs(sdirs, a.lidar.dirs, a.lidar.fan.n);
+    lar.dirs = sdirs;
+  }
   if (tid == 0) {
     mbar_init(bar, 1);
     s_abort = 0;
@@ -317,7 +323,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
       for (int li = wid; li < n;) {
         const int i = a0 + li;
         if constexpr (LIDAR) {
-          const LidarArgs& la = a.lidar;
+          const LidarArgs& la = lar;
           const size_t ro = (size_t)i * la.fan.n;
           const float hd = la.head ? la.head[i] : 0.f;
           if (use_tile) lidar_agent(vt, li, e.R, hd, la, la.depth + ro, la.cls ? la.cls + ro : nullptr, lh, lkeys, lane);

@@ -50,7 +50,8 @@ class gd_config(C.Structure):
                 ("dt", C.c_float), ("v_max", C.c_float), ("collision_penalty", C.c_float),
                 ("offroad_penalty", C.c_float), ("smooth_c", C.c_float), ("flags", C.c_uint32),
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
-                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float)]
+                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
+                ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32)]
 
 
 class gd_scene_batch(C.Structure):
@@ -66,7 +67,8 @@ class gd_info(C.Structure):
                 ("feat", C.c_int32), ("max_agents_per_world", C.c_int32), ("k_road", C.c_int32),
                 ("n_partners", C.c_int32), ("episode_len", C.c_int32), ("device_bytes", C.c_int64),
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
-                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32)]
+                ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
+                ("lidar_road_tile", C.c_int32), ("lidar_split", C.c_int32)]
 
 
 _lib = None

@@ -156,6 +156,33 @@ def test_lidar_fused_equals_per_stage_and_graph_equals_step_loop():
         assert torch.equal(a, b)
 
 
+def test_lidar_every_tuning_choice_gives_the_same_scan():
+    """CTA sizes 128 / 256 / 384 with and without the road tile, and the
+    split form (step, then a scan over all agents), on road grids of 6 and
+    12 m cells, produce bit-identical depths and classes."""
+    from paper_2408_01584_b300 import gd
+    sc = small_scene(seed=8)
+    A, n, T = sc.num_agents, 1000, 3
+    acts = torch.from_numpy(scenes.make_actions(T, A, 8)).cuda().contiguous()
+    ref = None
+    choices = [(b, t, 0) for b in (128, 256, 384) for t in (0, 1)] + [(256, 0, 1)]
+    for (block, no_tile, split), cell in [(c, cell) for c in choices for cell in (6.0, 12.0)]:
+        env = _env(sc, "fused", n, 2 * math.pi, lidar_block_size=block, lidar_no_tile=no_tile,
+                   lidar_split=split, road_cell=cell)
+        info = gd.gd_get_info(env.h)
+        assert info.lidar_block_size == block and info.lidar_road_tile == 1 - no_tile
+        assert info.lidar_split == split
+        depth = torch.empty(T, A, n, device="cuda")
+        cls = torch.empty(T, A, n, dtype=torch.uint8, device="cuda")
+        gd.gd_rollout_lidar(env.h, T, acts, None, depth, cls, True)
+        env.sync()
+        out = (depth.cpu(), cls.cpu())
+        if ref is None:
+            ref = out
+        assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]), (block, no_tile, split, cell)
+        env.close()
+
+
 @pytest.mark.parametrize("fov,head", [(2 * math.pi, False), (2 * math.pi / 3, True)])
 def test_lidar_full_size_workload_sampled(fov, head):
     """1024 worlds x 64 agents, 4000 road points each, 3000 rays: three
