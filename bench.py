@@ -28,10 +28,12 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
 def _kernel_source_hash():
-    import glob
+    """Hash of the sources the radial-observation k_world is compiled from
+    (its device code and the limits in the header)."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2408_01584_b300", "csrc", "*.cu*")))
+    csrc = os.path.join(ROOT, "paper_2408_01584_b300", "csrc")
+    files = [os.path.join(csrc, f) for f in ("gd_device.cuh", "observe_kernel.cuh", "world_kernel.cuh")]
     for f in files + [os.path.join(ROOT, "include", "gd.h")]:
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -315,9 +317,73 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
     return out
 
 
+def bench_lidar(workload, n_rays, fov, head, steps, warmup, dev, stream, flush, seed=0, cpu_s=8.0):
+    """Batched rollouts with the LiDAR / view-cone observation (Sec. 3.2
+    "Sensor modalities") instead of the radius filter: n_rays rays over fov
+    radians per agent per step, autotuned, one CUDA graph per episode; head
+    rotations (when `head`) drawn per step and agent in [-1, 1] rad.  The
+    oracle's scan of the first world's agents gives the CPU rate."""
+    import math
+    import numpy as np
+    import torch
+    from oracle import Oracle, OracleConfig
+    from oracle.oracle import num_threads
+    from paper_2408_01584_b300 import gd, scenes
+    wl = scenes.WORKLOADS[workload]
+    T = wl["steps"]
+    sc = scenes.workload_scene(workload, seed)
+    cfg = workload_cfg(workload)
+    with torch.cuda.stream(stream):
+        env = gd.Env(sc, stream=stream, lidar_rays=n_rays, lidar_fov=fov,
+                     **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        gd.gd_autotune(env.h)
+        info = gd.gd_get_info(env.h)
+        A = env.A
+        actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
+        hd = torch.from_numpy(np.random.default_rng(seed).uniform(-1, 1, (T, A)).astype(np.float32)).to(dev) \
+            if head else None
+
+        def run():
+            gd.gd_reset(env.h, None)
+            gd.gd_rollout_lidar(env.h, T, actions, hd, env.depth, env.cls, False)
+
+        for _ in range(warmup):
+            run()
+        ms = _time_rollouts(run, steps, stream, flush)
+        gd.gd_sync(env.h)
+    hbm, peak_kind = _peaks()
+    step_s = statistics.mean(ms) / T / 1e3
+    algo = 5.0 * n_rays + 70.0                      # depth float + class byte per ray, state/action/flags
+    achieved = algo * A / step_s / 1e9
+    # CPU: the oracle's brute-force scan of the first world's agents
+    orc = Oracle(sc.subset(0, 1), OracleConfig())
+    na = int(sc.agent_off[1])
+    t0 = time.perf_counter()
+    reps = 0
+    while time.perf_counter() - t0 < cpu_s or reps == 0:
+        orc.lidar(n_rays, fov)
+        reps += 1
+    cpu_dt = time.perf_counter() - t0
+    out = {"workload": workload, "observation": f"LiDAR {n_rays} rays over {math.degrees(fov):.0f} deg"
+           + (" with head rotation" if head else ""), "agents": A,
+           "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
+           "autotuned": {"lidar_block_size": info.lidar_block_size, "road_tile": info.lidar_road_tile,
+                         "split": info.lidar_split, "road_cell_m": round(float(info.road_cell), 3)},
+           "hbm": {"achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                   "frac": achieved / hbm, "algorithmic_bytes_per_agent_step": algo},
+           "cpu_baseline": {"value": reps * na / cpu_dt, "unit": "agent-scans/s", "cores": num_threads(),
+                            "kind": "oracle", "sample": f"{na} agents of world 0, {reps} scans, {cpu_dt:.1f} s"}}
+    env.close()
+    return out
+
+
 def run_profile(args):
     """Batched rollouts only (default kernel shape, no tuner, no other legs),
-    so that a profiler sees warm-up + timed k_world launches and nothing else."""
+    so that a profiler sees warm-up + timed k_world launches and nothing else.
+    --lidar N: the LiDAR rollout (N rays over --fov degrees, split form:
+    k_world step + k_lidar scan per simulator step) instead of the radial
+    one; --worlds W: the first W worlds of the workload only."""
+    import math
     import torch
     from paper_2408_01584_b300 import gd, scenes
     from paper_2408_01584_b300.build import build
@@ -326,22 +392,29 @@ def run_profile(args):
     wl = scenes.WORKLOADS[args.workload]
     T = wl["steps"]
     sc = scenes.workload_scene(args.workload, 0)
+    if args.worlds:
+        sc = sc.subset(0, args.worlds)
     cfg = workload_cfg(args.workload)
     stream = torch.cuda.Stream(dev)
+    lidar = dict(lidar_rays=args.lidar, lidar_fov=math.radians(args.fov), lidar_split=1) if args.lidar else {}
     with torch.cuda.stream(stream):
-        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED), **lidar)
         actions = torch.from_numpy(scenes.make_actions(T, env.A, 0)).to(dev)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
         def run():
             gd.gd_reset(env.h, None)
-            gd.gd_rollout(env.h, T, actions, env.obs, False, None, None)
+            if args.lidar:
+                gd.gd_rollout_lidar(env.h, T, actions, None, env.depth, env.cls, False)
+            else:
+                gd.gd_rollout(env.h, T, actions, env.obs, False, None, None)
 
         for _ in range(args.warmup):
             run()
         ms = _time_rollouts(run, args.steps, stream, flush)
         gd.gd_sync(env.h)
-    return {"profile": args.workload, "ms_per_episode": statistics.mean(ms), "launches_per_episode": T}
+    return {"profile": args.workload, "worlds": sc.num_worlds, "lidar_rays": args.lidar,
+            "ms_per_episode": statistics.mean(ms), "launches_per_episode": T * (2 if args.lidar else 1)}
 
 
 def run_ours(args, rank, world):
@@ -453,9 +526,12 @@ def run_ours(args, rank, world):
     del env_b, env_p
     if args.extras and world == 1:
         torch.cuda.empty_cache()
+        import math
         out["workloads"] = [bench_batched_forward("uneven_4096", 3, 1, dev, stream, flush),
                             bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush),
-                            bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush)]
+                            bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush),
+                            bench_lidar(args.workload, 3000, 2 * math.pi, False, 3, 1, dev, stream, flush),
+                            bench_lidar(args.workload, 3000, 2 * math.pi / 3, True, 3, 1, dev, stream, flush)]
     return out
 
 
@@ -469,8 +545,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="batched rollouts of the workload only, default tuning (for ncu captures)")
+    ap.add_argument("--lidar", type=int, default=0, help="with --profile: LiDAR rollout with this many rays")
+    ap.add_argument("--fov", type=float, default=360.0, help="with --profile --lidar: fan width (degrees)")
+    ap.add_argument("--worlds", type=int, default=0, help="with --profile: only the first W worlds")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the uneven, differentiable and forward+backward workloads")
+                    help="skip the uneven, differentiable, forward+backward and LiDAR workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
