@@ -8,7 +8,11 @@
 // Every quantity follows the paper (GPUDrive, arXiv 2408.01584) or, where the
 // paper is silent, the readings written next to the code:
 //   * dynamics: kinematic bicycle model, App. B (the seven equations for
-//     v-dot, v-bar, beta, x-dot, y-dot, theta-dot and the four update lines);
+//     v-dot, v-bar, beta, x-dot, y-dot, theta-dot and the four update lines),
+//     or the simplified invertible model of Sec. 3.2 "Agent dynamics" (a
+//     double integrator along the heading whose yaw turns by the steering
+//     curvature times the distance covered), and the expert-action inversion
+//     of a trajectory under either model;
 //   * collision: agents are convex boxes (Sec. 3.2 "Simulator sharp-edges",
 //     "Convex objects only"); the paper's BVH (Sec. 3.1) only prunes pairs,
 //     so the oracle tests every pair;
@@ -59,6 +63,7 @@ struct Config {
   int k_road, n_partners, episode_len;
   double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
   uint32_t flags;
+  int dynamics;    // 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
 };
 
 template <typename T>
@@ -99,6 +104,68 @@ void bicycle_step(const Config& c, T L, T accel, T steer, T& x, T& y, T& th, T& 
   y = y + ydot * dt;
   th = th + thdot * dt;
   v = clip<T>(v + vdot * dt, -vmax, vmax);
+}
+
+// ---- Sec. 3.2 "Agent dynamics": the simplified invertible model ------------
+// Readings where the paper is silent: the state is the same (x, y, theta, v)
+// with v the signed speed along the heading; the position is a double
+// integrator along the heading of the start of the step, so the distance
+// covered is ds = v dt + a dt^2 / 2; the yaw changes by the steering
+// command s times ds (s is a curvature, 1/m), which is the printed update
+// theta + s (v dt + a dt^2 / 2); the speed is v + a dt, not clipped (a clip
+// would make the model non-invertible).  The vehicle length plays no part.
+template <typename T>
+void invertible_step(const Config& c, T accel, T curv, T& x, T& y, T& th, T& v) {
+  const T dt = (T)c.dt;
+  const T ds = v * dt + (T)0.5 * accel * dt * dt;
+  x = x + std::cos(th) * ds;
+  y = y + std::sin(th) * ds;
+  th = th + curv * ds;
+  v = v + accel * dt;
+}
+
+template <typename T>
+void dynamics_step(const Config& c, T L, T a, T steer, T& x, T& y, T& th, T& v) {
+  if (c.dynamics == 1) invertible_step<T>(c, a, steer, x, y, th, v);
+  else bicycle_step<T>(c, L, a, steer, x, y, th, v);
+}
+
+// Heading change wrapped to (-pi, pi].
+template <typename T>
+T wrap_angle(T d) {
+  const T pi = (T)3.14159265358979323846;
+  while (d > pi) d -= 2 * pi;
+  while (d <= -pi) d += 2 * pi;
+  return d;
+}
+
+// Expert actions of one step of a trajectory, state s0 -> s1 (x, y, theta, v).
+// Both models: a = (v1 - v0) / dt.  Simplified model: s = dtheta / ds with
+// ds = v0 dt + a dt^2 / 2 (0 when |ds| <= 1e-6 m: a vehicle that does not
+// move has no defined curvature); replaying (a, s) reproduces theta, v and
+// the positions exactly.  Kinematic bicycle: with v-bar = v0 + a dt / 2 (no
+// clip) the yaw rate equation of App. B gives k = dtheta L / (v-bar dt) =
+// cos(beta) tan(delta) = u / sqrt(1 + u^2 / 4), u = tan(delta), so
+// u = k / sqrt(1 - k^2 / 4) for |k| < 2 (k clamped to +-1.99; delta = 0 when
+// |v-bar dt| <= 1e-6 m); theta and v are matched, the positions then follow
+// the slip angle, which is why this model is not fully invertible.
+template <typename T>
+void invert_step(const Config& c, T L, const T* s0, const T* s1, T& accel, T& steer) {
+  const T dt = (T)c.dt;
+  accel = (s1[3] - s0[3]) / dt;
+  const T dth = wrap_angle(s1[2] - s0[2]);
+  if (c.dynamics == 1) {
+    const T ds = s0[3] * dt + (T)0.5 * accel * dt * dt;
+    steer = std::fabs(ds) > (T)1e-6 ? dth / ds : (T)0;
+  } else {
+    const T vb = s0[3] + (T)0.5 * accel * dt;
+    if (std::fabs(vb * dt) <= (T)1e-6) {
+      steer = 0;
+    } else {
+      const T k = clip<T>(dth * L / (vb * dt), (T)-1.99, (T)1.99);
+      steer = std::atan(k / std::sqrt(1 - k * k / 4));
+    }
+  }
 }
 
 // ---- separating-axis penetration -----------------------------------------
@@ -253,7 +320,7 @@ void step(Env<T>& e, const float* actions, const float* post_state, float* rewar
         e.x[i] = post_state[4 * i + 0]; e.y[i] = post_state[4 * i + 1];
         e.th[i] = post_state[4 * i + 2]; e.v[i] = post_state[4 * i + 3];
       } else {
-        bicycle_step<T>(e.cfg, e.len[i], (T)actions[2 * i], (T)actions[2 * i + 1], e.x[i], e.y[i], e.th[i], e.v[i]);
+        dynamics_step<T>(e.cfg, e.len[i], (T)actions[2 * i], (T)actions[2 * i + 1], e.x[i], e.y[i], e.th[i], e.v[i]);
       }
     }
     decide_world(e, w, active, reward, done, world_done, cm, om, gm, sr);
@@ -515,6 +582,7 @@ typedef struct or_config {
   int32_t k_road, n_partners, episode_len;
   double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
   uint32_t flags;
+  int32_t dynamics;
 } or_config;
 
 void* or_create(const or_config* cfg, int precision, int32_t W, const int32_t* agent_off, const int32_t* road_off,
@@ -522,7 +590,7 @@ void* or_create(const or_config* cfg, int precision, int32_t W, const int32_t* a
                 const float* wid, const float* gx, const float* gy, const uint8_t* atype, const float* rx,
                 const float* ry, const uint8_t* rtype, const int32_t* rpoly) {
   Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
-           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags};
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
   auto* h = new Handle{precision, nullptr};
   if (precision == 32)
     h->env = make_env<float>(&c, W, agent_off, road_off, x, y, th, v, len, wid, gx, gy, atype, rx, ry, rtype, rpoly);
@@ -629,14 +697,27 @@ void or_set_state(void* hv, const float* state, const uint8_t* flags, const int3
   });
 }
 
-// Bicycle-model step of a flat array of independent agents (no world, no
-// flags): state double [n,4] in place, actions double [n,2], length double [n].
+// Dynamics step (cfg->dynamics selects the model) of a flat array of
+// independent agents (no world, no flags): state double [n,4] in place,
+// actions double [n,2], length double [n].
 void or_bicycle(const or_config* cfg, int64_t n, double* state, const double* actions, const double* length) {
   Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
-           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags};
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
   for (int64_t i = 0; i < n; ++i)
-    bicycle_step<double>(c, length[i], actions[2 * i], actions[2 * i + 1], state[4 * i], state[4 * i + 1],
-                         state[4 * i + 2], state[4 * i + 3]);
+    dynamics_step<double>(c, length[i], actions[2 * i], actions[2 * i + 1], state[4 * i], state[4 * i + 1],
+                          state[4 * i + 2], state[4 * i + 3]);
+}
+
+// Expert actions of trajectories under cfg->dynamics (see invert_step):
+// states double [steps+1, n, 4], length double [n]; actions double [steps, n, 2].
+void or_invert(const or_config* cfg, int32_t steps, int64_t n, const double* states, const double* length,
+               double* actions) {
+  Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
+  for (int t = 0; t < steps; ++t)
+    for (int64_t i = 0; i < n; ++i)
+      invert_step<double>(c, length[i], states + ((int64_t)t * n + i) * 4, states + ((int64_t)(t + 1) * n + i) * 4,
+                          actions[((int64_t)t * n + i) * 2], actions[((int64_t)t * n + i) * 2 + 1]);
 }
 
 // Penetration depth of two boxes (cx, cy, theta, length, width) and of a box

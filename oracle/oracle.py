@@ -37,7 +37,8 @@ class _Cfg(C.Structure):
     _fields_ = [("k_road", C.c_int32), ("n_partners", C.c_int32), ("episode_len", C.c_int32),
                 ("obs_radius", C.c_double), ("goal_radius", C.c_double), ("dt", C.c_double),
                 ("v_max", C.c_double), ("collision_penalty", C.c_double),
-                ("offroad_penalty", C.c_double), ("smooth_c", C.c_double), ("flags", C.c_uint32)]
+                ("offroad_penalty", C.c_double), ("smooth_c", C.c_double), ("flags", C.c_uint32),
+                ("dynamics", C.c_int32)]
 
 
 def load_oracle():
@@ -59,6 +60,7 @@ def load_oracle():
         lib.or_get_state.argtypes = [vp] * 5
         lib.or_set_state.argtypes = [vp] * 4
         lib.or_bicycle.argtypes = [C.POINTER(_Cfg), i64, vp, vp, vp]
+        lib.or_invert.argtypes = [C.POINTER(_Cfg), i32, i64, vp, vp, vp]
         lib.or_box_box.restype = C.c_double
         lib.or_box_box.argtypes = [vp, vp]
         lib.or_box_seg.restype = C.c_double
@@ -86,6 +88,7 @@ class OracleConfig:
     term_collision: bool = False
     term_offroad: bool = False
     auto_reset: bool = False
+    dynamics: int = 0          # 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
 
     @property
     def feat(self) -> int:
@@ -95,7 +98,8 @@ class OracleConfig:
         fl = (TERM_COLLISION if self.term_collision else 0) | (TERM_OFFROAD if self.term_offroad else 0) \
             | (AUTO_RESET if self.auto_reset else 0)
         return _Cfg(self.k_road, self.n_partners, self.episode_len, self.obs_radius, self.goal_radius,
-                    self.dt, self.v_max, self.collision_penalty, self.offroad_penalty, self.smooth_c, fl)
+                    self.dt, self.v_max, self.collision_penalty, self.offroad_penalty, self.smooth_c, fl,
+                    self.dynamics)
 
 
 def _p(a):
@@ -210,7 +214,8 @@ class Oracle:
 
 
 def bicycle(cfg: OracleConfig, state, actions, length):
-    """App. B step of independent agents in float64: state [n,4] (x, y,
+    """One dynamics step (cfg.dynamics: App. B, or the simplified invertible
+    model of Sec. 3.2) of independent agents in float64: state [n,4] (x, y,
     theta, v), actions [n,2] (accel, steer), length [n]; returns new state."""
     lib = load_oracle()
     s = np.array(state, dtype=np.float64, copy=True).reshape(-1, 4)
@@ -219,6 +224,19 @@ def bicycle(cfg: OracleConfig, state, actions, length):
     c = cfg.c()
     lib.or_bicycle(C.byref(c), s.shape[0], _p(s), _p(a), _p(L))
     return s
+
+
+def invert(cfg: OracleConfig, states, length):
+    """Expert actions [T, n, 2] of trajectories states [T+1, n, 4] under
+    cfg.dynamics (readings in oracle.cpp, above invert_step), float64."""
+    lib = load_oracle()
+    s = _c(states, np.float64)
+    T, n = s.shape[0] - 1, s.shape[1]
+    L = _c(np.broadcast_to(length, (n,)), np.float64)
+    out = np.zeros((T, n, 2))
+    c = cfg.c()
+    lib.or_invert(C.byref(c), T, n, _p(s), _p(L), _p(out))
+    return out
 
 
 def box_box(p, q) -> float:
