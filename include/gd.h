@@ -18,6 +18,9 @@
  *               and view-cone observations (Sec. 3.2 "Sensor modalities":
  *               rays cast against bounding boxes and road edges, all around
  *               or in a cone turned by a head-rotation action);
+ *   gd_invert_actions   expert actions that reproduce a trajectory (Sec. 3.2
+ *               "Agent dynamics": exact under the simplified invertible
+ *               model, heading and speed under the kinematic bicycle);
  *   gd_rollout_backward / gd_step_backward   adjoint of the dynamics, the
  *               ego-frame observation and a smooth goal-distance reward (the
  *               paper has no gradient; this is an extension).
@@ -38,8 +41,8 @@
  *     launched nothing.  gd_last_error(env) returns a message for the last
  *     error of that env (gd_last_error(NULL): the last gd_create error of
  *     the calling thread).  Faults found on the device (a non-finite
- *     action, a steering angle with |delta| >= pi/2) set a sticky error word
- *     that gd_sync reports.
+ *     action, a steering angle with |delta| >= pi/2 under the kinematic
+ *     bicycle) set a sticky error word that gd_sync reports.
  *   - Observation row layout (float32, F = 8 + 8P + 4K columns):
  *       ego[8]       = (v, length, width, goal_x', goal_y', collided,
  *                       offroad, goal_reached)
@@ -68,6 +71,10 @@ typedef enum gd_status {
   GD_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
   GD_ERR_STATE = 6         /* call not valid in the env's current state */
 } gd_status;
+
+/* gd_config.dynamics */
+#define GD_DYN_BICYCLE 0      /* kinematic bicycle model, App. B (default); steer = wheel angle (rad) */
+#define GD_DYN_INVERTIBLE 1   /* simplified invertible model, Sec. 3.2 "Agent dynamics"; steer = curvature (1/m) */
 
 /* gd_config.flags */
 #define GD_TERM_COLLISION 0x1u   /* agent/agent collision ends the agent's episode (Sec. 3.2) */
@@ -122,6 +129,11 @@ typedef struct gd_config {
                                 instead of a shared-memory tile (more warps per SM); default 0 */
   int32_t lidar_split;       /* 1: with GD_BATCHED the step and the LiDAR scan are two launches
                                 (the scan over all agents at once); default 0 = one fused launch */
+  int32_t dynamics;          /* GD_DYN_BICYCLE (default) or GD_DYN_INVERTIBLE: the simplified model,
+                                a double integrator along the heading of the start of the step,
+                                ds = v dt + a dt^2 / 2, x += cos(theta) ds, y += sin(theta) ds,
+                                theta += steer * ds, v += a dt (no speed clip; length unused);
+                                GD_DIFFERENTIABLE needs GD_DYN_BICYCLE */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -236,6 +248,24 @@ gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* 
  * or NULL; done: uint8 [T,A] or NULL. */
 gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, const float* head, float* depth,
                            uint8_t* cls, int32_t obs_per_step, float* reward, uint8_t* done);
+
+/* Expert actions of trajectories under the env's dynamics model (Sec. 3.2
+ * "Agent dynamics": actions computed from logged trajectories and replayed
+ * to imitate them).  For each agent i and step t, from states s0 = state(t),
+ * s1 = state(t+1):
+ *   accel = (v1 - v0) / dt;  dtheta = theta1 - theta0 wrapped to [-pi, pi];
+ *   GD_DYN_INVERTIBLE: steer = dtheta / (v0 dt + accel dt^2 / 2), 0 when that
+ *     distance is <= 1e-6 m; replaying the actions reproduces the trajectory
+ *     (the model is invertible);
+ *   GD_DYN_BICYCLE: with k = dtheta L / (v-bar dt), v-bar = v0 + accel dt / 2,
+ *     k clamped to +-1.99: steer = atan(k / sqrt(1 - k^2 / 4)), 0 when
+ *     |v-bar dt| <= 1e-6 m; replaying matches heading and speed while no
+ *     speed is clipped, not the positions (the model is not invertible).
+ * L is each agent's length from the scene.  Agents' flags are not used.
+ *   states:  device float [steps+1, A, 4] (x, y, theta, v), 16-byte aligned
+ *   actions: device float [steps, A, 2] (accel, steer), 8-byte aligned
+ * Asynchronous; errors: GD_ERR_INVALID_ARG (NULL, misaligned, steps < 0). */
+gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, float* actions);
 
 /* Differentiable rollout (an extension; the paper has no gradient).  Runs
  * `steps` fused steps from the current state, like gd_rollout, and writes

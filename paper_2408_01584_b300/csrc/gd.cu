@@ -13,6 +13,7 @@
 #include "step_kernels.cuh"
 #include "world_kernel.cuh"
 #include "lidar_kernel.cuh"
+#include "invert_kernel.cuh"
 #include "adjoint_kernel.cuh"
 
 using namespace gd;
@@ -430,6 +431,10 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_block_size must be 0, 128, 256 or 384");
   if (c->lidar_no_tile != 0 && c->lidar_no_tile != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_no_tile must be 0 or 1");
   if (c->lidar_split != 0 && c->lidar_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_split must be 0 or 1");
+  if (c->dynamics != GD_DYN_BICYCLE && c->dynamics != GD_DYN_INVERTIBLE)
+    return fail(nullptr, GD_ERR_INVALID_ARG, "dynamics must be GD_DYN_BICYCLE or GD_DYN_INVERTIBLE");
+  if (c->dynamics != GD_DYN_BICYCLE && (c->flags & GD_DIFFERENTIABLE))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE needs the kinematic bicycle (GD_DYN_BICYCLE)");
   if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
   const int W = s->num_worlds;
@@ -550,6 +555,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   d.cpen = cfg->collision_penalty; d.opn = cfg->offroad_penalty; d.smooth_c = cfg->smooth_c;
   d.agent_cell = max_diag * 1.01f + 0.01f;
   d.cflags = cfg->flags;
+  d.dyn = cfg->dynamics;
   std::vector<uint8_t> zeros_a(A, 0);
   std::vector<int> zeros_w(W, 0);
   int* p_aoff; int* p_roff; int* p_aw; float4* p_state; float4* p_init; float4* p_stat; uint8_t* p_type;
@@ -1012,6 +1018,25 @@ gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, con
   return GD_OK;
 }
 
+// ---- expert-action inversion -------------------------------------------------
+
+gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, float* actions) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
+  if (steps == 0 || env->A == 0) return GD_OK;
+  if (!states || !actions) return fail(env, GD_ERR_INVALID_ARG, "states and actions must not be NULL");
+  if (!aligned16(states) || ((uintptr_t)actions & 7u))
+    return fail(env, GD_ERR_INVALID_ARG, "states must be 16-byte and actions 8-byte aligned");
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long n = (long long)steps * env->A;
+  const int grid = (int)std::max(1LL, std::min<long long>((n + 255) / 256, 8LL * std::max(nsm, 1)));
+  k_invert<<<grid, 256, 0, env->stream>>>(env->d, steps, reinterpret_cast<const float4*>(states),
+                                         reinterpret_cast<float2*>(actions));
+  return launch_check(env, "gd_invert_actions");
+}
+
 // ---- differentiable rollouts ------------------------------------------------
 
 static gd_status need_diff(gd_env* env, const char* what) {
@@ -1330,7 +1355,8 @@ gd_status gd_sync(gd_env* env) {
   if (w) {
     cudaMemsetAsync(env->d.err, 0, sizeof(unsigned), env->stream);
     cudaStreamSynchronize(env->stream);
-    if (w & ERR_ACTION) return fail(env, GD_ERR_INVALID_ARG, "a step saw a non-finite action or |steer| >= pi/2");
+    if (w & ERR_ACTION)
+      return fail(env, GD_ERR_INVALID_ARG, "a step saw a non-finite action (or |steer| >= pi/2 for the kinematic bicycle)");
     if (w & ERR_TIMEOUT) return fail(env, GD_ERR_TIMEOUT, "a bounded device wait gave up");
     return fail(env, GD_ERR_CAPACITY, "a device-side capacity was exceeded");
   }

@@ -25,7 +25,7 @@
 
 namespace gd {
 
-constexpr unsigned ERR_ACTION = 1u;     // non-finite action or |steer| >= pi/2
+constexpr unsigned ERR_ACTION = 1u;     // non-finite action, or |steer| >= pi/2 (kinematic bicycle)
 constexpr unsigned ERR_TIMEOUT = 2u;    // a bounded wait gave up
 constexpr unsigned ERR_CAPACITY = 4u;   // a device-side capacity was exceeded
 
@@ -55,6 +55,7 @@ struct DevEnv {
   int W, A, N, K, P, F, T;
   float R, R2, goal_r, dt, vmax, cpen, opn, smooth_c, agent_cell;
   int topk;              // road top-K: 1 = bucket rank, 2 = bitonic sort when <= 256 points are in range
+  int dyn;               // 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
   uint32_t cflags;
   const int* agent_off;
   const int* road_off;
@@ -102,6 +103,37 @@ __device__ __forceinline__ void bicycle_step(float4& s, float accel, float steer
   s.y = fmaf(ydot, dt, s.y);
   s.z = fmaf(thdot, dt, s.z);
   s.w = clampf(fmaf(accel, dt, s.w), -vmax, vmax);
+}
+
+// Simplified invertible model (Sec. 3.2 "Agent dynamics"): the position is a
+// double integrator along the heading of the start of the step, the yaw
+// turns by the steering curvature `curv` (1/m) times the distance covered,
+// ds = v dt + a dt^2 / 2, and the speed is v + a dt (no clip, so the model
+// stays invertible).  Independent of the vehicle length.  Rounding spelled
+// out as in bicycle_step.
+__device__ __forceinline__ void invertible_step(float4& s, float accel, float curv, float dt) {
+  const float ds = fmaf(__fmul_rn(0.5f, accel), __fmul_rn(dt, dt), __fmul_rn(s.w, dt));
+  float sn, cs;
+  sincosf(s.z, &sn, &cs);
+  s.x = fmaf(cs, ds, s.x);
+  s.y = fmaf(sn, ds, s.y);
+  s.z = fmaf(curv, ds, s.z);
+  s.w = fmaf(accel, dt, s.w);
+}
+
+// One dynamics step of an agent; false when the action is not valid for the
+// model (non-finite, or |steer| >= pi/2 for the kinematic bicycle), in
+// which case the state is left unchanged.
+__device__ __forceinline__ bool dynamics_step(int dyn, float4& s, float accel, float steer, float L, float dt,
+                                              float vmax) {
+  if (!isfinite(accel) || !isfinite(steer)) return false;
+  if (dyn == 1) {
+    invertible_step(s, accel, steer, dt);
+    return true;
+  }
+  if (fabsf(steer) >= 1.5707963f) return false;
+  bicycle_step(s, accel, steer, L, dt, vmax);
+  return true;
 }
 
 // Ego-frame rotation by -theta of the offset (dx, dy), given c = cos theta,

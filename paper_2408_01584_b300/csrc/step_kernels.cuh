@@ -1,7 +1,8 @@
 // Per-stage step kernels (the "plain" form: one launch per stage).
 //
 //   k_reset_worlds  masked world reset (snapshot copy)
-//   k_dynamics      bicycle model of App. B for every agent still in the scene
+//   k_dynamics      bicycle model of App. B (or the simplified invertible model of
+//                   Sec. 3.2) for every agent still in the scene
 //   k_agent_grid    per world: uniform-grid keys of the active agents, sorted
 //   k_collide       per agent: oriented-box test against agents in the 3x3
 //                   neighbouring cells (replaces the paper's BVH broad phase, Sec. 3.1)
@@ -40,12 +41,11 @@ __global__ void k_dynamics(DevEnv e, const float2* __restrict__ actions) {
   if (i >= e.A) return;
   if (e.flags[i] & GD_FLAG_DONE) return;
   const float2 a = actions[i];
-  if (!isfinite(a.x) || !isfinite(a.y) || fabsf(a.y) >= 1.5707963f) {
+  float4 s = e.state[i];
+  if (!dynamics_step(e.dyn, s, a.x, a.y, e.stat[i].x, e.dt, e.vmax)) {
     atomicOr(e.err, ERR_ACTION);
     return;
   }
-  float4 s = e.state[i];
-  bicycle_step(s, a.x, a.y, e.stat[i].x, e.dt, e.vmax);
   e.state[i] = s;
 }
 

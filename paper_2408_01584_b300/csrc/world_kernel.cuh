@@ -1,5 +1,6 @@
 // Fused per-world kernel (the batched form): one persistent launch runs the
-// whole step -- masked reset, bicycle dynamics (App. B), agent grid and
+// whole step -- masked reset, dynamics (App. B or the simplified model of
+// Sec. 3.2), agent grid and
 // box collision, road-edge test, goal / reward / done (Sec. 3.2) -- and the
 // observation of every world, taking worlds from a work list with an
 // atomic counter (no grid-wide synchronisation).
@@ -188,11 +189,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
         ag.act0[tid] = !(f & GD_FLAG_DONE);
         if (!(f & GD_FLAG_DONE)) {
           const float2 u = a.actions[i];
-          if (!isfinite(u.x) || !isfinite(u.y) || fabsf(u.y) >= 1.5707963f) {
-            atomicOr(e.err, ERR_ACTION);
-          } else {
-            bicycle_step(s, u.x, u.y, e.stat[i].x, e.dt, e.vmax);
-          }
+          if (!dynamics_step(e.dyn, s, u.x, u.y, e.stat[i].x, e.dt, e.vmax)) atomicOr(e.err, ERR_ACTION);
           act = true;
           key = agent_cell_key((int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f),
                                (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f), tid);

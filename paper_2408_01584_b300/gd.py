@@ -32,7 +32,9 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
-           "gd_rollout_lidar")
+           "gd_rollout_lidar", "gd_invert_actions")
+
+GD_DYN_BICYCLE, GD_DYN_INVERTIBLE = 0, 1
 
 GD_MAX_LIDAR_RAYS = 8192
 LIDAR_NONE, LIDAR_AGENT, LIDAR_ROAD_EDGE = 0, 1, 2
@@ -51,7 +53,7 @@ class gd_config(C.Structure):
                 ("offroad_penalty", C.c_float), ("smooth_c", C.c_float), ("flags", C.c_uint32),
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
-                ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32)]
+                ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32)]
 
 
 class gd_scene_batch(C.Structure):
@@ -107,6 +109,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_observe_lidar.argtypes = [vp, vp, vp, vp]
     lib.gd_step_observe_lidar.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gd_rollout_lidar.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp]
+    lib.gd_invert_actions.argtypes = [vp, i32, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -219,6 +222,12 @@ def gd_rollout_lidar(env, steps, actions, head, depth, cls=None, obs_per_step=Fa
     _check(lib, env, lib.gd_rollout_lidar(env, int(steps), _ptr(actions, align=8), _ptr(head, align=4),
                                           _ptr(depth, align=4), _ptr(cls), int(bool(obs_per_step)), _ptr(reward),
                                           _ptr(done)))
+
+
+def gd_invert_actions(env, steps, states, actions):
+    """Expert actions [steps, A, 2] of trajectories states [steps+1, A, 4]."""
+    lib = load_library()
+    _check(lib, env, lib.gd_invert_actions(env, int(steps), _ptr(states, align=16), _ptr(actions, align=8)))
 
 
 def gd_rollout_objective(env, steps, actions, obs_weight, reward_weight, ell, obs=None):
