@@ -377,6 +377,71 @@ def bench_lidar(workload, n_rays, fov, head, steps, warmup, dev, stream, flush, 
     return out
 
 
+def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
+    """The simplified invertible model (Sec. 3.2 "Agent dynamics"): batched
+    rollouts of the workload under it, and gd_invert_actions over a 91-step
+    trajectory of every agent (expert-action inversion), against HBM: the
+    inversion reads each state once (16 B per agent-step plus the lengths)
+    and writes 8 B of actions."""
+    import numpy as np
+    import torch
+    from paper_2408_01584_b300 import gd, scenes
+    wl = scenes.WORKLOADS[workload]
+    T = wl["steps"]
+    sc = scenes.workload_scene(workload, seed)
+    cfg = workload_cfg(workload)
+    with torch.cuda.stream(stream):
+        env = gd.Env(sc, stream=stream, dynamics=gd.GD_DYN_INVERTIBLE, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+        gd.gd_autotune(env.h)
+        A = env.A
+        acts_h = scenes.make_actions(T, A, seed)
+        acts_h[:, :, 1] *= 0.2 / 0.7                     # curvature U[-0.2, 0.2] 1/m
+        actions = torch.from_numpy(acts_h).to(dev)
+
+        def run():
+            gd.gd_reset(env.h, None)
+            gd.gd_rollout(env.h, T, actions, env.obs, False, None, None)
+
+        for _ in range(warmup):
+            run()
+        ms = _time_rollouts(run, steps, stream, flush)
+        # a trajectory of every agent (no agent leaves: per-stage steps without termination)
+        envt = gd.Env(sc, stream=stream, goal_radius=0.0, dynamics=gd.GD_DYN_INVERTIBLE, k_road=0, n_partners=0)
+        states = torch.empty(T + 1, A, 4, device=dev)
+        states[0] = envt.get_state()[0]
+        for t in range(T):
+            gd.gd_step(envt.h, actions[t])
+            states[t + 1] = envt.get_state()[0]
+        rec = torch.empty(T, A, 2, device=dev)
+
+        def inv():
+            gd.gd_invert_actions(envt.h, T, states, rec)
+
+        for _ in range(warmup):
+            inv()
+        ms_inv = _time_rollouts(inv, max(steps, 5), stream, flush)
+        gd.gd_sync(env.h)
+        gd.gd_sync(envt.h)
+    # recovered vs. applied actions where the vehicle moved (curvature is
+    # undefined at rest and ill-conditioned near it)
+    moving = np.abs(states[:-1, :, 3].cpu().numpy() * float(envt.cfg.dt)) > 0.05
+    d = np.abs(rec.cpu().numpy() - acts_h)
+    err = [float(d[..., 0].max()), float(d[..., 1][moving].max())]
+    hbm, peak_kind = _peaks()
+    inv_s = statistics.mean(ms_inv) / 1e3
+    algo = (T + 1) * A * 16 + A * 16 + T * A * 8
+    out = {"workload": workload, "dynamics": "simplified invertible model", "agents": A,
+           "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
+           "inversion": {"value": T * A / inv_s, "unit": "agent-steps/s", "ms": statistics.mean(ms_inv),
+                         "max_abs_error_accel_curvature": err,
+                         "note": "curvature error over steps that moved more than 5 cm",
+                         "hbm": {"achieved": algo / inv_s / 1e9, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                                 "frac": algo / inv_s / 1e9 / hbm, "algorithmic_bytes": algo}}}
+    env.close()
+    envt.close()
+    return out
+
+
 def run_profile(args):
     """Batched rollouts only (default kernel shape, no tuner, no other legs),
     so that a profiler sees warm-up + timed k_world launches and nothing else.
@@ -531,7 +596,8 @@ def run_ours(args, rank, world):
                             bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush),
                             bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush),
                             bench_lidar(args.workload, 3000, 2 * math.pi, False, 3, 1, dev, stream, flush),
-                            bench_lidar(args.workload, 3000, 2 * math.pi / 3, True, 3, 1, dev, stream, flush)]
+                            bench_lidar(args.workload, 3000, 2 * math.pi / 3, True, 3, 1, dev, stream, flush),
+                            bench_invertible(args.workload, 3, 1, dev, stream, flush)]
     return out
 
 
@@ -549,7 +615,7 @@ def main():
     ap.add_argument("--fov", type=float, default=360.0, help="with --profile --lidar: fan width (degrees)")
     ap.add_argument("--worlds", type=int, default=0, help="with --profile: only the first W worlds")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the uneven, differentiable, forward+backward and LiDAR workloads")
+                    help="skip the uneven, differentiable, forward+backward, LiDAR and invertible-model workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

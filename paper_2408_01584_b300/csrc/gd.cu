@@ -1027,11 +1027,7 @@ gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, flo
   if (!states || !actions) return fail(env, GD_ERR_INVALID_ARG, "states and actions must not be NULL");
   if (!aligned16(states) || ((uintptr_t)actions & 7u))
     return fail(env, GD_ERR_INVALID_ARG, "states must be 16-byte and actions 8-byte aligned");
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const long long n = (long long)steps * env->A;
-  const int grid = (int)std::max(1LL, std::min<long long>((n + 255) / 256, 8LL * std::max(nsm, 1)));
+  const dim3 grid((unsigned)((env->A + 255) / 256), (unsigned)((steps + INV_CHUNK - 1) / INV_CHUNK));
   k_invert<<<grid, 256, 0, env->stream>>>(env->d, steps, reinterpret_cast<const float4*>(states),
                                          reinterpret_cast<float2*>(actions));
   return launch_check(env, "gd_invert_actions");

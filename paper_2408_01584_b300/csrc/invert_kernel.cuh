@@ -13,8 +13,11 @@
 // replays exactly; the bicycle matches heading and speed (not the slip of
 // the positions) while no speed is clipped.
 //
-// One thread per (step, agent), grid-stride; reads two float4 states and the
-// length, writes one float2: memory-bound.
+// One thread per (agent, chunk of INV_CHUNK steps): the chunk's INV_CHUNK + 1
+// float4 states are all loaded before any arithmetic (that many loads in
+// flight per thread), each state once for two steps, and INV_CHUNK float2
+// actions are written; consecutive threads take consecutive agents
+// (coalesced).  Memory-bound.
 #pragma once
 #include "gd_device.cuh"
 
@@ -37,13 +40,24 @@ __device__ __forceinline__ float2 invert_one(int dyn, float4 s0, float4 s1, floa
   return make_float2(a, steer);
 }
 
-// states: [steps + 1, A] float4; actions: [steps, A] float2.
+constexpr int INV_CHUNK = 8;
+
+// states: [steps + 1, A] float4; actions: [steps, A] float2.  Grid: x over
+// agents (blockDim.x each), y over chunks of INV_CHUNK steps.
 __global__ void k_invert(DevEnv e, int steps, const float4* __restrict__ states, float2* __restrict__ actions) {
-  const long long n = (long long)steps * e.A;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % e.A);
-    actions[q] = invert_one(e.dyn, states[q], states[q + e.A], e.stat[i].x, e.dt);
-  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e.A) return;
+  const int t0 = blockIdx.y * INV_CHUNK, t1 = min(t0 + INV_CHUNK, steps);
+  const float L = e.stat[i].x;
+  const size_t A = (size_t)e.A;
+  // all loads of the chunk first (INV_CHUNK + 1 in flight per thread), then the arithmetic
+  float4 st[INV_CHUNK + 1];
+#pragma unroll
+  for (int k = 0; k <= INV_CHUNK; ++k)
+    if (t0 + k <= t1) st[k] = states[(size_t)(t0 + k) * A + i];
+#pragma unroll
+  for (int k = 0; k < INV_CHUNK; ++k)
+    if (t0 + k < t1) actions[(size_t)(t0 + k) * A + i] = invert_one(e.dyn, st[k], st[k + 1], L, e.dt);
 }
 
 }  // namespace gd
