@@ -22,6 +22,10 @@
 //     collision penalties (Sec. 3.2 "Rewards");
 //   * termination on goal, optionally on collision; removal after the goal
 //     (Sec. 3.2 "Termination conditions");
+//   * the "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges",
+//     "Initialization modes"): only agents more than a set distance (2 m)
+//     from their goal at the start are controlled; the others (parked cars)
+//     stay where they are, visible to the rest;
 //   * observation: every agent and road point within a fixed radius, in the
 //     agent's relative frame (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1),
 //     truncated to the K / P nearest;
@@ -53,9 +57,9 @@
 namespace {
 
 // flag bits of the per-agent status byte (same meaning as the library's)
-constexpr uint8_t F_DONE = 1, F_GOAL = 2, F_COLLIDED = 4, F_OFFROAD = 8;
+constexpr uint8_t F_DONE = 1, F_GOAL = 2, F_COLLIDED = 4, F_OFFROAD = 8, F_STATIC = 16;
 // configuration flag bits
-constexpr uint32_t C_TERM_COLLISION = 1, C_TERM_OFFROAD = 2, C_AUTO_RESET = 4;
+constexpr uint32_t C_TERM_COLLISION = 1, C_TERM_OFFROAD = 2, C_AUTO_RESET = 4, C_NONTRIVIAL_INIT = 32;
 constexpr uint8_t ROAD_EDGE = 1;
 constexpr uint8_t PEDESTRIAN = 2;
 
@@ -64,6 +68,7 @@ struct Config {
   double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
   uint32_t flags;
   int dynamics;    // 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
+  double nontrivial_dist;   // m: with C_NONTRIVIAL_INIT, agents this close to their goal are not controlled
 };
 
 template <typename T>
@@ -231,12 +236,20 @@ void reset_world(Env<T>& e, int w) {
   e.world_done[w] = 0;
 }
 
+// End of a world's episode: every controlled agent done (a world with no
+// controlled agent only times out), or t = T.  Agents that are not
+// controlled (F_STATIC) never end and do not hold the episode open.
 template <typename T>
 bool world_is_done(const Env<T>& e, int w) {
   const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
-  bool all = a1 > a0;
-  for (int i = a0; i < a1; ++i) all = all && (e.flags[i] & F_DONE);
-  return all || e.t[w] >= e.cfg.episode_len;
+  int controlled = 0;
+  bool all = true;
+  for (int i = a0; i < a1; ++i) {
+    if (e.flags[i] & F_STATIC) continue;
+    ++controlled;
+    all = all && (e.flags[i] & F_DONE);
+  }
+  return (controlled > 0 && all) || e.t[w] >= e.cfg.episode_len;
 }
 
 // Decisions of one step for world w after the dynamics have moved its active
@@ -248,7 +261,7 @@ void decide_world(Env<T>& e, int w, const std::vector<uint8_t>& active, float* r
   const Config& c = e.cfg;
   const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
   for (int i = a0; i < a1; ++i) {
-    if (!active[i - a0]) {
+    if (!active[i - a0] || (e.flags[i] & F_STATIC)) {     // out of the scene, or not controlled
       if (reward) reward[i] = 0.f;
       if (coll_margin) coll_margin[i] = -INFINITY;
       if (off_margin) off_margin[i] = -INFINITY;
@@ -297,7 +310,7 @@ void decide_world(Env<T>& e, int w, const std::vector<uint8_t>& active, float* r
   e.t[w] += 1;
   e.world_done[w] = world_is_done(e, w) ? 1 : 0;
   if (done)
-    for (int i = a0; i < a1; ++i) done[i] = (e.flags[i] & F_DONE) ? 1 : 0;
+    for (int i = a0; i < a1; ++i) done[i] = (e.flags[i] & (F_DONE | F_STATIC)) ? 1 : 0;
   if (world_done) world_done[w] = e.world_done[w];
 }
 
@@ -315,7 +328,7 @@ void step(Env<T>& e, const float* actions, const float* post_state, float* rewar
     std::vector<uint8_t> active(a1 - a0);
     for (int i = a0; i < a1; ++i) {
       active[i - a0] = !(e.flags[i] & F_DONE);
-      if (!active[i - a0]) continue;                       // done agents are frozen
+      if (!active[i - a0] || (e.flags[i] & F_STATIC)) continue;   // done and uncontrolled agents do not move
       if (post_state) {
         e.x[i] = post_state[4 * i + 0]; e.y[i] = post_state[4 * i + 1];
         e.th[i] = post_state[4 * i + 2]; e.v[i] = post_state[4 * i + 3];
@@ -558,6 +571,11 @@ Env<T>* make_env(const Config* cfg, int W, const int32_t* agent_off, const int32
   e->rpoly.assign(rpoly, rpoly + e->N);
   e->x = e->x0; e->y = e->y0; e->th = e->th0; e->v = e->v0;
   e->flags0.assign(e->A, 0);
+  if (cfg->flags & C_NONTRIVIAL_INIT)
+    for (int i = 0; i < e->A; ++i) {
+      const double dx = (double)e->x0[i] - (double)e->gx[i], dy = (double)e->y0[i] - (double)e->gy[i];
+      if (std::sqrt(dx * dx + dy * dy) <= cfg->nontrivial_dist) e->flags0[i] = F_STATIC;
+    }
   e->flags = e->flags0;
   e->t.assign(W, 0);
   e->world_done.assign(W, 0);
@@ -583,6 +601,7 @@ typedef struct or_config {
   double obs_radius, goal_radius, dt, v_max, collision_penalty, offroad_penalty, smooth_c;
   uint32_t flags;
   int32_t dynamics;
+  double nontrivial_dist;
 } or_config;
 
 void* or_create(const or_config* cfg, int precision, int32_t W, const int32_t* agent_off, const int32_t* road_off,
@@ -590,7 +609,8 @@ void* or_create(const or_config* cfg, int precision, int32_t W, const int32_t* a
                 const float* wid, const float* gx, const float* gy, const uint8_t* atype, const float* rx,
                 const float* ry, const uint8_t* rtype, const int32_t* rpoly) {
   Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
-           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics,
+           cfg->nontrivial_dist};
   auto* h = new Handle{precision, nullptr};
   if (precision == 32)
     h->env = make_env<float>(&c, W, agent_off, road_off, x, y, th, v, len, wid, gx, gy, atype, rx, ry, rtype, rpoly);
@@ -702,7 +722,8 @@ void or_set_state(void* hv, const float* state, const uint8_t* flags, const int3
 // actions double [n,2], length double [n].
 void or_bicycle(const or_config* cfg, int64_t n, double* state, const double* actions, const double* length) {
   Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
-           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics,
+           cfg->nontrivial_dist};
   for (int64_t i = 0; i < n; ++i)
     dynamics_step<double>(c, length[i], actions[2 * i], actions[2 * i + 1], state[4 * i], state[4 * i + 1],
                           state[4 * i + 2], state[4 * i + 3]);
@@ -713,7 +734,8 @@ void or_bicycle(const or_config* cfg, int64_t n, double* state, const double* ac
 void or_invert(const or_config* cfg, int32_t steps, int64_t n, const double* states, const double* length,
                double* actions) {
   Config c{cfg->k_road, cfg->n_partners, cfg->episode_len, cfg->obs_radius, cfg->goal_radius, cfg->dt,
-           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics};
+           cfg->v_max, cfg->collision_penalty, cfg->offroad_penalty, cfg->smooth_c, cfg->flags, cfg->dynamics,
+           cfg->nontrivial_dist};
   for (int t = 0; t < steps; ++t)
     for (int64_t i = 0; i < n; ++i)
       invert_step<double>(c, length[i], states + ((int64_t)t * n + i) * 4, states + ((int64_t)(t + 1) * n + i) * 4,

@@ -20,8 +20,9 @@ _lib = None
 TERM_COLLISION = 1
 TERM_OFFROAD = 2
 AUTO_RESET = 4
+NONTRIVIAL_INIT = 32
 
-DONE, GOAL, COLLIDED, OFFROAD = 1, 2, 4, 8
+DONE, GOAL, COLLIDED, OFFROAD, STATIC = 1, 2, 4, 8, 16
 
 
 def build_oracle(force: bool = False) -> str:
@@ -38,7 +39,7 @@ class _Cfg(C.Structure):
                 ("obs_radius", C.c_double), ("goal_radius", C.c_double), ("dt", C.c_double),
                 ("v_max", C.c_double), ("collision_penalty", C.c_double),
                 ("offroad_penalty", C.c_double), ("smooth_c", C.c_double), ("flags", C.c_uint32),
-                ("dynamics", C.c_int32)]
+                ("dynamics", C.c_int32), ("nontrivial_dist", C.c_double)]
 
 
 def load_oracle():
@@ -89,6 +90,8 @@ class OracleConfig:
     term_offroad: bool = False
     auto_reset: bool = False
     dynamics: int = 0          # 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
+    nontrivial_init: bool = False   # Sec. 3.2 "Initialization modes": agents near their goal are not controlled
+    nontrivial_dist: float = 2.0
 
     @property
     def feat(self) -> int:
@@ -96,10 +99,10 @@ class OracleConfig:
 
     def c(self) -> _Cfg:
         fl = (TERM_COLLISION if self.term_collision else 0) | (TERM_OFFROAD if self.term_offroad else 0) \
-            | (AUTO_RESET if self.auto_reset else 0)
+            | (AUTO_RESET if self.auto_reset else 0) | (NONTRIVIAL_INIT if self.nontrivial_init else 0)
         return _Cfg(self.k_road, self.n_partners, self.episode_len, self.obs_radius, self.goal_radius,
                     self.dt, self.v_max, self.collision_penalty, self.offroad_penalty, self.smooth_c, fl,
-                    self.dynamics)
+                    self.dynamics, self.nontrivial_dist)
 
 
 def _p(a):

@@ -167,13 +167,17 @@ def _lanes(rng, n_pts, starts, headings):
 
 
 def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
-               type_mix=(1.0, 0.0, 0.0), agent_length=4.5, agent_width=2.0) -> Scene:
+               type_mix=(1.0, 0.0, 0.0), agent_length=4.5, agent_width=2.0, parked_frac=0.0) -> Scene:
     """Build a seeded scene.
 
     agents_per_world / road_per_world: int arrays [W] (A_w >= 0, N_w >= 2).
     n_poly: polylines per world (int, array [W] or None for the default
     2 * max(1, round(N_w / 200))); must be even (lane + edge pairs).
     type_mix: probabilities of (vehicle, cyclist, pedestrian).
+    parked_frac: each agent is, with this probability, parked: speed 0 and
+    its goal within 1.5 m of where it stands (the scenes of Sec. 3.2
+    "Initialization modes", where 25-75% of agents start at or near their
+    goal).  Drawn after everything else, so other draws do not change.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     A_w = np.asarray(agents_per_world, dtype=np.int64)
@@ -283,12 +287,22 @@ def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
     mix = mix / mix.sum()
     atype = rng.choice(3, size=A, p=mix).astype(np.uint8) if mix[0] < 1.0 else np.zeros(A, np.uint8)
 
+    x0, y0 = px[ln, kk], py[ln, kk]
+    gx, gy = px[ln, gk], py[ln, gk]
+    if parked_frac > 0.0:
+        parked = rng.random(A) < parked_frac
+        r = rng.uniform(0.0, 1.5, A)
+        ang = rng.uniform(0.0, 2 * math.pi, A)
+        gx = np.where(parked, x0 + r * np.cos(ang), gx)
+        gy = np.where(parked, y0 + r * np.sin(ang), gy)
+        v0 = np.where(parked, 0.0, v0)
+
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return Scene(
         agent_off=agent_off, road_off=road_off,
-        x=f32(px[ln, kk]), y=f32(py[ln, kk]), theta=f32(heading), v=f32(v0),
+        x=f32(x0), y=f32(y0), theta=f32(heading), v=f32(v0),
         length=np.full(A, agent_length, np.float32), width=np.full(A, agent_width, np.float32),
-        goal_x=f32(px[ln, gk]), goal_y=f32(py[ln, gk]), agent_type=atype,
+        goal_x=f32(gx), goal_y=f32(gy), agent_type=atype,
         road_x=road_x, road_y=road_y, road_type=road_type, road_poly=road_poly)
 
 
@@ -326,6 +340,14 @@ WORKLOADS = {
     "fwdbwd_8192": dict(worlds=8192, agents=("uniform", 32, 128), road=("uniform", 5000, 10000),
                         n_poly=None, k_road=200, n_partners=63, steps=91,
                         term_collision=True, term_offroad=True, auto_reset=False),
+    # 1,024 x 64 as plain_1024x64 with mixed agent types (70% vehicles, 15%
+    # cyclists, 15% pedestrians), half the agents parked at their goal, and
+    # the "all nontrivial" initialisation (only agents > 2 m from their goal
+    # are controlled)
+    "nontrivial_1024x64": dict(worlds=1024, agents=("fixed", 64), road=("fixed", 4000), n_poly=40,
+                               k_road=200, n_partners=63, steps=91,
+                               term_collision=True, term_offroad=True, auto_reset=True,
+                               type_mix=(0.7, 0.15, 0.15), parked_frac=0.5, nontrivial_init=True),
 }
 
 
@@ -351,4 +373,5 @@ def workload_scene(name: str, seed: int = 0, worlds: int | None = None) -> Scene
     N_w = _counts(wl["road"], W, rng)
     if worlds is not None:
         A_w, N_w = A_w[:worlds], N_w[:worlds]
-    return make_scene(A_w, N_w, seed, n_poly=wl["n_poly"])
+    return make_scene(A_w, N_w, seed, n_poly=wl["n_poly"], type_mix=wl.get("type_mix", (1.0, 0.0, 0.0)),
+                      parked_frac=wl.get("parked_frac", 0.0))
