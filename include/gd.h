@@ -82,12 +82,18 @@ typedef enum gd_status {
 #define GD_AUTO_RESET 0x4u       /* gd_step first resets worlds whose episode ended */
 #define GD_BATCHED 0x8u          /* persistent fused kernels over a world work list */
 #define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward */
+#define GD_NONTRIVIAL_INIT 0x20u /* "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges"):
+                                    agents within nontrivial_dist of their goal at the start are not
+                                    controlled (GD_FLAG_STATIC) */
 
 /* per-agent status byte (gd_get_state / gd_set_state) */
 #define GD_FLAG_DONE 0x1u
 #define GD_FLAG_GOAL 0x2u
 #define GD_FLAG_COLLIDED 0x4u
 #define GD_FLAG_OFFROAD 0x8u
+#define GD_FLAG_STATIC 0x10u   /* not controlled: does not move, is not scored, reports done = 1, and
+                                  stays in the scene (an obstacle, a partner, a LiDAR target); a
+                                  world's episode ends when its controlled agents are done */
 
 /* road point types and agent types */
 #define GD_ROAD_LANE 0
@@ -115,7 +121,7 @@ typedef struct gd_config {
   float collision_penalty;   /* subtracted from the reward on collision (0) */
   float offroad_penalty;     /* subtracted from the reward off road (0) */
   float smooth_c;            /* m, scale of the smooth goal reward (1) */
-  uint32_t flags;            /* GD_TERM_* | GD_AUTO_RESET | GD_BATCHED | GD_DIFFERENTIABLE */
+  uint32_t flags;            /* GD_TERM_* | GD_AUTO_RESET | GD_BATCHED | GD_DIFFERENTIABLE | GD_NONTRIVIAL_INIT */
   int32_t block_size;        /* threads per block of the observation kernel; 0 = default */
   float road_cell;           /* m, road-point grid cell; 0 = default (8) */
   int32_t topk_strategy;     /* road top-K method: 0 = default, 1 = bucket rank, 2 = bitonic sort */
@@ -134,6 +140,8 @@ typedef struct gd_config {
                                 ds = v dt + a dt^2 / 2, x += cos(theta) ds, y += sin(theta) ds,
                                 theta += steer * ds, v += a dt (no speed clip; length unused);
                                 GD_DIFFERENTIABLE needs GD_DYN_BICYCLE */
+  float nontrivial_dist;     /* m, with GD_NONTRIVIAL_INIT: agents at most this far from their goal
+                                at the start are not controlled (2; Sec. 3.2) */
 } gd_config;
 
 typedef struct gd_scene_batch {

@@ -386,6 +386,8 @@ void gd_default_config(gd_config* c) {
   c->topk_strategy = 0;
   c->lidar_rays = 0;
   c->lidar_fov = 6.28318530717958647692f;
+  c->dynamics = GD_DYN_BICYCLE;
+  c->nontrivial_dist = 2.f;
 }
 
 const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
@@ -435,6 +437,10 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     return fail(nullptr, GD_ERR_INVALID_ARG, "dynamics must be GD_DYN_BICYCLE or GD_DYN_INVERTIBLE");
   if (c->dynamics != GD_DYN_BICYCLE && (c->flags & GD_DIFFERENTIABLE))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE needs the kinematic bicycle (GD_DYN_BICYCLE)");
+  if (!(c->nontrivial_dist >= 0.f) || !finite(c->nontrivial_dist))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "nontrivial_dist must be >= 0");
+  if ((c->flags & GD_NONTRIVIAL_INIT) && (c->flags & GD_DIFFERENTIABLE))
+    return fail(nullptr, GD_ERR_INVALID_ARG, "GD_NONTRIVIAL_INIT cannot be combined with GD_DIFFERENTIABLE");
   if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
   const int W = s->num_worlds;
@@ -588,6 +594,10 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
   d.stat = p_stat; d.type = p_type; d.flags = p_flags; d.init_flags = p_iflags; d.t = p_t; d.world_done = p_wd;
   d.egrid = p_eg; d.ecell_start = p_ecs; d.esegs = p_es;
+  if ((cfg->flags & GD_NONTRIVIAL_INIT) && A > 0) {
+    k_mark_uncontrolled<<<blocks_for_host(A, 256), 256, 0, env->stream>>>(d, p_iflags, cfg->nontrivial_dist);
+    GD_TRY(cudaGetLastError());
+  }
   GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
   // batched form: worlds largest first (agents, then road points), a work

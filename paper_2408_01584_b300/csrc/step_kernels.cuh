@@ -35,11 +35,12 @@ __global__ void k_reset_worlds(DevEnv e, const uint8_t* __restrict__ mask) {
   }
 }
 
-// Thread per agent.  Done agents are frozen (removed from the scene).
+// Thread per agent.  Done agents are frozen (removed from the scene) and
+// uncontrolled ones (GD_FLAG_STATIC) stay where they are.
 __global__ void k_dynamics(DevEnv e, const float2* __restrict__ actions) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= e.A) return;
-  if (e.flags[i] & GD_FLAG_DONE) return;
+  if (e.flags[i] & (GD_FLAG_DONE | GD_FLAG_STATIC)) return;
   const float2 a = actions[i];
   float4 s = e.state[i];
   if (!dynamics_step(e.dyn, s, a.x, a.y, e.stat[i].x, e.dt, e.vmax)) {
@@ -111,12 +112,13 @@ __device__ __forceinline__ int upper_bound_u32(const uint32_t* a, int n, uint32_
 // Warp per agent: agent/agent collision through the agent grid.  The cell
 // is at least the largest box diagonal, so overlapping boxes sit in the same
 // or neighbouring cells; the three cells of one neighbouring column are one
-// contiguous key range.
+// contiguous key range.  Uncontrolled agents are in the grid (others collide
+// with them) but get no test of their own.
 __global__ void k_collide(DevEnv e) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= e.A) return;
-  if (e.flags[i] & GD_FLAG_DONE) return;
+  if (e.flags[i] & (GD_FLAG_DONE | GD_FLAG_STATIC)) return;
   const int w = e.agent_world[i];
   const int a0 = e.agent_off[w];
   const int n = e.agrid_n[w];
@@ -157,7 +159,7 @@ __global__ void k_offroad(DevEnv e) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (i >= e.A) return;
-  if (e.flags[i] & GD_FLAG_DONE) return;
+  if (e.flags[i] & (GD_FLAG_DONE | GD_FLAG_STATIC)) return;
   if (e.type[i] == GD_AGENT_PEDESTRIAN) {
     if (lane == 0) e.off[i] = 0;
     return;
@@ -186,18 +188,20 @@ __global__ void k_offroad(DevEnv e) {
 }
 
 // Warp per world: goal test, reward, flags, done; then the world's episode
-// step count and end-of-episode status.
+// step count and end-of-episode status: every controlled agent done (a world
+// without controlled agents only times out) or t = T.  Uncontrolled agents
+// score nothing and report done.
 __global__ void k_finish(DevEnv e, float* __restrict__ reward, uint8_t* __restrict__ done,
                          uint8_t* __restrict__ world_done) {
   const int lane = threadIdx.x & 31;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= e.W) return;
   const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
-  bool all_done = true;
+  bool all_done = true, any_ctrl = false;
   for (int i = a0 + lane; i < a1; i += WARP) {
     uint8_t f = e.flags[i];
     float r = 0.f;
-    if (!(f & GD_FLAG_DONE)) {
+    if (!(f & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
       const float4 s = e.state[i];
       const float4 st = e.stat[i];
       const float dx = s.x - st.z, dy = s.y - st.w;
@@ -214,14 +218,18 @@ __global__ void k_finish(DevEnv e, float* __restrict__ reward, uint8_t* __restri
       r = (first ? 1.f : 0.f) - (coll ? e.cpen : 0.f) - (offr ? e.opn : 0.f);
     }
     if (reward) reward[i] = r;
-    if (done) done[i] = (f & GD_FLAG_DONE) ? 1 : 0;
-    all_done = all_done && (f & GD_FLAG_DONE);
+    if (done) done[i] = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) ? 1 : 0;
+    if (!(f & GD_FLAG_STATIC)) {
+      any_ctrl = true;
+      all_done = all_done && (f & GD_FLAG_DONE);
+    }
   }
   all_done = __all_sync(0xffffffffu, all_done);
+  any_ctrl = __any_sync(0xffffffffu, any_ctrl);
   if (lane == 0) {
     const int t = e.t[w] + 1;
     e.t[w] = t;
-    const uint8_t wd = ((a1 > a0 && all_done) || t >= e.T) ? 1 : 0;
+    const uint8_t wd = ((any_ctrl && all_done) || t >= e.T) ? 1 : 0;
     e.world_done[w] = wd;
     if (world_done) world_done[w] = wd;
   }
@@ -232,9 +240,28 @@ __global__ void k_derive_world_done(DevEnv e) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= e.W) return;
   const int a0 = e.agent_off[w], a1 = e.agent_off[w + 1];
-  bool all = a1 > a0;
-  for (int i = a0; i < a1; ++i) all = all && (e.flags[i] & GD_FLAG_DONE);
-  e.world_done[w] = (all || e.t[w] >= e.T) ? 1 : 0;
+  bool all = true, any_ctrl = false;
+  for (int i = a0; i < a1; ++i) {
+    if (e.flags[i] & GD_FLAG_STATIC) continue;
+    any_ctrl = true;
+    all = all && (e.flags[i] & GD_FLAG_DONE);
+  }
+  e.world_done[w] = ((any_ctrl && all) || e.t[w] >= e.T) ? 1 : 0;
+}
+
+// Thread per agent, at create with GD_NONTRIVIAL_INIT ("all nontrivial"
+// initialisation, Sec. 3.2 "Simulator sharp-edges"): agents within `dist` of
+// their goal are not controlled.
+__global__ void k_mark_uncontrolled(DevEnv e, uint8_t* __restrict__ init_flags, float dist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e.A) return;
+  const float4 s = e.init_state[i];
+  const float4 st = e.stat[i];
+  const float dx = s.x - st.z, dy = s.y - st.w;
+  if (sqrtf(fmaf(dx, dx, __fmul_rn(dy, dy))) <= dist) {
+    init_flags[i] |= GD_FLAG_STATIC;
+    e.flags[i] |= GD_FLAG_STATIC;
+  }
 }
 
 }  // namespace gd

@@ -188,8 +188,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
         uint8_t f = reset ? e.init_flags[i] : e.flags[i];
         ag.act0[tid] = !(f & GD_FLAG_DONE);
         if (!(f & GD_FLAG_DONE)) {
+          // uncontrolled agents (GD_FLAG_STATIC) stay in the grid but do not move
           const float2 u = a.actions[i];
-          if (!dynamics_step(e.dyn, s, u.x, u.y, e.stat[i].x, e.dt, e.vmax)) atomicOr(e.err, ERR_ACTION);
+          if (!(f & GD_FLAG_STATIC) && !dynamics_step(e.dyn, s, u.x, u.y, e.stat[i].x, e.dt, e.vmax))
+            atomicOr(e.err, ERR_ACTION);
           act = true;
           key = agent_cell_key((int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f),
                                (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f), tid);
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
       __syncthreads();
       // collision and road edge: warp per agent, ballot-OR over candidates
       for (int li = wid; li < n; li += WARPS) {
-        if (ag.fl[li] & GD_FLAG_DONE) continue;
+        if (ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) continue;
         const float4 s = ag.st[li];
         const float4 sc = ag.sc[li];
         const float ca = ag.cs[li].x, sa = ag.cs[li].y;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
       // per agent, ballot-OR over the candidate segments
       if (!wait_tile()) return;
       for (int li = wid; li < n; li += WARPS) {
-        if ((ag.fl[li] & GD_FLAG_DONE) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
+        if ((ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
           if (lane == 0) ag.offr[li] = 0;
           continue;
         }
@@ -270,12 +272,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
       }
       __syncthreads();
       // goal, reward, flags, done
-      bool dn = true;
+      bool dn = true, ctrl = false;
       if (tid < n) {
         const int i = a0 + tid;
         uint8_t f = ag.fl[tid];
         float r = 0.f;
-        if (!(f & GD_FLAG_DONE)) {
+        ctrl = !(f & GD_FLAG_STATIC);
+        if (!(f & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
           const float4 s = ag.st[tid];
           const float4 sc = ag.sc[tid];
           const float dx = s.x - sc.z, dy = s.y - sc.w;
@@ -294,14 +297,17 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
         e.state[i] = ag.st[tid];
         e.flags[i] = f;
         if (a.reward) a.reward[i] = r;
-        if (a.done) a.done[i] = (f & GD_FLAG_DONE) ? 1 : 0;
-        dn = (f & GD_FLAG_DONE) != 0;
+        if (a.done) a.done[i] = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) ? 1 : 0;
+        dn = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) != 0;
       }
+      // end of episode: every controlled agent done (a world without
+      // controlled agents only times out), or t = T
       const int all_done = __syncthreads_and(dn);
+      const int any_ctrl = __syncthreads_or(ctrl);
       if (tid == 0) {
         const int t = (reset ? 0 : e.t[w]) + 1;
         e.t[w] = t;
-        const uint8_t wd = ((n > 0 && all_done) || t >= e.T) ? 1 : 0;
+        const uint8_t wd = ((any_ctrl && all_done) || t >= e.T) ? 1 : 0;
         e.world_done[w] = wd;
         if (a.world_done) a.world_done[w] = wd;
       }

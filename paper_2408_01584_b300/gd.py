@@ -24,8 +24,9 @@ GD_TERM_OFFROAD = 0x2
 GD_AUTO_RESET = 0x4
 GD_BATCHED = 0x8
 GD_DIFFERENTIABLE = 0x10
+GD_NONTRIVIAL_INIT = 0x20
 
-GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD = 1, 2, 4, 8
+GD_FLAG_DONE, GD_FLAG_GOAL, GD_FLAG_COLLIDED, GD_FLAG_OFFROAD, GD_FLAG_STATIC = 1, 2, 4, 8, 16
 
 # symbols declared in include/gd.h
 SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_reset", "gd_step", "gd_observe",
@@ -53,7 +54,8 @@ class gd_config(C.Structure):
                 ("offroad_penalty", C.c_float), ("smooth_c", C.c_float), ("flags", C.c_uint32),
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
-                ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32)]
+                ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32),
+                ("nontrivial_dist", C.c_float)]
 
 
 class gd_scene_batch(C.Structure):

@@ -1,0 +1,76 @@
+"""GPU parity of the "all nontrivial" initialisation (Sec. 3.2 "Simulator
+sharp-edges") on mixed-type scenes with parked agents, through the C ABI.
+
+* the uncontrolled set equals the oracle's (exceptions only within 1e-5 m of
+  the 2 m threshold, where float32 and float64 distances may disagree);
+* teacher-forced steps, per-stage and fused: states, decisions (reward,
+  done = 1 for uncontrolled agents, end of episode from controlled agents
+  only) and observation rows with parked cars among the partners;
+* fused and per-stage rollouts bit-identical.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2408_01584_b300 import scenes
+from tests._util import workload_config
+from tests.test_parity_gpu import gd_kwargs, teacher_forced
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _flags(ocfg, batched):
+    from paper_2408_01584_b300 import gd
+    return (gd.GD_TERM_COLLISION if ocfg.term_collision else 0) | (gd.GD_TERM_OFFROAD if ocfg.term_offroad else 0) \
+        | (gd.GD_AUTO_RESET if ocfg.auto_reset else 0) | gd.GD_NONTRIVIAL_INIT | (gd.GD_BATCHED if batched else 0)
+
+
+def test_uncontrolled_set_matches_oracle():
+    from paper_2408_01584_b300.gd import Env
+    sc = scenes.workload_scene("nontrivial_1024x64", 0, worlds=64)
+    ocfg = workload_config("nontrivial_1024x64", nontrivial_init=True)
+    env = Env(sc, **gd_kwargs(ocfg, flags=_flags(ocfg, False)))
+    g = env.get_state()[1].cpu().numpy()
+    o = Oracle(sc, ocfg).get_state()[1]
+    d = np.hypot(sc.x.astype(np.float64) - sc.goal_x, sc.y.astype(np.float64) - sc.goal_y)
+    diff = g != o
+    assert (np.abs(d[diff] - 2.0) <= 1e-5).all()
+    assert 0.3 < ((g & 16) != 0).mean() < 0.7
+    env.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_teacher_forced_nontrivial_mixed_types(batched):
+    sc = scenes.workload_scene("nontrivial_1024x64", 1, worlds=12)
+    ocfg = workload_config("nontrivial_1024x64", nontrivial_init=True, episode_len=9)
+    acts = scenes.make_actions(20, sc.num_agents, 1)
+    env, ex = teacher_forced(sc, ocfg, 20, acts, obs_every=4, gd_over=dict(flags=_flags(ocfg, batched)))
+    f = env.get_state()[1].cpu().numpy()
+    assert ((f & 16) != 0).any() and (sc.agent_type == 2).any() and (sc.agent_type == 1).any()
+    print("exceptions:", ex.items)
+    env.close()
+
+
+def test_nontrivial_fused_equals_per_stage():
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("nontrivial_1024x64", 2, worlds=32)
+    ocfg = workload_config("nontrivial_1024x64", nontrivial_init=True)
+    T = 30
+    acts = torch.from_numpy(scenes.make_actions(T, sc.num_agents, 2)).cuda().contiguous()
+    outs = []
+    for batched in (False, True):
+        env = gd.Env(sc, **gd_kwargs(ocfg, flags=_flags(ocfg, batched)))
+        obs = torch.empty(T, sc.num_agents, env.F, device="cuda")
+        rew = torch.empty(T, sc.num_agents, device="cuda")
+        done = torch.empty(T, sc.num_agents, dtype=torch.uint8, device="cuda")
+        gd.gd_rollout(env.h, T, acts, obs, True, rew, done)
+        s, f, t = env.get_state()
+        env.sync()
+        outs.append([x.cpu() for x in (s, f, t, obs, rew, done)])
+        env.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
+    done = outs[0][5].numpy()
+    static = (outs[0][1].numpy() & 16) != 0
+    assert (done[:, static] == 1).all()
