@@ -155,7 +155,7 @@ def workload_cfg(name):
     from paper_2408_01584_b300 import gd, scenes
     wl = scenes.WORKLOADS[name]
     fl = (gd.GD_TERM_COLLISION if wl["term_collision"] else 0) | (gd.GD_TERM_OFFROAD if wl["term_offroad"] else 0) \
-        | (gd.GD_AUTO_RESET if wl["auto_reset"] else 0)
+        | (gd.GD_AUTO_RESET if wl["auto_reset"] else 0) | (gd.GD_NONTRIVIAL_INIT if wl.get("nontrivial_init") else 0)
     return dict(k_road=wl["k_road"], n_partners=wl["n_partners"], episode_len=wl["steps"], flags=fl)
 
 
@@ -242,6 +242,27 @@ def active_agent_steps(done, agent_off):
     return total
 
 
+def controlled_agent_steps(done, static, agent_off):
+    """Agent-steps of controlled agents still in the scene at the start of
+    each step (the controlled-agent count of Sec. 4.1): uncontrolled agents
+    (static) never count; a controlled agent done after step t-1 is out at
+    step t unless its world's episode ended (every controlled agent done),
+    when the world restarts from its snapshot."""
+    import numpy as np
+    T, A = done.shape
+    W = len(agent_off) - 1
+    world = np.repeat(np.arange(W), np.diff(agent_off))
+    ctrl = ~static
+    n_ctrl = np.bincount(world, weights=ctrl, minlength=W)
+    total = int(ctrl.sum())
+    for t in range(1, T):
+        d = done[t - 1].astype(bool) & ctrl
+        n_out = np.bincount(world, weights=d, minlength=W)
+        ended = (n_out == n_ctrl) & (n_ctrl > 0)
+        total += int((ctrl & (~d | ended[world])).sum())
+    return total
+
+
 def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
     """Batched rollouts (fused kernel, CUDA graph) of another workload."""
     import torch
@@ -255,6 +276,7 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
         gd.gd_autotune(env.h)
         info = gd.gd_get_info(env.h)
         A = env.A
+        static = (env.get_state()[1].cpu().numpy() & gd.GD_FLAG_STATIC) != 0
         actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
         rew = torch.empty(T, A, device=dev)
         done = torch.empty(T, A, dtype=torch.uint8, device=dev)
@@ -268,9 +290,12 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
         ms = _time_rollouts(run, steps, stream, flush)
         gd.gd_sync(env.h)
     act = active_agent_steps(done.cpu().numpy(), sc.agent_off)
+    ctl = controlled_agent_steps(done.cpu().numpy(), static, sc.agent_off)
     out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
            "active_agent_steps_per_s": act * steps / (sum(ms) / 1e3),
+           "controlled_agent_steps_per_s": ctl * steps / (sum(ms) / 1e3),
+           "uncontrolled_agents": int(static.sum()),
            "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
                          "topk_strategy": info.topk_strategy}}
     env.close()
@@ -593,6 +618,7 @@ def run_ours(args, rank, world):
         torch.cuda.empty_cache()
         import math
         out["workloads"] = [bench_batched_forward("uneven_4096", 3, 1, dev, stream, flush),
+                            bench_batched_forward("nontrivial_1024x64", 3, 1, dev, stream, flush),
                             bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush),
                             bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush),
                             bench_lidar(args.workload, 3000, 2 * math.pi, False, 3, 1, dev, stream, flush),
