@@ -30,6 +30,9 @@
 //     agent's relative frame (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1),
 //     truncated to the K / P nearest;
 //   * smooth goal reward (not in the paper): r_s = -(sqrt(d^2 + c^2) - c);
+//   * polyline decimation at scene load (Sec. 3.1): the Visvalingam-Whyatt
+//     algorithm (the paper's citation: repeated elimination of the point of
+//     least effective area);
 //   * LiDAR / view cone: rays cast from the agent over the other agents'
 //     boxes and the road edges, in a full circle or a cone turned by a head
 //     rotation (Sec. 3.2 "Sensor modalities"; 3000 rays, 360 or 120 degrees
@@ -48,6 +51,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <set>
 #include <utility>
 #include <vector>
 #ifdef _OPENMP
@@ -545,6 +549,56 @@ void lidar(const Env<T>& e, int n, double fov, const float* head, const int32_t*
   }
 }
 
+// ---- Sec. 3.1: Visvalingam-Whyatt polyline decimation ---------------------
+// Effective area of point b between its current neighbours a and c (the
+// triangle they span).  The paper fixes no precision, so the removal
+// decisions are taken in the library kernel's: float32, in this operation
+// order, with no fused multiply-add (the oracle is built with
+// -ffp-contract=off).
+static float vw_area(float ax, float ay, float bx, float by, float cx, float cy) {
+  const float dx1 = bx - ax, dy1 = by - ay, dx2 = cx - ax, dy2 = cy - ay;
+  const float p = dx1 * dy2;
+  const float q = dx2 * dy1;
+  return 0.5f * std::fabs(p - q);
+}
+
+// One polyline of n points.  End points are kept.  Repeatedly the interior
+// point of least effective area (ties: lower index) is eliminated while that
+// area is below tol; its neighbours' areas are recomputed with their new
+// neighbours, and a recomputed area below the last eliminated one is raised
+// to it (so the elimination order follows the areas monotonically).
+static void vw_polyline(const float* x, const float* y, int n, float tol, uint8_t* keep) {
+  for (int i = 0; i < n; ++i) keep[i] = 1;
+  if (n < 3) return;
+  std::vector<int> prev(n), next(n);
+  std::vector<float> area(n, 0.f);
+  std::set<std::pair<float, int>> queue;
+  for (int i = 0; i < n; ++i) {
+    prev[i] = i - 1;
+    next[i] = i + 1;
+  }
+  for (int i = 1; i + 1 < n; ++i) {
+    area[i] = vw_area(x[i - 1], y[i - 1], x[i], y[i], x[i + 1], y[i + 1]);
+    queue.insert({area[i], i});
+  }
+  while (!queue.empty()) {
+    const std::pair<float, int> m = *queue.begin();
+    if (!(m.first < tol)) break;
+    queue.erase(queue.begin());
+    const int i = m.second;
+    keep[i] = 0;
+    const int a = prev[i], c = next[i];
+    next[a] = c;
+    prev[c] = a;
+    for (int j : {a, c}) {
+      if (j <= 0 || j >= n - 1) continue;
+      queue.erase({area[j], j});
+      area[j] = std::max(vw_area(x[prev[j]], y[prev[j]], x[j], y[j], x[next[j]], y[next[j]]), m.first);
+      queue.insert({area[j], j});
+    }
+  }
+}
+
 struct Handle {
   int precision;   // 64 or 32
   void* env;
@@ -763,6 +817,16 @@ void or_lidar(void* hv, int32_t n, double fov, const float* head, const int32_t*
               double* depth, uint8_t* cls, uint8_t* fragile, double* sens) {
   auto* h = static_cast<Handle*>(hv);
   OR_DISPATCH(h, lidar(e, n, fov, head, sel, nsel, band, depth, cls, fragile, sens));
+}
+
+// Visvalingam-Whyatt decimation of polylines (Sec. 3.1): polyline p is the
+// points poly_off[p] .. poly_off[p+1]-1 of x, y (float32); keep (uint8 [N])
+// gets 1 for the points that remain with area tolerance tol (m^2).
+void or_decimate(int32_t num_polylines, const int32_t* poly_off, const float* x, const float* y, float tol,
+                 uint8_t* keep) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int p = 0; p < num_polylines; ++p)
+    vw_polyline(x + poly_off[p], y + poly_off[p], poly_off[p + 1] - poly_off[p], tol, keep + poly_off[p]);
 }
 
 int or_num_threads(void) {

@@ -28,7 +28,8 @@ DONE, GOAL, COLLIDED, OFFROAD, STATIC = 1, 2, 4, 8, 16
 def build_oracle(force: bool = False) -> str:
     """Compile oracle.cpp into liboracle.so next to it (g++, OpenMP)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O3", "-std=c++17", "-fopenmp", "-shared", "-fPIC", "-Wall", _SRC, "-o", _LIB + ".tmp"]
+        cmd = ["g++", "-O3", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-Wall", _SRC,
+               "-o", _LIB + ".tmp"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -62,6 +63,7 @@ def load_oracle():
         lib.or_set_state.argtypes = [vp] * 4
         lib.or_bicycle.argtypes = [C.POINTER(_Cfg), i64, vp, vp, vp]
         lib.or_invert.argtypes = [C.POINTER(_Cfg), i32, i64, vp, vp, vp]
+        lib.or_decimate.argtypes = [i32, vp, vp, vp, C.c_float, vp]
         lib.or_box_box.restype = C.c_double
         lib.or_box_box.argtypes = [vp, vp]
         lib.or_box_seg.restype = C.c_double
@@ -240,6 +242,17 @@ def invert(cfg: OracleConfig, states, length):
     c = cfg.c()
     lib.or_invert(C.byref(c), T, n, _p(s), _p(L), _p(out))
     return out
+
+
+def decimate(poly_off, x, y, tol):
+    """Visvalingam-Whyatt keep mask (uint8 [N]) of the polylines
+    poly_off [P+1] over float32 points x, y with area tolerance tol (m^2)."""
+    lib = load_oracle()
+    off = _c(poly_off, np.int32)
+    xx, yy = _c(x, np.float32), _c(y, np.float32)
+    keep = np.zeros(xx.shape[0], np.uint8)
+    lib.or_decimate(len(off) - 1, _p(off), _p(xx), _p(yy), float(tol), _p(keep))
+    return keep
 
 
 def box_box(p, q) -> float:

@@ -128,10 +128,10 @@ class Scene:
         return out
 
 
-def _lanes(rng, n_pts, starts, headings):
-    """Sample lane centrelines.  ``n_pts[l]`` points for lane l, starting at
-    ``starts[l]`` with heading ``headings[l]``.  Returns (px, py, th) padded
-    arrays [L, nmax] (heading at each point) ."""
+def _lanes(rng, n_pts, starts, headings, spacing=1.0):
+    """Sample lane centrelines every ``spacing`` m of arc length.  ``n_pts[l]``
+    points for lane l, starting at ``starts[l]`` with heading ``headings[l]``.
+    Returns (px, py, th) padded arrays [L, nmax] (heading at each point)."""
     L = n_pts.shape[0]
     nmax = int(n_pts.max()) if L else 0
     straight = rng.random((L, _PIECES)) < 0.5
@@ -143,14 +143,14 @@ def _lanes(rng, n_pts, starts, headings):
     plen = np.maximum(plen, 1e-3)
     kappa = np.where(straight, 0.0, turn / plen)
     cum = np.cumsum(plen, axis=1)                      # end arc position of each piece
-    # piece index of each 1 m step (midpoint s = k + 0.5), vectorised across lanes
+    # piece index of each step (midpoint s = (k + 0.5) spacing), vectorised across lanes
     big = float(np.ceil(cum[:, -1].max() + 2.0)) if L else 1.0
     flat = (cum + big * np.arange(L)[:, None]).ravel()
-    s = np.arange(max(nmax - 1, 0), dtype=np.float64) + 0.5
+    s = (np.arange(max(nmax - 1, 0), dtype=np.float64) + 0.5) * spacing
     q = (s[None, :] + big * np.arange(L)[:, None]).ravel()
     piece = np.searchsorted(flat, q, side="right").reshape(L, -1) - _PIECES * np.arange(L)[:, None]
     piece = np.clip(piece, 0, _PIECES - 1)
-    k_step = np.take_along_axis(kappa, piece, axis=1)  # [L, nmax-1] curvature per step
+    k_step = np.take_along_axis(kappa, piece, axis=1) * spacing   # [L, nmax-1] heading change per step
     th = np.empty((L, nmax))
     th[:, 0] = headings
     if nmax > 1:
@@ -161,19 +161,23 @@ def _lanes(rng, n_pts, starts, headings):
     px[:, 0] = starts[:, 0]
     py[:, 0] = starts[:, 1]
     if nmax > 1:
-        px[:, 1:] = starts[:, 0:1] + np.cumsum(np.cos(mid), axis=1)
-        py[:, 1:] = starts[:, 1:2] + np.cumsum(np.sin(mid), axis=1)
+        px[:, 1:] = starts[:, 0:1] + np.cumsum(spacing * np.cos(mid), axis=1)
+        py[:, 1:] = starts[:, 1:2] + np.cumsum(spacing * np.sin(mid), axis=1)
     return px, py, th
 
 
 def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
-               type_mix=(1.0, 0.0, 0.0), agent_length=4.5, agent_width=2.0, parked_frac=0.0) -> Scene:
+               type_mix=(1.0, 0.0, 0.0), agent_length=4.5, agent_width=2.0, parked_frac=0.0,
+               spacing=1.0) -> Scene:
     """Build a seeded scene.
 
     agents_per_world / road_per_world: int arrays [W] (A_w >= 0, N_w >= 2).
     n_poly: polylines per world (int, array [W] or None for the default
     2 * max(1, round(N_w / 200))); must be even (lane + edge pairs).
     type_mix: probabilities of (vehicle, cyclist, pedestrian).
+    spacing: metres between consecutive polyline points (1 m by default;
+    0.1 m is the source sampling the paper decimates, Sec. 3.1).  The map
+    side and the agent / goal placement scale with the road length.
     parked_frac: each agent is, with this probability, parked: speed 0 and
     its goal within 1.5 m of where it stands (the scenes of Sec. 3.2
     "Initialization modes", where 25-75% of agents start at or near their
@@ -190,7 +194,7 @@ def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
         P_w = np.broadcast_to(np.asarray(n_poly, dtype=np.int64), (W,)).copy()
     assert (P_w % 2 == 0).all() and (P_w >= 2).all()
     nl_w = P_w // 2
-    side = 300.0 * np.sqrt(N_w / 4000.0)
+    side = 300.0 * np.sqrt(N_w * spacing / 4000.0)
 
     # points per lane: the lanes of world w share ceil(N_w/2) points, edges floor(N_w/2)
     lane_world = np.repeat(np.arange(W), nl_w)
@@ -208,7 +212,7 @@ def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
     half = 0.5 * side[lane_world]
     starts = np.stack([rng.uniform(-1.0, 1.0, L) * half, rng.uniform(-1.0, 1.0, L) * half], axis=1)
     heads = rng.uniform(0.0, 2 * math.pi, L)
-    px, py, th = _lanes(rng, lane_pts, starts, heads)
+    px, py, th = _lanes(rng, lane_pts, starts, heads, spacing)
     ex = px - _EDGE_OFFSET * np.sin(th)
     ey = py + _EDGE_OFFSET * np.cos(th)
 
@@ -256,7 +260,7 @@ def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
             if pending.size == 0:
                 break
             ln = lane_off[pending] + rng.integers(0, nl_w[pending])
-            hi = np.maximum(lane_pts[ln] - 21, 1)
+            hi = np.maximum(lane_pts[ln] - int(round(21 / spacing)), 1)
             kk = rng.integers(0, hi)
             cx, cy = px[ln, kk], py[ln, kk]
             chosen_lane[pending] = ln
@@ -281,7 +285,7 @@ def make_scene(agents_per_world, road_per_world, seed: int, n_poly=None,
     k1 = np.minimum(kk + 1, n_l - 1)
     k0 = np.where(k1 == kk, kk - 1, kk)
     heading = np.arctan2(py[ln, k1] - py[ln, k0], px[ln, k1] - px[ln, k0])
-    gk = np.minimum(kk + rng.integers(20, 61, A), n_l - 1)
+    gk = np.minimum(kk + np.round(rng.integers(20, 61, A) / spacing).astype(np.int64), n_l - 1)
     v0 = rng.uniform(0.0, 15.0, A)
     mix = np.asarray(type_mix, dtype=np.float64)
     mix = mix / mix.sum()
