@@ -372,6 +372,27 @@ const char* gd_last_error(const gd_env* env);
  * first call before any stream capture.  Every call reuses the same array
  * (nothing in it needs to start at zero: each call writes what it reads),
  * so calls that overlap on the GPU, e.g. on two streams, race. */
+/* ---- polyline decimation at scene load --------------------------------------
+ * Visvalingam-Whyatt decimation (Sec. 3.1: road polylines sampled every
+ * 0.1 m are mostly straight; dropping low-importance points cuts them 10-15x
+ * and speeds up the step).  For every polyline, the interior point of least
+ * effective area (the triangle it spans with its two current neighbours;
+ * ties: lower index) is eliminated while that area is below area_tol (m^2);
+ * its neighbours' areas are recomputed with their new neighbours and raised
+ * to the eliminated area if smaller.  End points are always kept.  Areas are
+ * float32 in a fixed rounding order, so the result is reproducible.
+ *   num_polylines P, num_points N (= poly_off[P])
+ *   poly_off  device int32 [P+1], CSR: polyline p is points poly_off[p] ..
+ *             poly_off[p+1]-1 (non-decreasing, poly_off[0] = 0)
+ *   x, y      device float [N]
+ *   keep      device uint8 [N] output: 1 = kept
+ * Stateless: it needs no env.  A scratch of 20 bytes per point is taken
+ * from the stream-ordered allocator for the call; one thread works through
+ * each polyline.  Errors: GD_ERR_INVALID_ARG (negative sizes, NULL, bad
+ * tolerance), GD_ERR_OOM; message in gd_last_error(NULL). */
+gd_status gd_decimate(int32_t num_polylines, int32_t num_points, const int32_t* poly_off, const float* x,
+                      const float* y, float area_tol, uint8_t* keep, void* cuda_stream);
+
 #define GD_NOALLOC_MAX_AGENTS 262144
 #define GD_NOALLOC_MAX_WORLDS 16384
 gd_status gd_collide_noalloc(int32_t num_worlds, const int32_t* agent_off, const float* state, const float* extent,

@@ -28,13 +28,14 @@ def sources():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/gd.cu (which includes the kernel headers) and
-    csrc/gd_noalloc.cu into libgd.so."""
+    """Compile csrc/gd.cu (which includes the kernel headers),
+    csrc/gd_noalloc.cu and csrc/gd_decimate.cu into libgd.so."""
     newest = max(os.path.getmtime(s) for s in sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     cmd = [_nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-        [os.path.join(CSRC, "gd.cu"), os.path.join(CSRC, "gd_noalloc.cu"), "-o", LIB + ".tmp"]
+        [os.path.join(CSRC, "gd.cu"), os.path.join(CSRC, "gd_noalloc.cu"), os.path.join(CSRC, "gd_decimate.cu"),
+         "-o", LIB + ".tmp"]
     subprocess.run(cmd, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB

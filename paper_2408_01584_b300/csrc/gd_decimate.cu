@@ -1,0 +1,166 @@
+// Polyline decimation at scene load (Sec. 3.1: a Visvalingam-Whyatt pass
+// that drops points of straight stretches, 10-15x fewer points).
+//
+// For every polyline: the interior point of least effective area (the
+// triangle it spans with its two current neighbours; ties: lower index) is
+// eliminated while that area is below the tolerance; its neighbours' areas
+// are recomputed with their new neighbours and raised to the eliminated
+// area if smaller.  End points stay.  The elimination is sequential within
+// a polyline, so one thread runs one polyline with a binary min-heap of
+// 64-bit keys (area bits << 32 | local index: areas are >= 0, so the bits
+// order like the values and the index breaks ties) and neighbour links, all
+// in a scratch buffer of 20 bytes per point allocated on the stream.  Areas
+// are float32 with the rounding spelled out (no contraction), so every
+// elimination decision is reproducible.
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gd.h"
+
+void gd_set_thread_error(const std::string& msg);
+
+namespace {
+
+__device__ __forceinline__ float vw_area(float ax, float ay, float bx, float by, float cx, float cy) {
+  const float dx1 = __fsub_rn(bx, ax), dy1 = __fsub_rn(by, ay), dx2 = __fsub_rn(cx, ax), dy2 = __fsub_rn(cy, ay);
+  return __fmul_rn(0.5f, fabsf(__fsub_rn(__fmul_rn(dx1, dy2), __fmul_rn(dx2, dy1))));
+}
+
+__device__ __forceinline__ unsigned long long vw_key(float area, int i) {
+  return ((unsigned long long)__float_as_uint(area) << 32) | (unsigned)i;
+}
+
+struct VwHeap {
+  unsigned long long* h;   // heap of keys
+  int* pos;                // heap position of each local point (-1: not in the heap)
+  int n;                   // entries
+
+  __device__ void place(int k, unsigned long long key) {
+    h[k] = key;
+    pos[(int)(key & 0xffffffffu)] = k;
+  }
+  __device__ void up(int k) {
+    const unsigned long long key = h[k];
+    while (k > 0) {
+      const int parent = (k - 1) >> 1;
+      const unsigned long long pk = h[parent];
+      if (pk <= key) break;
+      place(k, pk);
+      k = parent;
+    }
+    place(k, key);
+  }
+  __device__ void down(int k) {
+    const unsigned long long key = h[k];
+    for (;;) {
+      int c = 2 * k + 1;
+      if (c >= n) break;
+      unsigned long long ck = h[c];
+      if (c + 1 < n) {
+        const unsigned long long c2 = h[c + 1];
+        if (c2 < ck) {
+          ck = c2;
+          ++c;
+        }
+      }
+      if (key <= ck) break;
+      place(k, ck);
+      k = c;
+    }
+    place(k, key);
+  }
+};
+
+// One thread per polyline (grid-stride).  Scratch arrays are indexed by the
+// global point index.
+__global__ void k_vw(int num_polylines, const int* __restrict__ poly_off, const float* __restrict__ x,
+                     const float* __restrict__ y, float tol, uint8_t* __restrict__ keep, unsigned long long* heap,
+                     int* hpos, int* prv, int* nxt) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < num_polylines; p += gridDim.x * blockDim.x) {
+    const int o = poly_off[p], n = poly_off[p + 1] - o;
+    const float* px = x + o;
+    const float* py = y + o;
+    for (int i = 0; i < n; ++i) keep[o + i] = 1;
+    if (n < 3) continue;
+    int* pv = prv + o;
+    int* nx = nxt + o;
+    VwHeap hp{heap + o, hpos + o, n - 2};
+    for (int i = 0; i < n; ++i) {
+      pv[i] = i - 1;
+      nx[i] = i + 1;
+    }
+    hp.pos[0] = hp.pos[n - 1] = -1;
+    for (int i = 1; i + 1 < n; ++i)
+      hp.place(i - 1, vw_key(vw_area(px[i - 1], py[i - 1], px[i], py[i], px[i + 1], py[i + 1]), i));
+    for (int k = (hp.n >> 1) - 1; k >= 0; --k) hp.down(k);
+    while (hp.n > 0) {
+      const unsigned long long m = hp.h[0];
+      const float am = __uint_as_float((unsigned)(m >> 32));
+      if (!(am < tol)) break;
+      const int i = (int)(m & 0xffffffffu);
+      keep[o + i] = 0;
+      hp.pos[i] = -1;
+      if (--hp.n > 0) {
+        hp.place(0, hp.h[hp.n]);
+        hp.down(0);
+      }
+      const int a = pv[i], c = nx[i];
+      nx[a] = c;
+      pv[c] = a;
+      const int nb[2] = {a, c};
+      for (int q = 0; q < 2; ++q) {
+        const int j = nb[q];
+        if (j <= 0 || j >= n - 1) continue;
+        const float na = fmaxf(vw_area(px[pv[j]], py[pv[j]], px[j], py[j], px[nx[j]], py[nx[j]]), am);
+        const unsigned long long key = vw_key(na, j);
+        const int k = hp.pos[j];
+        const unsigned long long old = hp.h[k];
+        hp.h[k] = key;
+        if (key < old) hp.up(k); else hp.down(k);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" gd_status gd_decimate(int32_t num_polylines, int32_t num_points, const int32_t* poly_off, const float* x,
+                                 const float* y, float area_tol, uint8_t* keep, void* cuda_stream) {
+  if (num_polylines < 0 || num_points < 0) {
+    gd_set_thread_error("gd_decimate: num_polylines and num_points must be >= 0");
+    return GD_ERR_INVALID_ARG;
+  }
+  if (!(area_tol >= 0.f) || !(area_tol < 3.0e38f)) {
+    gd_set_thread_error("gd_decimate: area_tol must be finite and >= 0");
+    return GD_ERR_INVALID_ARG;
+  }
+  if (num_polylines == 0 || num_points == 0) return GD_OK;
+  if (!poly_off || !x || !y || !keep) {
+    gd_set_thread_error("gd_decimate: poly_off, x, y and keep must not be NULL");
+    return GD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const size_t n = (size_t)num_points;
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, n * (8 + 4 + 4 + 4), s);
+  if (e != cudaSuccess) {
+    gd_set_thread_error(std::string("gd_decimate: scratch: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA;
+  }
+  unsigned long long* heap = static_cast<unsigned long long*>(scratch);
+  int* hpos = reinterpret_cast<int*>(heap + n);
+  int* prv = hpos + n;
+  int* nxt = prv + n;
+  const int block = 128;
+  const int grid = (num_polylines + block - 1) / block;
+  k_vw<<<grid, block, 0, s>>>(num_polylines, poly_off, x, y, area_tol, keep, heap, hpos, prv, nxt);
+  e = cudaGetLastError();
+  cudaFreeAsync(scratch, s);
+  if (e != cudaSuccess) {
+    gd_set_thread_error(std::string("gd_decimate: launch: ") + cudaGetErrorString(e));
+    return GD_ERR_CUDA;
+  }
+  return GD_OK;
+}

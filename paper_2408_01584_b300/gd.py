@@ -33,7 +33,9 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
-           "gd_rollout_lidar", "gd_invert_actions")
+           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate")
+
+DECIMATE_AREA = 1e-3     # m^2, default tolerance of decimate_scene (10-15x on 0.1 m-sampled roads)
 
 GD_DYN_BICYCLE, GD_DYN_INVERTIBLE = 0, 1
 
@@ -112,6 +114,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_step_observe_lidar.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gd_rollout_lidar.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp]
     lib.gd_invert_actions.argtypes = [vp, i32, vp, vp]
+    lib.gd_decimate.argtypes = [i32, i32, vp, vp, vp, f32, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -230,6 +233,50 @@ def gd_invert_actions(env, steps, states, actions):
     """Expert actions [steps, A, 2] of trajectories states [steps+1, A, 4]."""
     lib = load_library()
     _check(lib, env, lib.gd_invert_actions(env, int(steps), _ptr(states, align=16), _ptr(actions, align=8)))
+
+
+def gd_decimate(poly_off, x, y, area_tol, keep, stream=None):
+    """Visvalingam-Whyatt keep mask of polylines: poly_off int32 [P+1], x, y
+    float [N] and keep uint8 [N] are CUDA tensors."""
+    lib = load_library()
+    st = lib.gd_decimate(int(poly_off.numel()) - 1, int(x.numel()), _ptr(poly_off, align=4), _ptr(x, align=4),
+                         _ptr(y, align=4), float(area_tol), _ptr(keep), C.c_void_p(stream or 0))
+    _check(lib, None, st)
+
+
+def polylines(scene):
+    """CSR offsets [P+1] of the scene's polylines: maximal runs of
+    consecutive road points of one world with the same polyline id."""
+    N = scene.num_road
+    brk = np.zeros(N, bool)
+    if N:
+        brk[0] = True
+        brk[1:] = scene.road_poly[1:] != scene.road_poly[:-1]
+        brk[scene.road_off[:-1][scene.road_off[:-1] < N]] = True
+    return np.append(np.nonzero(brk)[0], N).astype(np.int32)
+
+
+def decimate_scene(scene, area_tol=DECIMATE_AREA, stream=None):
+    """The scene with its road polylines decimated on the GPU (gd_decimate);
+    returns (decimated scene, keep mask uint8 [N] over the original points).
+    Road indices of the decimated scene count the kept points in order."""
+    import dataclasses
+    import torch
+    off = polylines(scene)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t_off = torch.from_numpy(off).to(dev)
+    tx = torch.from_numpy(np.ascontiguousarray(scene.road_x, np.float32)).to(dev)
+    ty = torch.from_numpy(np.ascontiguousarray(scene.road_y, np.float32)).to(dev)
+    keep = torch.empty(scene.num_road, dtype=torch.uint8, device=dev)
+    gd_decimate(t_off, tx, ty, area_tol, keep, stream)
+    k = keep.cpu().numpy()
+    m = k.astype(bool)
+    world = np.repeat(np.arange(scene.num_worlds), np.diff(scene.road_off))
+    road_off = np.zeros(scene.num_worlds + 1, np.int32)
+    road_off[1:] = np.cumsum(np.bincount(world[m], minlength=scene.num_worlds))
+    out = dataclasses.replace(scene, road_x=scene.road_x[m], road_y=scene.road_y[m], road_type=scene.road_type[m],
+                              road_poly=scene.road_poly[m], road_off=road_off)
+    return out, k
 
 
 def gd_rollout_objective(env, steps, actions, obs_weight, reward_weight, ell, obs=None):

@@ -352,6 +352,11 @@ WORKLOADS = {
                                k_road=200, n_partners=63, steps=91,
                                term_collision=True, term_offroad=True, auto_reset=True,
                                type_mix=(0.7, 0.15, 0.15), parked_frac=0.5, nontrivial_init=True),
+    # 256 worlds x 64 agents on roads sampled every 0.1 m (24 polylines of
+    # 1,000 points per world, the source sampling the paper decimates 10-15x)
+    "dense_roads_256x64": dict(worlds=256, agents=("fixed", 64), road=("fixed", 24000), n_poly=24, spacing=0.1,
+                               k_road=200, n_partners=63, steps=91,
+                               term_collision=True, term_offroad=True, auto_reset=True),
 }
 
 
@@ -378,4 +383,4 @@ def workload_scene(name: str, seed: int = 0, worlds: int | None = None) -> Scene
     if worlds is not None:
         A_w, N_w = A_w[:worlds], N_w[:worlds]
     return make_scene(A_w, N_w, seed, n_poly=wl["n_poly"], type_mix=wl.get("type_mix", (1.0, 0.0, 0.0)),
-                      parked_frac=wl.get("parked_frac", 0.0))
+                      parked_frac=wl.get("parked_frac", 0.0), spacing=wl.get("spacing", 1.0))

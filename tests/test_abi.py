@@ -113,6 +113,12 @@ def test_rejects_bad_arguments_before_any_launch(lib):
     neg.length = neg.length.copy()
     neg.length[0] = 0.0
     _expect(INV, gd.gd_create, gd.gd_default_config(), neg)
+    # decimation: validated before any CUDA call
+    assert lib.gd_decimate(-1, 10, None, None, None, C.c_float(1e-3), None, None) == INV
+    assert lib.gd_decimate(1, 10, None, None, None, C.c_float(float("nan")), None, None) == INV
+    assert lib.gd_decimate(1, 10, None, None, None, C.c_float(1e-3), None, None) == INV
+    assert lib.gd_decimate(0, 0, None, None, None, C.c_float(1e-3), None, None) == 0
+    assert "NULL" in gd.gd_last_error(None) or "must" in gd.gd_last_error(None)
     # NULL out pointer
     cfg = gd.gd_default_config()
     assert lib.gd_create(C.byref(cfg), None, None, None) == INV
