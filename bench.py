@@ -467,6 +467,56 @@ def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
     return out
 
 
+def bench_decimation(workload, steps, warmup, dev, stream, flush, seed=0):
+    """Scene-load decimation (Sec. 3.1): gd_decimate over every polyline of
+    the 0.1 m-sampled workload, and batched rollouts on the raw and on the
+    decimated roads (the paper's claim: 10-15x fewer points, faster steps)."""
+    import torch
+    from paper_2408_01584_b300 import gd, scenes
+    wl = scenes.WORKLOADS[workload]
+    T = wl["steps"]
+    sc = scenes.workload_scene(workload, seed)
+    cfg = workload_cfg(workload)
+    off = gd.polylines(sc)
+    with torch.cuda.stream(stream):
+        t_off = torch.from_numpy(off).to(dev)
+        tx = torch.from_numpy(sc.road_x).to(dev)
+        ty = torch.from_numpy(sc.road_y).to(dev)
+        keep = torch.empty(sc.num_road, dtype=torch.uint8, device=dev)
+
+        def dec():
+            gd.gd_decimate(t_off, tx, ty, gd.DECIMATE_AREA, keep, stream.cuda_stream)
+
+        for _ in range(warmup):
+            dec()
+        ms_dec = _time_rollouts(dec, max(steps, 3), stream, flush)
+        dsc, k = gd.decimate_scene(sc, stream=stream.cuda_stream)
+        rates = {}
+        for name, scene in (("raw", sc), ("decimated", dsc)):
+            env = gd.Env(scene, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
+            gd.gd_autotune(env.h)
+            actions = torch.from_numpy(scenes.make_actions(T, env.A, seed)).to(dev)
+
+            def run():
+                gd.gd_reset(env.h, None)
+                gd.gd_rollout(env.h, T, actions, env.obs, False, None, None)
+
+            for _ in range(warmup):
+                run()
+            ms = _time_rollouts(run, steps, stream, flush)
+            gd.gd_sync(env.h)
+            rates[name] = {"value": T * env.A * steps / (sum(ms) / 1e3), "unit": METRIC,
+                           "ms_per_episode": statistics.mean(ms), "road_points": scene.num_road,
+                           "device_bytes": int(gd.gd_get_info(env.h).device_bytes)}
+            env.close()
+    return {"workload": workload, "decimation": {"points_in": sc.num_road, "points_kept": int(k.sum()),
+                                                 "reduction": sc.num_road / max(int(k.sum()), 1),
+                                                 "polylines": len(off) - 1, "area_tol_m2": gd.DECIMATE_AREA,
+                                                 "ms": statistics.mean(ms_dec),
+                                                 "points_per_s": sc.num_road / (statistics.mean(ms_dec) / 1e3)},
+            "value": rates["decimated"]["value"], "unit": METRIC, "rollout": rates}
+
+
 def run_profile(args):
     """Batched rollouts only (default kernel shape, no tuner, no other legs),
     so that a profiler sees warm-up + timed k_world launches and nothing else.
@@ -623,7 +673,8 @@ def run_ours(args, rank, world):
                             bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush),
                             bench_lidar(args.workload, 3000, 2 * math.pi, False, 3, 1, dev, stream, flush),
                             bench_lidar(args.workload, 3000, 2 * math.pi / 3, True, 3, 1, dev, stream, flush),
-                            bench_invertible(args.workload, 3, 1, dev, stream, flush)]
+                            bench_invertible(args.workload, 3, 1, dev, stream, flush),
+                            bench_decimation("dense_roads_256x64", 3, 1, dev, stream, flush)]
     return out
 
 
@@ -641,7 +692,7 @@ def main():
     ap.add_argument("--fov", type=float, default=360.0, help="with --profile --lidar: fan width (degrees)")
     ap.add_argument("--worlds", type=int, default=0, help="with --profile: only the first W worlds")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
-                    help="skip the uneven, differentiable, forward+backward, LiDAR and invertible-model workloads")
+                    help="skip the uneven, differentiable, forward+backward, LiDAR, invertible-model and decimation workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
