@@ -297,7 +297,7 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
            "controlled_agent_steps_per_s": ctl * steps / (sum(ms) / 1e3),
            "uncontrolled_agents": int(static.sum()),
            "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                         "topk_strategy": info.topk_strategy}}
+                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile}}
     env.close()
     return out
 
@@ -598,7 +598,8 @@ def run_ours(args, rank, world):
         gd.gd_autotune(env_b.h)
         info = gd.gd_get_info(env_b.h)
         tuned = {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                 "topk_strategy": {1: "bucket rank", 2: "bitonic sort"}[info.topk_strategy]}
+                 "topk_strategy": {1: "bucket rank", 2: "bitonic sort"}[info.topk_strategy],
+                 "road_tile": info.road_tile}
         for _ in range(args.warmup):
             batched_rollout()
             plain_rollout()

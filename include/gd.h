@@ -142,6 +142,8 @@ typedef struct gd_config {
                                 GD_DIFFERENTIABLE needs GD_DYN_BICYCLE */
   float nontrivial_dist;     /* m, with GD_NONTRIVIAL_INIT: agents at most this far from their goal
                                 at the start are not controlled (2; Sec. 3.2) */
+  int32_t road_no_tile;      /* 1: the fused kernel reads each world's road block from global memory
+                                instead of copying it into shared memory (more CTAs per SM); default 0 */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -170,6 +172,8 @@ typedef struct gd_info {
   int32_t lidar_block_size;                         /* fused LiDAR kernel threads per block in use */
   int32_t lidar_road_tile;                          /* 1: it copies each world's road into shared memory */
   int32_t lidar_split;                              /* 1: step and LiDAR scan are two launches */
+  int32_t road_tile;                                /* 1: the fused kernel copies each world's road into
+                                                       shared memory */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -320,8 +324,9 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
 
 /* Autotuner of the fused (batched) kernel: times one step + observation
  * from the current state for every road grid cell in {6, 8, 12} m, CTA size
- * in {128, 256, 512} threads and top-K strategy in {1 bucket rank, 2 bitonic
- * sort when at most 256 points are in range}, and keeps the fastest
+ * in {128, 256, 512} threads, with and without the shared-memory road tile,
+ * and top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
+ * points are in range}, and keeps the fastest
  * (reported by gd_get_info).  With LiDAR enabled it then times the fused
  * step + LiDAR scan with 128, 256 and 384 threads per block, each with and
  * without the shared-memory road tile, and the split form (step, then a

@@ -53,6 +53,7 @@ struct gd_env {
   int* order = nullptr;        // [W] world order for the work list
   unsigned* counter = nullptr; // work counter
   int tile_cap = 0;            // bytes of the shared-memory road tile
+  int notile = 0;              // 1: k_world reads every road block from global memory (more CTAs per SM)
   size_t world_smem = 0;       // dynamic shared memory of k_world
   int world_grid = 0;          // persistent CTAs
   int warps = kWorldWarps;     // CTA size of k_world (4, 8 or 16 warps)
@@ -180,7 +181,7 @@ static cudaError_t shape_world(gd_env* env, size_t max_block, int smem_sm, int s
   const long two = ((long)smem_sm / 2 - 2048 - fixed) & ~15L;   // tile bytes, 2 CTAs/SM
   const long one = ((long)smem_blk - 1024 - fixed) & ~15L;      // 1 CTA/SM
   const long cap = ((long)max_block <= two) ? (long)max_block : one;
-  env->tile_cap = (int)std::max(16L, cap);
+  env->tile_cap = env->notile ? 16 : (int)std::max(16L, cap);
   env->world_smem = (size_t)fixed + (size_t)env->tile_cap;
   cudaError_t e = cudaFuncSetAttribute(k_world<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem);
   if (e != cudaSuccess) return e;
@@ -433,6 +434,7 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_block_size must be 0, 128, 256 or 384");
   if (c->lidar_no_tile != 0 && c->lidar_no_tile != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_no_tile must be 0 or 1");
   if (c->lidar_split != 0 && c->lidar_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_split must be 0 or 1");
+  if (c->road_no_tile != 0 && c->road_no_tile != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "road_no_tile must be 0 or 1");
   if (c->dynamics != GD_DYN_BICYCLE && c->dynamics != GD_DYN_INVERTIBLE)
     return fail(nullptr, GD_ERR_INVALID_ARG, "dynamics must be GD_DYN_BICYCLE or GD_DYN_INVERTIBLE");
   if (c->dynamics != GD_DYN_BICYCLE && (c->flags & GD_DIFFERENTIABLE))
@@ -628,6 +630,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
+  env->notile = cfg->road_no_tile;
   env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
   if (cfg->lidar_rays > 0) {
     const int n = cfg->lidar_rays;
@@ -689,6 +692,7 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->episode_len = env->cfg.episode_len;
   info->device_bytes = env->bytes;
   info->block_size = env->warps * 32;
+  info->road_tile = env->notile ? 0 : 1;
   info->road_cell = env->road_cell;
   info->topk_strategy = env->d.topk;
   info->lidar_rays = env->lidar_n;
@@ -1236,12 +1240,14 @@ gd_status gd_autotune(gd_env* env) {
   const float cells[] = {6.f, 8.f, 12.f};
   const int warps[] = {4, 8, 16};
   float best_ms = INFINITY, best_cell = env->road_cell;
-  int best_w = env->warps, best_st = d.topk;
+  int best_w = env->warps, best_st = d.topk, best_nt = env->notile;
   for (float c : cells) {
     const float cell = std::max(c, min_cell);
     if ((e = build_road(env, cell)) != cudaSuccess) break;
-    for (int wp : warps) {
+    for (int shape = 0; shape < 6; ++shape) {
+      const int wp = warps[shape % 3];
       env->warps = wp;
+      env->notile = shape / 3;
       if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
       for (int st = 1; st <= 2; ++st) {
         d.topk = st;
@@ -1262,6 +1268,7 @@ gd_status gd_autotune(gd_env* env) {
           best_cell = cell;
           best_w = wp;
           best_st = st;
+          best_nt = env->notile;
         }
       }
       if (e != cudaSuccess) break;
@@ -1270,6 +1277,7 @@ gd_status gd_autotune(gd_env* env) {
   }
   if (e == cudaSuccess) {
     env->warps = best_w;
+    env->notile = best_nt;
     d.topk = best_st;
     e = build_road(env, best_cell);
   }

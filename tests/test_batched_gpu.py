@@ -110,15 +110,17 @@ def test_graph_rollout_replay_and_full_size_agreement():
         np.testing.assert_array_equal(_np(s), plain["state"])
 
 
-@pytest.mark.parametrize("cell,block,topk", [(6.0, 128, 2), (8.0, 512, 1), (12.0, 256, 2), (10.0, 512, 2)])
-def test_tuning_choices_do_not_change_results(cell, block, topk):
-    # road grid cell, CTA size and top-K strategy are performance choices only
+@pytest.mark.parametrize("cell,block,topk,notile", [(6.0, 128, 2, 0), (8.0, 512, 1, 0), (12.0, 256, 2, 0),
+                                                    (10.0, 512, 2, 0), (8.0, 256, 1, 1), (12.0, 128, 2, 1)])
+def test_tuning_choices_do_not_change_results(cell, block, topk, notile):
+    # road grid cell, CTA size, top-K strategy and the road tile are performance choices only
     sc = small_scene(seed=12)
     ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
                         auto_reset=True)
     acts = scenes.make_actions(10, sc.num_agents, 12)
     plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
-    bat = _rollout(sc, _batched(ocfg, road_cell=cell, block_size=block, topk_strategy=topk), acts, "fused")
+    bat = _rollout(sc, _batched(ocfg, road_cell=cell, block_size=block, topk_strategy=topk, road_no_tile=notile),
+                   acts, "fused")
     for k in plain:
         np.testing.assert_array_equal(plain[k], bat[k], err_msg=k)
 
