@@ -28,15 +28,18 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
 def _kernel_source_hash():
-    """Hash of the sources the radial-observation k_world is compiled from
-    (its device code and the limits in the header)."""
+    """Hash of what the radial-observation k_world is compiled from: its
+    device headers (and the LiDAR arguments embedded in its parameter block)
+    and the constants (#define lines) of the C header.  The header's structs
+    are host-side and do not enter the kernel."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_01584_b300", "csrc")
-    files = [os.path.join(csrc, f) for f in ("gd_device.cuh", "observe_kernel.cuh", "world_kernel.cuh")]
-    for f in files + [os.path.join(ROOT, "include", "gd.h")]:
-        with open(f, "rb") as fh:
+    for f in ("gd_device.cuh", "observe_kernel.cuh", "world_kernel.cuh", "lidar_kernel.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(ROOT, "include", "gd.h")) as fh:
+        h.update("".join(l for l in fh if l.startswith("#define GD_")).encode())
     return h.hexdigest()[:16]
 
 
