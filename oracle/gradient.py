@@ -6,7 +6,11 @@ The objective of a rollout of T steps is
 where obs_t is the observation after step t (Sec. 3.2 "Sensor modalities",
 ego frame), r_s = -(sqrt(d_goal^2 + c^2) - c) is a smooth goal reward (not in
 the paper) counted for agents in the scene at the start of step t, and the
-state follows the bicycle model of App. B.  Collision, goal, done, selection
+state follows the bicycle model of App. B, or the simplified invertible
+model of Sec. 3.2 "Agent dynamics" (cfg.dynamics = 1).  Uncontrolled agents
+of the "all nontrivial" initialisation (flag bit 16) do not move and have no
+reward term (their reward is 0 too); like every agent still in the scene
+they observe and are observed.  Collision, goal, done, selection
 and clip decisions are the ones the brute-force oracle (oracle.cpp) takes
 along its own float64 trajectory; with those fixed, L is a smooth function of
 the actions and the initial state, and its gradient is taken here by PyTorch
@@ -73,6 +77,13 @@ def _bicycle(state, act, L, dt, vmax):
     return torch.stack([x, y, th2, v], -1)
 
 
+def _invertible(state, act, dt):
+    x, y, th, v = state.unbind(-1)
+    a, k = act.unbind(-1)
+    ds = v * dt + 0.5 * a * dt * dt
+    return torch.stack([x + torch.cos(th) * ds, y + torch.sin(th) * ds, th + k * ds, v + a * dt], -1)
+
+
 def objective_gradient(scene, cfg: OracleConfig, actions, obs_weight, reward_weight, d_ell=None, state0=None,
                        dec: Decisions | None = None):
     """Returns (ell [T,A] from the autograd forward, d_actions [T,A,2],
@@ -104,8 +115,9 @@ def objective_gradient(scene, cfg: OracleConfig, actions, obs_weight, reward_wei
     total = torch.zeros((), dtype=f64)
     ells = []
     for t in range(T):
-        act0 = torch.tensor((dec.flags_pre[t] & 1) == 0)
-        state = torch.where(act0[:, None], _bicycle(state, a[t], L, cfg.dt, cfg.v_max), state)
+        moving = torch.tensor((dec.flags_pre[t] & (1 | 16)) == 0)       # in the scene and controlled
+        nxt = _invertible(state, a[t], cfg.dt) if cfg.dynamics == 1 else _bicycle(state, a[t], L, cfg.dt, cfg.v_max)
+        state = torch.where(moving[:, None], nxt, state)
         fpost = dec.flags_post[t]
         live = torch.tensor((fpost & 1) == 0, dtype=f64)
         x, y, th, v = state.unbind(-1)
@@ -134,9 +146,9 @@ def objective_gradient(scene, cfg: OracleConfig, actions, obs_weight, reward_wei
             feats = torch.stack([c[:, None] * dx + s[:, None] * dy, -s[:, None] * dx + c[:, None] * dy, rtype[rg],
                                  torch.ones_like(dx)], -1)
             ell = ell + ((feats * wR).sum(-1) * rv).sum(-1)
-        # smooth goal reward of agents in the scene before the step
+        # smooth goal reward of controlled agents in the scene before the step
         rs = -(torch.sqrt((x - gx) ** 2 + (y - gy) ** 2 + c_s * c_s) - c_s)
-        ell = ell + reward_weight * torch.where(act0, rs, torch.zeros_like(rs))
+        ell = ell + reward_weight * torch.where(moving, rs, torch.zeros_like(rs))
         ells.append(ell.detach())
         total = total + (dl[t] * ell).sum()
     total.backward()

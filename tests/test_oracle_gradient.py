@@ -20,19 +20,26 @@ from paper_2408_01584_b300 import scenes
 from tests._util import tiny_scene
 
 CFG = OracleConfig(k_road=24, n_partners=5, episode_len=91, term_collision=True, term_offroad=True)
+# the simplified invertible model (curvature actions), and the "all nontrivial" initialisation
+INV = OracleConfig(k_road=24, n_partners=5, episode_len=91, term_collision=True, term_offroad=True, dynamics=1)
+NTR = OracleConfig(k_road=24, n_partners=5, episode_len=91, term_collision=True, term_offroad=True,
+                   nontrivial_init=True)
 
 
-def _problem(seed=0, T=10):
-    sc = scenes.make_scene(np.array([5, 8, 3]), np.array([600, 900, 400]), seed)
+def _problem(seed=0, T=10, cfg=CFG):
+    sc = scenes.make_scene(np.array([5, 8, 3]), np.array([600, 900, 400]), seed,
+                           parked_frac=0.4 if cfg.nontrivial_init else 0.0)
     acts = scenes.make_actions(T, sc.num_agents, seed)
+    if cfg.dynamics == 1:
+        acts[:, :, 1] *= 0.2 / 0.7
     rng = np.random.default_rng(seed)
     w = rng.uniform(0, 1, CFG.feat)
     d_ell = rng.uniform(0.5, 1.5, (T, sc.num_agents))
     return sc, acts, w, 0.7, d_ell
 
 
-def _objective(sc, acts, w, wr, d_ell, state0=None):
-    dec = oracle_rollout(sc, CFG, acts, w, wr, state0)
+def _objective(sc, acts, w, wr, d_ell, state0=None, cfg=CFG):
+    dec = oracle_rollout(sc, cfg, acts, w, wr, state0)
     return float((dec.ell * d_ell).sum()), dec
 
 
@@ -41,16 +48,19 @@ def _same_decisions(a, b):
                                            (a.road_idx, b.road_idx), (a.partner_idx, b.partner_idx)))
 
 
-def test_forward_objective_matches_cpp_oracle():
-    sc, acts, w, wr, d_ell = _problem(1)
-    ell, _, _, dec = objective_gradient(sc, CFG, acts, w, wr, d_ell)
+@pytest.mark.parametrize("cfg", [CFG, INV, NTR], ids=["bicycle", "invertible", "nontrivial"])
+def test_forward_objective_matches_cpp_oracle(cfg):
+    sc, acts, w, wr, d_ell = _problem(1, cfg=cfg)
+    ell, _, _, dec = objective_gradient(sc, cfg, acts, w, wr, d_ell)
     np.testing.assert_allclose(ell, dec.ell, rtol=1e-10, atol=1e-8)
+    if cfg.nontrivial_init:
+        assert ((dec.flags_pre[0] & 16) != 0).any()
 
 
-@pytest.mark.parametrize("seed", [2, 3])
-def test_directional_derivatives_match_finite_differences(seed):
-    sc, acts, w, wr, d_ell = _problem(seed)
-    _, ga, gs, dec = objective_gradient(sc, CFG, acts, w, wr, d_ell)
+@pytest.mark.parametrize("seed,cfg", [(2, CFG), (3, CFG), (4, INV), (5, NTR)], ids=["b2", "b3", "inv", "ntr"])
+def test_directional_derivatives_match_finite_differences(seed, cfg):
+    sc, acts, w, wr, d_ell = _problem(seed, cfg=cfg)
+    _, ga, gs, dec = objective_gradient(sc, cfg, acts, w, wr, d_ell)
     rng = np.random.default_rng(100 + seed)
     h = 1e-4
     s0 = sc.state().astype(np.float64)
@@ -66,8 +76,10 @@ def test_directional_derivatives_match_finite_differences(seed):
         if k % 2:
             ds[i] = rng.normal(size=4)
         # float32 inputs: perturb in float64 and let the oracle read float32 -> keep h large enough
-        lp, dp = _objective(sc, (acts + h * da).astype(np.float32), w, wr, d_ell, (s0 + h * ds).astype(np.float32))
-        lm, dm = _objective(sc, (acts - h * da).astype(np.float32), w, wr, d_ell, (s0 - h * ds).astype(np.float32))
+        lp, dp = _objective(sc, (acts + h * da).astype(np.float32), w, wr, d_ell, (s0 + h * ds).astype(np.float32),
+                            cfg)
+        lm, dm = _objective(sc, (acts - h * da).astype(np.float32), w, wr, d_ell, (s0 - h * ds).astype(np.float32),
+                            cfg)
         if not (_same_decisions(dp, dec) and _same_decisions(dm, dec)):
             excluded += 1
             continue
