@@ -138,8 +138,7 @@ typedef struct gd_config {
   int32_t dynamics;          /* GD_DYN_BICYCLE (default) or GD_DYN_INVERTIBLE: the simplified model,
                                 a double integrator along the heading of the start of the step,
                                 ds = v dt + a dt^2 / 2, x += cos(theta) ds, y += sin(theta) ds,
-                                theta += steer * ds, v += a dt (no speed clip; length unused);
-                                GD_DIFFERENTIABLE needs GD_DYN_BICYCLE */
+                                theta += steer * ds, v += a dt (no speed clip; length unused) */
   float nontrivial_dist;     /* m, with GD_NONTRIVIAL_INIT: agents at most this far from their goal
                                 at the start are not controlled (2; Sec. 3.2) */
   int32_t road_no_tile;      /* 1: the fused kernel reads each world's road block from global memory
@@ -284,8 +283,8 @@ gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, flo
  * the per-step objective terms
  *   ell[t,i] = sum_f obs_weight[f] * obs(t)[i,f] + reward_weight * r_s(t,i)
  * where obs(t) is the observation after step t and r_s = -(sqrt(d_goal^2 +
- * c^2) - c), c = smooth_c, for agents in the scene at the start of step t
- * (0 otherwise).  The state is checkpointed every ckpt_every steps for
+ * c^2) - c), c = smooth_c, for controlled agents in the scene at the start
+ * of step t (0 otherwise).  The state is checkpointed every ckpt_every steps for
  * gd_rollout_backward; `actions` must stay unchanged until then.
  * Requires GD_DIFFERENTIABLE; steps <= episode_len.
  *   actions: device float [T,A,2]; obs_weight: device float [F], 16-byte

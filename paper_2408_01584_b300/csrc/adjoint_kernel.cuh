@@ -1,6 +1,7 @@
 // Adjoint (reverse-mode derivative) of one simulator step.  The paper has
 // no gradient; this differentiates the step it defines: the bicycle model
-// of App. B, the ego-frame observation of Sec. 3.2 ("Sensor modalities")
+// of App. B (or the simplified model of Sec. 3.2 "Agent dynamics"), the
+// ego-frame observation of Sec. 3.2 ("Sensor modalities")
 // and a smooth goal reward r_s = -(sqrt(d_goal^2 + c^2) - c).  Collision,
 // goal, done, selection and clip decisions are held constant (piecewise-
 // constant parts of the step): the derivative of clip is 1 on [-v_max,
@@ -82,9 +83,27 @@ __device__ __forceinline__ void bicycle_adjoint(const float4 s, float accel, flo
   lam.w = fmaf(g_vbar, m1, lam.w * m2);
 }
 
+// Adjoint of the simplified invertible model (Sec. 3.2 "Agent dynamics"):
+// ds = v dt + a dt^2 / 2, x' = x + cos(theta) ds, y' = y + sin(theta) ds,
+// theta' = theta + k ds, v' = v + a dt, so with g = dL/d ds =
+// lam_x cos + lam_y sin + lam_theta k: dL/d theta = lam_theta + ds (-lam_x
+// sin + lam_y cos), dL/dv = lam_v + g dt, dL/da = g dt^2 / 2 + lam_v dt,
+// dL/dk = lam_theta ds.
+__device__ __forceinline__ void invertible_adjoint(const float4 s, float accel, float curv, float dt, float4& lam,
+                                                   float2& da) {
+  const float ds = fmaf(__fmul_rn(0.5f, accel), __fmul_rn(dt, dt), __fmul_rn(s.w, dt));
+  float sn, cs;
+  sincosf(s.z, &sn, &cs);
+  const float g = fmaf(lam.x, cs, fmaf(lam.y, sn, __fmul_rn(lam.z, curv)));
+  da.x = fmaf(__fmul_rn(g, 0.5f * dt), dt, __fmul_rn(lam.w, dt));
+  da.y = __fmul_rn(lam.z, ds);
+  lam.z = fmaf(ds, fmaf(-lam.x, sn, __fmul_rn(lam.y, cs)), lam.z);
+  lam.w = fmaf(g, dt, lam.w);
+}
+
 // Dynamic shared memory: [mbarrier, 128 B][road tile][AdjAgents][ObsWarpSmem x WARPS]
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 1) k_adjoint(DevEnv e, AdjArgs a) {
   extern __shared__ __align__(16) unsigned char asm_[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(asm_);
   unsigned char* tile = asm_ + 128;
@@ -236,8 +255,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
         (void)q;
       }
       const uint8_t f0 = a.fpre[ig];
-      if (!(f0 & GD_FLAG_DONE)) {
-        // smooth goal reward of an agent in the scene before the step
+      if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
+        // smooth goal reward of a controlled agent in the scene before the step
         const float m = a.row_scale ? a.row_scale[ig] : 1.f;
         const float rw = (a.rew_w ? a.rew_w[ig] : a.reward_w) * m;
         const float4 st = ag.st[j], sc = ag.sc[j];
@@ -252,9 +271,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_adjoint(DevEnv e, AdjArgs a) {
       lam.z += g.z;
       lam.w += g.w;
       float2 da = make_float2(0.f, 0.f);
-      if (!(f0 & GD_FLAG_DONE)) {
+      if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {      // done and uncontrolled agents do not move
         const float2 u = a.actions[ig];
-        bicycle_adjoint(a.pre[ig], u.x, u.y, ag.sc[j].x, e.dt, e.vmax, lam, da);
+        if (e.dyn == 1) invertible_adjoint(a.pre[ig], u.x, u.y, e.dt, lam, da);
+        else bicycle_adjoint(a.pre[ig], u.x, u.y, ag.sc[j].x, e.dt, e.vmax, lam, da);
       }
       a.lam[ig] = lam;
       a.d_actions[ig] = da;

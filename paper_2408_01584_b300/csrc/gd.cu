@@ -437,12 +437,8 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
   if (c->road_no_tile != 0 && c->road_no_tile != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "road_no_tile must be 0 or 1");
   if (c->dynamics != GD_DYN_BICYCLE && c->dynamics != GD_DYN_INVERTIBLE)
     return fail(nullptr, GD_ERR_INVALID_ARG, "dynamics must be GD_DYN_BICYCLE or GD_DYN_INVERTIBLE");
-  if (c->dynamics != GD_DYN_BICYCLE && (c->flags & GD_DIFFERENTIABLE))
-    return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE needs the kinematic bicycle (GD_DYN_BICYCLE)");
   if (!(c->nontrivial_dist >= 0.f) || !finite(c->nontrivial_dist))
     return fail(nullptr, GD_ERR_INVALID_ARG, "nontrivial_dist must be >= 0");
-  if ((c->flags & GD_NONTRIVIAL_INIT) && (c->flags & GD_DIFFERENTIABLE))
-    return fail(nullptr, GD_ERR_INVALID_ARG, "GD_NONTRIVIAL_INIT cannot be combined with GD_DIFFERENTIABLE");
   if ((c->flags & GD_DIFFERENTIABLE) && (c->flags & GD_AUTO_RESET))
     return fail(nullptr, GD_ERR_INVALID_ARG, "GD_DIFFERENTIABLE cannot be combined with GD_AUTO_RESET");
   const int W = s->num_worlds;

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
                                      : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, a.obs_w);
           if (lane == 0) {
             float rs = 0.f;
-            if (a.do_step && ag.act0[li]) {
+            if (a.do_step && ag.act0[li] && !(ag.fl[li] & GD_FLAG_STATIC)) {
               const float4 st = ag.st[li], sc = ag.sc[li];
               const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
               rs = c - sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));

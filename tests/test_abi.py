@@ -94,10 +94,8 @@ def test_rejects_bad_arguments_before_any_launch(lib):
     _expect(INV, gd.gd_create, gd.gd_default_config(lidar_rays=100, lidar_no_tile=2), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(lidar_rays=100, lidar_split=3), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(dynamics=2), sc)
-    _expect(INV, gd.gd_create, gd.gd_default_config(dynamics=gd.GD_DYN_INVERTIBLE, flags=gd.GD_DIFFERENTIABLE), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(nontrivial_dist=-1.0), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(road_no_tile=2), sc)
-    _expect(INV, gd.gd_create, gd.gd_default_config(flags=gd.GD_NONTRIVIAL_INIT | gd.GD_DIFFERENTIABLE), sc)
     big = scenes.make_scene(np.array([129]), np.array([500]), 0)
     _expect(CAP, gd.gd_create, gd.gd_default_config(), big)
     bad = scenes.workload_scene("plain_4x8", 0)

@@ -28,9 +28,9 @@ GRAD_RTOL = 1e-4     # max |g_gpu - g_oracle| / max |g_oracle| per world (float3
 def _kw(ocfg):
     from paper_2408_01584_b300 import gd
     fl = gd.GD_DIFFERENTIABLE | (gd.GD_TERM_COLLISION if ocfg.term_collision else 0) | \
-        (gd.GD_TERM_OFFROAD if ocfg.term_offroad else 0)
+        (gd.GD_TERM_OFFROAD if ocfg.term_offroad else 0) | (gd.GD_NONTRIVIAL_INIT if ocfg.nontrivial_init else 0)
     return dict(k_road=ocfg.k_road, n_partners=ocfg.n_partners, episode_len=ocfg.episode_len, flags=fl,
-                smooth_c=ocfg.smooth_c)
+                smooth_c=ocfg.smooth_c, dynamics=ocfg.dynamics)
 
 
 def _gpu_decisions(sc, ocfg, acts):
@@ -112,6 +112,25 @@ def test_gradient_small_ragged():
     T = 12
     acts = scenes.make_actions(T, sc.num_agents, 4)
     rng = np.random.default_rng(4)
+    w = rng.uniform(0, 1, ocfg.feat)
+    d_ell = rng.uniform(0.5, 1.5, (T, sc.num_agents))
+    _compare(sc, ocfg, acts, w, 0.7, d_ell, min_clean=2, min_steps=4)
+
+
+@pytest.mark.parametrize("variant", ["invertible", "nontrivial"])
+def test_gradient_model_variants(variant):
+    # the simplified invertible model (curvature actions), or the "all
+    # nontrivial" initialisation with parked agents (frozen, no reward term)
+    inv = variant == "invertible"
+    sc = scenes.make_scene(np.array([5, 8, 3, 12]), np.array([600, 900, 400, 1500]), 6,
+                           parked_frac=0.0 if inv else 0.4)
+    ocfg = OracleConfig(k_road=24, n_partners=5, episode_len=91, term_collision=True, term_offroad=True,
+                        dynamics=1 if inv else 0, nontrivial_init=not inv)
+    T = 12
+    acts = scenes.make_actions(T, sc.num_agents, 6)
+    if inv:
+        acts[:, :, 1] *= 0.2 / 0.7
+    rng = np.random.default_rng(6)
     w = rng.uniform(0, 1, ocfg.feat)
     d_ell = rng.uniform(0.5, 1.5, (T, sc.num_agents))
     _compare(sc, ocfg, acts, w, 0.7, d_ell, min_clean=2, min_steps=4)
