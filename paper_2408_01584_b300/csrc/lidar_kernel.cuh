@@ -14,9 +14,10 @@
 // that keeps at least LIDAR_NEAR_FULL away subtends an arc shorter than pi:
 // the arc between the extreme corner (box) or end point (segment)
 // directions.  It maps to one contiguous range of ray indices (two when it
-// wraps past the end of a full circle), widened by LIDAR_PAD and one more
-// ray at each end to absorb the rounding of atan2f and of the rotations
-// (below 1e-6 rad), and only those rays are tested exactly.  A
+// wraps past the end of a full circle), widened by LIDAR_PAD at each end to
+// absorb the rounding of atan2f, of the rotations and of the index
+// arithmetic (together below 1e-6 rad), and only those rays are tested
+// exactly.  A
 // closer obstacle is tested on every ray.  Each (obstacle, ray range) is an
 // item of a per-warp queue in shared memory; the warp drains the queue one
 // (item, ray) pair per lane, balanced by a prefix sum over the range
@@ -81,8 +82,9 @@ struct LidarArgs {
   int warp_bytes;          // lidar_warp_bytes(n)
 };
 
-// Ray ranges of the arc [lo, hi] (sensor-frame angles, hi - lo < pi + 2
-// rays): the copies of the arc shifted by -2pi, 0, +2pi that meet the fan.
+// Ray ranges of the arc [lo, hi] (sensor-frame angles, hi - lo < pi): the
+// copies of the arc shifted by -2pi, 0, +2pi that meet the fan, each range
+// the rays whose angle lies within LIDAR_PAD of the arc.
 __device__ __forceinline__ int arc_ranges(const LidarFan& f, float lo, float hi, bool full, unsigned& r0,
                                           unsigned& r1) {
   if (full) {
@@ -93,14 +95,15 @@ __device__ __forceinline__ int arc_ranges(const LidarFan& f, float lo, float hi,
   const float a0 = (lo - LIDAR_PAD - f.b0) * f.inv_step, b0 = (hi + LIDAR_PAD - f.b0) * f.inv_step;
   if (a0 > 0.f && b0 < (float)(f.n - 1)) {
     // inside the fan: the copies one turn away cannot reach it
-    const int k0 = (int)ceilf(a0) - 1, k1 = (int)floorf(b0) + 1;
+    const int k0 = (int)ceilf(a0), k1 = (int)floorf(b0);
+    if (k0 > k1) return 0;
     r0 = (unsigned)k0 | ((unsigned)(k1 - k0 + 1) << 16);
     return 1;
   }
 #pragma unroll
   for (int sft = -1; sft <= 1; ++sft) {
     const float a = fmaf((float)sft, f.wrap_steps, a0), b = fmaf((float)sft, f.wrap_steps, b0);
-    const int k0 = max((int)ceilf(a) - 1, 0), k1 = min((int)floorf(b) + 1, f.n - 1);
+    const int k0 = max((int)ceilf(a), 0), k1 = min((int)floorf(b), f.n - 1);
     if (k0 <= k1) {
       const unsigned r = (unsigned)k0 | ((unsigned)(k1 - k0 + 1) << 16);
       if (m == 0) r0 = r; else r1 = r;
