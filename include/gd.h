@@ -260,6 +260,17 @@ gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* 
 gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, const float* head, float* depth,
                            uint8_t* cls, int32_t obs_per_step, float* reward, uint8_t* done);
 
+/* Episode statistics of the current state (the rates the paper reports:
+ * goal reached, collision, off-road; Sec. 4): per world and in total, the
+ * GD_STATS counts (in this order) of agents in the scene (not done),
+ * controlled agents in the scene (not done, not GD_FLAG_STATIC), and agents
+ * with GD_FLAG_GOAL, GD_FLAG_COLLIDED and GD_FLAG_OFFROAD set.
+ *   per_world: device int32 [W, GD_STATS] or NULL
+ *   totals:    device int64 [GD_STATS] or NULL (not both NULL)
+ * Asynchronous. */
+#define GD_STATS 5
+gd_status gd_episode_stats(gd_env* env, int32_t* per_world, int64_t* totals);
+
 /* Expert actions of trajectories under the env's dynamics model (Sec. 3.2
  * "Agent dynamics": actions computed from logged trajectories and replayed
  * to imitate them).  For each agent i and step t, from states s0 = state(t),

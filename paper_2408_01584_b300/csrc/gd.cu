@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
 #include "step_kernels.cuh"
@@ -21,6 +23,13 @@ using namespace gd;
 namespace {
 
 thread_local std::string g_create_error;
+
+// NVTX range over a host entry point (a marker for profiler timelines; no
+// effect unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 constexpr int kObsWarpsDefault = 8;
 constexpr int kWorldWarps = 8;    // default CTA size of the fused kernel (warps); 4 and 16 also built
@@ -474,6 +483,7 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
 }
 
 gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_stream, gd_env** out) {
+  NvtxRange range_("gd_create");
   if (!out) return fail(nullptr, GD_ERR_INVALID_ARG, "out must not be NULL");
   *out = nullptr;
   gd_status st = validate(cfg, s);
@@ -708,6 +718,7 @@ static gd_status launch_check(gd_env* env, const char* what) {
 static inline unsigned blocks_for(long n, int per) { return (unsigned)std::max<long>(1, (n + per - 1) / per); }
 
 gd_status gd_reset(gd_env* env, const uint8_t* world_mask) {
+  NvtxRange range_("gd_reset");
   if (!env) return GD_ERR_INVALID_ARG;
   if (world_mask) {
     k_reset_worlds<<<blocks_for(env->W, 8), 256, 0, env->stream>>>(env->d, world_mask);
@@ -833,6 +844,7 @@ static bool batched(const gd_env* env) { return (env->cfg.flags & GD_BATCHED) !=
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done) {
+  NvtxRange range_("gd_step");
   if (!env) return GD_ERR_INVALID_ARG;
   if (!actions && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions must not be NULL");
   if (!aligned16(actions) && ((uintptr_t)actions & 7u)) return fail(env, GD_ERR_INVALID_ARG, "actions must be 8-byte aligned");
@@ -845,6 +857,7 @@ gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* don
 }
 
 gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partner_idx) {
+  NvtxRange range_("gd_observe");
   if (!env) return GD_ERR_INVALID_ARG;
   if (!obs && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "obs must not be NULL");
   if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
@@ -856,6 +869,7 @@ gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partne
 
 gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                           float* obs) {
+  NvtxRange range_("gd_step_observe");
   if (env && batched(env)) {
     if (!actions && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "actions must not be NULL");
     if (!obs && env->A > 0) return fail(env, GD_ERR_INVALID_ARG, "obs must not be NULL");
@@ -870,6 +884,7 @@ gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint
 
 gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step, float* reward,
                      uint8_t* done) {
+  NvtxRange range_("gd_rollout");
   if (!env) return GD_ERR_INVALID_ARG;
   if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
   if (steps == 0 || env->A == 0) return GD_OK;
@@ -937,6 +952,7 @@ static gd_status need_lidar(gd_env* env, const char* what) {
 static bool aligned4(const void* p) { return ((uintptr_t)p & 3u) == 0; }
 
 gd_status gd_observe_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls) {
+  NvtxRange range_("gd_observe_lidar");
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_lidar(env, "gd_observe_lidar");
   if (st != GD_OK) return st;
@@ -950,6 +966,7 @@ gd_status gd_observe_lidar(gd_env* env, const float* head, float* depth, uint8_t
 
 gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* head, float* reward, uint8_t* done,
                                 uint8_t* world_done, float* depth, uint8_t* cls) {
+  NvtxRange range_("gd_step_observe_lidar");
   if (!env) return GD_ERR_INVALID_ARG;
   if (batched(env)) {
     gd_status st = need_lidar(env, "gd_step_observe_lidar");
@@ -969,6 +986,7 @@ gd_status gd_step_observe_lidar(gd_env* env, const float* actions, const float* 
 
 gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, const float* head, float* depth,
                            uint8_t* cls, int32_t obs_per_step, float* reward, uint8_t* done) {
+  NvtxRange range_("gd_rollout_lidar");
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_lidar(env, "gd_rollout_lidar");
   if (st != GD_OK) return st;
@@ -1028,9 +1046,48 @@ gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, con
   return GD_OK;
 }
 
+// ---- episode statistics -------------------------------------------------------
+
+// Warp per world: counts of the agents in the scene, the controlled agents in
+// the scene, and the agents whose goal, collision and off-road flags are set.
+__global__ void k_episode_stats(DevEnv e, int32_t* __restrict__ per_world, unsigned long long* __restrict__ totals) {
+  const int lane = threadIdx.x & 31;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= e.W) return;
+  int c[GD_STATS] = {0, 0, 0, 0, 0};
+  for (int i = e.agent_off[w] + lane; i < e.agent_off[w + 1]; i += WARP) {
+    const uint8_t f = e.flags[i];
+    c[0] += !(f & GD_FLAG_DONE);
+    c[1] += !(f & (GD_FLAG_DONE | GD_FLAG_STATIC));
+    c[2] += (f & GD_FLAG_GOAL) != 0;
+    c[3] += (f & GD_FLAG_COLLIDED) != 0;
+    c[4] += (f & GD_FLAG_OFFROAD) != 0;
+  }
+#pragma unroll
+  for (int k = 0; k < GD_STATS; ++k)
+    for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], o);
+  if (lane < GD_STATS) {
+    const int v = c[0] * (lane == 0) + c[1] * (lane == 1) + c[2] * (lane == 2) + c[3] * (lane == 3) + c[4] * (lane == 4);
+    if (per_world) per_world[(size_t)w * GD_STATS + lane] = v;
+    if (totals && v) atomicAdd(totals + lane, (unsigned long long)v);
+  }
+}
+
+gd_status gd_episode_stats(gd_env* env, int32_t* per_world, int64_t* totals) {
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (!per_world && !totals) return fail(env, GD_ERR_INVALID_ARG, "per_world and totals are both NULL");
+  if (((uintptr_t)per_world & 3u) || ((uintptr_t)totals & 7u))
+    return fail(env, GD_ERR_INVALID_ARG, "per_world must be 4-byte and totals 8-byte aligned");
+  if (totals) cudaMemsetAsync(totals, 0, sizeof(int64_t) * GD_STATS, env->stream);
+  k_episode_stats<<<blocks_for(env->W, 8), 256, 0, env->stream>>>(env->d, per_world,
+                                                                  reinterpret_cast<unsigned long long*>(totals));
+  return launch_check(env, "gd_episode_stats");
+}
+
 // ---- expert-action inversion -------------------------------------------------
 
 gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, float* actions) {
+  NvtxRange range_("gd_invert_actions");
   if (!env) return GD_ERR_INVALID_ARG;
   if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
   if (steps == 0 || env->A == 0) return GD_OK;
@@ -1063,6 +1120,7 @@ static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t
 
 gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
                                float reward_weight, float* ell, float* obs) {
+  NvtxRange range_("gd_rollout_objective");
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_diff(env, "gd_rollout_objective");
   if (st != GD_OK) return st;
@@ -1137,6 +1195,7 @@ static void recompute_segment(gd_env* env, const float* actions0, int len) {
 
 gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
                               float* d_actions, float* d_state0) {
+  NvtxRange range_("gd_rollout_backward");
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_diff(env, "gd_rollout_backward");
   if (st != GD_OK) return st;
@@ -1164,6 +1223,7 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
 
 gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,
                            const float* obs_weight, const float* d_reward_s, float* d_state, float* d_actions) {
+  NvtxRange range_("gd_step_backward");
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_diff(env, "gd_step_backward");
   if (st != GD_OK) return st;
@@ -1203,6 +1263,7 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
 // (road cell, CTA size, top-K strategy) and keep the fastest; the state is
 // saved first and restored after every trial and at the end.
 gd_status gd_autotune(gd_env* env) {
+  NvtxRange range_("gd_autotune");
   if (!env) return GD_ERR_INVALID_ARG;
   if (env->A == 0) return GD_OK;
   const size_t A = (size_t)env->A, W = (size_t)env->W;
@@ -1356,6 +1417,7 @@ gd_status gd_selftest_timeout(gd_env* env, int32_t wait_us) {
 }
 
 gd_status gd_sync(gd_env* env) {
+  NvtxRange range_("gd_sync");
   if (!env) return GD_ERR_INVALID_ARG;
   cudaError_t e = cudaMemcpyAsync(env->h_err, env->d.err, sizeof(unsigned), cudaMemcpyDeviceToHost, env->stream);
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_sync");

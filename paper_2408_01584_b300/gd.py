@@ -33,7 +33,9 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
-           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate")
+           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats")
+
+GD_STATS = 5   # in the scene, controlled in the scene, goal, collided, off-road
 
 DECIMATE_AREA = 1e-3     # m^2, default tolerance of decimate_scene (10-15x on 0.1 m-sampled roads)
 
@@ -116,6 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_rollout_lidar.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp]
     lib.gd_invert_actions.argtypes = [vp, i32, vp, vp]
     lib.gd_decimate.argtypes = [i32, i32, vp, vp, vp, f32, vp, vp]
+    lib.gd_episode_stats.argtypes = [vp, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -234,6 +237,12 @@ def gd_invert_actions(env, steps, states, actions):
     """Expert actions [steps, A, 2] of trajectories states [steps+1, A, 4]."""
     lib = load_library()
     _check(lib, env, lib.gd_invert_actions(env, int(steps), _ptr(states, align=16), _ptr(actions, align=8)))
+
+
+def gd_episode_stats(env, per_world=None, totals=None):
+    """Counts (GD_STATS columns) per world (int32 [W, 5]) and in total (int64 [5])."""
+    lib = load_library()
+    _check(lib, env, lib.gd_episode_stats(env, _ptr(per_world, align=4), _ptr(totals, align=8)))
 
 
 def gd_decimate(poly_off, x, y, area_tol, keep, stream=None):

@@ -74,3 +74,25 @@ def test_nontrivial_fused_equals_per_stage():
     done = outs[0][5].numpy()
     static = (outs[0][1].numpy() & 16) != 0
     assert (done[:, static] == 1).all()
+
+
+def test_episode_stats_count_the_flags():
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("nontrivial_1024x64", 3, worlds=40)
+    ocfg = workload_config("nontrivial_1024x64", nontrivial_init=True)
+    env = gd.Env(sc, **gd_kwargs(ocfg, flags=_flags(ocfg, True)))
+    acts = torch.from_numpy(scenes.make_actions(15, sc.num_agents, 3)).cuda()
+    pw = torch.empty(sc.num_worlds, gd.GD_STATS, dtype=torch.int32, device="cuda")
+    tot = torch.empty(gd.GD_STATS, dtype=torch.int64, device="cuda")
+    world = np.repeat(np.arange(sc.num_worlds), np.diff(sc.agent_off))
+    for t in range(15):
+        env.step(acts[t])
+        gd.gd_episode_stats(env.h, pw, tot)
+        f = env.get_state()[1].cpu().numpy()
+        env.sync()
+        cols = [(f & 1) == 0, (f & (1 | 16)) == 0, (f & 2) != 0, (f & 4) != 0, (f & 8) != 0]
+        exp = np.stack([np.bincount(world, weights=c, minlength=sc.num_worlds) for c in cols], 1).astype(np.int64)
+        np.testing.assert_array_equal(pw.cpu().numpy(), exp)
+        np.testing.assert_array_equal(tot.cpu().numpy(), exp.sum(0))
+    assert exp[:, 0].sum() > exp[:, 1].sum()        # parked agents are in the scene but not controlled
+    env.close()
