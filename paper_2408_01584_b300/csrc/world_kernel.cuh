@@ -19,6 +19,12 @@
 
 namespace gd {
 
+// Road bytes one agent's observation reads from its world's block (the
+// candidates of its disk, about 500 points of 12 B at the default density):
+// below n * TILE_AGENT_BYTES a block is read from global memory instead of
+// being copied into the tile.
+constexpr unsigned TILE_AGENT_BYTES = 6144;
+
 struct FusedArgs {
   const float2* actions;     // [A] (step) or nullptr
   float* reward;             // [A] or nullptr
@@ -139,7 +145,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
     const GridDesc g = e.rgrid[w];
     const unsigned block = (unsigned)g.block_bytes;
     const unsigned char* gblock = e.arena + (size_t)e.arena_off[w] * 16;
-    const bool use_tile = nr > 0 && block <= (unsigned)a.tile_bytes;
+    // the tile pays when the world's agents would read more of the block
+    // than its size (each agent reads its disk's candidates, a few KB)
+    const bool use_tile = nr > 0 && block <= (unsigned)a.tile_bytes && (unsigned)n * TILE_AGENT_BYTES >= block;
     if (use_tile && tid == 0) {
       fence_proxy_async_smem();     // earlier generic reads of the tile before the async write
       mbar_arrive_expect_tx(bar, block);
