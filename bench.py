@@ -317,6 +317,8 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
     cfg = workload_cfg(workload)
     with torch.cuda.stream(stream):
         env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_DIFFERENTIABLE))
+        gd.gd_autotune(env.h)
+        info = gd.gd_get_info(env.h)
         A, F = env.A, env.F
         actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
         w = torch.from_numpy(np.random.default_rng(seed).uniform(0, 1, F).astype(np.float32)).to(dev)
@@ -340,7 +342,9 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
     out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC + " (forward+backward)",
            "ms_per_episode": statistics.mean(ms), "forward_only_ms_per_episode": statistics.mean(ms_f),
-           "ckpt_every": 10}
+           "ckpt_every": 10,
+           "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
+                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile}}
     env.close()
     return out
 

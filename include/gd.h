@@ -141,8 +141,9 @@ typedef struct gd_config {
                                 theta += steer * ds, v += a dt (no speed clip; length unused) */
   float nontrivial_dist;     /* m, with GD_NONTRIVIAL_INIT: agents at most this far from their goal
                                 at the start are not controlled (2; Sec. 3.2) */
-  int32_t road_no_tile;      /* 1: the fused kernel reads each world's road block from global memory
-                                instead of copying it into shared memory (more CTAs per SM); default 0 */
+  int32_t road_no_tile;      /* 1: the fused and adjoint kernels read each world's road block from
+                                global memory instead of copying it into shared memory (more CTAs per
+                                SM); default 0 */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -336,7 +337,8 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * from the current state for every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads, with and without the shared-memory road tile,
  * and top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
- * points are in range}, and keeps the fastest
+ * points are in range}, and keeps the fastest; with GD_DIFFERENTIABLE it
+ * also times one adjoint launch with and without the road tile
  * (reported by gd_get_info).  With LiDAR enabled it then times the fused
  * step + LiDAR scan with 128, 256 and 384 threads per block, each with and
  * without the shared-memory road tile, and the split form (step, then a

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_adjoint(DevEnv e, AdjArgs a) 
     const GridDesc g = e.rgrid[w];
     const unsigned block = (unsigned)g.block_bytes;
     const unsigned char* gblock = e.arena + (size_t)e.arena_off[w] * 16;
-    const bool use_tile = obs_term && nr > 0 && block <= (unsigned)a.tile_bytes;
+    const bool use_tile = obs_term && nr > 0 && block <= (unsigned)a.tile_bytes && (unsigned)n * TILE_AGENT_BYTES >= block;
     if (use_tile && tid == 0) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, block);

@@ -91,6 +91,7 @@ struct gd_env {
   float4* lam = nullptr;        // [A] adjoint of the state
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
+  int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
   size_t adj_smem = 0;
   int adj_grid = 0;
   const float* diff_actions = nullptr;   // actions of the last objective rollout
@@ -249,7 +250,7 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
   if (env->cfg.flags & GD_DIFFERENTIABLE) {
     const long two = ((long)smem_sm / 2 - 2048 - (long)kAdjFixedSmem) & ~15L;
     const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
-    env->adj_tile = (int)std::max(16L, ((long)max_block <= two) ? (long)max_block : one);
+    env->adj_tile = env->adj_notile ? 16 : (int)std::max(16L, ((long)max_block <= two) ? (long)max_block : one);
     env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
     e = cudaFuncSetAttribute(k_adjoint<kAdjWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->adj_smem);
     if (e != cudaSuccess) return e;
@@ -637,6 +638,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
   env->notile = cfg->road_no_tile;
+  env->adj_notile = cfg->road_no_tile;
   env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
   if (cfg->lidar_rays > 0) {
     const int n = cfg->lidar_rays;
@@ -1337,6 +1339,49 @@ gd_status gd_autotune(gd_env* env) {
     env->notile = best_nt;
     d.topk = best_st;
     e = build_road(env, best_cell);
+  }
+  // adjoint kernel (differentiable envs): road tile or not, timed on one
+  // step's adjoint about the current state
+  if (e == cudaSuccess && (env->cfg.flags & GD_DIFFERENTIABLE)) {
+    float* wts = nullptr;
+    float* dact = nullptr;
+    e = dev_alloc(env, &wts, (size_t)env->F);
+    if (e == cudaSuccess) e = dev_alloc(env, &dact, 2 * A);
+    if (e == cudaSuccess) {
+      std::vector<float> ones((size_t)env->F, 1.f);
+      e = cudaMemcpyAsync(wts, ones.data(), sizeof(float) * env->F, cudaMemcpyHostToDevice, env->stream);
+    }
+    if (e == cudaSuccess) {
+      copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, d.state, d.flags, d.t, d.world_done);
+      recompute_segment(env, act, 1);
+    }
+    float abest = INFINITY;
+    int abest_nt = env->adj_notile;
+    for (int nt = 0; nt < 2 && e == cudaSuccess; ++nt) {
+      env->adj_notile = nt;
+      if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
+      float ms = INFINITY;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
+        cudaEventRecord(e0, env->stream);
+        launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, act, wts, 0, nullptr, nullptr, 1.f,
+                       dact);
+        cudaEventRecord(e1, env->stream);
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms = std::min(ms, t);
+      }
+      if (e == cudaSuccess && ms < abest) {
+        abest = ms;
+        abest_nt = nt;
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
+    dev_free(env, wts);
+    dev_free(env, dact);
+    env->adj_notile = abest_nt;
+    if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
   // fused LiDAR kernel: CTA size, on the chosen road grid
   if (e == cudaSuccess && env->lidar_n > 0) {
