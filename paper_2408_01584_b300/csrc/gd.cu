@@ -34,6 +34,7 @@ struct NvtxRange {
 constexpr int kObsWarpsDefault = 8;
 constexpr int kWorldWarps = 8;    // default CTA size of the fused kernel (warps); 4 and 16 also built
 constexpr int kAdjWarps = 8;
+constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner trial
 
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
@@ -1262,8 +1263,9 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
 }
 
 // Time the fused step + observation on the env's current state for each
-// (road cell, CTA size, top-K strategy) and keep the fastest; the state is
-// saved first and restored after every trial and at the end.
+// (road cell, CTA size, road tile, top-K strategy) and keep the fastest (best
+// of three windows of kTuneSteps consecutive steps after a warm-up window);
+// the state is saved first and restored before every window and at the end.
 gd_status gd_autotune(gd_env* env) {
   NvtxRange range_("gd_autotune");
   if (!env) return GD_ERR_INVALID_ARG;
@@ -1311,10 +1313,11 @@ gd_status gd_autotune(gd_env* env) {
       for (int st = 1; st <= 2; ++st) {
         d.topk = st;
         float ms = INFINITY;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 4; ++rep) {
           copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
           cudaEventRecord(e0, env->stream);
-          launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
+          for (int k = 0; k < kTuneSteps; ++k)
+            launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
           cudaEventRecord(e1, env->stream);
           if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
           float t = 0.f;
@@ -1402,10 +1405,11 @@ gd_status gd_autotune(gd_env* env) {
       if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
       if (env->lw_warps != wp) continue;       // this many warps do not fit with this many rays
       float ms = INFINITY;
-      for (int rep = 0; rep < 3; ++rep) {
+      for (int rep = 0; rep < 4; ++rep) {
         copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
         cudaEventRecord(e0, env->stream);
-        launch_world_lidar(env, act, nullptr, nullptr, nullptr, nullptr, ldepth, lcls, 1);
+        for (int k = 0; k < kTuneSteps; ++k)
+          launch_world_lidar(env, act, nullptr, nullptr, nullptr, nullptr, ldepth, lcls, 1);
         cudaEventRecord(e1, env->stream);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float t = 0.f;
