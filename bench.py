@@ -623,16 +623,16 @@ def run_ours(args, rank, world):
         plain_ms = _time_rollouts(plain_rollout, max(2, min(args.steps, 5)), stream, flush)
         gd.gd_sync(env_p.h)
 
-        # e2e: the public rollout call with host buffers; copies in the timed region
+        # e2e: the public rollout call on host buffers (gd_rollout_host); the
+        # copies of actions in and rewards / done out are in the timed region
         reward_h = torch.empty(T, A, dtype=torch.float32).pin_memory()
         done_h = torch.empty(T, A, dtype=torch.uint8).pin_memory()
 
         def e2e_rollout():
-            actions.copy_(actions_h, non_blocking=True)
+            # the host-buffer rollout: the copies in and out run inside its
+            # graph, overlapped with the steps
             gd.gd_reset(env_b.h, None)
-            gd.gd_rollout(env_b.h, T, actions, env_b.obs, False, reward_d, done_d)
-            reward_h.copy_(reward_d, non_blocking=True)
-            done_h.copy_(done_d, non_blocking=True)
+            gd.gd_rollout_host(env_b.h, T, actions_h, env_b.obs, reward_h, done_h)
 
         e2e_ms = _time_rollouts(e2e_rollout, max(2, min(args.steps, 5)), stream, flush)
         gd.gd_sync(env_b.h)

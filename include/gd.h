@@ -290,6 +290,21 @@ gd_status gd_episode_stats(gd_env* env, int32_t* per_world, int64_t* totals);
  * Asynchronous; errors: GD_ERR_INVALID_ARG (NULL, misaligned, steps < 0). */
 gd_status gd_invert_actions(gd_env* env, int32_t steps, const float* states, float* actions);
 
+/* gd_rollout with the per-step inputs and outputs in HOST memory (the end-
+ * to-end call): actions_host [T,A,2] are copied in and reward_host [T,A] /
+ * done_host [T,A] copied out in chunks of 8 steps on a second stream, so
+ * that the copies overlap the steps; obs is device memory [A,F],
+ * overwritten every step.  The copies and launches are one captured CUDA
+ * graph (re-used while the pointers and steps are the same).  Host buffers
+ * must be page-locked (cudaHostAlloc or registered); reward_host and
+ * done_host may be NULL.  Asynchronous on the env's stream: the host buffers
+ * must stay untouched until gd_sync.  Requires GD_BATCHED.  A device staging
+ * of 13 bytes per agent-step is allocated on the first call.
+ * Errors: GD_ERR_STATE without GD_BATCHED, GD_ERR_INVALID_ARG for NULL,
+ * misaligned or pageable buffers. */
+gd_status gd_rollout_host(gd_env* env, int32_t steps, const float* actions_host, float* obs, float* reward_host,
+                          uint8_t* done_host);
+
 /* Differentiable rollout (an extension; the paper has no gradient).  Runs
  * `steps` fused steps from the current state, like gd_rollout, and writes
  * the per-step objective terms

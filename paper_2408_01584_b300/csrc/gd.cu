@@ -111,6 +111,14 @@ struct gd_env {
   size_t lw_smem = 0;
   int lw_grid = 0;
   cudaGraphExec_t lgraph = nullptr;   // captured LiDAR rollout
+  // rollout on host buffers: device staging and its captured pipeline
+  cudaGraphExec_t hgraph = nullptr;
+  const void* hg_key[4] = {};
+  int hg_steps = -1;
+  float* hs_act = nullptr;      // [steps, A, 2]
+  float* hs_rew = nullptr;      // [steps, A]
+  uint8_t* hs_done = nullptr;   // [steps, A]
+  int hs_cap = 0;               // steps the staging holds
   const void* lg_key[8] = {};
   int lg_steps = -1;
 };
@@ -371,6 +379,10 @@ static cudaError_t build_road(gd_env* env, float cell) {
     cudaGraphExecDestroy(env->lgraph);
     env->lgraph = nullptr;
   }
+  if (env->hgraph) {
+    cudaGraphExecDestroy(env->hgraph);
+    env->hgraph = nullptr;
+  }
   return cudaStreamSynchronize(env->stream);
 }
 
@@ -409,6 +421,7 @@ gd_status gd_destroy(gd_env* env) {
   cudaStreamSynchronize(env->stream);
   if (env->graph) cudaGraphExecDestroy(env->graph);
   if (env->lgraph) cudaGraphExecDestroy(env->lgraph);
+  if (env->hgraph) cudaGraphExecDestroy(env->hgraph);
   for (void* p : env->allocs) cudaFree(p);
   if (env->h_err) cudaFreeHost(env->h_err);
   delete env;
@@ -942,6 +955,134 @@ gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* ob
   }
   cudaError_t e = cudaGraphLaunch(env->graph, env->stream);
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout: graph launch");
+  return GD_OK;
+}
+
+// ---- rollout on host buffers ----------------------------------------------------
+
+static bool page_locked(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+constexpr int kHostChunk = 8;   // steps per copy chunk of gd_rollout_host
+
+gd_status gd_rollout_host(gd_env* env, int32_t steps, const float* actions_host, float* obs, float* reward_host,
+                          uint8_t* done_host) {
+  NvtxRange range_("gd_rollout_host");
+  if (!env) return GD_ERR_INVALID_ARG;
+  if (!batched(env)) return fail(env, GD_ERR_STATE, "gd_rollout_host needs GD_BATCHED");
+  if (steps < 0) return fail(env, GD_ERR_INVALID_ARG, "steps must be >= 0");
+  if (steps == 0 || env->A == 0) return GD_OK;
+  if (!actions_host || !obs) return fail(env, GD_ERR_INVALID_ARG, "actions_host and obs must not be NULL");
+  if (!aligned16(obs)) return fail(env, GD_ERR_INVALID_ARG, "obs must be 16-byte aligned");
+  if (!page_locked(actions_host) || (reward_host && !page_locked(reward_host)) || (done_host && !page_locked(done_host)))
+    return fail(env, GD_ERR_INVALID_ARG, "host buffers must be page-locked (cudaHostAlloc / pinned)");
+  const size_t A = (size_t)env->A;
+  cudaError_t e = cudaSuccess;
+  if (env->hs_cap < steps) {
+    dev_free(env, env->hs_act);
+    dev_free(env, env->hs_rew);
+    dev_free(env, env->hs_done);
+    env->hs_act = nullptr;
+    env->hs_rew = nullptr;
+    env->hs_done = nullptr;
+    env->hs_cap = 0;
+    e = dev_alloc(env, &env->hs_act, (size_t)steps * A * 2);
+    if (e == cudaSuccess) e = dev_alloc(env, &env->hs_rew, (size_t)steps * A);
+    if (e == cudaSuccess) e = dev_alloc(env, &env->hs_done, (size_t)steps * A);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_host: staging");
+    env->hs_cap = steps;
+    if (env->hgraph) {
+      cudaGraphExecDestroy(env->hgraph);
+      env->hgraph = nullptr;
+    }
+  }
+  const void* key[4] = {actions_host, obs, reward_host, done_host};
+  bool same = env->hgraph && env->hg_steps == steps;
+  for (int k = 0; k < 4 && same; ++k) same = env->hg_key[k] == key[k];
+  if (!same) {
+    if (env->hgraph) {
+      cudaGraphExecDestroy(env->hgraph);
+      env->hgraph = nullptr;
+    }
+    // capture: compute on stream cs, copies in on stream ci (all chunks in
+    // order, none waiting for compute), copies out on stream co (chunk c
+    // after its steps): the steps of chunk c wait only for its own copy in,
+    // and its copy out overlaps the steps of chunk c + 1
+    cudaStream_t cs = nullptr, ci = nullptr, co = nullptr;
+    std::vector<cudaEvent_t> evs;
+    auto event = [&]() {
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) evs.push_back(ev);
+      return ev;
+    };
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ci, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&co, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+      cudaEvent_t fork = event();
+      cudaEventRecord(fork, cs);
+      cudaStreamWaitEvent(ci, fork, 0);
+      cudaStreamWaitEvent(co, fork, 0);
+      std::vector<cudaEvent_t> in_done;
+      for (int t0 = 0; t0 < steps; t0 += kHostChunk) {
+        const int n = std::min(kHostChunk, steps - t0);
+        cudaMemcpyAsync(env->hs_act + (size_t)t0 * A * 2, actions_host + (size_t)t0 * A * 2,
+                        sizeof(float) * 2 * A * (size_t)n, cudaMemcpyHostToDevice, ci);
+        cudaEvent_t in = event();
+        cudaEventRecord(in, ci);
+        in_done.push_back(in);
+      }
+      int c = 0;
+      for (int t0 = 0; t0 < steps; t0 += kHostChunk, ++c) {
+        const int n = std::min(kHostChunk, steps - t0);
+        cudaStreamWaitEvent(cs, in_done[(size_t)c], 0);
+        for (int t = t0; t < t0 + n; ++t)
+          launch_world(env, env->hs_act + (size_t)t * A * 2, env->hs_rew + (size_t)t * A, env->hs_done + (size_t)t * A,
+                       nullptr, obs, nullptr, nullptr, 1, cs);
+        cudaEvent_t out = event();
+        cudaEventRecord(out, cs);
+        cudaStreamWaitEvent(co, out, 0);
+        if (reward_host)
+          cudaMemcpyAsync(reward_host + (size_t)t0 * A, env->hs_rew + (size_t)t0 * A, sizeof(float) * A * (size_t)n,
+                          cudaMemcpyDeviceToHost, co);
+        if (done_host)
+          cudaMemcpyAsync(done_host + (size_t)t0 * A, env->hs_done + (size_t)t0 * A, A * (size_t)n,
+                          cudaMemcpyDeviceToHost, co);
+      }
+      cudaEvent_t join_i = event(), join_o = event();
+      cudaEventRecord(join_i, ci);
+      cudaEventRecord(join_o, co);
+      cudaStreamWaitEvent(cs, join_i, 0);
+      cudaStreamWaitEvent(cs, join_o, 0);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    if (co) cudaStreamDestroy(co);
+    if (ci) cudaStreamDestroy(ci);
+    if (cs) cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(env, e, "gd_rollout_host: capture");
+    }
+    e = cudaGraphInstantiate(&env->hgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      env->hgraph = nullptr;
+      return cuda_fail(env, e, "gd_rollout_host: instantiate");
+    }
+    for (int k = 0; k < 4; ++k) env->hg_key[k] = key[k];
+    env->hg_steps = steps;
+  }
+  e = cudaGraphLaunch(env->hgraph, env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_host: graph launch");
   return GD_OK;
 }
 

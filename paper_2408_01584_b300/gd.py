@@ -33,7 +33,7 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
-           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats")
+           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats", "gd_rollout_host")
 
 GD_STATS = 5   # in the scene, controlled in the scene, goal, collided, off-road
 
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_invert_actions.argtypes = [vp, i32, vp, vp]
     lib.gd_decimate.argtypes = [i32, i32, vp, vp, vp, f32, vp, vp]
     lib.gd_episode_stats.argtypes = [vp, vp, vp]
+    lib.gd_rollout_host.argtypes = [vp, i32, vp, vp, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -237,6 +238,24 @@ def gd_invert_actions(env, steps, states, actions):
     """Expert actions [steps, A, 2] of trajectories states [steps+1, A, 4]."""
     lib = load_library()
     _check(lib, env, lib.gd_invert_actions(env, int(steps), _ptr(states, align=16), _ptr(actions, align=8)))
+
+
+def _hptr(t):
+    """Host pointer of a page-locked CPU tensor (or None)."""
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+        raise ValueError("expected a contiguous page-locked (pinned) CPU tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def gd_rollout_host(env, steps, actions_host, obs, reward_host=None, done_host=None):
+    """gd_rollout on pinned host tensors (actions [T,A,2], reward [T,A],
+    done [T,A]); obs is a CUDA tensor [A,F].  Call gd_sync before reading
+    the outputs."""
+    lib = load_library()
+    _check(lib, env, lib.gd_rollout_host(env, int(steps), _hptr(actions_host), _ptr(obs, align=16),
+                                         _hptr(reward_host), _hptr(done_host)))
 
 
 def gd_episode_stats(env, per_world=None, totals=None):

@@ -148,3 +148,43 @@ def test_autotune_then_rollout_matches_plain():
     np.testing.assert_array_equal(_np(obs), plain["obs"])
     np.testing.assert_array_equal(_np(rew), plain["reward"])
     print("autotuned:", info.block_size, info.road_cell, info.topk_strategy)
+
+
+def test_rollout_host_equals_device_rollout():
+    """gd_rollout_host (pinned host actions / rewards / done, copies overlapped
+    with the steps) gives the same results as gd_rollout on device buffers."""
+    from paper_2408_01584_b300 import gd
+    sc = small_scene(seed=31)
+    ocfg = OracleConfig(k_road=64, n_partners=16, episode_len=9, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    T, A = 21, sc.num_agents                     # three copy chunks of 8, the last one partial
+    acts = scenes.make_actions(T, A, 31)
+    outs = []
+    for host in (False, True):
+        env = gd.Env(sc, **_batched(ocfg))
+        if host:
+            a_h = torch.from_numpy(acts).pin_memory()
+            r_h = torch.empty(T, A).pin_memory()
+            d_h = torch.empty(T, A, dtype=torch.uint8).pin_memory()
+            for _ in range(2):                   # the second call replays the captured graph
+                gd.gd_reset(env.h)
+                gd.gd_rollout_host(env.h, T, a_h, env.obs, r_h, d_h)
+            env.sync()
+            r, d = r_h.clone(), d_h.clone()
+            with pytest.raises(ValueError):                                    # the binding refuses pageable memory
+                gd.gd_rollout_host(env.h, T, torch.from_numpy(acts), env.obs)
+            import ctypes
+            st = gd.load_library().gd_rollout_host(env.h, T, ctypes.c_void_p(acts.ctypes.data),
+                                                   ctypes.c_void_p(env.obs.data_ptr()), None, None)
+            assert st == 1 and "page-locked" in gd.gd_last_error(env.h)     # and so does the C ABI
+        else:
+            r = torch.empty(T, A, device="cuda")
+            d = torch.empty(T, A, dtype=torch.uint8, device="cuda")
+            gd.gd_rollout(env.h, T, torch.from_numpy(acts).cuda(), env.obs, False, r, d)
+            env.sync()
+            r, d = r.cpu(), d.cpu()
+        s, f, t = env.get_state()
+        outs.append((r, d, env.obs.cpu(), s.cpu(), f.cpu(), t.cpu()))
+        env.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
