@@ -348,8 +348,8 @@ gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_sta
 gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t);
 gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, const int32_t* t);
 
-/* Autotuner of the fused (batched) kernel: times one step + observation
- * from the current state for every road grid cell in {6, 8, 12} m, CTA size
+/* Autotuner of the fused (batched) kernel: times the step + observation for
+ * every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads, with and without the shared-memory road tile,
  * and top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
  * points are in range}, and keeps the fastest; with GD_DIFFERENTIABLE it
@@ -359,6 +359,10 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * without the shared-memory road tile, and the split form (step, then a
  * scan over all agents), and keeps the fastest (a scratch of
  * A * lidar_rays * 5 bytes is held during the call).  Every combination gives the same results.
+ * Each combination is timed over windows of 4 steps at three points of an
+ * episode: the current state and the states 1 and 2 strides of zero-action
+ * steps later (stride: episode_len / 3, at most 32 steps).  A scratch of
+ * 3 * (33 A + 5 W) + 8 A bytes is held during the call.
  * Synchronises the env's stream; the simulation state is unchanged
  * afterwards.  A captured gd_rollout graph is dropped and re-captured on the
  * next call. */

@@ -34,7 +34,8 @@ struct NvtxRange {
 constexpr int kObsWarpsDefault = 8;
 constexpr int kWorldWarps = 8;    // default CTA size of the fused kernel (warps); 4 and 16 also built
 constexpr int kAdjWarps = 8;
-constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner trial
+constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window
+constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
 
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
@@ -612,6 +613,13 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   GD_TRY(dev_alloc(env, &d.coll, (size_t)A));
   GD_TRY(dev_alloc(env, &d.off, (size_t)A));
   GD_TRY(dev_alloc(env, &d.err, 1));
+  {
+    // selection anchors: no earlier selection, so the first one covers the whole radius
+    std::vector<float4> anc((size_t)std::max(A, 1), make_float4(0.f, 0.f, INFINITY, 0.f));
+    float4* p_anc;
+    GD_TRY(upload(env, &p_anc, anc.data(), (size_t)A));
+    d.anchor = p_anc;
+  }
   GD_TRY(cudaMemsetAsync(d.err, 0, sizeof(unsigned), env->stream));
   GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
@@ -1403,24 +1411,32 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
   return launch_check(env, "gd_set_state");
 }
 
-// Time the fused step + observation on the env's current state for each
-// (road cell, CTA size, road tile, top-K strategy) and keep the fastest (best
-// of three windows of kTuneSteps consecutive steps after a warm-up window);
-// the state is saved first and restored before every window and at the end.
+// Time the fused step + observation for each (road cell, CTA size, road
+// tile, top-K strategy) and keep the fastest.  A step's cost changes over an
+// episode (agents leave, the road selections move with their anchors), so a
+// trial is timed at kTunePhases points of an episode: the env's current
+// state and the states kTunePhases - 1 strides of zero-action steps later
+// (stride: a third of the episode, at most 32 steps).  Each phase is saved
+// once, with its selection anchors, and restored exactly before each of its
+// windows of kTuneSteps steps; a trial's time is the sum over the phases,
+// best of three after a warm-up.  The current state is restored at the end.
 gd_status gd_autotune(gd_env* env) {
   NvtxRange range_("gd_autotune");
   if (!env) return GD_ERR_INVALID_ARG;
   if (env->A == 0) return GD_OK;
   const size_t A = (size_t)env->A, W = (size_t)env->W;
+  const int P = kTunePhases;
   float4* sS = nullptr;
   uint8_t* sF = nullptr;
   int* sT = nullptr;
   uint8_t* sWD = nullptr;
+  float4* sAn = nullptr;
   float* act = nullptr;
-  cudaError_t e = dev_alloc(env, &sS, A);
-  if (e == cudaSuccess) e = dev_alloc(env, &sF, A);
-  if (e == cudaSuccess) e = dev_alloc(env, &sT, W);
-  if (e == cudaSuccess) e = dev_alloc(env, &sWD, W);
+  cudaError_t e = dev_alloc(env, &sS, P * A);
+  if (e == cudaSuccess) e = dev_alloc(env, &sF, P * A);
+  if (e == cudaSuccess) e = dev_alloc(env, &sT, P * W);
+  if (e == cudaSuccess) e = dev_alloc(env, &sWD, P * W);
+  if (e == cudaSuccess) e = dev_alloc(env, &sAn, P * A);
   if (e == cudaSuccess) e = dev_alloc(env, &act, 2 * A);
   if (e == cudaSuccess && !env->obs_scratch) e = dev_alloc(env, &env->obs_scratch, A * (size_t)env->F);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1429,15 +1445,51 @@ gd_status gd_autotune(gd_env* env) {
   auto cleanup = [&]() {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    dev_free(env, sS); dev_free(env, sF); dev_free(env, sT); dev_free(env, sWD); dev_free(env, act);
+    dev_free(env, sS); dev_free(env, sF); dev_free(env, sT); dev_free(env, sWD); dev_free(env, sAn);
+    dev_free(env, act);
   };
   if (e != cudaSuccess) {
     cleanup();
     return cuda_fail(env, e, "gd_autotune: scratch");
   }
   DevEnv& d = env->d;
-  copy_snapshot(env, sS, sF, sT, sWD, d.state, d.flags, d.t, d.world_done);
+  auto save = [&](int p) {
+    copy_snapshot(env, sS + p * A, sF + p * A, sT + p * W, sWD + p * W, d.state, d.flags, d.t, d.world_done);
+    cudaMemcpyAsync(sAn + p * A, d.anchor, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  };
+  auto restore = [&](int p) {
+    copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS + p * A, sF + p * A, sT + p * W, sWD + p * W);
+    cudaMemcpyAsync(d.anchor, sAn + p * A, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  };
   cudaMemsetAsync(act, 0, sizeof(float) * 2 * A, env->stream);
+  const int stride = std::min(32, std::max(1, env->cfg.episode_len / P));
+  save(0);
+  for (int p = 1; p < P; ++p) {
+    for (int k = 0; k < stride; ++k)
+      launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
+    save(p);
+  }
+  // time `launch` (kTuneSteps steps) at every phase: best of three sums
+  // after a warm-up
+  auto time_phases = [&](auto&& launch, float& best) -> cudaError_t {
+    best = INFINITY;
+    for (int rep = 0; rep < 4; ++rep) {
+      float sum = 0.f;
+      for (int p = 0; p < P; ++p) {
+        restore(p);
+        cudaEventRecord(e0, env->stream);
+        for (int k = 0; k < kTuneSteps; ++k) launch();
+        cudaEventRecord(e1, env->stream);
+        cudaError_t err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) return err;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        sum += t;
+      }
+      if (rep > 0) best = std::min(best, sum);
+    }
+    return cudaSuccess;
+  };
   const float min_cell = (2.f * env->cfg.obs_radius + 0.01f) / (float)(MAX_ROWS - 2);
   const float cells[] = {6.f, 8.f, 12.f};
   const int warps[] = {4, 8, 16};
@@ -1454,17 +1506,8 @@ gd_status gd_autotune(gd_env* env) {
       for (int st = 1; st <= 2; ++st) {
         d.topk = st;
         float ms = INFINITY;
-        for (int rep = 0; rep < 4; ++rep) {
-          copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
-          cudaEventRecord(e0, env->stream);
-          for (int k = 0; k < kTuneSteps; ++k)
-            launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
-          cudaEventRecord(e1, env->stream);
-          if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-          float t = 0.f;
-          cudaEventElapsedTime(&t, e0, e1);
-          if (rep > 0) ms = std::min(ms, t);
-        }
+        e = time_phases([&] { launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1); },
+                        ms);
         if (e != cudaSuccess) break;
         if (ms < best_ms) {
           best_ms = ms;
@@ -1496,6 +1539,7 @@ gd_status gd_autotune(gd_env* env) {
       e = cudaMemcpyAsync(wts, ones.data(), sizeof(float) * env->F, cudaMemcpyHostToDevice, env->stream);
     }
     if (e == cudaSuccess) {
+      restore(0);
       copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, d.state, d.flags, d.t, d.world_done);
       recompute_segment(env, act, 1);
     }
@@ -1546,17 +1590,7 @@ gd_status gd_autotune(gd_env* env) {
       if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
       if (env->lw_warps != wp) continue;       // this many warps do not fit with this many rays
       float ms = INFINITY;
-      for (int rep = 0; rep < 4; ++rep) {
-        copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
-        cudaEventRecord(e0, env->stream);
-        for (int k = 0; k < kTuneSteps; ++k)
-          launch_world_lidar(env, act, nullptr, nullptr, nullptr, nullptr, ldepth, lcls, 1);
-        cudaEventRecord(e1, env->stream);
-        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) ms = std::min(ms, t);
-      }
+      e = time_phases([&] { launch_world_lidar(env, act, nullptr, nullptr, nullptr, nullptr, ldepth, lcls, 1); }, ms);
       if (e == cudaSuccess && ms < lbest) {
         lbest = ms;
         lbest_w = wp;
@@ -1572,7 +1606,7 @@ gd_status gd_autotune(gd_env* env) {
     env->lw_split = lbest_sp;
     if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
-  copy_snapshot(env, d.state, d.flags, d.t, d.world_done, sS, sF, sT, sWD);
+  restore(0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_autotune");

@@ -13,6 +13,9 @@
 //                  block's offset in 16-byte units, rgrid[w].block_bytes its size
 //   esegs[]        float4 (x0, y0, x1, y1) road-edge segments listed under every
 //                  edge-grid cell their bounding box touches
+//   anchor[A]      float4 (x, y, r_K, 0): where each agent last selected its road
+//                  points and the distance of the K-th (+inf if fewer than K were
+//                  in range); it bounds the next selection's disk
 //   lsegs[]        float4 (x0, y0, x1, y1) road-edge segments of each world, each
 //                  listed once, under the road-grid cell of its first point, in
 //                  cell order; lcell[rgrid[w].cell_base + c] = first segment of
@@ -74,6 +77,7 @@ struct DevEnv {
   const GridDesc* egrid;
   const int* ecell_start;
   const float4* esegs;
+  float4* anchor;        // [A] (x, y, r_K, 0) of each agent's last road selection, or nullptr
   const float4* lsegs;   // road-edge segments by road-grid cell of the first point (LiDAR)
   const int* lcell;      // their cell starts
   // scratch of the per-stage form

@@ -438,7 +438,8 @@ __device__ __forceinline__ void write_partners(const WorldView& v, int P, int n_
 template <bool LOSS>
 __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
-                                               ObsWarpSmem& sm, int lane, const float* __restrict__ w = nullptr) {
+                                               ObsWarpSmem& sm, int lane, float4* anchor,
+                                               const float* __restrict__ w = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
@@ -478,7 +479,28 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     }
     const int np = select_partners(v, li, e.P, e.R2, st.x, st.y, sm, lane);
     write_partners<LOSS>(v, e.P, np, st.x, st.y, c, s, sm, lane, row + 2, pidx, LOSS ? w + 8 : nullptr, acc);
-    const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+    // The road does not move, so the disk that held the K nearest points at
+    // the last selection, grown by the distance moved since, holds at least
+    // K points: the selection over it equals the one over the whole radius.
+    float Rs = e.R, Rs2 = e.R2;
+    if (anchor) {
+      const float4 an = *anchor;
+      const float r = an.z + sqrtf(dist2(st.x - an.x, st.y - an.y)) + 1e-3f;
+      if (r < e.R) {
+        Rs = r;
+        Rs2 = r * r;
+      }
+    }
+    int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
+    if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+    if (anchor && lane == 0) {
+      float rk = __int_as_float(0x7f800000);     // +inf: fewer than K in range
+      if (nroad == e.K && e.K > 0) {
+        const float2 q = v.xy[sm.sel[e.K - 1]];
+        rk = sqrtf(dist2(q.x - st.x, q.y - st.y));
+      }
+      *anchor = make_float4(st.x, st.y, rk, 0.f);
+    }
     write_road<LOSS>(v, e.K, nroad, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx,
                      LOSS ? w + 8 + 8 * e.P : nullptr, acc);
   }
@@ -551,7 +573,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
   observe_agent<false>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
-                partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane);
+                partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane, e.anchor ? e.anchor + i : nullptr);
 }
 
 }  // namespace gd

@@ -348,8 +348,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
         int32_t* ridx = a.road_idx ? a.road_idx + (size_t)i * e.K : nullptr;
         int32_t* pidx = a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr;
         if (a.ell) {
-          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, a.obs_w)
-                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, a.obs_w);
+          float4* anc = e.anchor ? e.anchor + i : nullptr;
+          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, anc, a.obs_w)
+                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, anc, a.obs_w);
           if (lane == 0) {
             float rs = 0.f;
             if (a.do_step && ag.act0[li] && !(ag.fl[li] & GD_FLAG_STATIC)) {
@@ -360,9 +361,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) 
             a.ell[i] = fmaf(a.reward_w, rs, dot);
           }
         } else if (use_tile) {
-          observe_agent<false>(e, vt, li, orow, ridx, pidx, osm, lane);
+          observe_agent<false>(e, vt, li, orow, ridx, pidx, osm, lane, e.anchor ? e.anchor + i : nullptr);
         } else {
-          observe_agent<false>(e, vg, li, orow, ridx, pidx, osm, lane);
+          observe_agent<false>(e, vg, li, orow, ridx, pidx, osm, lane, e.anchor ? e.anchor + i : nullptr);
         }
         int nx = 0;
         if (lane == 0) nx = atomicAdd(&s_next, 1);

@@ -211,3 +211,25 @@ def test_lidar_full_size_workload_sampled(fov, head):
           f"fragile {fragile}")
     assert seen[2] > 0
     env.close()
+
+
+def test_lidar_sees_parked_agents_under_nontrivial_init():
+    """Mixed-type scene, half the agents parked and not controlled
+    (GD_NONTRIVIAL_INIT): parked boxes block rays like any agent."""
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("nontrivial_1024x64", 4, worlds=10)
+    env = _env(sc, "fused", 1000, 2 * math.pi, flags=FLAGS_TERM | gd.GD_NONTRIVIAL_INIT)
+    orc = Oracle(sc, OracleConfig(term_collision=True, term_offroad=True, nontrivial_init=True))
+    acts = scenes.make_actions(3, sc.num_agents, 4)
+    hits_on_parked = 0
+    for t in range(3):
+        env.step(torch.from_numpy(acts[t]).cuda())
+        depth, cls = env.lidar()
+        s, f, tt = env.get_state()
+        env.sync()
+        orc.set_state(s.cpu().numpy(), f.cpu().numpy(), tt.cpu().numpy())
+        ref = orc.lidar(1000)
+        compare(depth.cpu().numpy(), cls.cpu().numpy(), ref, f"nontrivial step {t}")
+        hits_on_parked += int((cls.cpu().numpy() == 1).sum())
+    assert ((f.cpu().numpy() & 16) != 0).any() and hits_on_parked > 0
+    env.close()
