@@ -203,10 +203,13 @@ static cudaError_t shape_world(gd_env* env, size_t max_block, int smem_sm, int s
   const long cap = ((long)max_block <= two) ? (long)max_block : one;
   env->tile_cap = env->notile ? 16 : (int)std::max(16L, cap);
   env->world_smem = (size_t)fixed + (size_t)env->tile_cap;
-  cudaError_t e = cudaFuncSetAttribute(k_world<WARPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem);
+  // without the tile: the register-capped instantiation (more CTAs per SM)
+  const void* fn = env->notile ? reinterpret_cast<const void*>(k_world<WARPS, false, true>)
+                               : reinterpret_cast<const void*>(k_world<WARPS>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<WARPS>, WARPS * 32, env->world_smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, WARPS * 32, env->world_smem);
   if (e != cudaSuccess) return e;
   env->world_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
   return cudaSuccess;
@@ -798,10 +801,20 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
-  switch (env->warps) {
-    case 4: k_world<4><<<env->world_grid, 4 * 32, env->world_smem, stream>>>(*dv, a); break;
-    case 16: k_world<16><<<env->world_grid, 16 * 32, env->world_smem, stream>>>(*dv, a); break;
-    default: k_world<8><<<env->world_grid, 8 * 32, env->world_smem, stream>>>(*dv, a); break;
+  const dim3 grid(env->world_grid);
+  const size_t smem = env->world_smem;
+  if (env->notile) {
+    switch (env->warps) {
+      case 4: k_world<4, false, true><<<grid, 4 * 32, smem, stream>>>(*dv, a); break;
+      case 16: k_world<16, false, true><<<grid, 16 * 32, smem, stream>>>(*dv, a); break;
+      default: k_world<8, false, true><<<grid, 8 * 32, smem, stream>>>(*dv, a); break;
+    }
+  } else {
+    switch (env->warps) {
+      case 4: k_world<4><<<grid, 4 * 32, smem, stream>>>(*dv, a); break;
+      case 16: k_world<16><<<grid, 16 * 32, smem, stream>>>(*dv, a); break;
+      default: k_world<8><<<grid, 8 * 32, smem, stream>>>(*dv, a); break;
+    }
   }
 }
 

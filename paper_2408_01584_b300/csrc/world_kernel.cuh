@@ -105,8 +105,13 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // Dynamic shared memory: [mbarrier, 128 B][road tile, tile_bytes][FusedAgents]
 // then per warp an ObsWarpSmem (radial observation) or LidarWarpHead + one
 // key per ray followed by the CTA's copy of the ray directions (LIDAR).
-template <int WARPS, bool LIDAR = false>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_world(DevEnv e, FusedArgs a) {
+// LEAN: the instantiation for the form without the road tile.  Its shared
+// memory leaves room for 32 warps per SM, and the kernel is bound by
+// shared-memory latency, so registers are capped at 64 per thread (no
+// spills) to let all 32 be resident; the tile form keeps its registers (its
+// tile holds it at 2 CTAs per SM anyway).
+template <int WARPS, bool LIDAR = false, bool LEAN = false>
+__global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(wsm);
   unsigned char* tile = wsm + 128;

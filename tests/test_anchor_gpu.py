@@ -1,0 +1,125 @@
+"""GPU parity of the anchored road selection (Sec. 3.2 "Sensor modalities":
+the K nearest road points within the observation radius), through the C ABI.
+
+Each agent keeps (x, y, r_K) of its last road selection, and the next
+selection scans the radius r_K + |dp| only, falling back to the full radius
+when that finds fewer than K points.  The cases below make the anchor as
+stale as it can get between two selections and compare each observation,
+element by element, with the oracle's brute force over the whole radius:
+* gd_set_state moves agents by 1e-4 m to 80 m (past the 50 m radius), to
+  sparse ground where fewer than K points are in range, and back;
+* gd_autotune rebuilds the road grid and reruns trials between two
+  selections: the observation after it equals the one before it.
+Both the per-stage and the fused (batched) forms are checked.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, OracleConfig
+from paper_2408_01584_b300 import scenes
+from tests import parity
+from tests._util import small_scene, tiny_scene
+from tests.test_parity_gpu import gd_kwargs, teacher_forced
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _flags(batched):
+    from paper_2408_01584_b300 import gd
+    return gd.GD_BATCHED if batched else 0
+
+
+def _compare(env, ora, s, f, t, ocfg, ex, tag):
+    ora.set_state(s, f, t)
+    gobs, gri, gpi = env.observe(with_idx=True)
+    env.sync()
+    oobs, ori, opi = ora.observe()
+    parity.check_obs(_np(gobs), _np(gri), _np(gpi), ora, oobs, ori, opi, ocfg.k_road, ocfg.n_partners,
+                     ocfg.obs_radius, ex, tag)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_selection_after_jumps(batched):
+    sc = small_scene(seed=4)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=91)
+    from paper_2408_01584_b300.gd import Env
+    env = Env(sc, **gd_kwargs(ocfg, flags=_flags(batched)))
+    ora = Oracle(sc, ocfg)
+    ex = parity.Exceptions()
+    s0, f0, t0 = [_np(x) for x in env.get_state()]
+    _compare(env, ora, s0, f0, t0, ocfg, ex, 0)        # first selection: full radius, anchors set
+    rng = np.random.default_rng(4)
+    A = sc.num_agents
+    s = s0.copy()
+    for k, scale in enumerate((1e-4, 1e-2, 3.0, 20.0, 80.0, 3.0, 1e-3)):
+        ang = rng.uniform(0, 2 * np.pi, A)
+        r = scale * rng.uniform(0.5, 1.0, A)
+        s = s.copy()
+        s[:, 0] += (r * np.cos(ang)).astype(np.float32)
+        s[:, 1] += (r * np.sin(ang)).astype(np.float32)
+        s[:, 2] = rng.uniform(-np.pi, np.pi, A).astype(np.float32)
+        env.set_state(torch.from_numpy(s).cuda(), torch.from_numpy(f0).cuda(), torch.from_numpy(t0).cuda())
+        _compare(env, ora, s, f0, t0, ocfg, ex, k + 1)
+    # jump back to the start: the anchors are now 80+ m away
+    env.set_state(torch.from_numpy(s0).cuda(), torch.from_numpy(f0).cuda(), torch.from_numpy(t0).cuda())
+    _compare(env, ora, s0, f0, t0, ocfg, ex, 99)
+    print("exceptions:", ex.items)
+    env.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_fewer_than_k_after_leaving_dense_ground(batched):
+    # one world: a dense 41 x 41 point patch (1 m pitch) and an agent that
+    # jumps from its middle to 65 m away, where only the patch's edge (about
+    # 164 points) is in range, then to 45 m (about 980), 120 m (nothing in
+    # range) and back
+    pts = [(float(i), float(j), (i + j) % 2, i + 20) for i in range(-20, 21) for j in range(-20, 21)]
+    car = (0.0, 0.0, 0.0, 5.0, 4.5, 2.0, 30.0, 0.0, 0)
+    car2 = (3.0, 7.0, 0.5, 2.0, 4.5, 2.0, 30.0, 0.0, 0)
+    sc = tiny_scene([([car, car2], pts)])
+    ocfg = OracleConfig(k_road=200, n_partners=3, episode_len=91)
+    from paper_2408_01584_b300.gd import Env
+    env = Env(sc, **gd_kwargs(ocfg, flags=_flags(batched)))
+    ora = Oracle(sc, ocfg)
+    ex = parity.Exceptions()
+    s, f, t = [_np(x) for x in env.get_state()]
+    _compare(env, ora, s, f, t, ocfg, ex, 0)
+    for k, (x, y) in enumerate(((65.0, 0.0), (45.0, 0.0), (67.0, 3.0), (120.0, -40.0), (0.5, 0.5), (0.5, 0.6))):
+        s = s.copy()
+        s[0, 0], s[0, 1] = x, y
+        env.set_state(torch.from_numpy(s).cuda(), torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda())
+        _compare(env, ora, s, f, t, ocfg, ex, k + 1)
+        n_in = np.sum(np.hypot(np.array([p[0] for p in pts]) - x, np.array([p[1] for p in pts]) - y) <= 50.0)
+        if k == 0:
+            assert 0 < n_in < 200          # the fallback case: fewer than K in range
+        if k == 1:
+            assert n_in > 200
+    env.close()
+
+
+def test_autotune_between_selections_keeps_the_observation():
+    from paper_2408_01584_b300 import gd
+    sc = small_scene(seed=5)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=91)
+    env = gd.Env(sc, **gd_kwargs(ocfg, flags=gd.GD_BATCHED))
+    acts = scenes.make_actions(20, sc.num_agents, 5)
+    for t in range(6):
+        env.step(torch.from_numpy(np.ascontiguousarray(acts[t])).cuda())
+    before = [x.clone() for x in env.observe(with_idx=True)]
+    state_before = [x.clone() for x in env.get_state()]
+    gd.gd_autotune(env.h)
+    after = env.observe(with_idx=True)
+    env.sync()
+    for a, b in zip(before, after):
+        assert torch.equal(a, b)
+    for a, b in zip(state_before, env.get_state()):
+        assert torch.equal(a, b)
+    # and the tuned kernel keeps matching the oracle on the following steps
+    _, ex = teacher_forced(sc, ocfg, 8, acts[6:], env=env)
+    print("exceptions:", ex.items)
+    env.close()
