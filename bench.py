@@ -43,10 +43,11 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _measured_traffic(workload):
-    """DRAM bytes per k_world launch from the committed ncu capture of this
-    workload, or None when the kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", f"k_world_{workload}.traffic.json")
+def _measured_traffic(workload, kernel="k_world"):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture of
+    this workload, or None when the kernel sources changed since the
+    capture."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -160,6 +161,33 @@ def workload_cfg(name):
     fl = (gd.GD_TERM_COLLISION if wl["term_collision"] else 0) | (gd.GD_TERM_OFFROAD if wl["term_offroad"] else 0) \
         | (gd.GD_AUTO_RESET if wl["auto_reset"] else 0) | (gd.GD_NONTRIVIAL_INIT if wl.get("nontrivial_init") else 0)
     return dict(k_road=wl["k_road"], n_partners=wl["n_partners"], episode_len=wl["steps"], flags=fl)
+
+
+# Observation launch of the split form, per agent besides the row (4F) and
+# the road: the agent's state (16 B), extents and goal (16 B) and flags (1 B).
+OBS_AGENT_BYTES = 33.0
+
+
+def per_kernel_launch_us(env, actions, T, stream, flush):
+    """Average duration of the step launch and of the observation launch of
+    the split form, from CUDA events around each launch of one episode issued
+    call by call (gd_step, then gd_observe) after an L2 flush."""
+    import torch
+    from paper_2408_01584_b300 import gd
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(T)]
+    gd.gd_reset(env.h, None)
+    flush.zero_()
+    for t in range(T):
+        ev[t][0].record(stream)
+        gd.gd_step(env.h, actions[t], env.reward, env.done, env.world_done)
+        ev[t][1].record(stream)
+        gd.gd_observe(env.h, env.obs)
+        ev[t][2].record(stream)
+    stream.synchronize()
+    gd.gd_sync(env.h)
+    step = statistics.mean(e[0].elapsed_time(e[1]) for e in ev) * 1e3
+    obs = statistics.mean(e[1].elapsed_time(e[2]) for e in ev) * 1e3
+    return {"step": step, "observe": obs}
 
 
 def algorithmic_bytes_per_agent_step(scene, F):
@@ -300,7 +328,7 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
            "controlled_agent_steps_per_s": ctl * steps / (sum(ms) / 1e3),
            "uncontrolled_agents": int(static.sum()),
            "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile}}
+                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile, "obs_split": info.obs_split}}
     env.close()
     return out
 
@@ -344,7 +372,7 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
            "ms_per_episode": statistics.mean(ms), "forward_only_ms_per_episode": statistics.mean(ms_f),
            "ckpt_every": 10,
            "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile}}
+                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile, "obs_split": info.obs_split}}
     env.close()
     return out
 
@@ -525,11 +553,13 @@ def bench_decimation(workload, steps, warmup, dev, stream, flush, seed=0):
 
 
 def run_profile(args):
-    """Batched rollouts only (default kernel shape, no tuner, no other legs),
-    so that a profiler sees warm-up + timed k_world launches and nothing else.
-    --lidar N: the LiDAR rollout (N rays over --fov degrees, split form:
-    k_world step + k_lidar scan per simulator step) instead of the radial
-    one; --worlds W: the first W worlds of the workload only."""
+    """Batched rollouts only (no tuner, no other legs), so that a profiler
+    sees warm-up + timed k_world launches and nothing else.  --shape
+    B,C,T: CTA size B, road cell C m, road tile T (0/1) instead of the
+    library's default shape; --lidar N: the LiDAR rollout (N rays over --fov
+    degrees, split form: k_world step + k_lidar scan per simulator step)
+    instead of the radial one; --worlds W: the first W worlds of the
+    workload only."""
     import math
     import torch
     from paper_2408_01584_b300 import gd, scenes
@@ -544,8 +574,12 @@ def run_profile(args):
     cfg = workload_cfg(args.workload)
     stream = torch.cuda.Stream(dev)
     lidar = dict(lidar_rays=args.lidar, lidar_fov=math.radians(args.fov), lidar_split=1) if args.lidar else {}
+    shape = {}
+    if args.shape:
+        b, c, t = args.shape.split(",")
+        shape = dict(block_size=int(b), road_cell=float(c), road_no_tile=0 if int(t) else 1)
     with torch.cuda.stream(stream):
-        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED), **lidar)
+        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED), **lidar, **shape)
         actions = torch.from_numpy(scenes.make_actions(T, env.A, 0)).to(dev)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -560,7 +594,7 @@ def run_profile(args):
             run()
         ms = _time_rollouts(run, args.steps, stream, flush)
         gd.gd_sync(env.h)
-    return {"profile": args.workload, "worlds": sc.num_worlds, "lidar_rays": args.lidar,
+    return {"profile": args.workload, "shape": args.shape or "default", "worlds": sc.num_worlds, "lidar_rays": args.lidar,
             "ms_per_episode": statistics.mean(ms), "launches_per_episode": T * (2 if args.lidar else 1)}
 
 
@@ -590,7 +624,7 @@ def run_ours(args, rank, world):
     n_plain_launch = 6 + (1 if cfg["flags"] & gd.GD_AUTO_RESET else 0) + 1
 
     def batched_rollout():
-        # reset + one CUDA graph of T fused launches (step + observation of every world)
+        # reset + one CUDA graph of T simulator steps (fused: one launch per step; split: two)
         gd.gd_reset(env_b.h, None)
         gd.gd_rollout(env_b.h, T, actions, env_b.obs, False, reward_d, done_d)
 
@@ -606,7 +640,7 @@ def run_ours(args, rank, world):
         info = gd.gd_get_info(env_b.h)
         tuned = {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
                  "topk_strategy": {1: "bucket rank", 2: "bitonic sort"}[info.topk_strategy],
-                 "road_tile": info.road_tile}
+                 "road_tile": info.road_tile, "obs_split": info.obs_split}
         for _ in range(args.warmup):
             batched_rollout()
             plain_rollout()
@@ -636,17 +670,33 @@ def run_ours(args, rank, world):
 
         e2e_ms = _time_rollouts(e2e_rollout, max(2, min(args.steps, 5)), stream, flush)
         gd.gd_sync(env_b.h)
+        kernel_us = per_kernel_launch_us(env_b, actions, T, stream, flush) if info.obs_split else None
     agent_steps = T * A * world
     value = agent_steps * args.steps / (total_ms / 1e3)
     bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F)
-    launch_s = statistics.mean(ms) / T / 1e3          # one fused launch = one simulator step of every world
     hbm, peak_kind = _peaks()
-    achieved = (bytes_obs + bytes_road) * A / launch_s / 1e9
+    if kernel_us:
+        # split form: the observation launch dominates (row write, agent state, road once per world)
+        kernel = "k_observe_split (radial observation of every agent)"
+        launch_s = kernel_us["observe"] / 1e6
+        roof_bytes = 4.0 * F + OBS_AGENT_BYTES + bytes_road
+        launches = 2 * args.steps * T
+        step_kernel = {"kernel": "k_world (step only)", "avg_launch_us": kernel_us["step"]}
+    else:
+        kernel = "k_world (fused step + observation)"
+        launch_s = statistics.mean(ms) / T / 1e3      # one fused launch = one simulator step of every world
+        roof_bytes = bytes_obs + bytes_road
+        launches = args.steps * T
+        step_kernel = None
+    achieved = roof_bytes * A / launch_s / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "form": "batched (persistent fused kernel, 91-step CUDA graph)",
+        "config": {"workload": args.workload,
+                   "form": ("batched, split: per step a persistent step kernel over worlds and a persistent "
+                            "observation kernel over agents; 91-step CUDA graph") if kernel_us else
+                           "batched (persistent fused kernel, 91-step CUDA graph)",
                    "autotuned": tuned,
                    "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
                    "n_partners": cfg["n_partners"], "episode_steps": T, "feat": F,
@@ -656,12 +706,16 @@ def run_ours(args, rank, world):
                    "parallelism": f"independent worlds, {world} GPU(s), no collective"},
         "e2e": {"value": agent_steps / world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": METRIC,
                 "h2d_bytes_per_step": int(T * A * 8), "d2h_bytes_per_step": int(T * A * 5)},
-        "gpu_launches": int(args.steps * T),
-        "roofline": {"bound": "hbm", "kernel": "k_world (fused step + observation)", "achieved": achieved,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": _measured_traffic(args.workload),
-                     "algorithmic_bytes_per_agent_step": bytes_obs + bytes_road,
-                     "avg_launch_us": launch_s * 1e6, "launches_timed": args.steps * T},
+                     "traffic": _measured_traffic(args.workload, "k_observe_split" if kernel_us else "k_world"),
+                     "algorithmic_bytes_per_agent_step": roof_bytes,
+                     "avg_launch_us": launch_s * 1e6,
+                     "timing": ("CUDA events around each launch of one extra episode issued call by call "
+                                "(gd_step, then gd_observe)") if kernel_us else
+                               "episode time of the timed graph replays / 91",
+                     **({"step_kernel": step_kernel} if step_kernel else {})},
         "active_agent_steps_per_s": active_agent_steps(done_d.cpu().numpy(), sc.agent_off) * args.steps
         / (total_ms / 1e3),
         "plain": {"value": T * A * len(plain_ms) / (sum(plain_ms) / 1e3), "unit": METRIC,
@@ -696,6 +750,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="batched rollouts of the workload only, default tuning (for ncu captures)")
+    ap.add_argument("--shape", default="", help="with --profile: k_world shape 'block,cell_m,tile', e.g. 256,12,0")
     ap.add_argument("--lidar", type=int, default=0, help="with --profile: LiDAR rollout with this many rays")
     ap.add_argument("--fov", type=float, default=360.0, help="with --profile --lidar: fan width (degrees)")
     ap.add_argument("--worlds", type=int, default=0, help="with --profile: only the first W worlds")

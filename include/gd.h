@@ -144,6 +144,11 @@ typedef struct gd_config {
   int32_t road_no_tile;      /* 1: the fused and adjoint kernels read each world's road block from
                                 global memory instead of copying it into shared memory (more CTAs per
                                 SM); default 0 */
+  int32_t obs_split;         /* radial observation with GD_BATCHED: 1 (default) = the step (a
+                                persistent kernel over worlds) then the observation (a persistent
+                                kernel over agents, no per-world barriers) as two launches; 0 = both
+                                in one fused launch.  gd_rollout_objective always uses the fused
+                                launch.  Both give identical results. */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -174,6 +179,7 @@ typedef struct gd_info {
   int32_t lidar_split;                              /* 1: step and LiDAR scan are two launches */
   int32_t road_tile;                                /* 1: the fused kernel copies each world's road into
                                                        shared memory */
+  int32_t obs_split;                                /* 1: step and radial observation are two launches */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -351,8 +357,9 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
 /* Autotuner of the fused (batched) kernel: times the step + observation for
  * every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads, with and without the shared-memory road tile,
- * and top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
- * points are in range}, and keeps the fastest; with GD_DIFFERENTIABLE it
+ * top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
+ * points are in range}, and (without GD_DIFFERENTIABLE) the split or fused
+ * observation (obs_split), and keeps the fastest; with GD_DIFFERENTIABLE it
  * also times one adjoint launch with and without the road tile
  * (reported by gd_get_info).  With LiDAR enabled it then times the fused
  * step + LiDAR scan with 128, 256 and 384 threads per block, each with and

@@ -37,6 +37,23 @@ constexpr int kAdjWarps = 8;
 constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
 
+// Split form's observation kernel: CTA size and shared memory.
+constexpr int kSplitWarps = 8;
+constexpr size_t kSplitSmem = kSplitWarps * sizeof(ObsWarpSmem);
+// Let `fn` request up to the device's opt-in maximum of dynamic shared
+// memory.  The attribute belongs to the kernel, not to an env, so every env
+// sets the same value (an env with smaller tiles cannot shrink another's
+// limit); occupancy follows the size each launch requests.
+inline cudaError_t allow_max_smem(const void* fn) {
+  int dev = 0, mx = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);   // the limit excludes static shared memory
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  return e;
+}
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
 constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(ObsWarpSmem);
@@ -67,7 +84,12 @@ struct gd_env {
   int notile = 0;              // 1: k_world reads every road block from global memory (more CTAs per SM)
   size_t world_smem = 0;       // dynamic shared memory of k_world
   int world_grid = 0;          // persistent CTAs
+  size_t step_smem = 0;        // k_world launched without observation: no per-warp observation scratch
+  int step_grid = 0;           // its persistent CTAs
   int warps = kWorldWarps;     // CTA size of k_world (4, 8 or 16 warps)
+  int split = 1;               // radial observation: 1 = k_world step, then k_observe_split over agents
+  int so_grid = 0;             // persistent CTAs of k_observe_split
+  unsigned* ocounter = nullptr;  // its agent counter
   float road_cell = 8.f;       // road grid cell (m)
   size_t max_block = 16;       // largest road block (bytes)
   // host copy of the road, to rebuild the road blocks for another cell size
@@ -203,15 +225,24 @@ static cudaError_t shape_world(gd_env* env, size_t max_block, int smem_sm, int s
   const long cap = ((long)max_block <= two) ? (long)max_block : one;
   env->tile_cap = env->notile ? 16 : (int)std::max(16L, cap);
   env->world_smem = (size_t)fixed + (size_t)env->tile_cap;
+  // a launch without observation (the split form's step, gd_step) needs no
+  // per-warp observation scratch: the register-capped instantiation with
+  // the barrier, the agents and the tile only
+  env->step_smem = (size_t)world_fixed_smem(0) + (size_t)env->tile_cap;
   // without the tile: the register-capped instantiation (more CTAs per SM)
   const void* fn = env->notile ? reinterpret_cast<const void*>(k_world<WARPS, false, true>)
                                : reinterpret_cast<const void*>(k_world<WARPS>);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->world_smem);
+  const void* lean = reinterpret_cast<const void*>(k_world<WARPS, false, true>);
+  cudaError_t e = allow_max_smem(fn);
+  if (e == cudaSuccess) e = allow_max_smem(lean);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, WARPS * 32, env->world_smem);
   if (e != cudaSuccess) return e;
   env->world_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lean, WARPS * 32, env->step_smem);
+  if (e != cudaSuccess) return e;
+  env->step_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
   return cudaSuccess;
 }
 
@@ -224,8 +255,7 @@ static cudaError_t shape_world_lidar(gd_env* env, size_t max_block, int smem_sm,
   // without a tile every world reads its road from global memory (L1/L2)
   env->lw_tile = env->lw_notile ? 16 : (int)std::max(16L, cap);
   env->lw_smem = (size_t)fixed + (size_t)env->lw_tile;
-  cudaError_t e = cudaFuncSetAttribute(k_world<WARPS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)env->lw_smem);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(k_world<WARPS, true>));
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_world<WARPS, true>, WARPS * 32, env->lw_smem);
@@ -249,6 +279,15 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     default: env->warps = 8; e = shape_world<8>(env, max_block, smem_sm, smem_blk, nsm); break;
   }
   if (e != cudaSuccess) return e;
+  {
+    int per_sm = 0;
+    e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps>));
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observe_split<kSplitWarps>, kSplitWarps * 32,
+                                                        kSplitSmem);
+    if (e != cudaSuccess) return e;
+    env->so_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (env->A + kSplitWarps - 1) / kSplitWarps));
+  }
   if (env->lidar_n > 0) {
     // the tile shrinks first; if even a 16-byte tile does not fit, fewer warps
     while (env->lw_warps > 4 && lidar_fixed_smem(env->lw_warps, env->lidar_n) + 16 + 1024 > (size_t)smem_blk)
@@ -265,7 +304,7 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
     env->adj_tile = env->adj_notile ? 16 : (int)std::max(16L, ((long)max_block <= two) ? (long)max_block : one);
     env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
-    e = cudaFuncSetAttribute(k_adjoint<kAdjWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)env->adj_smem);
+    e = allow_max_smem(reinterpret_cast<const void*>(k_adjoint<kAdjWarps>));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<kAdjWarps>, kAdjWarps * 32, env->adj_smem);
@@ -416,6 +455,7 @@ void gd_default_config(gd_config* c) {
   c->lidar_fov = 6.28318530717958647692f;
   c->dynamics = GD_DYN_BICYCLE;
   c->nontrivial_dist = 2.f;
+  c->obs_split = 1;
 }
 
 const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
@@ -453,6 +493,7 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
   if (c->block_size != 0 && c->block_size != 128 && c->block_size != 256 && c->block_size != 512)
     return fail(nullptr, GD_ERR_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
   if (c->topk_strategy < 0 || c->topk_strategy > 2) return fail(nullptr, GD_ERR_INVALID_ARG, "topk_strategy must be 0..2");
+  if (c->obs_split != 0 && c->obs_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "obs_split must be 0 or 1");
   if (c->lidar_rays < 0 || c->lidar_rays > GD_MAX_LIDAR_RAYS)
     return fail(nullptr, GD_ERR_CAPACITY, "lidar_rays outside 0..GD_MAX_LIDAR_RAYS");
   if (!(c->lidar_fov >= 1e-3f) || !(c->lidar_fov <= 6.2831855f))
@@ -632,8 +673,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     k_mark_uncontrolled<<<blocks_for_host(A, 256), 256, 0, env->stream>>>(d, p_iflags, cfg->nontrivial_dist);
     GD_TRY(cudaGetLastError());
   }
-  GD_TRY(cudaFuncSetAttribute(k_observe<kObsWarpsDefault>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(kObsWarpsDefault * sizeof(ObsWarpSmem))));
+  GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_observe<kObsWarpsDefault>)));
   // batched form: worlds largest first (agents, then road points), a work
   // counter, and a road tile sized for two CTAs per SM when every world fits,
   // else one CTA per SM with the largest tile
@@ -647,6 +687,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     });
     GD_TRY(upload(env, &env->order, order.data(), (size_t)W));
     GD_TRY(dev_alloc(env, &env->counter, 1));
+    GD_TRY(dev_alloc(env, &env->ocounter, 1));
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
     env->C = cfg->ckpt_every;
@@ -662,6 +703,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
+  env->split = cfg->obs_split;
   env->notile = cfg->road_no_tile;
   env->adj_notile = cfg->road_no_tile;
   env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
@@ -692,15 +734,15 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     switch (wp) {
       case 12:
-        GD_TRY(cudaFuncSetAttribute(k_lidar<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<12>)));
         GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<12>, 12 * 32, ls));
         break;
       case 8:
-        GD_TRY(cudaFuncSetAttribute(k_lidar<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<8>)));
         GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<8>, 8 * 32, ls));
         break;
       default:
-        GD_TRY(cudaFuncSetAttribute(k_lidar<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ls));
+        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<4>)));
         GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<4>, 4 * 32, ls));
         break;
     }
@@ -733,6 +775,7 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->lidar_block_size = env->lw_warps * 32;
   info->lidar_road_tile = env->lw_notile ? 0 : 1;
   info->lidar_split = env->lw_split;
+  info->obs_split = env->split;
   return GD_OK;
 }
 
@@ -779,12 +822,22 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
 }
 
 // Batched form: one persistent fused launch (work counter cleared first).
+// With env->split, an observation without the objective is the step launch
+// (nothing observed) followed by k_observe_split over all agents.
 static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
+  if (obs && !ell && env->split) {
+    // split form: the step over worlds, then the observation over agents
+    if (do_step) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv);
+    cudaMemsetAsync(env->ocounter, 0, sizeof(unsigned), stream);
+    k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(*dv, obs, road_idx, partner_idx,
+                                                                                        env->ocounter);
+    return;
+  }
   FusedArgs a{};
   a.actions = reinterpret_cast<const float2*>(actions);
   a.reward = reward;
@@ -801,9 +854,10 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
-  const dim3 grid(env->world_grid);
-  const size_t smem = env->world_smem;
-  if (env->notile) {
+  const bool step_only = obs == nullptr;
+  const dim3 grid(step_only ? env->step_grid : env->world_grid);
+  const size_t smem = step_only ? env->step_smem : env->world_smem;
+  if (env->notile || step_only) {
     switch (env->warps) {
       case 4: k_world<4, false, true><<<grid, 4 * 32, smem, stream>>>(*dv, a); break;
       case 16: k_world<16, false, true><<<grid, 16 * 32, smem, stream>>>(*dv, a); break;
@@ -1507,33 +1561,43 @@ gd_status gd_autotune(gd_env* env) {
   const float cells[] = {6.f, 8.f, 12.f};
   const int warps[] = {4, 8, 16};
   float best_ms = INFINITY, best_cell = env->road_cell;
-  int best_w = env->warps, best_st = d.topk, best_nt = env->notile;
+  int best_w = env->warps, best_st = d.topk, best_nt = env->notile, best_sp = env->split;
+  // a differentiable env's objective rollouts always use the fused launch
+  const int sp_lo = (env->cfg.flags & GD_DIFFERENTIABLE) ? env->split : 0;
+  const int sp_hi = (env->cfg.flags & GD_DIFFERENTIABLE) ? env->split : 1;
+  const int keep_split = env->split;
+  if (env->cfg.flags & GD_DIFFERENTIABLE) env->split = 0;
   for (float c : cells) {
     const float cell = std::max(c, min_cell);
     if ((e = build_road(env, cell)) != cudaSuccess) break;
-    for (int shape = 0; shape < 6; ++shape) {
-      const int wp = warps[shape % 3];
-      env->warps = wp;
-      env->notile = shape / 3;
-      if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
-      for (int st = 1; st <= 2; ++st) {
-        d.topk = st;
-        float ms = INFINITY;
-        e = time_phases([&] { launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1); },
-                        ms);
-        if (e != cudaSuccess) break;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_cell = cell;
-          best_w = wp;
-          best_st = st;
-          best_nt = env->notile;
+    for (int sp = sp_lo; sp <= sp_hi && e == cudaSuccess; ++sp) {
+      if (!(env->cfg.flags & GD_DIFFERENTIABLE)) env->split = sp;
+      for (int shape = 0; shape < 6; ++shape) {
+        const int wp = warps[shape % 3];
+        env->warps = wp;
+        env->notile = shape / 3;
+        if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
+        for (int st = 1; st <= 2; ++st) {
+          d.topk = st;
+          float ms = INFINITY;
+          e = time_phases(
+              [&] { launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1); }, ms);
+          if (e != cudaSuccess) break;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_cell = cell;
+            best_w = wp;
+            best_st = st;
+            best_nt = env->notile;
+            best_sp = sp;
+          }
         }
+        if (e != cudaSuccess) break;
       }
-      if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) break;
   }
+  env->split = (env->cfg.flags & GD_DIFFERENTIABLE) ? keep_split : best_sp;
   if (e == cudaSuccess) {
     env->warps = best_w;
     env->notile = best_nt;

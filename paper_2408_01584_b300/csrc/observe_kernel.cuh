@@ -150,32 +150,30 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   const int total = road_rows(v, R, R2, ex, ey, sm, lane, nrows);
 
   // pass 1: histogram of d^2 buckets + compact list of in-radius positions.
-  // Lane l walks the contiguous chunk [l*chunk, (l+1)*chunk) of the flat
-  // candidate list, four candidates per round: the four loads are
-  // independent, and lanes sit far apart in the disk so their histogram
-  // atomics rarely hit the same bucket.
+  // The warp walks the flat candidate list 4 x 32 entries per round, lane l
+  // taking entries l, l + 32, l + 64, l + 96: each load instruction reads 32
+  // consecutive points (two 128-byte lines when the road is read through
+  // L1/L2, no bank conflict in the tile), the four loads are independent,
+  // and the compact list comes out in memory order, which keeps pass 2's
+  // loads coalesced too.  Neighbouring points along a road differ in
+  // distance by far more than a bucket's width, so the histogram atomics
+  // rarely collide.
   for (int b = lane; b < OBS_NB; b += WARP) sm.cur[b] = 0;
   __syncwarp();
   int n_in = 0;
   const unsigned lt = (1u << lane) - 1u;
   {
     constexpr int U = 4;
-    // odd chunk: lane l reads 8-byte points 8*chunk bytes after lane l-1,
-    // which puts the 16 lanes of each 64-bit shared-memory phase on 16
-    // different bank pairs
-    const int chunk = ((total + WARP - 1) / WARP) | 1;
-    const int fbeg = lane * chunk, fend = min(fbeg + chunk, total);
     int r = 0;
-    while (r + 1 < nrows && (int)sm.row_excl[r + 1] <= fbeg) ++r;
-    unsigned rs = sm.row_start[r], rx = sm.row_excl[r];
-    unsigned re = (r + 1 < nrows) ? sm.row_excl[r + 1] : 0xffffffffu;
-    for (int j = 0; j < chunk; j += U) {
+    unsigned rs = sm.row_start[0], rx = 0;
+    unsigned re = (nrows > 1) ? sm.row_excl[1] : 0xffffffffu;
+    for (int f0 = 0; f0 < total; f0 += U * WARP) {
       unsigned pu[U];
       bool vu[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int f = fbeg + j + u;
-        vu[u] = f < fend;
+        const int f = f0 + u * WARP + lane;
+        vu[u] = f < total;
         if (vu[u]) {
           while ((unsigned)f >= re) {
             ++r;
@@ -550,18 +548,11 @@ __device__ __forceinline__ bool offroad_from_block(const WorldView& v, float cx,
   return __any_sync(0xffffffffu, hit);
 }
 
-// Per-stage form: one warp per agent over the whole batch, everything read
-// from global memory.  Dynamic shared memory: WARPS * sizeof(ObsWarpSmem).
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restrict__ obs,
-                                                       int32_t* __restrict__ road_idx,
-                                                       int32_t* __restrict__ partner_idx) {
-  extern __shared__ __align__(16) unsigned char obs_smem_raw[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * WARPS + wib;
-  if (i >= e.A) return;
-  ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[wib];
+// Observation row of agent i with everything read from global memory (the
+// world's agents and road block through L1/L2).
+__device__ __forceinline__ void observe_global(const DevEnv& e, int i, float* __restrict__ obs,
+                                               int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
+                                               ObsWarpSmem& sm, int lane) {
   const int w = e.agent_world[i];
   const int a0 = e.agent_off[w];
   WorldView v;
@@ -573,7 +564,46 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
   observe_agent<false>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
-                partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane, e.anchor ? e.anchor + i : nullptr);
+                       partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
+                       e.anchor ? e.anchor + i : nullptr);
+}
+
+// Per-stage form: one warp per agent over the whole batch.  Dynamic shared
+// memory: WARPS * sizeof(ObsWarpSmem).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restrict__ obs,
+                                                       int32_t* __restrict__ road_idx,
+                                                       int32_t* __restrict__ partner_idx) {
+  extern __shared__ __align__(16) unsigned char obs_smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * WARPS + wib;
+  if (i >= e.A) return;
+  observe_global(e, i, obs, road_idx, partner_idx, reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[wib], lane);
+}
+
+// Batched split form, after the step (k_world without observation):
+// persistent warps, each claims the next agent from `counter` (cleared
+// before the launch) until all A are observed.  No per-world barrier, so a
+// warp that drew a done agent (an all-zero row) moves straight on; agents
+// are claimed in index order, which keeps a world's agents, and its road
+// block in L1/L2, together.  Registers are capped for 32 warps per SM (its
+// shared memory allows them).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv e, float* __restrict__ obs,
+                                                                           int32_t* __restrict__ road_idx,
+                                                                           int32_t* __restrict__ partner_idx,
+                                                                           unsigned* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char obs_smem_raw[];
+  const int lane = threadIdx.x & 31;
+  ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[threadIdx.x >> 5];
+  for (;;) {
+    unsigned i = 0;
+    if (lane == 0) i = atomicAdd(counter, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= (unsigned)e.A) break;
+    observe_global(e, (int)i, obs, road_idx, partner_idx, sm, lane);
+  }
 }
 
 }  // namespace gd

@@ -59,7 +59,7 @@ class gd_config(C.Structure):
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32),
-                ("nontrivial_dist", C.c_float), ("road_no_tile", C.c_int32)]
+                ("nontrivial_dist", C.c_float), ("road_no_tile", C.c_int32), ("obs_split", C.c_int32)]
 
 
 class gd_scene_batch(C.Structure):
@@ -77,7 +77,7 @@ class gd_info(C.Structure):
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_road_tile", C.c_int32), ("lidar_split", C.c_int32),
-                ("road_tile", C.c_int32)]
+                ("road_tile", C.c_int32), ("obs_split", C.c_int32)]
 
 
 _lib = None

@@ -96,6 +96,8 @@ def test_rejects_bad_arguments_before_any_launch(lib):
     _expect(INV, gd.gd_create, gd.gd_default_config(dynamics=2), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(nontrivial_dist=-1.0), sc)
     _expect(INV, gd.gd_create, gd.gd_default_config(road_no_tile=2), sc)
+    _expect(INV, gd.gd_create, gd.gd_default_config(obs_split=2), sc)
+    assert gd.gd_default_config().obs_split == 1      # split observation by default
     big = scenes.make_scene(np.array([129]), np.array([500]), 0)
     _expect(CAP, gd.gd_create, gd.gd_default_config(), big)
     bad = scenes.workload_scene("plain_4x8", 0)

@@ -1,6 +1,8 @@
-"""GPU parity of the batched form (GD_BATCHED: persistent fused per-world
-kernel with the road tile in shared memory, whole rollouts as one CUDA
-graph) against the oracle, and bitwise equality with the per-stage form.
+"""GPU parity of the batched form (GD_BATCHED: persistent per-world kernel
+with the road tile in shared memory, whole rollouts as one CUDA graph)
+against the oracle, and bitwise equality with the per-stage form, for both
+the split observation (step launch, then a persistent kernel over agents;
+the default) and the fused one (obs_split = 0).
 """
 import numpy as np
 import pytest
@@ -21,13 +23,16 @@ def _batched(ocfg, **over):
     return kw
 
 
-def test_batched_teacher_forced_ragged_with_resets():
+@pytest.mark.parametrize("split", [1, 0])
+def test_batched_teacher_forced_ragged_with_resets(split):
     sc = small_scene(seed=3)
     ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=7, term_collision=True, term_offroad=True,
                         auto_reset=True)
     acts = scenes.make_actions(20, sc.num_agents, 3)
     from paper_2408_01584_b300.gd import Env
-    env = Env(sc, **_batched(ocfg))
+    env = Env(sc, **_batched(ocfg, obs_split=split))
+    from paper_2408_01584_b300 import gd
+    assert gd.gd_get_info(env.h).obs_split == split
     _, ex = teacher_forced(sc, ocfg, 20, acts, env=env)
     print("exceptions:", ex.items)
 
@@ -76,14 +81,15 @@ def _rollout(sc, kw, acts, mode):
     return dict(obs=np.stack(obs_all), reward=np.stack(rew_all), done=np.stack(dn_all), state=_np(s), flags=_np(f))
 
 
+@pytest.mark.parametrize("split", [1, 0])
 @pytest.mark.parametrize("mode", ["stepwise", "fused", "graph"])
-def test_batched_bitwise_equals_plain(mode):
+def test_batched_bitwise_equals_plain(mode, split):
     sc = small_scene(seed=9)
     ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
                         auto_reset=True)
     acts = scenes.make_actions(12, sc.num_agents, 9)
     plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
-    bat = _rollout(sc, _batched(ocfg), acts, mode)
+    bat = _rollout(sc, _batched(ocfg, obs_split=split), acts, mode)
     for k in plain:
         np.testing.assert_array_equal(plain[k], bat[k], err_msg=k)
 
@@ -110,19 +116,44 @@ def test_graph_rollout_replay_and_full_size_agreement():
         np.testing.assert_array_equal(_np(s), plain["state"])
 
 
-@pytest.mark.parametrize("cell,block,topk,notile", [(6.0, 128, 2, 0), (8.0, 512, 1, 0), (12.0, 256, 2, 0),
-                                                    (10.0, 512, 2, 0), (8.0, 256, 1, 1), (12.0, 128, 2, 1)])
-def test_tuning_choices_do_not_change_results(cell, block, topk, notile):
-    # road grid cell, CTA size, top-K strategy and the road tile are performance choices only
+@pytest.mark.parametrize("cell,block,topk,notile,split", [(6.0, 128, 2, 0, 1), (8.0, 512, 1, 0, 0), (12.0, 256, 2, 0, 1),
+                                                          (10.0, 512, 2, 0, 0), (8.0, 256, 1, 1, 1), (12.0, 128, 2, 1, 0),
+                                                          (8.0, 128, 1, 1, 0), (6.0, 512, 2, 1, 1)])
+def test_tuning_choices_do_not_change_results(cell, block, topk, notile, split):
+    # road grid cell, CTA size, top-K strategy, the road tile and the split
+    # observation are performance choices only
     sc = small_scene(seed=12)
     ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
                         auto_reset=True)
     acts = scenes.make_actions(10, sc.num_agents, 12)
     plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
-    bat = _rollout(sc, _batched(ocfg, road_cell=cell, block_size=block, topk_strategy=topk, road_no_tile=notile),
-                   acts, "fused")
+    bat = _rollout(sc, _batched(ocfg, road_cell=cell, block_size=block, topk_strategy=topk, road_no_tile=notile,
+                                obs_split=split), acts, "fused")
     for k in plain:
         np.testing.assert_array_equal(plain[k], bat[k], err_msg=k)
+
+
+@pytest.mark.parametrize("split", [1, 0])
+def test_index_outputs_split_and_fused(split):
+    # gd_observe with road / partner index outputs, batched, equals the per-stage form
+    from paper_2408_01584_b300 import gd
+    sc = small_scene(seed=14)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = torch.from_numpy(scenes.make_actions(5, sc.num_agents, 14)).cuda().contiguous()
+    outs = []
+    for kw in (gd_kwargs(ocfg), _batched(ocfg, obs_split=split)):
+        env = gd.Env(sc, **kw)
+        res = []
+        for t in range(5):
+            env.step(acts[t])
+            res.append([_np(x).copy() for x in env.observe(with_idx=True)])
+        env.sync()
+        outs.append(res)
+        env.close()
+    for a, b in zip(*outs):
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
 
 
 def test_autotune_then_rollout_matches_plain():
@@ -139,6 +170,7 @@ def test_autotune_then_rollout_matches_plain():
         np.testing.assert_array_equal(b, a)           # the tuner leaves the state as it was
     info = gd.gd_get_info(env.h)
     assert info.block_size in (128, 256, 512) and info.topk_strategy in (1, 2) and info.road_cell >= 3.3
+    assert info.obs_split in (0, 1)
     a = torch.from_numpy(acts).cuda().contiguous()
     obs = torch.zeros(ocfg.episode_len, env.A, env.F, device="cuda")
     rew = torch.zeros(ocfg.episode_len, env.A, device="cuda")
@@ -188,3 +220,31 @@ def test_rollout_host_equals_device_rollout():
         env.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def test_envs_with_different_shared_memory_coexist():
+    # a kernel's shared-memory limit belongs to the kernel, not to an env: an
+    # env created later with fewer rays, a coarser grid and no road tile must
+    # not break the launches of an earlier env that needs more
+    from paper_2408_01584_b300 import gd
+    sc = small_scene(seed=21)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=9)
+    acts = torch.from_numpy(scenes.make_actions(2, sc.num_agents, 21)).cuda().contiguous()
+
+    def run(env):
+        env.step(acts[0])
+        depth, cls = env.lidar()
+        obs = env.observe()[0]
+        env.sync()
+        return _np(depth).copy(), _np(cls).copy(), _np(obs).copy()
+
+    ref_env = gd.Env(sc, **_batched(ocfg, lidar_rays=3000, road_cell=6.0))
+    ref = run(ref_env)
+    ref_env.close()
+    big = gd.Env(sc, **_batched(ocfg, lidar_rays=3000, road_cell=6.0))
+    small = gd.Env(sc, **_batched(ocfg, lidar_rays=64, road_cell=12.0, road_no_tile=1, lidar_no_tile=1))
+    run(small)
+    for x, y in zip(run(big), ref):
+        np.testing.assert_array_equal(x, y)
+    big.close()
+    small.close()
