@@ -110,6 +110,10 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // shared-memory latency, so registers are capped at 64 per thread (no
 // spills) to let all 32 be resident; the tile form keeps its registers (its
 // tile holds it at 2 CTAs per SM anyway).
+// Lanes per agent in the step's collision and (without the tile) road-edge
+// tests: WARP / STEP_G agents per warp at once.
+constexpr int STEP_G = 8;
+
 template <int WARPS, bool LIDAR = false, bool LEAN = false>
 __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(DevEnv e, FusedArgs a) {
   extern __shared__ __align__(16) unsigned char wsm[];
@@ -227,61 +231,99 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       if (act) ag.key[rank] = key;
       if (tid == 0) s_nact = nact;
       __syncthreads();
-      // collision and road edge: warp per agent, ballot-OR over candidates
-      for (int li = wid; li < n; li += WARPS) {
-        if (ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) continue;
-        const float4 s = ag.st[li];
-        const float4 sc = ag.sc[li];
-        const float ca = ag.cs[li].x, sa = ag.cs[li].y;
-        const int cx = (int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f);
-        const int cy = (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f);
-        // lanes 0..5 bound the three neighbouring columns in parallel:
-        // lane 2k / 2k+1 = lower / upper bound of column cx - 1 + k
-        int bound = 0;
-        if (lane < 6) {
-          const int c = cx - 1 + (lane >> 1);
-          if (c >= 0 && c <= 4095) {
-            const bool upper = lane & 1;
-            const uint32_t v = upper ? agent_cell_key(c, min(cy + 1, 4095), 255) : agent_cell_key(c, max(cy - 1, 0), 0);
-            int l = 0, h = s_nact;
-            while (l < h) {
-              const int m = (l + h) >> 1;
-              if (upper ? (ag.key[m] <= v) : (ag.key[m] < v)) l = m + 1; else h = m;
+      // collision: a group of STEP_G lanes per agent (WARP / STEP_G agents
+      // per warp at once), OR over the candidates of the group
+      {
+        const int gl = lane & (STEP_G - 1);
+        const unsigned gmask = ((1u << STEP_G) - 1u) << (lane & ~(STEP_G - 1));
+        for (int b0 = wid * (WARP / STEP_G); b0 < n; b0 += WARPS * (WARP / STEP_G)) {
+          const int li = b0 + lane / STEP_G;
+          const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC));
+          float4 s = make_float4(0.f, 0.f, 0.f, 0.f), sc = s;
+          float ca = 1.f, sa = 0.f;
+          // lanes 0..5 of the group bound the three neighbouring columns in
+          // parallel: lane 2k / 2k+1 = lower / upper bound of column cx - 1 + k
+          int bound = 0;
+          if (act) {
+            s = ag.st[li];
+            sc = ag.sc[li];
+            ca = ag.cs[li].x;
+            sa = ag.cs[li].y;
+            const int cx = (int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f);
+            const int cy = (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f);
+            if (gl < 6) {
+              const int c = cx - 1 + (gl >> 1);
+              if (c >= 0 && c <= 4095) {
+                const bool upper = gl & 1;
+                const uint32_t v =
+                    upper ? agent_cell_key(c, min(cy + 1, 4095), 255) : agent_cell_key(c, max(cy - 1, 0), 0);
+                int l = 0, h = s_nact;
+                while (l < h) {
+                  const int m = (l + h) >> 1;
+                  if (upper ? (ag.key[m] <= v) : (ag.key[m] < v)) l = m + 1; else h = m;
+                }
+                bound = l;
+              }
             }
-            bound = l;
           }
-        }
-        bool hit = false;
+          bool hit = false;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int b = __shfl_sync(0xffffffffu, bound, 2 * k), en = __shfl_sync(0xffffffffu, bound, 2 * k + 1);
-          for (int q = b + lane; q < en; q += WARP) {
-            const int j = (int)(ag.key[q] & 0xffu);
-            if (j == li) continue;
-            const float4 sj = ag.st[j];
-            const float4 tj = ag.sc[j];
-            const float cb = ag.cs[j].x, sb = ag.cs[j].y;
-            hit |= box_box_depth(sj.x - s.x, sj.y - s.y, ca, sa, 0.5f * sc.x, 0.5f * sc.y, cb, sb, 0.5f * tj.x,
-                                 0.5f * tj.y) > 0.f;
+          for (int k = 0; k < 3; ++k) {
+            const int b = __shfl_sync(gmask, bound, 2 * k, STEP_G), en = __shfl_sync(gmask, bound, 2 * k + 1, STEP_G);
+            for (int q = b + gl; q < en; q += STEP_G) {
+              const int j = (int)(ag.key[q] & 0xffu);
+              if (j == li) continue;
+              const float4 sj = ag.st[j];
+              const float4 tj = ag.sc[j];
+              const float cb = ag.cs[j].x, sb = ag.cs[j].y;
+              hit |= box_box_depth(sj.x - s.x, sj.y - s.y, ca, sa, 0.5f * sc.x, 0.5f * sc.y, cb, sb, 0.5f * tj.x,
+                                   0.5f * tj.y) > 0.f;
+            }
           }
+          hit = (__ballot_sync(0xffffffffu, hit) & gmask) != 0u;
+          if (act && gl == 0) ag.coll[li] = hit ? 1 : 0;
         }
-        hit = __any_sync(0xffffffffu, hit);
-        if (lane == 0) ag.coll[li] = hit ? 1 : 0;
       }
-      // road edges, from the world's road block (shared-memory tile): warp
-      // per agent, ballot-OR over the candidate segments
+      // road edges: from the shared-memory tile a warp per agent, ballot-OR
+      // over the candidate segments; else from the edge grid (segments under
+      // every cell their bounding box touches, so the cells under the box's
+      // own bounding box hold every segment it can cross), a group of STEP_G
+      // lanes per agent
       if (!wait_tile()) return;
-      for (int li = wid; li < n; li += WARPS) {
-        if ((ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
-          if (lane == 0) ag.offr[li] = 0;
-          continue;
+      if (use_tile) {
+        for (int li = wid; li < n; li += WARPS) {
+          if ((ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
+            if (lane == 0) ag.offr[li] = 0;
+            continue;
+          }
+          const float4 s = ag.st[li];
+          const float4 sc = ag.sc[li];
+          const bool off = offroad_from_block(vt, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane);
+          if (lane == 0) ag.offr[li] = off ? 1 : 0;
         }
-        const float4 s = ag.st[li];
-        const float4 sc = ag.sc[li];
-        const bool off = use_tile
-                             ? offroad_from_block(vt, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane)
-                             : offroad_from_block(vg, s.x, s.y, ag.cs[li].x, ag.cs[li].y, 0.5f * sc.x, 0.5f * sc.y, lane);
-        if (lane == 0) ag.offr[li] = off ? 1 : 0;
+      } else {
+        const GridDesc eg = e.egrid[w];
+        for (int b0 = wid * (WARP / STEP_G); b0 < n; b0 += WARPS * (WARP / STEP_G)) {
+          const int li = b0 + lane / STEP_G;
+          const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) && ag.ty[li] != GD_AGENT_PEDESTRIAN;
+          float4 s = make_float4(0.f, 0.f, 0.f, 0.f), sc = s;
+          float2 cs = make_float2(1.f, 0.f);
+          int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
+          if (act) {
+            s = ag.st[li];
+            sc = ag.sc[li];
+            cs = ag.cs[li];
+            const float hl = 0.5f * sc.x, hw = 0.5f * sc.y;
+            const float ex = hl * fabsf(cs.x) + hw * fabsf(cs.y) + 1e-3f, ey = hl * fabsf(cs.y) + hw * fabsf(cs.x) + 1e-3f;
+            cx0 = (int)clampf(floorf((s.x - ex - eg.ox) * eg.inv_cs), 0.f, (float)(eg.nx - 1));
+            cx1 = (int)clampf(floorf((s.x + ex - eg.ox) * eg.inv_cs), -1.f, (float)(eg.nx - 1));
+            cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
+            cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
+          }
+          const bool off = offroad_cells_grouped<STEP_G>(e.ecell_start + eg.cell_base, eg.nx, e.esegs, cx0, cx1, cy0,
+                                                         cy1, s.x, s.y, cs.x, cs.y, 0.5f * sc.x, 0.5f * sc.y, lane);
+          if (li < n && (lane & (STEP_G - 1)) == 0) ag.offr[li] = (act && off) ? 1 : 0;
+        }
       }
       __syncthreads();
       // goal, reward, flags, done
