@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_adjoint(DevEnv e, AdjArgs a) 
           const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
           const float* wroad = wrow + 8 + 8 * e.P;
           for (int r = lane; r < nroad; r += WARP) {
-            const float2 q = v.xy[sm.sel[r]];
+            const float2 q = v.xy[sel_pos(sm.sel[r])];
             const float dx = q.x - st.x, dy = q.y - st.y;
             const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
             const float wa = __ldg(wroad + 4 * r), wb = __ldg(wroad + 4 * r + 1);

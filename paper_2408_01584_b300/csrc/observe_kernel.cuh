@@ -23,10 +23,11 @@
 // overflows, pass 2 walks the rows again.  Every rank is exact: the output
 // equals a full sort.
 //
-// Key = (d^2 bits << 32) | (local index << 16) | (position in the world's
-// cell-sorted points): d^2 >= 0 so its bits order like the value, the local
-// index breaks ties, and the position (a bijection of the index) locates the
-// point without a separate array.
+// Key = (d^2 bits << 32) | (local index << 17) | (type << 16) | (position in
+// the world's cell-sorted points): d^2 >= 0 so its bits order like the
+// value, the local index breaks ties (the type bit below it never decides),
+// and the low 32 bits carry everything the row writer needs besides the
+// point's coordinates: index, type and the position that locates the point.
 #pragma once
 #include "gd_device.cuh"
 
@@ -34,20 +35,23 @@ namespace gd {
 
 constexpr int OBS_NB = 256;        // d^2 buckets
 constexpr int OBS_CAP = 288;       // keys kept per warp (>= GD_MAX_K_ROAD)
-constexpr int OBS_CAND = 768;      // compact list of in-radius positions
+constexpr int OBS_CAND = 512;      // compact list of in-radius positions (more: pass 2 walks the rows again)
 constexpr int BITONIC_MAX = 256;   // strategy 2 sorts at most this many keys
 static_assert(OBS_CAP >= GD_MAX_K_ROAD, "selection capacity must hold K keys");
 static_assert(OBS_CAP >= BITONIC_MAX && OBS_CAND >= BITONIC_MAX, "bitonic keys must fit");
+static_assert((OBS_NB / WARP) % 2 == 0, "a lane's buckets must fill whole histogram words");
+static_assert(GD_MAX_ROAD_PER_WORLD < 65536, "bucket counts and cursors must fit 16 bits");
 
 struct ObsWarpSmem {
-  unsigned cur[OBS_NB];            // histogram, then scatter cursor
+  unsigned cur[OBS_NB / 2];        // histogram, then scatter cursor: bucket b in the 16-bit half b & 1 of
+                                   // word b / 2 (counts and cursors stay <= GD_MAX_ROAD_PER_WORLD < 2^16)
   unsigned short off[OBS_NB + 2];  // first rank of each bucket
   union {
     unsigned long long keys[OBS_CAP];                     // road keys, bucket order
     unsigned long long pkeys[GD_MAX_AGENTS_PER_WORLD];    // partner keys
   } u;
   unsigned short cand[OBS_CAND];   // positions of the in-radius points (pass 1)
-  unsigned short sel[GD_MAX_K_ROAD];                      // road: position of rank r
+  unsigned sel[GD_MAX_K_ROAD];                            // road: low 32 bits of the key of rank r
   unsigned char psel[GD_MAX_PARTNERS + 1];                // partner: local index of rank r
   unsigned row_start[MAX_ROWS];
   unsigned row_excl[MAX_ROWS];
@@ -68,9 +72,15 @@ struct WorldView {
   GridDesc g;
 };
 
-__device__ __forceinline__ unsigned long long road_key(float d2, unsigned idx, unsigned pos) {
-  return ((unsigned long long)__float_as_uint(d2) << 32) | (idx << 16) | pos;
+// meta = local index | type << 15 (the road block's 16-bit word)
+__device__ __forceinline__ unsigned long long road_key(float d2, unsigned meta, unsigned pos) {
+  return ((unsigned long long)__float_as_uint(d2) << 32) | ((meta & 0x7fffu) << 17) | ((meta >> 15) << 16) | pos;
 }
+__device__ __forceinline__ unsigned sel_pos(unsigned k) { return k & 0xffffu; }
+__device__ __forceinline__ unsigned sel_type(unsigned k) { return (k >> 16) & 1u; }
+__device__ __forceinline__ unsigned sel_index(unsigned k) { return k >> 17; }
+// 16-bit bucket counter b of the packed histogram
+__device__ __forceinline__ unsigned bucket_shift(int b) { return (unsigned)(b & 1) << 4; }
 __device__ __forceinline__ unsigned long long partner_key(float d2, unsigned j) {
   return ((unsigned long long)__float_as_uint(d2) << 32) | j;
 }
@@ -138,8 +148,9 @@ __device__ __forceinline__ void walk_rows(const SM& sm, int nrows, int total, in
   }
 }
 
-// Road selection of one agent at (ex, ey): the positions of the n_sel <= K
-// nearest in-radius points, in rank order, land in sm.sel; returns n_sel.
+// Road selection of one agent at (ex, ey): the low 32 bits of the keys
+// (index, type, position) of the n_sel <= K nearest in-radius points, in
+// rank order, land in sm.sel; returns n_sel.
 __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, float R2, float ex, float ey,
                                            ObsWarpSmem& sm, int lane, int strategy = 1) {
   if (K == 0) return 0;
@@ -158,15 +169,15 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   // loads coalesced too.  Neighbouring points along a road differ in
   // distance by far more than a bucket's width, so the histogram atomics
   // rarely collide.
-  for (int b = lane; b < OBS_NB; b += WARP) sm.cur[b] = 0;
+  for (int b = lane; b < OBS_NB / 2; b += WARP) sm.cur[b] = 0;
   __syncwarp();
   int n_in = 0;
   const unsigned lt = (1u << lane) - 1u;
   {
-    constexpr int U = 4;
     int r = 0;
     unsigned rs = sm.row_start[0], rx = 0;
     unsigned re = (nrows > 1) ? sm.row_excl[1] : 0xffffffffu;
+    constexpr int U = 4;
     for (int f0 = 0; f0 < total; f0 += U * WARP) {
       unsigned pu[U];
       bool vu[U];
@@ -191,7 +202,10 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
       for (int u = 0; u < U; ++u) {
         const float d2 = dist2(qu[u].x - ex, qu[u].y - ey);
         const bool in = vu[u] && d2 <= R2;
-        if (in) atomicAdd(&sm.cur[bucket_of(d2, binv)], 1u);
+        if (in) {
+          const int bk = bucket_of(d2, binv);
+          atomicAdd(&sm.cur[bk >> 1], 1u << bucket_shift(bk));
+        }
         const unsigned m = __ballot_sync(0xffffffffu, in);
         const int slot = n_in + __popc(m & lt);
         if (in && slot < OBS_CAND) sm.cand[slot] = (unsigned short)pu[u];
@@ -206,7 +220,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   int mine = 0;
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    cnt[k] = sm.cur[lane * PER + k];
+    cnt[k] = (sm.cur[(lane * PER + k) >> 1] >> bucket_shift(k)) & 0xffffu;
     mine += (int)cnt[k];
   }
   const int incl = warp_incl_scan(mine, lane);
@@ -215,10 +229,12 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   {
     unsigned run = (unsigned)(incl - mine);
     int cand = OBS_NB;
+    unsigned lo_half = 0;
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       sm.off[lane * PER + k] = (unsigned short)run;
-      sm.cur[lane * PER + k] = run;     // scatter cursor
+      // scatter cursors, two per word
+      if (k & 1) sm.cur[(lane * PER + k) >> 1] = lo_half | (run << 16); else lo_half = run;
       if ((int)run < K && (int)(run + cnt[k]) >= K) cand = min(cand, lane * PER + k);
       run += cnt[k];
     }
@@ -241,7 +257,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
       if (k < n_in) {
         const unsigned p = sm.cand[k];
         const float2 q = xy[p];
-        key = road_key(dist2(q.x - ex, q.y - ey), meta[p] & 0x7fffu, p);
+        key = road_key(dist2(q.x - ex, q.y - ey), meta[p], p);
       }
       sm.u.keys[k] = key;
     }
@@ -259,7 +275,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
         __syncwarp();
       }
     }
-    for (int r = lane; r < n_sel; r += WARP) sm.sel[r] = (unsigned short)(sm.u.keys[r] & 0xffffu);
+    for (int r = lane; r < n_sel; r += WARP) sm.sel[r] = (unsigned)sm.u.keys[r];
     __syncwarp();
     return n_sel;
   }
@@ -299,7 +315,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
       const unsigned long long mid = lo + ((hi - lo) >> 1);
       unsigned cntle = 0;
       for_each_in_radius([&](unsigned p, float d2) {
-        if (bucket_of(d2, binv) == bstar && road_key(d2, meta[p] & 0x7fffu, p) <= mid) ++cntle;
+        if (bucket_of(d2, binv) == bstar && road_key(d2, meta[p], p) <= mid) ++cntle;
       });
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cntle += __shfl_xor_sync(0xffffffffu, cntle, o);
@@ -313,9 +329,10 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   for_each_in_radius([&](unsigned p, float d2) {
     const int b = bucket_of(d2, binv);
     if (b <= bstar) {
-      const unsigned long long key = road_key(d2, meta[p] & 0x7fffu, p);
+      const unsigned long long key = road_key(d2, meta[p], p);
       if (b < bstar || key <= tau) {
-        const unsigned slot = atomicAdd(&sm.cur[b], 1u);
+        const unsigned sh = bucket_shift(b);
+        const unsigned slot = (atomicAdd(&sm.cur[b >> 1], 1u << sh) >> sh) & 0xffffu;
         if (slot < (unsigned)OBS_CAP) sm.u.keys[slot] = key;
       }
     }
@@ -330,7 +347,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     int r = lo, q = lo;
     for (; q + 1 < hi; q += 2) r += (int)(sm.u.keys[q] < key) + (int)(sm.u.keys[q + 1] < key);
     if (q < hi) r += sm.u.keys[q] < key;
-    if (r < n_sel) sm.sel[r] = (unsigned short)(key & 0xffffu);
+    if (r < n_sel) sm.sel[r] = (unsigned)key;
   }
   __syncwarp();
   return n_sel;
@@ -344,18 +361,17 @@ __device__ __forceinline__ void write_road(const WorldView& v, int K, int n_sel,
                                            const ObsWarpSmem& sm, int lane, float4* __restrict__ out4,
                                            int32_t* __restrict__ ridx, const float* __restrict__ w, float& acc) {
   const float2* __restrict__ xy = v.xy;
-  const uint16_t* __restrict__ meta = v.meta;
-  // write K slots, coalesced, streaming (evict-first) stores
+  // write K slots, coalesced, streaming (evict-first) stores; index and type
+  // come with the selection, so only the coordinates are read
   for (int r = lane; r < K; r += WARP) {
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
     int idx = -1;
     if (r < n_sel) {
-      const unsigned p = sm.sel[r];
-      const float2 q = xy[p];
-      const unsigned mt = meta[p];
+      const unsigned sk = sm.sel[r];
+      const float2 q = xy[sel_pos(sk)];
       const float dx = q.x - ex, dy = q.y - ey;
-      o = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), (float)(mt >> 15), 1.f);
-      idx = (int)(mt & 0x7fffu);
+      o = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), (float)sel_type(sk), 1.f);
+      idx = (int)sel_index(sk);
     }
     __stcs(out4 + r, o);
     if (ridx) ridx[r] = idx;
@@ -494,7 +510,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     if (anchor && lane == 0) {
       float rk = __int_as_float(0x7f800000);     // +inf: fewer than K in range
       if (nroad == e.K && e.K > 0) {
-        const float2 q = v.xy[sm.sel[e.K - 1]];
+        const float2 q = v.xy[sel_pos(sm.sel[e.K - 1])];
         rk = sqrtf(dist2(q.x - st.x, q.y - st.y));
       }
       *anchor = make_float4(st.x, st.y, rk, 0.f);
