@@ -89,7 +89,7 @@ struct gd_env {
   int warps = kWorldWarps;     // CTA size of k_world (4, 8 or 16 warps)
   int split = 1;               // radial observation: 1 = k_world step, then k_observe_split over agents
   int so_grid = 0;             // persistent CTAs of k_observe_split
-  unsigned* ocounter = nullptr;  // its agent counter
+  unsigned* ocounter = nullptr;  // its agent counters (OBS_STRIPES)
   float road_cell = 8.f;       // road grid cell (m)
   size_t max_block = 16;       // largest road block (bytes)
   // host copy of the road, to rebuild the road blocks for another cell size
@@ -687,7 +687,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     });
     GD_TRY(upload(env, &env->order, order.data(), (size_t)W));
     GD_TRY(dev_alloc(env, &env->counter, 1));
-    GD_TRY(dev_alloc(env, &env->ocounter, 1));
+    GD_TRY(dev_alloc(env, &env->ocounter, OBS_STRIPES));
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
     env->C = cfg->ckpt_every;
@@ -833,7 +833,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   if (obs && !ell && env->split) {
     // split form: the step over worlds, then the observation over agents
     if (do_step) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv);
-    cudaMemsetAsync(env->ocounter, 0, sizeof(unsigned), stream);
+    cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
     k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(*dv, obs, road_idx, partner_idx,
                                                                                         env->ocounter);
     return;

@@ -648,24 +648,29 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
 }
 
 // Batched split form, after the step (k_world without observation):
-// persistent warps, each claims the next agent from `counter` (cleared
-// before the launch) until all A are observed.  No per-world barrier, so a
-// warp that drew a done agent (an all-zero row) moves straight on; agents
-// are claimed in index order, which keeps a world's agents, and its road
-// block in L1/L2, together.  Registers are capped for 32 warps per SM (its
-// shared memory allows them).
+// persistent warps claim agents one at a time until all A are observed.
+// The claims are striped over OBS_STRIPES counters (cleared before the
+// launch), so that they do not all queue on one address: warp g draws from
+// counter c = g mod OBS_STRIPES the agents c, c + OBS_STRIPES, ...  No
+// per-world barrier, so a warp that drew a done agent (an all-zero row)
+// moves straight on; agents go out in index order, which keeps a world's
+// agents, and its road block in L1/L2, together.  Registers are capped for
+// 32 warps per SM (its shared memory allows them).
+constexpr unsigned OBS_STRIPES = 16;
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv e, float* __restrict__ obs,
                                                                            int32_t* __restrict__ road_idx,
                                                                            int32_t* __restrict__ partner_idx,
-                                                                           unsigned* __restrict__ counter) {
+                                                                           unsigned* __restrict__ counters) {
   extern __shared__ __align__(16) unsigned char obs_smem_raw[];
   const int lane = threadIdx.x & 31;
   ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[threadIdx.x >> 5];
+  const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % OBS_STRIPES;
   for (;;) {
-    unsigned i = 0;
-    if (lane == 0) i = atomicAdd(counter, 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
+    unsigned k = 0;
+    if (lane == 0) k = atomicAdd(counters + c, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    const unsigned i = c + OBS_STRIPES * k;
     if (i >= (unsigned)e.A) break;
     observe_global(e, (int)i, obs, road_idx, partner_idx, sm, lane);
   }
