@@ -147,8 +147,8 @@ typedef struct gd_config {
   int32_t obs_split;         /* radial observation with GD_BATCHED: 1 (default) = the step (a
                                 persistent kernel over worlds) then the observation (a persistent
                                 kernel over agents, no per-world barriers) as two launches; 0 = both
-                                in one fused launch.  gd_rollout_objective always uses the fused
-                                launch.  Both give identical results. */
+                                in one fused launch.  Both give identical results, objective terms of
+                                gd_rollout_objective included. */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -358,8 +358,8 @@ gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, co
  * every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads, with and without the shared-memory road tile,
  * top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256
- * points are in range}, and (without GD_DIFFERENTIABLE) the split or fused
- * observation (obs_split), and keeps the fastest; with GD_DIFFERENTIABLE it
+ * points are in range}, and the split or fused observation (obs_split),
+ * and keeps the fastest; with GD_DIFFERENTIABLE it
  * also times one adjoint launch with and without the road tile
  * (reported by gd_get_info).  With LiDAR enabled it then times the fused
  * step + LiDAR scan with 128, 256 and 384 threads per block, each with and

@@ -41,6 +41,8 @@ struct AdjArgs {
   float reward_w;
   float4* lam;              // [A] in: dL/d post-step state; out: dL/d pre-step state
   float2* d_actions;        // [A] out: dL/d (accel, steer)
+  const float* rk;          // [A] each agent's K-th road distance at this step in the forward rollout
+                            // (bounds the re-selection's disk), or nullptr: the full radius
   unsigned* counter;
   const int* order;
   int tile_bytes;
@@ -102,8 +104,11 @@ __device__ __forceinline__ void invertible_adjoint(const float4 s, float accel, 
 }
 
 // Dynamic shared memory: [mbarrier, 128 B][road tile][AdjAgents][ObsWarpSmem x WARPS]
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_adjoint(DevEnv e, AdjArgs a) {
+// LEAN: the instantiation for the form without the road tile, whose shared
+// memory leaves room for 32 warps per SM; registers are capped at 64 per
+// thread (no spills) so that they can all be resident.
+template <int WARPS, bool LEAN = false>
+__global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(DevEnv e, AdjArgs a) {
   extern __shared__ __align__(16) unsigned char asm_[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(asm_);
   unsigned char* tile = asm_ + 128;
@@ -202,7 +207,18 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_adjoint(DevEnv e, AdjArgs a) 
             gt += fmaf(wa.x, yp, -__fmul_rn(wa.y, xp)) + fmaf(wa.z, sd, -__fmul_rn(wa.w, cd));
           }
           // road points
-          const int nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+          // the forward selection's K-th distance bounds the disk that holds
+          // the same K points (the full radius when it had fewer than K)
+          float Rs = e.R, Rs2 = e.R2;
+          if (a.rk) {
+            const float r = a.rk[i] + 1e-3f;
+            if (r < e.R) {
+              Rs = r;
+              Rs2 = r * r;
+            }
+          }
+          int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
+          if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
           const float* wroad = wrow + 8 + 8 * e.P;
           for (int r = lane; r < nroad; r += WARP) {
             const float2 q = v.xy[sel_pos(sm.sel[r])];

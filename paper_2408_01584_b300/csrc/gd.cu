@@ -113,6 +113,7 @@ struct gd_env {
   int* segT = nullptr;          // [W]
   uint8_t* segWD = nullptr;     // [W]
   float4* lam = nullptr;        // [A] adjoint of the state
+  float* rk_hist = nullptr;     // [episode_len][A] K-th road distance of each agent at each objective step
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
   int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
@@ -282,6 +283,7 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
   {
     int per_sm = 0;
     e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps>));
+    if (e == cudaSuccess) e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps, true>));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observe_split<kSplitWarps>, kSplitWarps * 32,
                                                         kSplitSmem);
@@ -304,10 +306,13 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     const long one = ((long)smem_blk - 1024 - (long)kAdjFixedSmem) & ~15L;
     env->adj_tile = env->adj_notile ? 16 : (int)std::max(16L, ((long)max_block <= two) ? (long)max_block : one);
     env->adj_smem = kAdjFixedSmem + (size_t)env->adj_tile;
-    e = allow_max_smem(reinterpret_cast<const void*>(k_adjoint<kAdjWarps>));
+    // without the tile: the register-capped instantiation (more CTAs per SM)
+    const void* afn = env->adj_notile ? reinterpret_cast<const void*>(k_adjoint<kAdjWarps, true>)
+                                      : reinterpret_cast<const void*>(k_adjoint<kAdjWarps>);
+    e = allow_max_smem(afn);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint<kAdjWarps>, kAdjWarps * 32, env->adj_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, afn, kAdjWarps * 32, env->adj_smem);
     if (e != cudaSuccess) return e;
     env->adj_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
   }
@@ -701,6 +706,9 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
     GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
+    // K-th road distances of the objective rollout; 0x7f7f7f7f (3.4e38) = no bound
+    GD_TRY(dev_alloc(env, &env->rk_hist, (size_t)cfg->episode_len * A));
+    GD_TRY(cudaMemsetAsync(env->rk_hist, 0x7f, sizeof(float) * (size_t)cfg->episode_len * A, env->stream));
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
   env->split = cfg->obs_split;
@@ -827,15 +835,23 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
 static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
-                         float reward_w = 0.f, float* ell = nullptr) {
+                         float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
-  if (obs && !ell && env->split) {
+  if (obs && env->split && (!ell || do_step)) {
     // split form: the step over worlds, then the observation over agents
-    if (do_step) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv);
+    // (with the objective: the step writes r_s to ell, the observation
+    // completes it)
+    if (do_step)
+      launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv, nullptr, 0.f, ell);
     cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
-    k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(*dv, obs, road_idx, partner_idx,
-                                                                                        env->ocounter);
+    const SplitLoss loss{obs_w, reward_w, ell, rk_out};
+    if (ell)
+      k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+          *dv, obs, road_idx, partner_idx, env->ocounter, loss);
+    else
+      k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+          *dv, obs, road_idx, partner_idx, env->ocounter, loss);
     return;
   }
   FusedArgs a{};
@@ -853,6 +869,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.obs_w = obs_w;
   a.reward_w = reward_w;
   a.ell = ell;
+  a.rk_out = (ell && obs) ? rk_out : nullptr;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
@@ -1364,7 +1381,7 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
                     d.world_done);
     }
     launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, nullptr, nullptr,
-                 obs_weight, reward_weight, ell + (size_t)t * A);
+                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A);
   }
   env->diff_actions = actions;
   env->diff_steps = steps;
@@ -1373,7 +1390,7 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
 
 static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, const float4* post, const uint8_t* fpost,
                            const float* actions, const float* obs_w, long long stride, const float* row_scale,
-                           const float* rew_w, float reward_w, float* d_actions) {
+                           const float* rew_w, float reward_w, float* d_actions, const float* rk = nullptr) {
   AdjArgs a;
   a.pre = pre;
   a.fpre = fpre;
@@ -1387,11 +1404,15 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
   a.reward_w = reward_w;
   a.lam = env->lam;
   a.d_actions = reinterpret_cast<float2*>(d_actions);
+  a.rk = rk;
   a.counter = env->counter;
   a.order = env->order;
   a.tile_bytes = env->adj_tile;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), env->stream);
-  k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
+  if (env->adj_notile)
+    k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
+  else
+    k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
 }
 
 // Recompute `len` steps of the segment starting from segS[0] / segF[0] /
@@ -1433,7 +1454,7 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
       const int t = t0 + k;
       launch_adjoint(env, env->segS + k * A, env->segF + k * A, env->segS + (k + 1) * A, env->segF + (k + 1) * A,
                      env->diff_actions + (size_t)t * A * 2, obs_weight, 0, d_ell ? d_ell + (size_t)t * A : nullptr,
-                     nullptr, reward_weight, d_actions + (size_t)t * A * 2);
+                     nullptr, reward_weight, d_actions + (size_t)t * A * 2, env->rk_hist + (size_t)t * A);
     }
   }
   if (d_state0) cudaMemcpyAsync(d_state0, env->lam, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
@@ -1562,16 +1583,11 @@ gd_status gd_autotune(gd_env* env) {
   const int warps[] = {4, 8, 16};
   float best_ms = INFINITY, best_cell = env->road_cell;
   int best_w = env->warps, best_st = d.topk, best_nt = env->notile, best_sp = env->split;
-  // a differentiable env's objective rollouts always use the fused launch
-  const int sp_lo = (env->cfg.flags & GD_DIFFERENTIABLE) ? env->split : 0;
-  const int sp_hi = (env->cfg.flags & GD_DIFFERENTIABLE) ? env->split : 1;
-  const int keep_split = env->split;
-  if (env->cfg.flags & GD_DIFFERENTIABLE) env->split = 0;
   for (float c : cells) {
     const float cell = std::max(c, min_cell);
     if ((e = build_road(env, cell)) != cudaSuccess) break;
-    for (int sp = sp_lo; sp <= sp_hi && e == cudaSuccess; ++sp) {
-      if (!(env->cfg.flags & GD_DIFFERENTIABLE)) env->split = sp;
+    for (int sp = 0; sp <= 1 && e == cudaSuccess; ++sp) {
+      env->split = sp;
       for (int shape = 0; shape < 6; ++shape) {
         const int wp = warps[shape % 3];
         env->warps = wp;
@@ -1597,7 +1613,7 @@ gd_status gd_autotune(gd_env* env) {
     }
     if (e != cudaSuccess) break;
   }
-  env->split = (env->cfg.flags & GD_DIFFERENTIABLE) ? keep_split : best_sp;
+  env->split = best_sp;
   if (e == cudaSuccess) {
     env->warps = best_w;
     env->notile = best_nt;

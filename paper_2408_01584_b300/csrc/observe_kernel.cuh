@@ -453,7 +453,7 @@ template <bool LOSS>
 __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
                                                ObsWarpSmem& sm, int lane, float4* anchor,
-                                               const float* __restrict__ w = nullptr) {
+                                               const float* __restrict__ w = nullptr, float* rk_slot = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
@@ -507,13 +507,14 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     }
     int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
     if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
-    if (anchor && lane == 0) {
+    if ((anchor || rk_slot) && lane == 0) {
       float rk = __int_as_float(0x7f800000);     // +inf: fewer than K in range
       if (nroad == e.K && e.K > 0) {
         const float2 q = v.xy[sel_pos(sm.sel[e.K - 1])];
         rk = sqrtf(dist2(q.x - st.x, q.y - st.y));
       }
-      *anchor = make_float4(st.x, st.y, rk, 0.f);
+      if (anchor) *anchor = make_float4(st.x, st.y, rk, 0.f);
+      if (rk_slot) *rk_slot = rk;
     }
     write_road<LOSS>(v, e.K, nroad, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx,
                      LOSS ? w + 8 + 8 * e.P : nullptr, acc);
@@ -615,9 +616,13 @@ __device__ __forceinline__ bool offroad_cells_grouped(const int* __restrict__ cs
 
 // Observation row of agent i with everything read from global memory (the
 // world's agents and road block through L1/L2).
-__device__ __forceinline__ void observe_global(const DevEnv& e, int i, float* __restrict__ obs,
-                                               int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
-                                               ObsWarpSmem& sm, int lane) {
+// With LOSS, returns (to every lane) wrow . row for the weight row wrow,
+// and writes the agent's K-th road distance to rk_slot if given.
+template <bool LOSS = false>
+__device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* __restrict__ obs,
+                                                int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
+                                                ObsWarpSmem& sm, int lane, const float* __restrict__ wrow = nullptr,
+                                                float* rk_slot = nullptr) {
   const int w = e.agent_world[i];
   const int a0 = e.agent_off[w];
   WorldView v;
@@ -628,9 +633,9 @@ __device__ __forceinline__ void observe_global(const DevEnv& e, int i, float* __
   v.n = e.agent_off[w + 1] - a0;
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
-  observe_agent<false>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
-                       partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
-                       e.anchor ? e.anchor + i : nullptr);
+  return observe_agent<LOSS>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
+                             partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
+                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot);
 }
 
 // Per-stage form: one warp per agent over the whole batch.  Dynamic shared
@@ -647,6 +652,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
   observe_global(e, i, obs, road_idx, partner_idx, reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[wib], lane);
 }
 
+// Objective of the split form (LOSS): ell[i] holds the agent's smooth goal
+// reward r_s from the step launch and becomes reward_w * r_s + w . row, with
+// the same single rounding as the fused kernel; rk[i] gets the K-th road
+// distance.
+struct SplitLoss {
+  const float* w;      // [F] weight row, 16-byte aligned
+  float reward_w;
+  float* ell;          // [A]
+  float* rk;           // [A] or nullptr
+};
+
 // Batched split form, after the step (k_world without observation):
 // persistent warps claim agents one at a time until all A are observed.
 // The claims are striped over OBS_STRIPES counters (cleared before the
@@ -657,11 +673,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_observe(DevEnv e, float* __restr
 // agents, and its road block in L1/L2, together.  Registers are capped for
 // 32 warps per SM (its shared memory allows them).
 constexpr unsigned OBS_STRIPES = 16;
-template <int WARPS>
+template <int WARPS, bool LOSS = false>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv e, float* __restrict__ obs,
                                                                            int32_t* __restrict__ road_idx,
                                                                            int32_t* __restrict__ partner_idx,
-                                                                           unsigned* __restrict__ counters) {
+                                                                           unsigned* __restrict__ counters,
+                                                                           SplitLoss loss) {
   extern __shared__ __align__(16) unsigned char obs_smem_raw[];
   const int lane = threadIdx.x & 31;
   ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[threadIdx.x >> 5];
@@ -672,7 +689,13 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
     k = __shfl_sync(0xffffffffu, k, 0);
     const unsigned i = c + OBS_STRIPES * k;
     if (i >= (unsigned)e.A) break;
-    observe_global(e, (int)i, obs, road_idx, partner_idx, sm, lane);
+    if (LOSS) {
+      const float dot = observe_global<true>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
+                                             loss.rk ? loss.rk + i : nullptr);
+      if (lane == 0) loss.ell[i] = fmaf(loss.reward_w, loss.ell[i], dot);
+    } else {
+      observe_global(e, (int)i, obs, road_idx, partner_idx, sm, lane);
+    }
   }
 }
 

@@ -38,10 +38,13 @@ struct FusedArgs {
   int tile_bytes;            // bytes of the shared-memory road tile
   int do_step;
   // objective terms ell[i] = obs_w . obs row + reward_w * r_s (agents in the
-  // scene at the start of the step), written when ell != nullptr
+  // scene at the start of the step), written when ell != nullptr; a launch
+  // without observation (obs == nullptr) writes r_s alone, for the split
+  // observation launch to complete
   const float* obs_w;        // [F], 16-byte aligned
   float reward_w;
   float* ell;                // [A] or nullptr
+  float* rk_out;             // [A] with ell: each observed agent's K-th road distance (+inf: fewer), or nullptr
   LidarArgs lidar;           // LiDAR observation (k_world<W, true>); lidar.depth == nullptr: none
 };
 
@@ -354,6 +357,18 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         if (a.reward) a.reward[i] = r;
         if (a.done) a.done[i] = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) ? 1 : 0;
         dn = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) != 0;
+        if (a.ell && !observe) {
+          // split objective: the smooth goal reward of an agent in the scene
+          // at the start of the step goes to ell[i]; the observation launch
+          // that follows folds it in (ell[i] = reward_w * ell[i] + obs term)
+          float rs = 0.f;
+          if (ag.act0[tid] && !(f & GD_FLAG_STATIC)) {
+            const float4 st = ag.st[tid], sc = ag.sc[tid];
+            const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
+            rs = c - sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));
+          }
+          a.ell[i] = rs;
+        }
       }
       // end of episode: every controlled agent done (a world without
       // controlled agents only times out), or t = T
@@ -396,8 +411,9 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         int32_t* pidx = a.partner_idx ? a.partner_idx + (size_t)i * e.P : nullptr;
         if (a.ell) {
           float4* anc = e.anchor ? e.anchor + i : nullptr;
-          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, anc, a.obs_w)
-                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, anc, a.obs_w);
+          float* rks = a.rk_out ? a.rk_out + i : nullptr;
+          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks)
+                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks);
           if (lane == 0) {
             float rs = 0.f;
             if (a.do_step && ag.act0[li] && !(ag.fl[li] & GD_FLAG_STATIC)) {

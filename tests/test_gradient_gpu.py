@@ -179,3 +179,60 @@ def test_backward_is_deterministic_and_step_backward_matches():
     ref = max(np.abs(ga_o).max(), np.abs(gs_o).max())
     assert np.abs(d_act.cpu().numpy() - ga_o[0]).max() / ref < GRAD_RTOL
     assert np.abs(d_state.cpu().numpy() - gs_o).max() / ref < GRAD_RTOL
+
+
+def _objective_and_gradient(sc, ocfg, acts, w, **over):
+    from paper_2408_01584_b300 import gd
+    env = gd.Env(sc, **dict(_kw(ocfg), **over))
+    T = acts.shape[0]
+    ell = torch.empty(T, sc.num_agents, device="cuda")
+    obs = torch.empty(sc.num_agents, env.F, device="cuda")
+    gd.gd_rollout_objective(env.h, T, acts, w, 0.5, ell, obs)
+    da = torch.empty(T, sc.num_agents, 2, device="cuda")
+    ds = torch.empty(sc.num_agents, 4, device="cuda")
+    gd.gd_rollout_backward(env.h, w, 0.5, None, da, ds)
+    env.sync()
+    out = [x.cpu().numpy() for x in (ell, obs, da, ds)]
+    env.close()
+    return out
+
+
+@pytest.mark.parametrize("T", [1, 7])
+def test_split_and_fused_objective_and_gradients_are_identical(T):
+    # the split observation completes the objective term the step launch
+    # started (r_s), with the fused kernel's rounding: same terms, same rows,
+    # same gradients
+    sc = scenes.make_scene(np.array([6, 9, 17]), np.array([700, 800, 1500]), 8)
+    ocfg = OracleConfig(k_road=48, n_partners=7, episode_len=91)
+    acts = torch.from_numpy(scenes.make_actions(T, sc.num_agents, 8)).cuda().contiguous()
+    w = torch.from_numpy(np.random.default_rng(8).uniform(0, 1, ocfg.feat).astype(np.float32)).cuda()
+    fused = _objective_and_gradient(sc, ocfg, acts, w, obs_split=0)
+    split = _objective_and_gradient(sc, ocfg, acts, w, obs_split=1)
+    for a, b in zip(fused, split):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_bounded_reselection_equals_full_radius():
+    # gd_rollout_backward re-selects each agent's road points inside the disk
+    # of the forward step's K-th distance; gd_step_backward re-selects over
+    # the full radius: from the same state the gradients are bit-identical
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([12, 20]), np.array([900, 2500]), 9)
+    ocfg = OracleConfig(k_road=200, n_partners=15, episode_len=91)
+    acts = torch.from_numpy(scenes.make_actions(1, sc.num_agents, 9)).cuda().contiguous()
+    w = torch.from_numpy(np.random.default_rng(9).uniform(0, 1, ocfg.feat).astype(np.float32)).cuda()
+    env = gd.Env(sc, **_kw(ocfg))
+    ell = torch.empty(1, sc.num_agents, device="cuda")
+    gd.gd_rollout_objective(env.h, 1, acts, w, 0.5, ell, env.obs)
+    da = torch.empty(1, sc.num_agents, 2, device="cuda")
+    ds = torch.empty(sc.num_agents, 4, device="cuda")
+    gd.gd_rollout_backward(env.h, w, 0.5, None, da, ds)
+    gd.gd_reset(env.h)
+    d_state = torch.empty(sc.num_agents, 4, device="cuda")
+    d_act = torch.empty(sc.num_agents, 2, device="cuda")
+    rew = torch.full((sc.num_agents,), 0.5, device="cuda")
+    gd.gd_step_backward(env.h, acts[0], None, None, w, rew, d_state, d_act)
+    env.sync()
+    np.testing.assert_array_equal(da[0].cpu().numpy(), d_act.cpu().numpy())
+    np.testing.assert_array_equal(ds.cpu().numpy(), d_state.cpu().numpy())
+    env.close()
