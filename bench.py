@@ -479,7 +479,8 @@ def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
 
         for _ in range(warmup):
             inv()
-        ms_inv = _time_rollouts(inv, max(steps, 5), stream, flush)
+        # a single launch of ~30 us: the median of 9 (each after an L2 flush)
+        ms_inv = _time_rollouts(inv, max(steps, 9), stream, flush)
         gd.gd_sync(env.h)
         gd.gd_sync(envt.h)
     # recovered vs. applied actions where the vehicle moved (curvature is
@@ -488,11 +489,12 @@ def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
     d = np.abs(rec.cpu().numpy() - acts_h)
     err = [float(d[..., 0].max()), float(d[..., 1][moving].max())]
     hbm, peak_kind = _peaks()
-    inv_s = statistics.mean(ms_inv) / 1e3
+    inv_s = statistics.median(ms_inv) / 1e3
     algo = (T + 1) * A * 16 + A * 16 + T * A * 8
     out = {"workload": workload, "dynamics": "simplified invertible model", "agents": A,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
-           "inversion": {"value": T * A / inv_s, "unit": "agent-steps/s", "ms": statistics.mean(ms_inv),
+           "inversion": {"value": T * A / inv_s, "unit": "agent-steps/s", "ms": statistics.median(ms_inv),
+                         "timing": f"median of {len(ms_inv)} launches, each after an L2 flush",
                          "max_abs_error_accel_curvature": err,
                          "note": "curvature error over steps that moved more than 5 cm",
                          "hbm": {"achieved": algo / inv_s / 1e9, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
