@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
   __shared__ int s_nact;
   __shared__ int s_abort;
   __shared__ int s_next;
+  __shared__ GridDesc s_eg;   // the world's edge-grid descriptor, read early (used after the collision stage)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   ObsWarpSmem& osm = reinterpret_cast<ObsWarpSmem*>(warp_base)[wid];
   unsigned char* lbase = warp_base + (size_t)wid * (size_t)a.lidar.warp_bytes;
@@ -146,8 +147,13 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
   __syncthreads();
   unsigned phase = 0;
   const bool observe = LIDAR ? a.lidar.depth != nullptr : a.obs != nullptr;
+  // the first world of each CTA is world order[blockIdx.x] (the grid never
+  // exceeds W); the rest are claimed from the counter (cleared before the
+  // launch), after those
+  bool first = true;
   for (;;) {
-    if (tid == 0) s_w = (int)atomicAdd(a.counter, 1u);
+    if (tid == 0) s_w = first ? (int)blockIdx.x : (int)(gridDim.x + atomicAdd(a.counter, 1u));
+    first = false;
     __syncthreads();
     const int k = s_w;
     if (k >= e.W) break;
@@ -165,7 +171,10 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       mbar_arrive_expect_tx(bar, block);
       tma_load_1d(tile, gblock, block, bar);
     }
-    if (tid == 0) s_next = WARPS;
+    if (tid == 0) {
+      s_next = WARPS;
+      if (a.do_step) s_eg = e.egrid[w];
+    }
     // Two views of the world: one on the shared-memory tile, one on the
     // global road block.  Each use site picks one with a uniform branch, so
     // the shared path compiles to shared-memory accesses.
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
           if (lane == 0) ag.offr[li] = off ? 1 : 0;
         }
       } else {
-        const GridDesc eg = e.egrid[w];
+        const GridDesc& eg = s_eg;
         for (int b0 = wid * (WARP / STEP_G); b0 < n; b0 += WARPS * (WARP / STEP_G)) {
           const int li = b0 + lane / STEP_G;
           const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) && ag.ty[li] != GD_AGENT_PEDESTRIAN;
