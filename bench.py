@@ -27,15 +27,22 @@ METRIC = "agent-steps/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
-def _kernel_source_hash():
-    """Hash of what the radial-observation k_world is compiled from: its
-    device headers (and the LiDAR arguments embedded in its parameter block)
-    and the constants (#define lines) of the C header.  The header's structs
-    are host-side and do not enter the kernel."""
+# Device headers each profiled kernel is compiled from.
+KERNEL_SOURCES = {
+    "k_observe_split": ("gd_device.cuh", "observe_kernel.cuh"),
+    # the fused kernel also embeds the LiDAR arguments in its parameter block
+    "k_world": ("gd_device.cuh", "observe_kernel.cuh", "world_kernel.cuh", "lidar_kernel.cuh"),
+}
+
+
+def _kernel_source_hash(kernel="k_world"):
+    """Hash of what `kernel` is compiled from: its device headers and the
+    constants (#define lines) of the C header.  The header's structs are
+    host-side and do not enter the kernel."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2408_01584_b300", "csrc")
-    for f in ("gd_device.cuh", "observe_kernel.cuh", "world_kernel.cuh", "lidar_kernel.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(ROOT, "include", "gd.h")) as fh:
@@ -53,7 +60,7 @@ def _measured_traffic(workload, kernel="k_world"):
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("source_hash") == _kernel_source_hash() else None
+    return rec["dram_bytes_per_launch"] if rec.get("source_hash") == _kernel_source_hash(kernel) else None
 
 
 def _peaks():
