@@ -197,13 +197,24 @@ def per_kernel_launch_us(env, actions, T, stream, flush):
     return {"step": step, "observe": obs}
 
 
-def algorithmic_bytes_per_agent_step(scene, F):
-    """Observation write 4F + state/action/flags ~70 B + the world's road
-    tile read once per step (12 B per point: x, y, type/index) / A_w."""
+def algorithmic_bytes_per_agent_step(scene, F, radius=50.0):
+    """Observation write 4F + state/action/flags ~70 B, and the road: 12 B
+    (x, y, type/index) for every distinct road point of a world within the
+    observation radius of at least one of its agents, per agent.  The road
+    set is taken at the initial state, with every agent in the scene, so it
+    bounds the set of any later step from above."""
     import numpy as np
-    A_w = np.diff(scene.agent_off).astype(np.float64)
-    N_w = np.diff(scene.road_off).astype(np.float64)
-    road = float((12.0 * N_w).sum() / max(A_w.sum(), 1.0))
+    from scipy.spatial import cKDTree
+    pts = 0
+    for w in range(scene.num_worlds):
+        a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
+        r0, r1 = scene.road_off[w], scene.road_off[w + 1]
+        if a1 == a0 or r1 == r0:
+            continue
+        tree = cKDTree(np.stack([scene.road_x[r0:r1], scene.road_y[r0:r1]], 1).astype(np.float64))
+        near = tree.query_ball_point(np.stack([scene.x[a0:a1], scene.y[a0:a1]], 1).astype(np.float64), radius)
+        pts += len(set().union(*near))
+    road = 12.0 * pts / max(scene.num_agents, 1)
     return 4.0 * F + 70.0, road
 
 
@@ -682,7 +693,7 @@ def run_ours(args, rank, world):
         kernel_us = per_kernel_launch_us(env_b, actions, T, stream, flush) if info.obs_split else None
     agent_steps = T * A * world
     value = agent_steps * args.steps / (total_ms / 1e3)
-    bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F)
+    bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F, float(env_b.cfg.obs_radius))
     hbm, peak_kind = _peaks()
     if kernel_us:
         # split form: the observation launch dominates (row write, agent state, road once per world)
