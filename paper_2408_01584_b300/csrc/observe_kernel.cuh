@@ -446,6 +446,29 @@ __device__ __forceinline__ void write_partners(const WorldView& v, int P, int n_
   }
 }
 
+// Row of an agent removed from the scene (flags f has GD_FLAG_DONE): all
+// zero except the three flags; index lists all -1.  With LOSS, lane 0
+// returns w . row (the other lanes 0).
+template <bool LOSS>
+__device__ __forceinline__ float write_done_row(const DevEnv& e, uint8_t f, float* __restrict__ obs_row,
+                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
+                                                const float* __restrict__ w, int lane) {
+  float4* row = reinterpret_cast<float4*>(obs_row);
+  const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
+              fg = (f & GD_FLAG_GOAL) ? 1.f : 0.f;
+  const int n4 = e.F >> 2;
+  for (int k = lane; k < n4; k += WARP) {
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k == 1) o = make_float4(0.f, fc, fo, fg);
+    __stcs(row + k, o);
+  }
+  if (ridx) for (int k = lane; k < e.K; k += WARP) ridx[k] = -1;
+  if (pidx) for (int k = lane; k < e.P; k += WARP) pidx[k] = -1;
+  float acc = 0.f;
+  if (LOSS && lane == 0) acc = fmaf(__ldg(w + 5), fc, fmaf(__ldg(w + 6), fo, __fmul_rn(__ldg(w + 7), fg)));
+  return acc;
+}
+
 // One full observation row of local agent li of the world in view v.
 // With LOSS, returns (to every lane) w . row for the weight row w (F
 // floats); otherwise returns 0.
@@ -460,16 +483,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
               fg = (f & GD_FLAG_GOAL) ? 1.f : 0.f;
   float acc = 0.f;
   if (f & GD_FLAG_DONE) {
-    // removed from the scene: all-zero row except the three flags
-    const int n4 = e.F >> 2;
-    for (int k = lane; k < n4; k += WARP) {
-      float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (k == 1) o = make_float4(0.f, fc, fo, fg);
-      __stcs(row + k, o);
-    }
-    if (ridx) for (int k = lane; k < e.K; k += WARP) ridx[k] = -1;
-    if (pidx) for (int k = lane; k < e.P; k += WARP) pidx[k] = -1;
-    if (LOSS && lane == 0) acc = fmaf(__ldg(w + 5), fc, fmaf(__ldg(w + 6), fo, __fmul_rn(__ldg(w + 7), fg)));
+    acc = write_done_row<LOSS>(e, f, obs_row, ridx, pidx, w, lane);
   } else {
     const float4 st = v.state[li];
     const float4 sc = v.stat[li];
@@ -689,13 +703,19 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
     k = __shfl_sync(0xffffffffu, k, 0);
     const unsigned i = c + OBS_STRIPES * k;
     if (i >= (unsigned)e.A) break;
-    if (LOSS) {
-      const float dot = observe_global<true>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
-                                             loss.rk ? loss.rk + i : nullptr);
-      if (lane == 0) loss.ell[i] = fmaf(loss.reward_w, loss.ell[i], dot);
+    // an agent removed from the scene needs only its flags: no world loads
+    const uint8_t f = e.flags[i];
+    float* orow = obs + (size_t)i * e.F;
+    int32_t* ridx = road_idx ? road_idx + (size_t)i * e.K : nullptr;
+    int32_t* pidx = partner_idx ? partner_idx + (size_t)i * e.P : nullptr;
+    float dot;
+    if (f & GD_FLAG_DONE) {
+      dot = write_done_row<LOSS>(e, f, orow, ridx, pidx, loss.w, lane);
     } else {
-      observe_global(e, (int)i, obs, road_idx, partner_idx, sm, lane);
+      dot = observe_global<LOSS>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
+                                 LOSS && loss.rk ? loss.rk + i : nullptr);
     }
+    if (LOSS && lane == 0) loss.ell[i] = fmaf(loss.reward_w, loss.ell[i], dot);
   }
 }
 
