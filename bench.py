@@ -716,7 +716,7 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload,
                    "form": ("batched, split: per step a persistent step kernel over worlds and a persistent "
                             "observation kernel over agents; 91-step CUDA graph") if kernel_us else
-                           "batched (persistent fused kernel, 91-step CUDA graph)",
+                           "batched, fused: one persistent kernel per simulator step; 91-step CUDA graph",
                    "autotuned": tuned,
                    "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
                    "n_partners": cfg["n_partners"], "episode_steps": T, "feat": F,

@@ -13,7 +13,7 @@
  *   gd_observe  each agent's ego-frame observation: the K nearest road
  *               points and P nearest other agents within the observation
  *               radius (Sec. 3.2 "Sensor modalities"; 50 m in Fig. 1);
- *   gd_step_observe, gd_rollout   the same, fused, and whole episodes;
+ *   gd_step_observe, gd_rollout   the same in one call, and whole episodes;
  *   gd_observe_lidar, gd_step_observe_lidar, gd_rollout_lidar   the LiDAR
  *               and view-cone observations (Sec. 3.2 "Sensor modalities":
  *               rays cast against bounding boxes and road edges, all around
@@ -80,7 +80,8 @@ typedef enum gd_status {
 #define GD_TERM_COLLISION 0x1u   /* agent/agent collision ends the agent's episode (Sec. 3.2) */
 #define GD_TERM_OFFROAD 0x2u     /* crossing a road edge ends the agent's episode (Sec. 3.2) */
 #define GD_AUTO_RESET 0x4u       /* gd_step first resets worlds whose episode ended */
-#define GD_BATCHED 0x8u          /* persistent fused kernels over a world work list */
+#define GD_BATCHED 0x8u          /* persistent kernels: the step over a world work list, the observation
+                                    over an agent counter (or fused with the step, obs_split = 0) */
 #define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward */
 #define GD_NONTRIVIAL_INIT 0x20u /* "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges"):
                                     agents within nontrivial_dist of their goal at the start are not
@@ -122,7 +123,8 @@ typedef struct gd_config {
   float offroad_penalty;     /* subtracted from the reward off road (0) */
   float smooth_c;            /* m, scale of the smooth goal reward (1) */
   uint32_t flags;            /* GD_TERM_* | GD_AUTO_RESET | GD_BATCHED | GD_DIFFERENTIABLE | GD_NONTRIVIAL_INIT */
-  int32_t block_size;        /* threads per block of the observation kernel; 0 = default */
+  int32_t block_size;        /* threads per block of the batched step kernel (and of the fused
+                                observation); 0 = default (256), 128, 256 or 512 */
   float road_cell;           /* m, road-point grid cell; 0 = default (8) */
   int32_t topk_strategy;     /* road top-K method: 0 = default, 1 = bucket rank, 2 = bitonic sort */
   int32_t lidar_rays;        /* rays per agent of the LiDAR observation, 0..GD_MAX_LIDAR_RAYS;
@@ -169,7 +171,7 @@ typedef struct gd_info {
   int32_t num_worlds, num_agents, num_road, feat;   /* feat = F */
   int32_t max_agents_per_world, k_road, n_partners, episode_len;
   int64_t device_bytes;                             /* device memory owned by the env */
-  int32_t block_size;                               /* fused-kernel threads per block in use */
+  int32_t block_size;                               /* threads per block of the batched step kernel in use */
   float road_cell;                                  /* road grid cell in use (m) */
   int32_t topk_strategy;                            /* road top-K method in use */
   int32_t lidar_rays;                               /* rays per agent (0 = LiDAR not enabled) */
@@ -177,7 +179,7 @@ typedef struct gd_info {
   int32_t lidar_block_size;                         /* fused LiDAR kernel threads per block in use */
   int32_t lidar_road_tile;                          /* 1: it copies each world's road into shared memory */
   int32_t lidar_split;                              /* 1: step and LiDAR scan are two launches */
-  int32_t road_tile;                                /* 1: the fused kernel copies each world's road into
+  int32_t road_tile;                                /* 1: the batched step kernel copies each world's road into
                                                        shared memory */
   int32_t obs_split;                                /* 1: step and radial observation are two launches */
 } gd_info;
@@ -218,7 +220,8 @@ gd_status gd_step(gd_env* env, const float* actions, float* reward, uint8_t* don
  * partner_idx: device int32 [A,P] local agent indices or NULL. */
 gd_status gd_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* partner_idx);
 
-/* gd_step followed by gd_observe; one fused launch when GD_BATCHED is set. */
+/* gd_step followed by gd_observe; with GD_BATCHED, two launches (obs_split = 1)
+ * or one fused launch (obs_split = 0). */
 gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                           float* obs);
 
@@ -354,7 +357,7 @@ gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_sta
 gd_status gd_get_state(gd_env* env, float* state, uint8_t* flags, int32_t* t);
 gd_status gd_set_state(gd_env* env, const float* state, const uint8_t* flags, const int32_t* t);
 
-/* Autotuner of the fused (batched) kernel: times the step + observation for
+/* Autotuner of the batched form: times the step + observation for
  * every road grid cell in {6, 8, 12} m, CTA size
  * in {128, 256, 512} threads, with and without the shared-memory road tile,
  * top-K strategy in {1 bucket rank, 2 bitonic sort when at most 256

@@ -32,7 +32,7 @@ struct NvtxRange {
 };
 
 constexpr int kObsWarpsDefault = 8;
-constexpr int kWorldWarps = 8;    // default CTA size of the fused kernel (warps); 4 and 16 also built
+constexpr int kWorldWarps = 8;    // default CTA size of k_world (warps); 4 and 16 also built
 constexpr int kAdjWarps = 8;
 constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
