@@ -835,16 +835,20 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
 static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
-                         float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr) {
+                         float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
+                         unsigned* clear_ocounters = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
     // split form: the step over worlds, then the observation over agents
     // (with the objective: the step writes r_s to ell, the observation
     // completes it)
+    // the step launch clears the observation counters; without a step, a memset does
     if (do_step)
-      launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv, nullptr, 0.f, ell);
-    cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
+      launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv, nullptr, 0.f, ell,
+                   nullptr, env->ocounter);
+    else
+      cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
     const SplitLoss loss{obs_w, reward_w, ell, rk_out};
     if (ell)
       k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
@@ -870,6 +874,8 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   a.rk_out = (ell && obs) ? rk_out : nullptr;
+  a.clear = clear_ocounters;
+  a.clear_n = clear_ocounters ? (int)OBS_STRIPES : 0;
   cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);

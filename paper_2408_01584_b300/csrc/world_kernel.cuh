@@ -45,6 +45,8 @@ struct FusedArgs {
   float reward_w;
   float* ell;                // [A] or nullptr
   float* rk_out;             // [A] with ell: each observed agent's K-th road distance (+inf: fewer), or nullptr
+  unsigned* clear;           // cleared (clear_n words) by the launch, for the launch that follows; or nullptr
+  int clear_n;
   LidarArgs lidar;           // LiDAR observation (k_world<W, true>); lidar.depth == nullptr: none
 };
 
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
     mbar_init(bar, 1);
     s_abort = 0;
   }
+  // the split form's observation counters, for the observation launch that follows
+  if (a.clear && blockIdx.x == 0 && tid < a.clear_n) a.clear[tid] = 0u;
   __syncthreads();
   unsigned phase = 0;
   const bool observe = LIDAR ? a.lidar.depth != nullptr : a.obs != nullptr;
