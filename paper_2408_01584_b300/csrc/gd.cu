@@ -79,7 +79,8 @@ struct gd_env {
   int obs_warps = kObsWarpsDefault;
   // batched form
   int* order = nullptr;        // [W] world order for the work list
-  unsigned* counter = nullptr; // work counter
+  unsigned* counter = nullptr; // [2] k_world's work counter and exit tally (zero between launches)
+  unsigned* acounter = nullptr; // k_adjoint's work counter
   int tile_cap = 0;            // bytes of the shared-memory road tile
   int notile = 0;              // 1: k_world reads every road block from global memory (more CTAs per SM)
   size_t world_smem = 0;       // dynamic shared memory of k_world
@@ -691,7 +692,10 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
       return cp > cq;
     });
     GD_TRY(upload(env, &env->order, order.data(), (size_t)W));
-    GD_TRY(dev_alloc(env, &env->counter, 1));
+    // k_world's work counter and exit tally (each launch leaves them at zero), the adjoint's counter
+    GD_TRY(dev_alloc(env, &env->counter, 2));
+    GD_TRY(cudaMemsetAsync(env->counter, 0, 2 * sizeof(unsigned), env->stream));
+    GD_TRY(dev_alloc(env, &env->acounter, 1));
     GD_TRY(dev_alloc(env, &env->ocounter, OBS_STRIPES));
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
@@ -829,7 +833,7 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
       d, obs, road_idx, partner_idx);
 }
 
-// Batched form: one persistent fused launch (work counter cleared first).
+// Batched form: one persistent launch (its work counter was left at zero by the previous one).
 // With env->split, an observation without the objective is the step launch
 // (nothing observed) followed by k_observe_split over all agents.
 static void launch_world(gd_env* env, const float* actions, float* reward, uint8_t* done, uint8_t* world_done,
@@ -876,7 +880,6 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.rk_out = (ell && obs) ? rk_out : nullptr;
   a.clear = clear_ocounters;
   a.clear_n = clear_ocounters ? (int)OBS_STRIPES : 0;
-  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
   const size_t smem = step_only ? env->step_smem : env->world_smem;
@@ -945,7 +948,6 @@ static void launch_world_lidar(gd_env* env, const float* actions, float* reward,
   a.tile_bytes = env->lw_tile;
   a.do_step = do_step;
   a.lidar = lidar_args(env, head, depth, cls);
-  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), stream);
   switch (env->lw_warps) {
     case 4: k_world<4, true><<<env->lw_grid, 4 * 32, env->lw_smem, stream>>>(env->d, a); break;
     case 12: k_world<12, true><<<env->lw_grid, 12 * 32, env->lw_smem, stream>>>(env->d, a); break;
@@ -1411,10 +1413,10 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
   a.lam = env->lam;
   a.d_actions = reinterpret_cast<float2*>(d_actions);
   a.rk = rk;
-  a.counter = env->counter;
+  a.counter = env->acounter;
   a.order = env->order;
   a.tile_bytes = env->adj_tile;
-  cudaMemsetAsync(env->counter, 0, sizeof(unsigned), env->stream);
+  cudaMemsetAsync(env->acounter, 0, sizeof(unsigned), env->stream);
   if (env->adj_notile)
     k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
   else

@@ -33,7 +33,7 @@ struct FusedArgs {
   float* obs;                // [A,F] or nullptr (no observation)
   int32_t* road_idx;         // [A,K] or nullptr
   int32_t* partner_idx;      // [A,P] or nullptr
-  unsigned* counter;         // work counter, zero at launch
+  unsigned* counter;         // [2] work counter and exit tally: zero at launch, left at zero by the launch
   const int* order;          // [W] world order (largest first)
   int tile_bytes;            // bytes of the shared-memory road tile
   int do_step;
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       // every cell their bounding box touches, so the cells under the box's
       // own bounding box hold every segment it can cross), a group of STEP_G
       // lanes per agent
-      if (!wait_tile()) return;
+      if (!wait_tile()) break;
       if (use_tile) {
         for (int li = wid; li < n; li += WARPS) {
           if ((ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) || ag.ty[li] == GD_AGENT_PEDESTRIAN) {
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       ag.fl[tid] = e.flags[a0 + tid];
     }
     if (observe) {
-      if (!wait_tile()) return;
+      if (!wait_tile()) break;
       // warps take the world's agents one at a time (first WARPS statically)
       for (int li = wid; li < n;) {
         const int i = a0 + li;
@@ -447,6 +447,14 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       }
     }
     __syncthreads();
+  }
+  // the last CTA out leaves the work counter and the exit tally at zero for
+  // the next launch, so no memset separates two launches (every CTA has made
+  // its last claim before it counts itself out)
+  __syncthreads();
+  if (tid == 0 && atomicAdd(a.counter + 1, 1u) == gridDim.x - 1) {
+    a.counter[0] = 0u;
+    a.counter[1] = 0u;
   }
 }
 
