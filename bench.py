@@ -183,7 +183,7 @@ def per_kernel_launch_us(env, actions, T, stream, flush):
     from paper_2408_01584_b300 import gd
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(T)]
     gd.gd_reset(env.h, None)
-    flush.zero_()
+    flush_l2(flush)
     for t in range(T):
         ev[t][0].record(stream)
         gd.gd_step(env.h, actions[t], env.reward, env.done, env.world_done)
@@ -258,13 +258,23 @@ def whole_job_rate(units_per_rank, local_ms, world, device):
     return t, units_per_rank * world / (t / 1e3)
 
 
+def flush_l2(flush, k=0):
+    """Flush L2 (126 MB) on the current stream: write the first half of
+    `flush` (256 MB), then read the second half, so that the write's dirty
+    lines go back to HBM here and not inside the timed kernel that follows,
+    and L2 holds clean lines of neither its inputs nor its outputs."""
+    half = flush.numel() // 2
+    flush[:half].fill_(float(k))
+    flush[half:].sum()
+
+
 def _time_rollouts(run, n, stream, flush):
-    """Time n calls of run() with CUDA events on `stream`; L2 flushed (256 MB
-    write) before each, outside the timed interval.  Returns ms per call."""
+    """Time n calls of run() with CUDA events on `stream`; L2 flushed (see
+    flush_l2) before each, outside the timed interval.  Returns ms per call."""
     import torch
     ms = []
     for k in range(n):
-        flush.fill_(float(k))
+        flush_l2(flush, k)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         run()
@@ -601,7 +611,7 @@ def run_profile(args):
     with torch.cuda.stream(stream):
         env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED), **lidar, **shape)
         actions = torch.from_numpy(scenes.make_actions(T, env.A, 0)).to(dev)
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # see flush_l2
 
         def run():
             gd.gd_reset(env.h, None)
@@ -638,7 +648,7 @@ def run_ours(args, rank, world):
         A, F = env_b.A, env_b.F
         actions_h = torch.from_numpy(scenes.make_actions(T, A, seed=rank)).pin_memory()
         actions = actions_h.to(dev, non_blocking=True)
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # see flush_l2
         reward_d = torch.empty(T, A, dtype=torch.float32, device=dev)
         done_d = torch.empty(T, A, dtype=torch.uint8, device=dev)
     n_plain_launch = 6 + (1 if cfg["flags"] & gd.GD_AUTO_RESET else 0) + 1
@@ -721,7 +731,7 @@ def run_ours(args, rank, world):
                    "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
                    "n_partners": cfg["n_partners"], "episode_steps": T, "feat": F,
                    "step": "one 91-step episode of every world",
-                   "l2": "flushed (256 MB write) before each timed episode; observation output "
+                   "l2": "flushed (256 MB write, then 256 MB read) before each timed episode; observation output "
                          f"{A * F * 4 / 1e6:.0f} MB per simulator step > 126 MB L2",
                    "parallelism": f"independent worlds, {world} GPU(s), no collective"},
         "e2e": {"value": agent_steps / world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": METRIC,
