@@ -840,7 +840,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
-                         unsigned* clear_ocounters = nullptr) {
+                         unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
@@ -878,8 +878,8 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   a.rk_out = (ell && obs) ? rk_out : nullptr;
-  a.clear = clear_ocounters;
-  a.clear_n = clear_ocounters ? (int)OBS_STRIPES : 0;
+  a.clear = clear;
+  a.clear_n = clear ? clear_n : 0;
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
   const size_t smem = step_only ? env->step_smem : env->world_smem;
@@ -913,12 +913,15 @@ static LidarArgs lidar_args(const gd_env* env, const float* head, float* depth, 
 
 // Stand-alone LiDAR scan of every agent: persistent CTAs, warps take agents
 // from a counter (cleared first); the scene is read from global memory.
-static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls, cudaStream_t stream = nullptr) {
+// `cleared`: the launch before it (the split form's step) already cleared
+// the agent counter.
+static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* cls, cudaStream_t stream = nullptr,
+                         bool cleared = false) {
   if (!stream) stream = env->stream;
   const LidarArgs la = lidar_args(env, head, depth, cls);
   const int wp = env->lidar_obs_warps;
   const size_t smem = wp * (size_t)la.warp_bytes + lidar_dirs_bytes(env->lidar_n);
-  cudaMemsetAsync(env->lcounter, 0, sizeof(unsigned), stream);
+  if (!cleared) cudaMemsetAsync(env->lcounter, 0, sizeof(unsigned), stream);
   switch (wp) {
     case 12: k_lidar<12><<<env->lo_grid, 12 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
     case 8: k_lidar<8><<<env->lo_grid, 8 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
@@ -934,8 +937,11 @@ static void launch_world_lidar(gd_env* env, const float* actions, float* reward,
   if (!stream) stream = env->stream;
   if (env->lw_split) {
     // split form: the fused step without observation, then the stand-alone scan
-    if (do_step) launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream);
-    launch_lidar(env, head, depth, cls, stream);
+    // the step launch clears the scan's agent counter
+    if (do_step)
+      launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, nullptr, nullptr, 0.f,
+                   nullptr, nullptr, env->lcounter, 1);
+    launch_lidar(env, head, depth, cls, stream, do_step != 0);
     return;
   }
   FusedArgs a{};

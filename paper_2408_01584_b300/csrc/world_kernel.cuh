@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
     mbar_init(bar, 1);
     s_abort = 0;
   }
-  // the split form's observation counters, for the observation launch that follows
+  // the counters of the observation launch that follows (split forms)
   if (a.clear && blockIdx.x == 0 && tid < a.clear_n) a.clear[tid] = 0u;
   __syncthreads();
   unsigned phase = 0;
