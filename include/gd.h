@@ -82,7 +82,9 @@ typedef enum gd_status {
 #define GD_AUTO_RESET 0x4u       /* gd_step first resets worlds whose episode ended */
 #define GD_BATCHED 0x8u          /* persistent kernels: the step over a world work list, the observation
                                     over an agent counter (or fused with the step, obs_split = 0) */
-#define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward */
+#define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward, and each agent's K-th road
+                                    distance at every step of gd_rollout_objective (4 B x A x
+                                    episode_len), which bounds the backward's re-selection */
 #define GD_NONTRIVIAL_INIT 0x20u /* "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges"):
                                     agents within nontrivial_dist of their goal at the start are not
                                     controlled (GD_FLAG_STATIC) */
