@@ -162,6 +162,16 @@ class Clocks:
                 "source": "nvml 20 ms" if self.proc is None else "nvidia-smi 50 ms"}
 
 
+def workload_description(name, seed=0):
+    """The workload keys of the JSON line's config, shared by both arms."""
+    from paper_2408_01584_b300 import scenes
+    wl = scenes.WORKLOADS[name]
+    sc = scenes.workload_scene(name, seed)
+    return {"workload": name, "worlds": sc.num_worlds, "agents": sc.num_agents, "road_points": sc.num_road,
+            "k_road": wl["k_road"], "n_partners": wl["n_partners"], "episode_steps": wl["steps"],
+            "feat": 8 + 8 * wl["n_partners"] + 4 * wl["k_road"], "step": f"one {wl['steps']}-step episode of every world"}
+
+
 def workload_cfg(name):
     from paper_2408_01584_b300 import gd, scenes
     wl = scenes.WORKLOADS[name]
@@ -796,7 +806,8 @@ def main():
         out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC, "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": args.workload}, "cpu_baseline": cb,
+               "config": dict(workload_description(args.workload), form="the oracle on the host cores (see cpu_baseline)"),
+               "cpu_baseline": cb,
                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
