@@ -613,15 +613,28 @@ __device__ __forceinline__ bool offroad_cells_grouped(const int* __restrict__ cs
         if (gl >= o) incl += t;
       }
       const int total = __shfl_sync(gmask, incl, G - 1, G);
-      for (int f0 = 0; f0 < total; f0 += G) {
-        const int f = f0 + gl;
-        int p = -1;
+      // U segments per lane per round: their loads are all in flight before
+      // the first test
+      constexpr int U = 4;
+      for (int f0 = 0; f0 < total; f0 += U * G) {
+        int p[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) p[u] = -1;
         for (int k = 0; k < nr; ++k) {
           const int ik = __shfl_sync(gmask, incl, k, G), lk = __shfl_sync(gmask, len, k, G);
           const int sk = __shfl_sync(gmask, start, k, G);
-          if (f >= ik - lk && f < ik) p = sk + (f - (ik - lk));
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int f = f0 + u * G + gl;
+            if (f >= ik - lk && f < ik) p[u] = sk + (f - (ik - lk));
+          }
         }
-        if (p >= 0) hit |= box_seg_depth(cx, cy, ca, sa, hl, hw, segs[p]) > 0.f;
+        float4 sg[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) sg[u] = p[u] >= 0 ? segs[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (p[u] >= 0) hit |= box_seg_depth(cx, cy, ca, sa, hl, hw, sg[u]) > 0.f;
       }
     }
   }
