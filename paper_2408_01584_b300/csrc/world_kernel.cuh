@@ -115,9 +115,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // shared-memory latency, so registers are capped at 64 per thread (no
 // spills) to let all 32 be resident; the tile form keeps its registers (its
 // tile holds it at 2 CTAs per SM anyway).
-// Lanes per agent in the step's collision and (without the tile) road-edge
-// tests: WARP / STEP_G agents per warp at once.
+// Lanes per agent in the step's collision test (the column bounds take 6)
+// and, without the tile, its road-edge test: WARP / STEP_G (EDGE_G) agents
+// per warp at once.
 constexpr int STEP_G = 8;
+constexpr int EDGE_G = 4;
 
 template <int WARPS, bool LIDAR = false, bool LEAN = false>
 __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(DevEnv e, FusedArgs a) {
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       // road edges: from the shared-memory tile a warp per agent, ballot-OR
       // over the candidate segments; else from the edge grid (segments under
       // every cell their bounding box touches, so the cells under the box's
-      // own bounding box hold every segment it can cross), a group of STEP_G
+      // own bounding box hold every segment it can cross), a group of EDGE_G
       // lanes per agent
       if (!wait_tile()) break;
       if (use_tile) {
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         }
       } else {
         const GridDesc& eg = s_eg;
-        for (int b0 = wid * (WARP / STEP_G); b0 < n; b0 += WARPS * (WARP / STEP_G)) {
-          const int li = b0 + lane / STEP_G;
+        for (int b0 = wid * (WARP / EDGE_G); b0 < n; b0 += WARPS * (WARP / EDGE_G)) {
+          const int li = b0 + lane / EDGE_G;
           const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) && ag.ty[li] != GD_AGENT_PEDESTRIAN;
           float4 s = make_float4(0.f, 0.f, 0.f, 0.f), sc = s;
           float2 cs = make_float2(1.f, 0.f);
@@ -336,9 +338,9 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
             cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
             cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
           }
-          const bool off = offroad_cells_grouped<STEP_G>(e.ecell_start + eg.cell_base, eg.nx, e.esegs, cx0, cx1, cy0,
+          const bool off = offroad_cells_grouped<EDGE_G>(e.ecell_start + eg.cell_base, eg.nx, e.esegs, cx0, cx1, cy0,
                                                          cy1, s.x, s.y, cs.x, cs.y, 0.5f * sc.x, 0.5f * sc.y, lane);
-          if (li < n && (lane & (STEP_G - 1)) == 0) ag.offr[li] = (act && off) ? 1 : 0;
+          if (li < n && (lane & (EDGE_G - 1)) == 0) ag.offr[li] = (act && off) ? 1 : 0;
         }
       }
       __syncthreads();
