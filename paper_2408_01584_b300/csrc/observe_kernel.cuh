@@ -362,22 +362,38 @@ __device__ __forceinline__ void write_road(const WorldView& v, int K, int n_sel,
                                            int32_t* __restrict__ ridx, const float* __restrict__ w, float& acc) {
   const float2* __restrict__ xy = v.xy;
   // write K slots, coalesced, streaming (evict-first) stores; index and type
-  // come with the selection, so only the coordinates are read
-  for (int r = lane; r < K; r += WARP) {
-    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-    int idx = -1;
-    if (r < n_sel) {
-      const unsigned sk = sm.sel[r];
-      const float2 q = xy[sel_pos(sk)];
-      const float dx = q.x - ex, dy = q.y - ey;
-      o = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), (float)sel_type(sk), 1.f);
-      idx = (int)sel_index(sk);
+  // come with the selection, so only the coordinates are read, U slots per
+  // lane per round with their loads in flight together
+  constexpr int U = 4;
+  for (int r0 = 0; r0 < K; r0 += U * WARP) {
+    unsigned sk[U];
+    float2 q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u * WARP + lane;
+      sk[u] = r < n_sel ? sm.sel[r] : 0u;
     }
-    __stcs(out4 + r, o);
-    if (ridx) ridx[r] = idx;
-    if (LOSS) {
-      const float4 wr = __ldg(reinterpret_cast<const float4*>(w) + r);
-      acc = fmaf(wr.x, o.x, fmaf(wr.y, o.y, fmaf(wr.z, o.z, fmaf(wr.w, o.w, acc))));
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      q[u] = (r0 + u * WARP + lane < n_sel) ? xy[sel_pos(sk[u])] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = r0 + u * WARP + lane;
+      if (r < K) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        int idx = -1;
+        if (r < n_sel) {
+          const float dx = q[u].x - ex, dy = q[u].y - ey;
+          o = make_float4(rot_x(c, s, dx, dy), rot_y(c, s, dx, dy), (float)sel_type(sk[u]), 1.f);
+          idx = (int)sel_index(sk[u]);
+        }
+        __stcs(out4 + r, o);
+        if (ridx) ridx[r] = idx;
+        if (LOSS) {
+          const float4 wr = __ldg(reinterpret_cast<const float4*>(w) + r);
+          acc = fmaf(wr.x, o.x, fmaf(wr.y, o.y, fmaf(wr.z, o.z, fmaf(wr.w, o.w, acc))));
+        }
+      }
     }
   }
 }
