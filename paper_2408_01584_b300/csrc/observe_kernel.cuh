@@ -407,19 +407,24 @@ __device__ __forceinline__ int select_partners(const WorldView& v, int li, int P
   if (P == 0) return 0;
   int n = 0;
   const unsigned lt = (1u << lane) - 1u;
-  for (int j0 = 0; j0 < v.n; j0 += WARP) {
-    const int j = j0 + lane;
-    bool ok = false;
-    unsigned long long key = 0;
-    if (j < v.n && j != li && !(v.flags[j] & GD_FLAG_DONE)) {
-      const float4 q = v.state[j];
-      const float d2 = dist2(q.x - ex, q.y - ey);
-      ok = d2 <= R2;
-      key = partner_key(d2, (unsigned)j);
+  // two candidates per lane per round: both loads go out before either test
+  for (int j0 = 0; j0 < v.n; j0 += 2 * WARP) {
+    bool live[2];
+    float4 q[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = j0 + u * WARP + lane;
+      live[u] = j < v.n && j != li && !(v.flags[j] & GD_FLAG_DONE);
+      q[u] = live[u] ? v.state[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, ok);
-    if (ok) sm.u.pkeys[n + __popc(m & lt)] = key;
-    n += __popc(m);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const float d2 = dist2(q[u].x - ex, q[u].y - ey);
+      const bool ok = live[u] && d2 <= R2;
+      const unsigned m = __ballot_sync(0xffffffffu, ok);
+      if (ok) sm.u.pkeys[n + __popc(m & lt)] = partner_key(d2, (unsigned)(j0 + u * WARP + lane));
+      n += __popc(m);
+    }
   }
   __syncwarp();
   const int n_sel = min(P, n);
@@ -501,6 +506,8 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
   if (f & GD_FLAG_DONE) {
     acc = write_done_row<LOSS>(e, f, obs_row, ridx, pidx, w, lane);
   } else {
+    // the anchor is read here, ahead of the row's stores that it could alias
+    const float4 an = anchor ? *anchor : make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
     const float4 st = v.state[li];
     const float4 sc = v.stat[li];
     float c, s;
@@ -528,7 +535,6 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     // K points: the selection over it equals the one over the whole radius.
     float Rs = e.R, Rs2 = e.R2;
     if (anchor) {
-      const float4 an = *anchor;
       const float r = an.z + sqrtf(dist2(st.x - an.x, st.y - an.y)) + 1e-3f;
       if (r < e.R) {
         Rs = r;
