@@ -497,7 +497,8 @@ template <bool LOSS>
 __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
                                                ObsWarpSmem& sm, int lane, float4* anchor,
-                                               const float* __restrict__ w = nullptr, float* rk_slot = nullptr) {
+                                               const float* __restrict__ w = nullptr, float* rk_slot = nullptr,
+                                               const float4* own = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
@@ -508,8 +509,9 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
   } else {
     // the anchor is read here, ahead of the row's stores that it could alias
     const float4 an = anchor ? *anchor : make_float4(0.f, 0.f, __int_as_float(0x7f800000), 0.f);
-    const float4 st = v.state[li];
-    const float4 sc = v.stat[li];
+    // own: the agent's state and extents/goal, read by the caller already
+    const float4 st = own ? own[0] : v.state[li];
+    const float4 sc = own ? own[1] : v.stat[li];
     float c, s;
     if (v.cs) {
       c = v.cs[li].x;
@@ -672,6 +674,8 @@ __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* _
                                                 int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
                                                 ObsWarpSmem& sm, int lane, const float* __restrict__ wrow = nullptr,
                                                 float* rk_slot = nullptr) {
+  // the agent's own state first: it does not wait for the world's loads
+  const float4 own[2] = {e.state[i], e.stat[i]};
   const int w = e.agent_world[i];
   const int a0 = e.agent_off[w];
   WorldView v;
@@ -684,7 +688,7 @@ __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* _
   v.g = e.rgrid[w];
   return observe_agent<LOSS>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
                              partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
-                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot);
+                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own);
 }
 
 // Per-stage form: one warp per agent over the whole batch.  Dynamic shared
