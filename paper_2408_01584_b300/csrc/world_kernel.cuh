@@ -219,13 +219,21 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       uint32_t key = 0;
       if (tid < n) {
         const int i = a0 + tid;
-        float4 s = reset ? e.init_state[i] : e.state[i];
-        uint8_t f = reset ? e.init_flags[i] : e.flags[i];
+        // every load of the agent goes out at once; a world that restarts
+        // (rare) then reads its initial snapshot
+        float4 s = e.state[i];
+        uint8_t f = e.flags[i];
+        const float2 u = a.actions[i];
+        const float4 sci = e.stat[i];
+        const uint8_t ty = e.type[i];
+        if (reset) {
+          s = e.init_state[i];
+          f = e.init_flags[i];
+        }
         ag.act0[tid] = !(f & GD_FLAG_DONE);
         if (!(f & GD_FLAG_DONE)) {
           // uncontrolled agents (GD_FLAG_STATIC) stay in the grid but do not move
-          const float2 u = a.actions[i];
-          if (!(f & GD_FLAG_STATIC) && !dynamics_step(e.dyn, s, u.x, u.y, e.stat[i].x, e.dt, e.vmax))
+          if (!(f & GD_FLAG_STATIC) && !dynamics_step(e.dyn, s, u.x, u.y, sci.x, e.dt, e.vmax))
             atomicOr(e.err, ERR_ACTION);
           act = true;
           key = agent_cell_key((int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f),
@@ -235,9 +243,9 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         float sn, cn;
         sincosf(s.z, &sn, &cn);
         ag.cs[tid] = make_float2(cn, sn);
-        ag.sc[tid] = e.stat[i];
+        ag.sc[tid] = sci;
         ag.fl[tid] = f;
-        ag.ty[tid] = e.type[i];
+        ag.ty[tid] = ty;
         ag.key[tid] = key;
       }
       const int nact = __syncthreads_count(act);
