@@ -128,7 +128,7 @@ struct gd_env {
   float2* ray_dirs = nullptr;   // [n] (cos, sin) of the ray angles in the sensor frame
   int lidar_obs_warps = 12;     // stand-alone k_lidar CTA size (warps: 12, 8 or 4)
   int lo_grid = 0;              // its persistent CTAs
-  unsigned* lcounter = nullptr; // its agent counter
+  unsigned* lcounter = nullptr; // its agent counters (LIDAR_STRIPES)
   int lw_split = 0;             // batched form: 1 = k_world step + k_lidar, 0 = one fused k_world
   int lw_warps = 8;             // fused LiDAR kernel CTA size (4, 8 or 12 warps)
   int lw_notile = 0;            // 1: no shared-memory road tile (more warps per SM)
@@ -736,7 +736,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaGetDevice(&dev));
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     env->lw_split = cfg->lidar_split;
-    GD_TRY(dev_alloc(env, &env->lcounter, 1));
+    GD_TRY(dev_alloc(env, &env->lcounter, LIDAR_STRIPES));
     // stand-alone scan: the most warps whose shared memory fits one CTA
     int wp = 12;
     while (wp > 4 && wp * lidar_warp_bytes(n) + lidar_dirs_bytes(n) + 1024 > (size_t)smem_blk) wp -= 4;
@@ -921,7 +921,7 @@ static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* 
   const LidarArgs la = lidar_args(env, head, depth, cls);
   const int wp = env->lidar_obs_warps;
   const size_t smem = wp * (size_t)la.warp_bytes + lidar_dirs_bytes(env->lidar_n);
-  if (!cleared) cudaMemsetAsync(env->lcounter, 0, sizeof(unsigned), stream);
+  if (!cleared) cudaMemsetAsync(env->lcounter, 0, LIDAR_STRIPES * sizeof(unsigned), stream);
   switch (wp) {
     case 12: k_lidar<12><<<env->lo_grid, 12 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
     case 8: k_lidar<8><<<env->lo_grid, 8 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
@@ -940,7 +940,7 @@ static void launch_world_lidar(gd_env* env, const float* actions, float* reward,
     // the step launch clears the scan's agent counter
     if (do_step)
       launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, nullptr, nullptr, 0.f,
-                   nullptr, nullptr, env->lcounter, 1);
+                   nullptr, nullptr, env->lcounter, (int)LIDAR_STRIPES);
     launch_lidar(env, head, depth, cls, stream, do_step != 0);
     return;
   }

@@ -40,6 +40,7 @@ constexpr float LIDAR_NEAR_FULL = 0.1f;      // m: obstacles this close are test
 constexpr float LIDAR_PAD = 1e-5f;           // rad added at both ends of an arc (atan2f and rotation rounding)
 constexpr unsigned LIDAR_EMPTY = 0xffffffffu;
 constexpr float LIDAR_PI = 3.14159265358979f;
+constexpr unsigned LIDAR_STRIPES = 16;       // claim counters of the stand-alone scan
 
 struct LidarWarpHead {
   float4 ga[LIDAR_ITEMS];        // segment: (w', d') in the sensor frame; box: (o, cos psi, sin psi)
@@ -482,7 +483,7 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
 
 // Stand-alone scan of every agent (the per-stage form, and the second
 // launch of the split batched form): persistent CTAs, each warp takes the
-// next agent from a global counter, so no warp waits for another.  The
+// next agent from one of LIDAR_STRIPES counters, so no warp waits for another.  The
 // scene is read from global memory.  Dynamic shared memory: WARPS *
 // warp_bytes, then the ray directions.
 template <int WARPS>
@@ -497,11 +498,23 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_lidar(DevEnv e, LidarArgs la,
   unsigned char* base = lidar_smem_raw + (size_t)wib * la.warp_bytes;
   LidarWarpHead& h = *reinterpret_cast<LidarWarpHead*>(base);
   unsigned* keys = reinterpret_cast<unsigned*>(base + sizeof(LidarWarpHead));
+  // claims striped over LIDAR_STRIPES counters (warp g draws agents c,
+  // c + LIDAR_STRIPES, ... from counter c = g mod LIDAR_STRIPES), so they do
+  // not all queue on one address
+  const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % LIDAR_STRIPES;
   for (;;) {
-    int i = 0;
-    if (lane == 0) i = (int)atomicAdd(counter, 1u);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= e.A) break;
+    unsigned k = 0;
+    if (lane == 0) k = atomicAdd(counter + c, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    const unsigned iu = c + LIDAR_STRIPES * k;
+    if (iu >= (unsigned)e.A) break;
+    const int i = (int)iu;
+    if (e.flags[i] & GD_FLAG_DONE) {
+      // removed from the scene: an all-zero row, no world loads
+      lidar_write(keys, la.fan.n, e.R, true, la.depth + (size_t)i * la.fan.n,
+                  la.cls ? la.cls + (size_t)i * la.fan.n : nullptr, lane);
+      continue;
+    }
     const int w = e.agent_world[i];
     const int a0 = e.agent_off[w];
     WorldView v;
