@@ -1,17 +1,19 @@
-// Fused per-world kernel (the batched form): one persistent launch runs the
-// whole step -- masked reset, dynamics (App. B or the simplified model of
-// Sec. 3.2), agent grid and
-// box collision, road-edge test, goal / reward / done (Sec. 3.2) -- and the
-// observation of every world, taking worlds from a work list with an
-// atomic counter (no grid-wide synchronisation).
+// Per-world kernel of the batched form: one persistent launch runs the whole
+// step -- masked reset, dynamics (App. B or the simplified model of Sec.
+// 3.2), agent grid and box collision, road-edge test, goal / reward / done
+// (Sec. 3.2) -- of every world, and (the fused form) its observation, taking
+// worlds from a work list: each CTA's first world by its index, the rest
+// from an atomic counter that the last CTA out leaves at zero for the next
+// launch (no grid-wide synchronisation, no memset between launches).  In the
+// split form the observation is a second launch, k_observe_split.
 //
-// Per world the CTA keeps the agents in shared memory and copies the
-// world's cell-sorted road points into a shared-memory tile with one
-// cp.async.bulk (TMA) copy, issued first so that it overlaps the step
-// stages.  Worlds whose road does not fit the tile read it from global
-// memory instead.  The mbarrier wait is bounded: after ~2 s the CTA sets
-// ERR_TIMEOUT, waits once more (bounded) for its copy and leaves; other
-// CTAs keep draining the work list.
+// Per world the CTA keeps the agents in shared memory and, when it pays,
+// copies the world's cell-sorted road points into a shared-memory tile with
+// one cp.async.bulk (TMA) copy, issued first so that it overlaps the step
+// stages; otherwise the road is read from global memory (the road-edge test
+// from the edge grid).  The mbarrier wait is bounded: after ~2 s the CTA
+// sets ERR_TIMEOUT, waits once more (bounded) for its copy and leaves the
+// world loop; other CTAs keep draining the work list.
 #pragma once
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
