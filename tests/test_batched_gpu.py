@@ -182,9 +182,11 @@ def test_autotune_then_rollout_matches_plain():
     print("autotuned:", info.block_size, info.road_cell, info.topk_strategy)
 
 
-def test_rollout_host_equals_device_rollout():
+@pytest.mark.parametrize("split", [1, 0])
+def test_rollout_host_equals_device_rollout(split):
     """gd_rollout_host (pinned host actions / rewards / done, copies overlapped
-    with the steps) gives the same results as gd_rollout on device buffers."""
+    with the steps) gives the same results as gd_rollout on device buffers
+    (split form), with the split or the fused observation."""
     from paper_2408_01584_b300 import gd
     sc = small_scene(seed=31)
     ocfg = OracleConfig(k_road=64, n_partners=16, episode_len=9, term_collision=True, term_offroad=True,
@@ -193,7 +195,7 @@ def test_rollout_host_equals_device_rollout():
     acts = scenes.make_actions(T, A, 31)
     outs = []
     for host in (False, True):
-        env = gd.Env(sc, **_batched(ocfg))
+        env = gd.Env(sc, **_batched(ocfg, obs_split=split if host else 1))
         if host:
             a_h = torch.from_numpy(acts).pin_memory()
             r_h = torch.empty(T, A).pin_memory()
