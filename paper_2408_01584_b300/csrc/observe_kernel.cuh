@@ -603,68 +603,6 @@ __device__ __forceinline__ bool offroad_from_block(const WorldView& v, float cx,
   return __any_sync(0xffffffffu, hit);
 }
 
-// Road-edge crossing for WARP / G boxes at once, from a grid of segments in
-// global memory (cst: the world's cell starts, nx cells per row; segs: the
-// segments listed under the cells): lane group q = lane / G (G lanes, a power
-// of two <= 32) tests its own box against the segments of cells [cx0, cx1] x
-// [cy0, cy1] (an empty range when the group has no box).  Lane r of a group
-// reads the bounds of row r and the rows' segments are walked as one list,
-// so the groups' loads go out in the same instructions and their latencies
-// overlap.  Every lane of the warp must call it; each lane gets its group's
-// result.
-template <int G>
-__device__ __forceinline__ bool offroad_cells_grouped(const int* __restrict__ cst, int nx,
-                                                      const float4* __restrict__ segs, int cx0, int cx1, int cy0,
-                                                      int cy1, float cx, float cy, float ca, float sa, float hl,
-                                                      float hw, int lane) {
-  const int gl = lane & (G - 1);
-  const unsigned gmask = G == WARP ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  bool hit = false;
-  if (cx0 <= cx1) {
-    // group-uniform from here on: the group's lanes share the cell range
-    for (int r0 = cy0; r0 <= cy1; r0 += G) {
-      const int nr = min(cy1 - r0 + 1, G);
-      int start = 0, len = 0;
-      if (gl < nr) {
-        const int* row = cst + (r0 + gl) * nx;
-        start = row[cx0];
-        len = row[cx1 + 1] - start;
-      }
-      int incl = len;
-#pragma unroll
-      for (int o = 1; o < G; o <<= 1) {
-        const int t = __shfl_up_sync(gmask, incl, o, G);
-        if (gl >= o) incl += t;
-      }
-      const int total = __shfl_sync(gmask, incl, G - 1, G);
-      // U segments per lane per round: their loads are all in flight before
-      // the first test
-      constexpr int U = 4;
-      for (int f0 = 0; f0 < total; f0 += U * G) {
-        int p[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) p[u] = -1;
-        for (int k = 0; k < nr; ++k) {
-          const int ik = __shfl_sync(gmask, incl, k, G), lk = __shfl_sync(gmask, len, k, G);
-          const int sk = __shfl_sync(gmask, start, k, G);
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int f = f0 + u * G + gl;
-            if (f >= ik - lk && f < ik) p[u] = sk + (f - (ik - lk));
-          }
-        }
-        float4 sg[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) sg[u] = p[u] >= 0 ? segs[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (p[u] >= 0) hit |= box_seg_depth(cx, cy, ca, sa, hl, hw, sg[u]) > 0.f;
-      }
-    }
-  }
-  return (__ballot_sync(0xffffffffu, hit) & gmask) != 0u;
-}
-
 // Observation row of agent i with everything read from global memory (the
 // world's agents and road block through L1/L2).
 // With LOSS, returns (to every lane) wrow . row for the weight row wrow,

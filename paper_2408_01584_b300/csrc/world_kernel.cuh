@@ -62,6 +62,8 @@ struct FusedAgents {
   uint8_t coll[GD_MAX_AGENTS_PER_WORLD];
   uint8_t offr[GD_MAX_AGENTS_PER_WORLD];
   uint8_t act0[GD_MAX_AGENTS_PER_WORLD];     // in the scene at the start of the step
+  int eoff[GD_MAX_AGENTS_PER_WORLD];         // road-edge test: the agent's first (agent, segment) pair
+  int2 erow[GD_MAX_AGENTS_PER_WORLD][3];     // road-edge test: (first segment, count) per cell row
 };
 
 // ---- TMA bulk copy + mbarrier (inline PTX) --------------------------------
@@ -117,11 +119,14 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // shared-memory latency, so registers are capped at 64 per thread (no
 // spills) to let all 32 be resident; the tile form keeps its registers (its
 // tile holds it at 2 CTAs per SM anyway).
-// Lanes per agent in the step's collision test (the column bounds take 6)
-// and, without the tile, its road-edge test: WARP / STEP_G (EDGE_G) agents
-// per warp at once.
+// Lanes per agent in the step's collision test (the column bounds take 6):
+// WARP / STEP_G agents per warp at once.
 constexpr int STEP_G = 8;
-constexpr int EDGE_G = 4;
+// Road-edge test without the tile: cell rows per agent read up front (a box
+// over more rows walks the rest itself) and (agent, segment) pairs per
+// thread per round.
+constexpr int EDGE_ROWS = 3;
+constexpr int EDGE_U = 4;
 
 template <int WARPS, bool LIDAR = false, bool LEAN = false>
 __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(DevEnv e, FusedArgs a) {
@@ -134,7 +139,9 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
   __shared__ int s_nact;
   __shared__ int s_abort;
   __shared__ int s_next;
+  __shared__ int s_esum[WARPS];  // road-edge test: pairs per warp
   __shared__ GridDesc s_eg;   // the world's edge-grid descriptor, read early (used after the collision stage)
+  static_assert(WARPS * 32 >= GD_MAX_AGENTS_PER_WORLD, "the step stages take one thread per agent");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   ObsWarpSmem& osm = reinterpret_cast<ObsWarpSmem*>(warp_base)[wid];
   unsigned char* lbase = warp_base + (size_t)wid * (size_t)a.lidar.warp_bytes;
@@ -315,8 +322,11 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       // road edges: from the shared-memory tile a warp per agent, ballot-OR
       // over the candidate segments; else from the edge grid (segments under
       // every cell their bounding box touches, so the cells under the box's
-      // own bounding box hold every segment it can cross), a group of EDGE_G
-      // lanes per agent
+      // own bounding box hold every segment it can cross), over the world's
+      // (agent, segment) pairs: each agent's thread reads the segment ranges
+      // of its cell rows, a block scan lays the agents' pairs end to end, and
+      // every thread tests EDGE_U pairs per round, so the whole world's
+      // segment loads go out in one or two rounds whatever the agents' counts
       if (!wait_tile()) break;
       if (use_tile) {
         for (int li = wid; li < n; li += WARPS) {
@@ -331,26 +341,108 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         }
       } else {
         const GridDesc& eg = s_eg;
-        for (int b0 = wid * (WARP / EDGE_G); b0 < n; b0 += WARPS * (WARP / EDGE_G)) {
-          const int li = b0 + lane / EDGE_G;
-          const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC)) && ag.ty[li] != GD_AGENT_PEDESTRIAN;
-          float4 s = make_float4(0.f, 0.f, 0.f, 0.f), sc = s;
-          float2 cs = make_float2(1.f, 0.f);
-          int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
-          if (act) {
-            s = ag.st[li];
-            sc = ag.sc[li];
-            cs = ag.cs[li];
+        const int* __restrict__ cst = e.ecell_start + eg.cell_base;
+        int cnt = 0;
+        if (tid < n) {
+          bool hit = false;
+          int2 rw[EDGE_ROWS];
+#pragma unroll
+          for (int r = 0; r < EDGE_ROWS; ++r) rw[r] = make_int2(0, 0);
+          if (!(ag.fl[tid] & (GD_FLAG_DONE | GD_FLAG_STATIC)) && ag.ty[tid] != GD_AGENT_PEDESTRIAN) {
+            const float4 s = ag.st[tid];
+            const float4 sc = ag.sc[tid];
+            const float2 cs = ag.cs[tid];
             const float hl = 0.5f * sc.x, hw = 0.5f * sc.y;
             const float ex = hl * fabsf(cs.x) + hw * fabsf(cs.y) + 1e-3f, ey = hl * fabsf(cs.y) + hw * fabsf(cs.x) + 1e-3f;
-            cx0 = (int)clampf(floorf((s.x - ex - eg.ox) * eg.inv_cs), 0.f, (float)(eg.nx - 1));
-            cx1 = (int)clampf(floorf((s.x + ex - eg.ox) * eg.inv_cs), -1.f, (float)(eg.nx - 1));
-            cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
-            cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
+            const int cx0 = (int)clampf(floorf((s.x - ex - eg.ox) * eg.inv_cs), 0.f, (float)(eg.nx - 1));
+            const int cx1 = (int)clampf(floorf((s.x + ex - eg.ox) * eg.inv_cs), -1.f, (float)(eg.nx - 1));
+            const int cy0 = (int)clampf(floorf((s.y - ey - eg.oy) * eg.inv_cs), 0.f, (float)(eg.ny - 1));
+            const int cy1 = (int)clampf(floorf((s.y + ey - eg.oy) * eg.inv_cs), -1.f, (float)(eg.ny - 1));
+            if (cx0 <= cx1) {
+              int b[EDGE_ROWS], en[EDGE_ROWS];
+#pragma unroll
+              for (int r = 0; r < EDGE_ROWS; ++r) {
+                b[r] = en[r] = 0;
+                if (cy0 + r <= cy1) {
+                  const int* row = cst + (cy0 + r) * eg.nx;
+                  b[r] = row[cx0];
+                  en[r] = row[cx1 + 1];
+                }
+              }
+#pragma unroll
+              for (int r = 0; r < EDGE_ROWS; ++r) rw[r] = make_int2(b[r], en[r] - b[r]);
+              // rows past EDGE_ROWS (boxes over EDGE_ROWS cells high): this thread walks them
+              for (int cy = cy0 + EDGE_ROWS; cy <= cy1; ++cy) {
+                const int* row = cst + cy * eg.nx;
+                for (int q = row[cx0], qe = row[cx1 + 1]; q < qe; ++q)
+                  hit |= box_seg_depth(s.x, s.y, cs.x, cs.y, hl, hw, e.esegs[q]) > 0.f;
+              }
+            }
           }
-          const bool off = offroad_cells_grouped<EDGE_G>(e.ecell_start + eg.cell_base, eg.nx, e.esegs, cx0, cx1, cy0,
-                                                         cy1, s.x, s.y, cs.x, cs.y, 0.5f * sc.x, 0.5f * sc.y, lane);
-          if (li < n && (lane & (EDGE_G - 1)) == 0) ag.offr[li] = (act && off) ? 1 : 0;
+#pragma unroll
+          for (int r = 0; r < EDGE_ROWS; ++r) {
+            ag.erow[tid][r] = rw[r];
+            cnt += rw[r].y;
+          }
+          ag.offr[tid] = hit ? 1 : 0;
+        }
+        // exclusive scan of the counts: the agents' pairs laid end to end
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < WARP; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == WARP - 1) s_esum[wid] = incl;
+        __syncthreads();
+        int total = 0, base = 0;
+#pragma unroll
+        for (int q = 0; q < WARPS; ++q) {
+          const int t = s_esum[q];
+          base += q < wid ? t : 0;
+          total += t;
+        }
+        if (tid < n) ag.eoff[tid] = base + incl - cnt;
+        __syncthreads();
+        // EDGE_U pairs per thread per round, their loads in flight together
+        for (int f0 = 0; f0 < total; f0 += EDGE_U * WARPS * WARP) {
+          int p[EDGE_U], who[EDGE_U];
+#pragma unroll
+          for (int u = 0; u < EDGE_U; ++u) {
+            const int f = f0 + u * WARPS * WARP + tid;
+            p[u] = -1;
+            who[u] = 0;
+            if (f < total) {
+              // the last agent whose pairs start at or before f owns pair f
+              int lo = 0, hi = n - 1;
+              while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ag.eoff[mid] <= f) lo = mid; else hi = mid - 1;
+              }
+              int rel = f - ag.eoff[lo];
+              int q = -1;
+#pragma unroll
+              for (int r = 0; r < EDGE_ROWS; ++r) {
+                const int2 rr = ag.erow[lo][r];
+                if (q < 0 && rel < rr.y) q = rr.x + rel;
+                if (q < 0) rel -= rr.y;
+              }
+              p[u] = q;
+              who[u] = lo;
+            }
+          }
+          float4 sg[EDGE_U];
+#pragma unroll
+          for (int u = 0; u < EDGE_U; ++u) sg[u] = p[u] >= 0 ? e.esegs[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < EDGE_U; ++u) {
+            if (p[u] < 0) continue;
+            const int li = who[u];
+            const float4 s = ag.st[li];
+            const float4 sc = ag.sc[li];
+            const float2 cs = ag.cs[li];
+            if (box_seg_depth(s.x, s.y, cs.x, cs.y, 0.5f * sc.x, 0.5f * sc.y, sg[u]) > 0.f) ag.offr[li] = 1;
+          }
         }
       }
       __syncthreads();

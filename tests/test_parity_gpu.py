@@ -140,3 +140,43 @@ def test_full_size_plain_1024x64_sampled_steps():
     agents = np.sort(rng.choice(sc.num_agents, 4096, replace=False))
     _, ex = teacher_forced(sc, ocfg, 3, acts, obs_every=1, obs_agents=agents)
     print("exceptions:", len(ex))
+
+
+def _long_box_scene(seed):
+    # one world: horizontal road edges 9 m apart and two vertical ones, each
+    # its own polyline, 3 m between points; boxes 5 to 45 m long at headings
+    # that put them over 1 to 6 rows of the 8 m edge grid
+    rng = np.random.default_rng(seed)
+    pts, poly = [], 0
+    for k in range(-4, 5):
+        pts += [(float(x), 9.0 * k + 0.3, 1, poly) for x in np.arange(-60.0, 61.0, 3.0)]
+        poly += 1
+    for x0 in (-50.0, 50.0):
+        pts += [(x0, float(y), 1, poly) for y in np.arange(-45.0, 46.0, 3.0)]
+        poly += 1
+    pts += [(float(x), float(y), 0, poly + 1) for x, y in rng.uniform(-55, 55, (200, 2))]
+    agents = []
+    for q in range(40):
+        length = float((5.0, 12.0, 20.0, 30.0, 45.0)[q % 5])
+        theta = float((0.0, np.pi / 2, np.pi / 3, 1.2, -np.pi / 2, 2.9)[q % 6])
+        x, y = rng.uniform(-40, 40), rng.uniform(-32, 32)
+        agents.append((x, y, theta, 1.0, length, 2.5, x + 30.0, y, 0))
+    return tiny_scene([(agents, pts)])
+
+
+@pytest.mark.parametrize("form", ["per_stage", "batched_edge_grid", "batched_tile"])
+def test_road_edges_under_long_boxes(form):
+    # the road-edge test of boxes that span more cell rows than the step reads
+    # up front, against the oracle's test over every edge segment
+    from paper_2408_01584_b300 import gd
+    sc = _long_box_scene(3)
+    ocfg = OracleConfig(k_road=16, n_partners=7, episode_len=91)
+    over = {} if form == "per_stage" else dict(flags=gd_kwargs(ocfg)["flags"] | gd.GD_BATCHED,
+                                              road_no_tile=1 if form == "batched_edge_grid" else 0)
+    acts = scenes.make_actions(6, sc.num_agents, 3)
+    env, ex = teacher_forced(sc, ocfg, 6, acts, obs_every=3, gd_over=over)
+    flags = _np(env.get_state()[1])
+    n_off = int(np.sum((flags & 8) != 0))
+    assert 0 < n_off < sc.num_agents, n_off    # both outcomes occur
+    print("offroad:", n_off, "exceptions:", ex.items)
+    env.close()
