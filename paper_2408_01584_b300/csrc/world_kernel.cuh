@@ -62,8 +62,8 @@ struct FusedAgents {
   uint8_t coll[GD_MAX_AGENTS_PER_WORLD];
   uint8_t offr[GD_MAX_AGENTS_PER_WORLD];
   uint8_t act0[GD_MAX_AGENTS_PER_WORLD];     // in the scene at the start of the step
-  int eoff[GD_MAX_AGENTS_PER_WORLD];         // road-edge test: the agent's first (agent, segment) pair
-  int2 erow[GD_MAX_AGENTS_PER_WORLD][3];     // road-edge test: (first segment, count) per cell row
+  int poff[GD_MAX_AGENTS_PER_WORLD];         // collision / road-edge test: the agent's first pair
+  int2 prow[GD_MAX_AGENTS_PER_WORLD][3];     // collision / road-edge test: (first, count) per range
 };
 
 // ---- TMA bulk copy + mbarrier (inline PTX) --------------------------------
@@ -119,13 +119,11 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // shared-memory latency, so registers are capped at 64 per thread (no
 // spills) to let all 32 be resident; the tile form keeps its registers (its
 // tile holds it at 2 CTAs per SM anyway).
-// Lanes per agent in the step's collision test (the column bounds take 6):
-// WARP / STEP_G agents per warp at once.
-constexpr int STEP_G = 8;
 // Road-edge test without the tile: cell rows per agent read up front (a box
-// over more rows walks the rest itself) and (agent, segment) pairs per
-// thread per round.
+// over more rows walks the rest itself; the pair lists hold 3 ranges per
+// agent) and (agent, segment) pairs per thread per round.
 constexpr int EDGE_ROWS = 3;
+static_assert(EDGE_ROWS == 3, "the pair lists hold three ranges per agent");
 constexpr int EDGE_U = 4;
 
 template <int WARPS, bool LIDAR = false, bool LEAN = false>
@@ -139,7 +137,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
   __shared__ int s_nact;
   __shared__ int s_abort;
   __shared__ int s_next;
-  __shared__ int s_esum[WARPS];  // road-edge test: pairs per warp
+  __shared__ int s_psum[WARPS];  // pair lists: pairs per warp
   __shared__ GridDesc s_eg;   // the world's edge-grid descriptor, read early (used after the collision stage)
   static_assert(WARPS * 32 >= GD_MAX_AGENTS_PER_WORLD, "the step stages take one thread per agent");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -221,6 +219,43 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       }
       return true;
     };
+    // Pair lists of the collision and road-edge tests: thread tid < n holds
+    // the cnt pairs of agent tid as up to 3 ranges (first, count) in
+    // ag.prow[tid].  lay_pairs lays the agents' pairs end to end (ag.poff:
+    // exclusive offsets, by a block scan) and returns the world's total;
+    // pair_at gives pair f's agent (the last whose pairs start at or before
+    // f) and its index in the agent's ranges.
+    auto lay_pairs = [&](int cnt) -> int {
+      const int incl = warp_incl_scan(cnt, lane);
+      if (lane == WARP - 1) s_psum[wid] = incl;
+      __syncthreads();
+      int total = 0, base = 0;
+#pragma unroll
+      for (int q = 0; q < WARPS; ++q) {
+        const int t = s_psum[q];
+        base += q < wid ? t : 0;
+        total += t;
+      }
+      if (tid < n) ag.poff[tid] = base + incl - cnt;
+      __syncthreads();
+      return total;
+    };
+    auto pair_at = [&](int f, int& who) -> int {
+      int lo = 0, hi = n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ag.poff[mid] <= f) lo = mid; else hi = mid - 1;
+      }
+      who = lo;
+      int rel = f - ag.poff[lo], q = -1;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int2 rr = ag.prow[lo][r];
+        if (q < 0 && rel < rr.y) q = rr.x + rel;
+        if (q < 0) rel -= rr.y;
+      }
+      return q;
+    };
     if (a.do_step) {
       const bool reset = (e.cflags & GD_AUTO_RESET) && e.world_done[w];
       const float inv = 1.f / e.agent_cell;
@@ -266,57 +301,61 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
       if (act) ag.key[rank] = key;
       if (tid == 0) s_nact = nact;
       __syncthreads();
-      // collision: a group of STEP_G lanes per agent (WARP / STEP_G agents
-      // per warp at once), OR over the candidates of the group
+      // collision over the world's (agent, candidate) pairs: each active
+      // agent's thread bounds the three neighbouring columns of the agent
+      // grid (rows cy - 1 .. cy + 1 of a column are one run of the sorted
+      // keys; six independent binary searches), the pairs are laid end to
+      // end and every thread tests one per round
       {
-        const int gl = lane & (STEP_G - 1);
-        const unsigned gmask = ((1u << STEP_G) - 1u) << (lane & ~(STEP_G - 1));
-        for (int b0 = wid * (WARP / STEP_G); b0 < n; b0 += WARPS * (WARP / STEP_G)) {
-          const int li = b0 + lane / STEP_G;
-          const bool act = li < n && !(ag.fl[li] & (GD_FLAG_DONE | GD_FLAG_STATIC));
-          float4 s = make_float4(0.f, 0.f, 0.f, 0.f), sc = s;
-          float ca = 1.f, sa = 0.f;
-          // lanes 0..5 of the group bound the three neighbouring columns in
-          // parallel: lane 2k / 2k+1 = lower / upper bound of column cx - 1 + k
-          int bound = 0;
-          if (act) {
-            s = ag.st[li];
-            sc = ag.sc[li];
-            ca = ag.cs[li].x;
-            sa = ag.cs[li].y;
+        int cnt = 0;
+        if (tid < n) {
+          int lo[6], hi[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) lo[k] = hi[k] = 0;
+          if (!(ag.fl[tid] & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
+            const float4 s = ag.st[tid];
             const int cx = (int)clampf(floorf((s.x - g.ox) * inv), 0.f, 4095.f);
             const int cy = (int)clampf(floorf((s.y - g.oy) * inv), 0.f, 4095.f);
-            if (gl < 6) {
-              const int c = cx - 1 + (gl >> 1);
-              if (c >= 0 && c <= 4095) {
-                const bool upper = gl & 1;
-                const uint32_t v =
-                    upper ? agent_cell_key(c, min(cy + 1, 4095), 255) : agent_cell_key(c, max(cy - 1, 0), 0);
-                int l = 0, h = s_nact;
-                while (l < h) {
-                  const int m = (l + h) >> 1;
-                  if (upper ? (ag.key[m] <= v) : (ag.key[m] < v)) l = m + 1; else h = m;
+            uint32_t v[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+              const int c = cx - 1 + (k >> 1);
+              v[k] = (k & 1) ? agent_cell_key(c, min(cy + 1, 4095), 255) : agent_cell_key(c, max(cy - 1, 0), 0);
+              // a column off the grid has no candidates
+              if (c >= 0 && c <= 4095) hi[k] = s_nact;
+            }
+            // lower bound (even k) / upper bound (odd k) of each column's run;
+            // 8 halvings cover the at most 128 keys
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) {
+                if (lo[k] < hi[k]) {
+                  const int m = (lo[k] + hi[k]) >> 1;
+                  if ((k & 1) ? (ag.key[m] <= v[k]) : (ag.key[m] < v[k])) lo[k] = m + 1; else hi[k] = m;
                 }
-                bound = l;
               }
             }
           }
-          bool hit = false;
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int b = __shfl_sync(gmask, bound, 2 * k, STEP_G), en = __shfl_sync(gmask, bound, 2 * k + 1, STEP_G);
-            for (int q = b + gl; q < en; q += STEP_G) {
-              const int j = (int)(ag.key[q] & 0xffu);
-              if (j == li) continue;
-              const float4 sj = ag.st[j];
-              const float4 tj = ag.sc[j];
-              const float cb = ag.cs[j].x, sb = ag.cs[j].y;
-              hit |= box_box_depth(sj.x - s.x, sj.y - s.y, ca, sa, 0.5f * sc.x, 0.5f * sc.y, cb, sb, 0.5f * tj.x,
-                                   0.5f * tj.y) > 0.f;
-            }
+          for (int r = 0; r < 3; ++r) {
+            ag.prow[tid][r] = make_int2(lo[2 * r], lo[2 * r + 1] - lo[2 * r]);
+            cnt += lo[2 * r + 1] - lo[2 * r];
           }
-          hit = (__ballot_sync(0xffffffffu, hit) & gmask) != 0u;
-          if (act && gl == 0) ag.coll[li] = hit ? 1 : 0;
+          ag.coll[tid] = 0;
+        }
+        const int total = lay_pairs(cnt);
+        for (int f = tid; f < total; f += WARPS * WARP) {
+          int li;
+          const int j = (int)(ag.key[pair_at(f, li)] & 0xffu);
+          if (j == li) continue;
+          const float4 s = ag.st[li], sc = ag.sc[li];
+          const float2 ci = ag.cs[li];
+          const float4 sj = ag.st[j], tj = ag.sc[j];
+          const float2 cj = ag.cs[j];
+          if (box_box_depth(sj.x - s.x, sj.y - s.y, ci.x, ci.y, 0.5f * sc.x, 0.5f * sc.y, cj.x, cj.y, 0.5f * tj.x,
+                            0.5f * tj.y) > 0.f)
+            ag.coll[li] = 1;
         }
       }
       // road edges: from the shared-memory tile a warp per agent, ballot-OR
@@ -381,29 +420,12 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
           }
 #pragma unroll
           for (int r = 0; r < EDGE_ROWS; ++r) {
-            ag.erow[tid][r] = rw[r];
+            ag.prow[tid][r] = rw[r];
             cnt += rw[r].y;
           }
           ag.offr[tid] = hit ? 1 : 0;
         }
-        // exclusive scan of the counts: the agents' pairs laid end to end
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < WARP; o <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        if (lane == WARP - 1) s_esum[wid] = incl;
-        __syncthreads();
-        int total = 0, base = 0;
-#pragma unroll
-        for (int q = 0; q < WARPS; ++q) {
-          const int t = s_esum[q];
-          base += q < wid ? t : 0;
-          total += t;
-        }
-        if (tid < n) ag.eoff[tid] = base + incl - cnt;
-        __syncthreads();
+        const int total = lay_pairs(cnt);
         // EDGE_U pairs per thread per round, their loads in flight together
         for (int f0 = 0; f0 < total; f0 += EDGE_U * WARPS * WARP) {
           int p[EDGE_U], who[EDGE_U];
@@ -412,24 +434,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
             const int f = f0 + u * WARPS * WARP + tid;
             p[u] = -1;
             who[u] = 0;
-            if (f < total) {
-              // the last agent whose pairs start at or before f owns pair f
-              int lo = 0, hi = n - 1;
-              while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (ag.eoff[mid] <= f) lo = mid; else hi = mid - 1;
-              }
-              int rel = f - ag.eoff[lo];
-              int q = -1;
-#pragma unroll
-              for (int r = 0; r < EDGE_ROWS; ++r) {
-                const int2 rr = ag.erow[lo][r];
-                if (q < 0 && rel < rr.y) q = rr.x + rel;
-                if (q < 0) rel -= rr.y;
-              }
-              p[u] = q;
-              who[u] = lo;
-            }
+            if (f < total) p[u] = pair_at(f, who[u]);
           }
           float4 sg[EDGE_U];
 #pragma unroll
