@@ -290,13 +290,23 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         ag.sc[tid] = sci;
         ag.fl[tid] = f;
         ag.ty[tid] = ty;
-        ag.key[tid] = key;
+        // an agent out of the grid (done) and the slots past n hold a key
+        // above every cell's, so the rank below counts active keys only
+        ag.key[tid] = act ? key : 0xffffffffu;
+      } else if (tid < GD_MAX_AGENTS_PER_WORLD) {
+        ag.key[tid] = 0xffffffffu;
       }
       const int nact = __syncthreads_count(act);
-      // agent grid: rank of each active key among the active keys
+      // agent grid: rank of each active key among the active keys (keys are
+      // distinct: the low byte is the agent's index), four keys per load
       uint32_t rank = 0;
-      if (act)
-        for (int q = 0; q < n; ++q) rank += (!(ag.fl[q] & GD_FLAG_DONE)) && ag.key[q] < key;
+      if (act) {
+        const uint4* __restrict__ k4 = reinterpret_cast<const uint4*>(ag.key);
+        for (int q = 0; q < (n + 3) >> 2; ++q) {
+          const uint4 kq = k4[q];
+          rank += (kq.x < key) + (kq.y < key) + (kq.z < key) + (kq.w < key);
+        }
+      }
       __syncthreads();
       if (act) ag.key[rank] = key;
       if (tid == 0) s_nact = nact;
