@@ -50,8 +50,9 @@ struct ObsWarpSmem {
     unsigned long long keys[OBS_CAP];                     // road keys, bucket order
     unsigned long long pkeys[GD_MAX_AGENTS_PER_WORLD];    // partner keys
   } u;
-  unsigned short cand[OBS_CAND];   // positions of the in-radius points (pass 1)
-  unsigned sel[GD_MAX_K_ROAD];                            // road: low 32 bits of the key of rank r
+  unsigned cand[OBS_CAND];         // low key words (index, type, position) of the in-radius points (pass 1)
+  unsigned sel[GD_MAX_K_ROAD];     // road: low 32 bits of the key of rank r; during the selection, the d^2
+                                   // bits of in-radius point k < GD_MAX_K_ROAD of the compact list
   unsigned char psel[GD_MAX_PARTNERS + 1];                // partner: local index of rank r
   unsigned row_start[MAX_ROWS];
   unsigned row_excl[MAX_ROWS];
@@ -72,9 +73,13 @@ struct WorldView {
   GridDesc g;
 };
 
-// meta = local index | type << 15 (the road block's 16-bit word)
-__device__ __forceinline__ unsigned long long road_key(float d2, unsigned meta, unsigned pos) {
-  return ((unsigned long long)__float_as_uint(d2) << 32) | ((meta & 0x7fffu) << 17) | ((meta >> 15) << 16) | pos;
+// Low 32 bits of a road key from meta = local index | type << 15 (the road
+// block's 16-bit word) and the block position; the key puts d^2 above them.
+__device__ __forceinline__ unsigned road_lo(unsigned meta, unsigned pos) {
+  return ((meta & 0x7fffu) << 17) | ((meta >> 15) << 16) | pos;
+}
+__device__ __forceinline__ unsigned long long road_key(float d2, unsigned lo) {
+  return ((unsigned long long)__float_as_uint(d2) << 32) | lo;
 }
 __device__ __forceinline__ unsigned sel_pos(unsigned k) { return k & 0xffffu; }
 __device__ __forceinline__ unsigned sel_type(unsigned k) { return (k >> 16) & 1u; }
@@ -160,15 +165,17 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   int nrows;
   const int total = road_rows(v, R, R2, ex, ey, sm, lane, nrows);
 
-  // pass 1: histogram of d^2 buckets + compact list of in-radius positions.
-  // The warp walks the flat candidate list 4 x 32 entries per round, lane l
-  // taking entries l, l + 32, l + 64, l + 96: each load instruction reads 32
-  // consecutive points (two 128-byte lines when the road is read through
-  // L1/L2, no bank conflict in the tile), the four loads are independent,
-  // and the compact list comes out in memory order, which keeps pass 2's
-  // loads coalesced too.  Neighbouring points along a road differ in
-  // distance by far more than a bucket's width, so the histogram atomics
-  // rarely collide.
+  // pass 1: histogram of d^2 buckets + compact list of the in-radius
+  // points' low key words (index, type, position; their d^2 go to the sel
+  // array, free until the ranking, for the first GD_MAX_K_ROAD), so that
+  // pass 2 reads shared memory only: its reloads of the points missed L1
+  // and took 44% of the selection.  The warp walks the flat candidate list
+  // 4 x 32 entries per round, lane l taking entries l, l + 32, l + 64,
+  // l + 96: each load instruction reads 32 consecutive points (two 128-byte
+  // lines when the road is read through L1/L2, no bank conflict in the
+  // tile) and their meta words, and the loads are independent.
+  // Neighbouring points along a road differ in distance by far more than a
+  // bucket's width, so the histogram atomics rarely collide.
   for (int b = lane; b < OBS_NB / 2; b += WARP) sm.cur[b] = 0;
   __syncwarp();
   int n_in = 0;
@@ -196,8 +203,11 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
         pu[u] = vu[u] ? rs + ((unsigned)f - rx) : 0u;
       }
       float2 qu[U];
+      unsigned mu[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) qu[u] = xy[pu[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u) mu[u] = meta[pu[u]];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const float d2 = dist2(qu[u].x - ex, qu[u].y - ey);
@@ -208,7 +218,10 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
         }
         const unsigned m = __ballot_sync(0xffffffffu, in);
         const int slot = n_in + __popc(m & lt);
-        if (in && slot < OBS_CAND) sm.cand[slot] = (unsigned short)pu[u];
+        if (in && slot < OBS_CAND) {
+          sm.cand[slot] = road_lo(mu[u], pu[u]);
+          if (slot < GD_MAX_K_ROAD) sm.sel[slot] = __float_as_uint(d2);
+        }
         n_in += __popc(m);
       }
     }
@@ -254,11 +267,7 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     while (m < n_in) m <<= 1;
     for (int k = lane; k < m; k += WARP) {
       unsigned long long key = ~0ull;
-      if (k < n_in) {
-        const unsigned p = sm.cand[k];
-        const float2 q = xy[p];
-        key = road_key(dist2(q.x - ex, q.y - ey), meta[p], p);
-      }
+      if (k < n_in) key = road_key(__uint_as_float(sm.sel[k]), sm.cand[k]);   // k < BITONIC_MAX <= GD_MAX_K_ROAD
       sm.u.keys[k] = key;
     }
     __syncwarp();
@@ -279,28 +288,24 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     __syncwarp();
     return n_sel;
   }
-  // Calls fn(p, d2) for every in-radius point, from the compact list when
-  // it holds them all, else by walking the rows again.
+  // Calls fn(lo, d2) for every in-radius point (lo: the low key word), from
+  // the compact list when it holds them all (d^2 from the cache for the
+  // first GD_MAX_K_ROAD, else from the point again), else by walking the
+  // rows again.
   auto for_each_in_radius = [&](auto&& fn) {
     if (compact) {
-      constexpr int U = 4;
-      for (int k0 = lane; k0 < n_in; k0 += U * WARP) {
-        unsigned pu[U];
-        float2 qu[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) pu[u] = (k0 + u * WARP < n_in) ? sm.cand[k0 + u * WARP] : 0u;
-#pragma unroll
-        for (int u = 0; u < U; ++u) qu[u] = xy[pu[u]];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (k0 + u * WARP < n_in) fn(pu[u], dist2(qu[u].x - ex, qu[u].y - ey));
+      for (int k = lane; k < min(n_in, GD_MAX_K_ROAD); k += WARP) fn(sm.cand[k], __uint_as_float(sm.sel[k]));
+      for (int k = GD_MAX_K_ROAD + lane; k < n_in; k += WARP) {
+        const unsigned lo = sm.cand[k];
+        const float2 q = xy[sel_pos(lo)];
+        fn(lo, dist2(q.x - ex, q.y - ey));
       }
     } else {
       walk_rows(sm, nrows, total, lane, [&](unsigned p, bool valid) {
         if (valid) {
           const float2 q = xy[p];
           const float d2 = dist2(q.x - ex, q.y - ey);
-          if (d2 <= R2) fn(p, d2);
+          if (d2 <= R2) fn(road_lo(meta[p], p), d2);
         }
       });
     }
@@ -314,8 +319,8 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     while (lo < hi) {
       const unsigned long long mid = lo + ((hi - lo) >> 1);
       unsigned cntle = 0;
-      for_each_in_radius([&](unsigned p, float d2) {
-        if (bucket_of(d2, binv) == bstar && road_key(d2, meta[p], p) <= mid) ++cntle;
+      for_each_in_radius([&](unsigned lo, float d2) {
+        if (bucket_of(d2, binv) == bstar && road_key(d2, lo) <= mid) ++cntle;
       });
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) cntle += __shfl_xor_sync(0xffffffffu, cntle, o);
@@ -326,10 +331,10 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     __syncwarp();
   }
   // pass 2: scatter keys of buckets <= b* into their bucket slices
-  for_each_in_radius([&](unsigned p, float d2) {
+  for_each_in_radius([&](unsigned lo, float d2) {
     const int b = bucket_of(d2, binv);
     if (b <= bstar) {
-      const unsigned long long key = road_key(d2, meta[p], p);
+      const unsigned long long key = road_key(d2, lo);
       if (b < bstar || key <= tau) {
         const unsigned sh = bucket_shift(b);
         const unsigned slot = (atomicAdd(&sm.cur[b >> 1], 1u << sh) >> sh) & 0xffffu;

@@ -77,7 +77,8 @@ def test_fewer_than_k_after_leaving_dense_ground(batched):
     # one world: a dense 41 x 41 point patch (1 m pitch) and an agent that
     # jumps from its middle to 65 m away, where only the patch's edge (about
     # 164 points) is in range, then to 45 m (about 980), 120 m (nothing in
-    # range) and back
+    # range), back, and to 60 m (369 in range: more than the selection keeps
+    # d^2 of, fewer than its compact list holds)
     pts = [(float(i), float(j), (i + j) % 2, i + 20) for i in range(-20, 21) for j in range(-20, 21)]
     car = (0.0, 0.0, 0.0, 5.0, 4.5, 2.0, 30.0, 0.0, 0)
     car2 = (3.0, 7.0, 0.5, 2.0, 4.5, 2.0, 30.0, 0.0, 0)
@@ -89,7 +90,8 @@ def test_fewer_than_k_after_leaving_dense_ground(batched):
     ex = parity.Exceptions()
     s, f, t = [_np(x) for x in env.get_state()]
     _compare(env, ora, s, f, t, ocfg, ex, 0)
-    for k, (x, y) in enumerate(((65.0, 0.0), (45.0, 0.0), (67.0, 3.0), (120.0, -40.0), (0.5, 0.5), (0.5, 0.6))):
+    for k, (x, y) in enumerate(((65.0, 0.0), (45.0, 0.0), (67.0, 3.0), (120.0, -40.0), (0.5, 0.5), (0.5, 0.6),
+                                (65.0, 0.0), (60.0, 0.0), (62.0, 1.0))):
         s = s.copy()
         s[0, 0], s[0, 1] = x, y
         env.set_state(torch.from_numpy(s).cuda(), torch.from_numpy(f).cuda(), torch.from_numpy(t).cuda())
@@ -99,6 +101,8 @@ def test_fewer_than_k_after_leaving_dense_ground(batched):
             assert 0 < n_in < 200          # the fallback case: fewer than K in range
         if k == 1:
             assert n_in > 200
+        if k == 7:
+            assert 256 < n_in <= 512
     env.close()
 
 
