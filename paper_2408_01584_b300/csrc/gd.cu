@@ -57,6 +57,13 @@ inline cudaError_t allow_max_smem(const void* fn) {
 // Fixed shared memory of the fused and adjoint kernels besides the road tile.
 constexpr size_t world_fixed_smem(int warps) { return 128 + sizeof(FusedAgents) + warps * sizeof(ObsWarpSmem); }
 constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(ObsWarpSmem);
+// Occupancy the layouts are sized for: 228 KB of shared memory per SM, of
+// which the hardware keeps 1 KB per resident CTA.  Growing the per-warp
+// scratch past these drops a CTA per SM (the adjoint went from 3 to 2 and
+// its backward pass slowed by a fifth).
+constexpr size_t kSmemPerSM = 228 * 1024, kSmemPerCta = 1024;
+static_assert(4 * (kSplitSmem + kSmemPerCta) <= kSmemPerSM, "k_observe_split: 4 CTAs of 8 warps per SM");
+static_assert(3 * (kAdjFixedSmem + 16 + kSmemPerCta) <= kSmemPerSM, "k_adjoint without the tile: 3 CTAs per SM");
 // Fixed shared memory of the fused LiDAR kernel besides the road tile.
 inline size_t lidar_fixed_smem(int warps, int n) {
   return 128 + sizeof(FusedAgents) + warps * lidar_warp_bytes(n) + lidar_dirs_bytes(n);

@@ -35,7 +35,8 @@ namespace gd {
 
 constexpr int OBS_NB = 256;        // d^2 buckets
 constexpr int OBS_CAP = 288;       // keys kept per warp (>= GD_MAX_K_ROAD)
-constexpr int OBS_CAND = 512;      // compact list of in-radius positions (more: pass 2 walks the rows again)
+constexpr int OBS_CAND = 448;      // compact list of in-radius points (more: pass 2 walks the rows again);
+                                   // its size keeps 3 adjoint CTAs per SM
 constexpr int BITONIC_MAX = 256;   // strategy 2 sorts at most this many keys
 static_assert(OBS_CAP >= GD_MAX_K_ROAD, "selection capacity must hold K keys");
 static_assert(OBS_CAP >= BITONIC_MAX && OBS_CAND >= BITONIC_MAX, "bitonic keys must fit");

@@ -102,7 +102,7 @@ def test_fewer_than_k_after_leaving_dense_ground(batched):
         if k == 1:
             assert n_in > 200
         if k == 7:
-            assert 256 < n_in <= 512
+            assert 256 < n_in <= 448
     env.close()
 
 
