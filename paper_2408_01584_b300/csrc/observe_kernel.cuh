@@ -171,10 +171,10 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
   // array, free until the ranking, for the first GD_MAX_K_ROAD), so that
   // pass 2 reads shared memory only: its reloads of the points missed L1
   // and took 44% of the selection.  The warp walks the flat candidate list
-  // 4 x 32 entries per round, lane l taking entries l, l + 32, l + 64,
-  // l + 96: each load instruction reads 32 consecutive points (two 128-byte
-  // lines when the road is read through L1/L2, no bank conflict in the
-  // tile) and their meta words, and the loads are independent.
+  // U x 32 entries per round, lane l taking entries l, l + 32, ...: each
+  // load instruction reads 32 consecutive points (two 128-byte lines when
+  // the road is read through L1/L2, no bank conflict in the tile) and their
+  // meta words, and the loads are independent.
   // Neighbouring points along a road differ in distance by far more than a
   // bucket's width, so the histogram atomics rarely collide.
   for (int b = lane; b < OBS_NB / 2; b += WARP) sm.cur[b] = 0;
@@ -185,7 +185,9 @@ __device__ __forceinline__ int select_road(const WorldView& v, int K, float R, f
     int r = 0;
     unsigned rs = sm.row_start[0], rx = 0;
     unsigned re = (nrows > 1) ? sm.row_excl[1] : 0xffffffffu;
-    constexpr int U = 4;
+    // U = 3 measured fastest on the 1,024 x 64 workload (2: -2%, 4: -4%,
+    // 6 and 8 spill under the 64-register cap)
+    constexpr int U = 3;
     for (int f0 = 0; f0 < total; f0 += U * WARP) {
       unsigned pu[U];
       bool vu[U];
