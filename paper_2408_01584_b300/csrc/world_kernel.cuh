@@ -13,7 +13,10 @@
 // stages; otherwise the road is read from global memory (the road-edge test
 // from the edge grid).  The mbarrier wait is bounded: after ~2 s the CTA
 // sets ERR_TIMEOUT, waits once more (bounded) for its copy and leaves the
-// world loop; other CTAs keep draining the work list.
+// world loop; other CTAs keep draining the work list.  Collision and the
+// road-edge test (without the tile) run over the world's (agent, candidate)
+// pairs laid end to end, so the CTA's threads share a world's tests evenly
+// however the candidates fall among its agents.
 #pragma once
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
