@@ -62,7 +62,7 @@ constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(Ob
 // scratch past these drops a CTA per SM (the adjoint went from 3 to 2 and
 // its backward pass slowed by a fifth).
 constexpr size_t kSmemPerSM = 228 * 1024, kSmemPerCta = 1024;
-static_assert(4 * (kSplitSmem + kSmemPerCta) <= kSmemPerSM, "k_observe_split: 4 CTAs of 8 warps per SM");
+static_assert((32 / kSplitWarps) * (kSplitSmem + kSmemPerCta) <= kSmemPerSM, "k_observe_split: 32 warps per SM");
 static_assert(3 * (kAdjFixedSmem + 16 + kSmemPerCta) <= kSmemPerSM, "k_adjoint without the tile: 3 CTAs per SM");
 // Fixed shared memory of the fused LiDAR kernel besides the road tile.
 inline size_t lidar_fixed_smem(int warps, int n) {
