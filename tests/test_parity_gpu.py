@@ -109,9 +109,12 @@ def test_dense_collisions_and_offroad():
     assert (f & 4).any() and (f & 8).any()      # the scene does exercise both tests
 
 
-def test_edge_worlds():
+@pytest.mark.parametrize("form", ["per_stage", "batched_edge_grid", "batched_tile"])
+def test_edge_worlds(form):
     # an empty world, a world without road, a lone agent far off the map,
-    # pedestrians and cyclists, K and P larger than anything in range
+    # pedestrians and cyclists, K and P larger than anything in range; the
+    # batched forms run every step stage (pair lists included) on worlds of
+    # 0 to 3 agents
     far = (5000.0, -3000.0, 0.3, 5.0, 4.5, 2.0, 5050.0, -3000.0, 0)
     ped = (0.0, 0.0, 0.0, 1.0, 0.8, 0.8, 3.0, 0.0, scenes.PEDESTRIAN)
     cyc = (0.0, 3.0, 0.0, 4.0, 1.8, 0.7, 40.0, 3.0, scenes.CYCLIST)
@@ -121,7 +124,10 @@ def test_edge_worlds():
                      ([ped, cyc, car], edge)])
     ocfg = OracleConfig(k_road=256, n_partners=127, episode_len=10, term_offroad=True, term_collision=True)
     acts = scenes.make_actions(6, sc.num_agents, 2)
-    teacher_forced(sc, ocfg, 6, acts)
+    from paper_2408_01584_b300 import gd
+    over = {} if form == "per_stage" else dict(flags=gd_kwargs(ocfg)["flags"] | gd.GD_BATCHED,
+                                              road_no_tile=1 if form == "batched_edge_grid" else 0)
+    teacher_forced(sc, ocfg, 6, acts, gd_over=over)
 
 
 def test_zero_slots():
