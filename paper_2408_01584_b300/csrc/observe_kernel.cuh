@@ -13,9 +13,10 @@
 //
 // Top-K selection ("bucket rank"): d^2 in [0, R^2] is split into NB equal
 // buckets (equal-area annuli).  Pass 1 walks the rows, counts in-radius
-// points per bucket and keeps their positions in a compact list.  An
-// exclusive scan gives each bucket's first rank and the bucket b* holding
-// rank K.  Pass 2 walks the compact list and scatters the keys of buckets
+// points per bucket and keeps their keys' low words (and the first 256 d^2)
+// in a compact list.  An exclusive scan gives each bucket's first rank and
+// the bucket b* holding rank K.  Pass 2 walks the compact list in shared
+// memory and scatters the keys of buckets
 // <= b* into their bucket's slice of shared memory; the rank of a key is its
 // bucket's first rank plus the number of smaller keys in its bucket.  If
 // buckets <= b* do not fit, the exact K-th key is found by bisection over
