@@ -606,6 +606,10 @@ def run_profile(args):
     from paper_2408_01584_b300.build import build
     build()
     dev = torch.device("cuda", 0)
+    if args.fwdbwd:
+        stream = torch.cuda.Stream(dev)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # see flush_l2
+        return dict(bench_fwdbwd(args.workload, args.steps, args.warmup, dev, stream, flush), profile=args.workload)
     wl = scenes.WORKLOADS[args.workload]
     T = wl["steps"]
     sc = scenes.workload_scene(args.workload, 0)
@@ -794,6 +798,8 @@ def main():
     ap.add_argument("--lidar", type=int, default=0, help="with --profile: LiDAR rollout with this many rays")
     ap.add_argument("--fov", type=float, default=360.0, help="with --profile --lidar: fan width (degrees)")
     ap.add_argument("--worlds", type=int, default=0, help="with --profile: only the first W worlds")
+    ap.add_argument("--fwdbwd", action="store_true",
+                    help="with --profile: the workload's forward+backward leg (objective rollout + adjoint), autotuned")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip the uneven, differentiable, forward+backward, LiDAR, invertible-model and decimation workloads")
     args = ap.parse_args()
