@@ -9,7 +9,9 @@ synthetic actions.  Inputs are resident in HBM when the timed region starts
 buffers and the copies inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload plain_1024x64] [--no-cpu-baseline]
+                       [--workload plain_1024x64] [--no-cpu-baseline] [--no-extras]
+       python bench.py --profile [--shape B,C,T] [--lidar N [--fov DEG]] [--worlds W] [--fwdbwd]
+                       (one leg alone, for ncu captures)
 """
 from __future__ import annotations
 
