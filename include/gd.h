@@ -153,6 +153,10 @@ typedef struct gd_config {
                                 kernel over agents, no per-world barriers) as two launches; 0 = both
                                 in one fused launch.  Both give identical results, objective terms of
                                 gd_rollout_objective included. */
+  int32_t adjoint_split;     /* adjoint of a step (GD_DIFFERENTIABLE): 1 (default) = two launches, the
+                                observer side over agents (no per-world barriers) then a thread per
+                                agent for the partner side and the dynamics; 0 = one fused launch over
+                                worlds.  Both give bit-identical gradients. */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -184,6 +188,9 @@ typedef struct gd_info {
   int32_t road_tile;                                /* 1: the batched step kernel copies each world's road into
                                                        shared memory */
   int32_t obs_split;                                /* 1: step and radial observation are two launches */
+  int32_t adjoint_split;                            /* 1: the step's adjoint is two launches (split form) */
+  int32_t adjoint_road_tile;                        /* 1: the fused adjoint copies each world's road into
+                                                       shared memory */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -317,14 +324,18 @@ gd_status gd_rollout_host(gd_env* env, int32_t steps, const float* actions_host,
                           uint8_t* done_host);
 
 /* Differentiable rollout (an extension; the paper has no gradient).  Runs
- * `steps` fused steps from the current state, like gd_rollout, and writes
+ * `steps` steps from the current state, like gd_rollout, and writes
  * the per-step objective terms
  *   ell[t,i] = sum_f obs_weight[f] * obs(t)[i,f] + reward_weight * r_s(t,i)
  * where obs(t) is the observation after step t and r_s = -(sqrt(d_goal^2 +
  * c^2) - c), c = smooth_c, for controlled agents in the scene at the start
  * of step t (0 otherwise).  The state is checkpointed every ckpt_every steps for
  * gd_rollout_backward; `actions` must stay unchanged until then.
- * Requires GD_DIFFERENTIABLE; steps <= episode_len.
+ * Requires GD_DIFFERENTIABLE; steps <= episode_len.  With GD_BATCHED the
+ * rollout (checkpoint copies and step launches) is one captured CUDA graph,
+ * re-used while steps and the pointer and weight arguments are the same;
+ * without it every launch is issued from the host.  Both give identical
+ * results.
  *   actions: device float [T,A,2]; obs_weight: device float [F], 16-byte
  *   aligned; ell: device float [T,A]; obs: device float [A,F] overwritten
  *   every step, or NULL (an internal buffer is used). */
@@ -336,11 +347,29 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
  * state.  Collision, goal, done, selection and clip decisions are held
  * constant.  Recomputes the states between checkpoints; the env's current
  * state is not changed.  obs_weight / reward_weight must be the values used
- * in the forward call.
+ * in the forward call.  With GD_BATCHED the whole backward pass (per
+ * segment, last first: the checkpoint copy, the recomputed steps, the
+ * adjoint of each step in reverse) is one captured CUDA graph with no
+ * memset or copy node per step, re-used while the arguments are the same;
+ * without it every launch is issued from the host.
  *   d_ell: device float [T,A] or NULL; d_actions: device float [T,A,2];
  *   d_state0: device float [A,4] or NULL. */
 gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
                               float* d_actions, float* d_state0);
+
+/* Instrumentation (no counterpart in the paper): the same backward pass as
+ * gd_rollout_backward, with the same arguments and results, but every launch
+ * issued from the host with CUDA events around it.  Blocks until done; then
+ * ms[k] holds the total milliseconds and launches[k] the number of launches
+ * of kind k (GD_BWD_KINDS entries each, host memory):
+ *   0 checkpoint copies (k_copy_snapshot), one per segment;
+ *   1 recomputed steps (the step kernel, out of place), one per step;
+ *   2 the adjoint's observer side (split form) or the whole fused adjoint;
+ *   3 the split adjoint's per-agent part (partner side and dynamics).
+ * Per-launch averages are ms[k] / launches[k]. */
+#define GD_BWD_KINDS 4
+gd_status gd_time_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                           float* d_actions, float* d_state0, float* ms, int32_t* launches);
 
 /* Adjoint of one step about the CURRENT state and the given actions
  * (the step is not applied; requires GD_DIFFERENTIABLE): given
@@ -393,33 +422,6 @@ gd_status gd_sync(gd_env* env);
 
 const char* gd_last_error(const gd_env* env);
 
-/* ---- allocation-free collision query ---------------------------------------
- * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: a program whose GPU memory is owned by
- * another pool allocator (cudaMalloc from this library would fail or escape
- * that pool's accounting), or a latency-critical loop that cannot take the
- * synchronisation cudaMalloc / cudaFree may cause.  gd_create allocates, so
- * such callers use this stateless call instead.
- *
- * Computes, for every agent, whether its box overlaps the box of another
- * active agent of the same world (the test behind GD_FLAG_COLLIDED of
- * gd_step), through a per-world uniform grid.
- *   agent_off  HOST int32 [num_worlds+1], CSR offsets (as in gd_scene_batch)
- *   state      device float [A,4] = (x, y, theta, v), 16-byte aligned
- *   extent     device float [A,2] = (length, width), 8-byte aligned
- *   active     device uint8 [A] (0 = not in the scene) or NULL = all active
- *   cell       grid cell in m; must be >= the largest box diagonal, or
- *              collisions between boxes more than one cell apart are missed
- *   collided   device uint8 [A] output: 1 = overlap, 0 = none or inactive
- * Working memory is one fixed array in the library (GD_NOALLOC_MAX_AGENTS
- * agents, GD_NOALLOC_MAX_WORLDS worlds; about 1.2 MB held on every GPU that
- * loads the library until the process exits).  No call allocates.  Larger
- * inputs return GD_ERR_CAPACITY; bad arguments GD_ERR_INVALID_ARG; the text
- * is in gd_last_error(NULL).  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  Every call reuses the same array
- * (nothing in it needs to start at zero: each call writes what it reads),
- * so calls that overlap on the GPU, e.g. on two streams, race. */
 /* ---- polyline decimation at scene load --------------------------------------
  * Visvalingam-Whyatt decimation (Sec. 3.1: road polylines sampled every
  * 0.1 m are mostly straight; dropping low-importance points cuts them 10-15x
@@ -441,6 +443,38 @@ const char* gd_last_error(const gd_env* env);
 gd_status gd_decimate(int32_t num_polylines, int32_t num_points, const int32_t* poly_off, const float* x,
                       const float* y, float area_tol, uint8_t* keep, void* cuda_stream);
 
+/* ---- allocation-free collision query ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: a program whose GPU memory is owned by
+ * another pool allocator (cudaMalloc from this library would fail or escape
+ * that pool's accounting), or a latency-critical loop that cannot take the
+ * synchronisation cudaMalloc / cudaFree may cause.  gd_create allocates, so
+ * such callers use this stateless call instead.
+ *
+ * Computes, for every agent, whether its box overlaps the box of another
+ * active agent of the same world (the test behind GD_FLAG_COLLIDED of
+ * gd_step), through a per-world uniform grid.
+ *   agent_off  HOST int32 [num_worlds+1], CSR offsets (as in gd_scene_batch)
+ *   state      device float [A,4] = (x, y, theta, v), 16-byte aligned
+ *   extent     device float [A,2] = (length, width), 8-byte aligned
+ *   active     device uint8 [A] (0 = not in the scene) or NULL = all active
+ *   cell       grid cell in m; must be >= the largest box diagonal, or
+ *              collisions between boxes more than one cell apart are missed
+ *   collided   device uint8 [A] output: 1 = overlap, 0 = none or inactive
+ * Working memory is one fixed array in the library (GD_NOALLOC_MAX_AGENTS
+ * agents, GD_NOALLOC_MAX_WORLDS worlds; about 1.2 MB held on every GPU that
+ * loads the library until the process exits).  Larger inputs return
+ * GD_ERR_CAPACITY; bad arguments GD_ERR_INVALID_ARG; the text is in
+ * gd_last_error(NULL).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call
+ * before any stream capture.  With lazy module loading (the CUDA default)
+ * that first call also loads the library's device code on the device, and
+ * the driver then takes the array's memory (about 1.2 MB): make the first
+ * call at initialisation, before a pool allocator reserves the GPU's
+ * memory.  No later call allocates.  Each call copies agent_off from host
+ * memory to the array on the given stream.  Every call reuses the same
+ * array (nothing in it needs to start at zero: each call writes what it
+ * reads), so calls that overlap on the GPU, e.g. on two streams, race. */
 #define GD_NOALLOC_MAX_AGENTS 262144
 #define GD_NOALLOC_MAX_WORLDS 16384
 gd_status gd_collide_noalloc(int32_t num_worlds, const int32_t* agent_off, const float* state, const float* extent,

@@ -14,13 +14,19 @@
 // incoming adjoint lam (d L / d post-step state from later steps) and maps
 // it back through the dynamics:  lam <- J_s^T lam,  d_action = J_a^T lam.
 //
-// One CTA per world (persistent, work list as in the forward kernel).
-// Warp per agent: re-run the forward selection (same code, same state, so
-// the same sets), accumulate the gradient on its own state (lanes over
-// slots, shuffle-tree reduction) and record which slot each partner sits in.
-// Thread per agent: gather the gradient it receives as somebody's partner in
-// ascending order of the observer (a fixed order, so the sums are
-// deterministic), add the reward term, apply the dynamics adjoint.
+// Two forms compute the same sums in the same order, so their gradients are
+// bit-identical:
+//   split (default): k_adj_observer, persistent warps that claim agents one
+//     at a time (no per-world barrier): re-run the forward selection from
+//     global memory (same code, same state, so the same sets), accumulate the
+//     gradient on the observer's own state (lanes over slots, shuffle-tree
+//     reduction) and record which slot each partner sits in; then
+//     k_adj_dynamics, a thread per agent: gather the gradient it receives as
+//     somebody's partner in ascending order of the observer (a fixed order,
+//     so the sums are deterministic), add the reward term, apply the
+//     dynamics adjoint;
+//   fused: k_adjoint, one CTA per world (persistent, work list as in the
+//     forward kernel), both parts with the world in shared memory.
 #pragma once
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
@@ -43,10 +49,19 @@ struct AdjArgs {
   float2* d_actions;        // [A] out: dL/d (accel, steer)
   const float* rk;          // [A] each agent's K-th road distance at this step in the forward rollout
                             // (bounds the re-selection's disk), or nullptr: the full radius
-  unsigned* counter;
+  unsigned* counter;         // fused form: [2] work counter and exit tally, left at zero by each launch
   const int* order;
   int tile_bytes;
+  int lam_zero;              // 1: the incoming lam is zero (the last step of a rollout); lam is not read
+  float4* lam_copy;          // [A] or nullptr: a second copy of the outgoing lam (d_state0 of the first step)
+  // split form
+  float4* g_obs;             // [A] observer-side gradient on each agent's own state (agents in the scene)
+  float2* cs_obs;            // [A] (cos, sin) of each observer's post-step heading (agents in the scene)
+  uint8_t* slot;             // [A][GD_MAX_AGENTS_PER_WORLD] slot of local partner j in observer i's row, 0xff = none
+  unsigned* ocounter;        // [ADJ_STRIPES] agent claims of k_adj_observer; k_adj_dynamics leaves them at zero
 };
+
+constexpr unsigned ADJ_STRIPES = 32;
 
 struct AdjAgents {
   float4 st[GD_MAX_AGENTS_PER_WORLD];   // post-step state
@@ -103,10 +118,132 @@ __device__ __forceinline__ void invertible_adjoint(const float4 s, float accel, 
   lam.w = fmaf(g, dt, lam.w);
 }
 
+// ---- arithmetic shared by both forms ---------------------------------------
+
+// Observer side of agent li's row (post-step state st, heading (c, s), weight
+// row wrow): d (w . row) / d(own state) as (x, y, theta, v), summed over the
+// ego features, the partner slots and the road slots (lanes over slots, then
+// a shuffle tree), returned to every lane.  on_partner(r, j) is called once
+// per selected partner (slot r, local index j) by the lane that handles it.
+template <typename OnPartner>
+__device__ __forceinline__ float4 observer_gradient(const DevEnv& e, const WorldView& v, int li, float4 st, float4 sc,
+                                                    float c, float s, const float* __restrict__ wrow, float Rs,
+                                                    float Rs2, ObsWarpSmem& sm, int lane, OnPartner&& on_partner) {
+  float gx = 0.f, gy = 0.f, gt = 0.f, gv = 0.f;
+  if (lane == 0) {
+    // ego: speed and goal offset in the ego frame
+    const float dx = sc.z - st.x, dy = sc.w - st.y;
+    const float f3 = rot_x(c, s, dx, dy), f4 = rot_y(c, s, dx, dy);
+    const float w3 = __ldg(wrow + 3), w4 = __ldg(wrow + 4);
+    gv = __ldg(wrow + 0);
+    gx = fmaf(-c, w3, __fmul_rn(s, w4));
+    gy = fmaf(-s, w3, -__fmul_rn(c, w4));
+    gt = fmaf(w3, f4, -__fmul_rn(w4, f3));
+  }
+  // partners: the observer side here, the partner side in the gather
+  const int np = select_partners(v, li, e.P, e.R2, st.x, st.y, sm, lane);
+  for (int r = lane; r < np; r += WARP) {
+    const int j = sm.psel[r];
+    on_partner(r, j);
+    const float4 wa = __ldg(reinterpret_cast<const float4*>(wrow + 8 + 8 * r));
+    const float4 q = v.state[j];
+    float2 cj;
+    if (v.cs) cj = v.cs[j]; else sincosf(q.z, &cj.y, &cj.x);
+    const float dx = q.x - st.x, dy = q.y - st.y;
+    const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
+    const float cd = rot_x(c, s, cj.x, cj.y), sd = rot_y(c, s, cj.x, cj.y);
+    gx += fmaf(-c, wa.x, __fmul_rn(s, wa.y));
+    gy += fmaf(-s, wa.x, -__fmul_rn(c, wa.y));
+    gt += fmaf(wa.x, yp, -__fmul_rn(wa.y, xp)) + fmaf(wa.z, sd, -__fmul_rn(wa.w, cd));
+  }
+  // road points: the forward selection's K-th distance bounds the disk that
+  // holds the same K points (the full radius when it had fewer than K)
+  int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
+  if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+  const float* wroad = wrow + 8 + 8 * e.P;
+  for (int r = lane; r < nroad; r += WARP) {
+    const float2 q = v.xy[sel_pos(sm.sel[r])];
+    const float dx = q.x - st.x, dy = q.y - st.y;
+    const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
+    const float wa = __ldg(wroad + 4 * r), wb = __ldg(wroad + 4 * r + 1);
+    gx += fmaf(-c, wa, __fmul_rn(s, wb));
+    gy += fmaf(-s, wa, -__fmul_rn(c, wb));
+    gt += fmaf(wa, yp, -__fmul_rn(wb, xp));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gx += __shfl_xor_sync(0xffffffffu, gx, o);
+    gy += __shfl_xor_sync(0xffffffffu, gy, o);
+    gt += __shfl_xor_sync(0xffffffffu, gt, o);
+  }
+  return make_float4(gx, gy, gt, gv);
+}
+
+// Radius of the re-selection of agent i: the forward step's K-th road
+// distance + 1e-3 m when it is below R, else R.
+__device__ __forceinline__ void reselect_radius(const DevEnv& e, const AdjArgs& a, int i, float& Rs, float& Rs2) {
+  Rs = e.R;
+  Rs2 = e.R2;
+  if (a.rk) {
+    const float r = a.rk[i] + 1e-3f;
+    if (r < e.R) {
+      Rs = r;
+      Rs2 = r * r;
+    }
+  }
+}
+
+// Partner side: the gradient agent j (heading (cj.x, cj.y)) receives from
+// observer i (heading (ci, si), weight row wrow, multiplier m) that holds it
+// in slot r.
+__device__ __forceinline__ void partner_term(float4& g, float ci, float si, float2 cj, const float* __restrict__ wrow,
+                                             int r, float m) {
+  const float4 wa = __ldg(reinterpret_cast<const float4*>(wrow + 8 + 8 * r));
+  const float we = __ldg(wrow + 8 + 8 * r + 4);
+  const float cd = rot_x(ci, si, cj.x, cj.y), sd = rot_y(ci, si, cj.x, cj.y);
+  g.x += m * fmaf(ci, wa.x, -__fmul_rn(si, wa.y));
+  g.y += m * fmaf(si, wa.x, __fmul_rn(ci, wa.y));
+  g.z += m * fmaf(-wa.z, sd, __fmul_rn(wa.w, cd));
+  g.w += m * we;
+}
+
+// Last part for agent ig: the smooth goal reward term (a controlled agent in
+// the scene before the step), lam += g, then the dynamics adjoint; writes
+// lam (and lam_copy) and d_actions.  st, sc: post-step state and extents/goal.
+__device__ __forceinline__ void finish_agent(const DevEnv& e, const AdjArgs& a, int ig, float4 g, float4 st,
+                                             float4 sc) {
+  const uint8_t f0 = a.fpre[ig];
+  if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
+    const float m = a.row_scale ? a.row_scale[ig] : 1.f;
+    const float rw = (a.rew_w ? a.rew_w[ig] : a.reward_w) * m;
+    const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
+    const float qn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));
+    g.x -= rw * dx / qn;
+    g.y -= rw * dy / qn;
+  }
+  float4 lam = a.lam_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : a.lam[ig];
+  lam.x += g.x;
+  lam.y += g.y;
+  lam.z += g.z;
+  lam.w += g.w;
+  float2 da = make_float2(0.f, 0.f);
+  if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {      // done and uncontrolled agents do not move
+    const float2 u = a.actions[ig];
+    if (e.dyn == 1) invertible_adjoint(a.pre[ig], u.x, u.y, e.dt, lam, da);
+    else bicycle_adjoint(a.pre[ig], u.x, u.y, sc.x, e.dt, e.vmax, lam, da);
+  }
+  a.lam[ig] = lam;
+  if (a.lam_copy) a.lam_copy[ig] = lam;
+  a.d_actions[ig] = da;
+}
+
+// ---- fused form --------------------------------------------------------------
+
 // Dynamic shared memory: [mbarrier, 128 B][road tile][AdjAgents][ObsWarpSmem x WARPS]
 // LEAN: the instantiation for the form without the road tile, whose shared
 // memory leaves room for 32 warps per SM; registers are capped at 64 per
-// thread (no spills) so that they can all be resident.
+// thread (no spills) so that they can all be resident.  Worlds come from a
+// counter that the last CTA out leaves at zero (no memset between launches).
 template <int WARPS, bool LEAN = false>
 __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(DevEnv e, AdjArgs a) {
   extern __shared__ __align__(16) unsigned char asm_[];
@@ -159,12 +296,15 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
     }
     __syncthreads();
     if (s_abort) {
+      // the copy did not land in time: record it, give the copy one more
+      // bounded chance, and leave the world loop (the exit tally below still
+      // counts this CTA out)
       if (tid == 0) {
         atomicOr(e.err, ERR_TIMEOUT);
         mbar_wait_bounded(bar, phase ^ 1u);
       }
       __syncthreads();
-      return;
+      break;
     }
     if (obs_term) {
       WorldView v;
@@ -178,66 +318,14 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
       for (int li = wid; li < n;) {
         if (!(ag.fl[li] & GD_FLAG_DONE)) {
           const int i = a0 + li;
-          const float* wrow = a.obs_w + (size_t)i * a.obs_w_stride;
-          const float4 st = ag.st[li], sc = ag.sc[li];
-          const float c = ag.cs[li].x, s = ag.cs[li].y;
-          float gx = 0.f, gy = 0.f, gt = 0.f, gv = 0.f;
-          if (lane == 0) {
-            // ego: speed and goal offset in the ego frame
-            const float dx = sc.z - st.x, dy = sc.w - st.y;
-            const float f3 = rot_x(c, s, dx, dy), f4 = rot_y(c, s, dx, dy);
-            const float w3 = __ldg(wrow + 3), w4 = __ldg(wrow + 4);
-            gv = __ldg(wrow + 0);
-            gx = fmaf(-c, w3, __fmul_rn(s, w4));
-            gy = fmaf(-s, w3, -__fmul_rn(c, w4));
-            gt = fmaf(w3, f4, -__fmul_rn(w4, f3));
-          }
-          // partners: the observer side here, the partner side in the gather below
-          const int np = select_partners(v, li, e.P, e.R2, st.x, st.y, sm, lane);
-          for (int r = lane; r < np; r += WARP) {
-            const int j = sm.psel[r];
-            ag.slot_of[li][j] = (uint8_t)r;
-            const float4 wa = __ldg(reinterpret_cast<const float4*>(wrow + 8 + 8 * r));
-            const float4 q = ag.st[j];
-            const float dx = q.x - st.x, dy = q.y - st.y;
-            const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
-            const float cd = rot_x(c, s, ag.cs[j].x, ag.cs[j].y), sd = rot_y(c, s, ag.cs[j].x, ag.cs[j].y);
-            gx += fmaf(-c, wa.x, __fmul_rn(s, wa.y));
-            gy += fmaf(-s, wa.x, -__fmul_rn(c, wa.y));
-            gt += fmaf(wa.x, yp, -__fmul_rn(wa.y, xp)) + fmaf(wa.z, sd, -__fmul_rn(wa.w, cd));
-          }
-          // road points
-          // the forward selection's K-th distance bounds the disk that holds
-          // the same K points (the full radius when it had fewer than K)
-          float Rs = e.R, Rs2 = e.R2;
-          if (a.rk) {
-            const float r = a.rk[i] + 1e-3f;
-            if (r < e.R) {
-              Rs = r;
-              Rs2 = r * r;
-            }
-          }
-          int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
-          if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
-          const float* wroad = wrow + 8 + 8 * e.P;
-          for (int r = lane; r < nroad; r += WARP) {
-            const float2 q = v.xy[sel_pos(sm.sel[r])];
-            const float dx = q.x - st.x, dy = q.y - st.y;
-            const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
-            const float wa = __ldg(wroad + 4 * r), wb = __ldg(wroad + 4 * r + 1);
-            gx += fmaf(-c, wa, __fmul_rn(s, wb));
-            gy += fmaf(-s, wa, -__fmul_rn(c, wb));
-            gt += fmaf(wa, yp, -__fmul_rn(wb, xp));
-          }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            gx += __shfl_xor_sync(0xffffffffu, gx, o);
-            gy += __shfl_xor_sync(0xffffffffu, gy, o);
-            gt += __shfl_xor_sync(0xffffffffu, gt, o);
-          }
+          float Rs, Rs2;
+          reselect_radius(e, a, i, Rs, Rs2);
+          const float4 gr = observer_gradient(e, v, li, ag.st[li], ag.sc[li], ag.cs[li].x, ag.cs[li].y,
+                                              a.obs_w + (size_t)i * a.obs_w_stride, Rs, Rs2, sm, lane,
+                                              [&](int r, int j) { ag.slot_of[li][j] = (uint8_t)r; });
           if (lane == 0) {
             const float m = a.row_scale ? a.row_scale[i] : 1.f;
-            ag.g[li] = make_float4(m * gx, m * gy, m * gt, m * gv);
+            ag.g[li] = make_float4(m * gr.x, m * gr.y, m * gr.z, m * gr.w);
           }
           __syncwarp();
         }
@@ -249,54 +337,117 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
     __syncthreads();
     if (tid < n) {
       const int j = tid, ig = a0 + j;
-      float4 g = ag.g[j];
+      float4 gj = ag.g[j];
       if (obs_term) {
         // partner side: every observer i that has j in slot r, ascending i
-        const float4 q = ag.st[j];
         const float2 cj = ag.cs[j];
         for (int i = 0; i < n; ++i) {
           const int r = ag.slot_of[i][j];
           if (r == 0xff) continue;
-          const float ci = ag.cs[i].x, si = ag.cs[i].y;
-          const float* wrow = a.obs_w + (size_t)(a0 + i) * a.obs_w_stride;
-          const float4 wa = __ldg(reinterpret_cast<const float4*>(wrow + 8 + 8 * r));
-          const float we = __ldg(wrow + 8 + 8 * r + 4);
-          const float m = a.row_scale ? a.row_scale[a0 + i] : 1.f;
-          const float cd = rot_x(ci, si, cj.x, cj.y), sd = rot_y(ci, si, cj.x, cj.y);
-          g.x += m * fmaf(ci, wa.x, -__fmul_rn(si, wa.y));
-          g.y += m * fmaf(si, wa.x, __fmul_rn(ci, wa.y));
-          g.z += m * fmaf(-wa.z, sd, __fmul_rn(wa.w, cd));
-          g.w += m * we;
+          partner_term(gj, ag.cs[i].x, ag.cs[i].y, cj, a.obs_w + (size_t)(a0 + i) * a.obs_w_stride, r,
+                       a.row_scale ? a.row_scale[a0 + i] : 1.f);
         }
-        (void)q;
       }
-      const uint8_t f0 = a.fpre[ig];
-      if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
-        // smooth goal reward of a controlled agent in the scene before the step
-        const float m = a.row_scale ? a.row_scale[ig] : 1.f;
-        const float rw = (a.rew_w ? a.rew_w[ig] : a.reward_w) * m;
-        const float4 st = ag.st[j], sc = ag.sc[j];
-        const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
-        const float qn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));
-        g.x -= rw * dx / qn;
-        g.y -= rw * dy / qn;
-      }
-      float4 lam = a.lam[ig];
-      lam.x += g.x;
-      lam.y += g.y;
-      lam.z += g.z;
-      lam.w += g.w;
-      float2 da = make_float2(0.f, 0.f);
-      if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {      // done and uncontrolled agents do not move
-        const float2 u = a.actions[ig];
-        if (e.dyn == 1) invertible_adjoint(a.pre[ig], u.x, u.y, e.dt, lam, da);
-        else bicycle_adjoint(a.pre[ig], u.x, u.y, ag.sc[j].x, e.dt, e.vmax, lam, da);
-      }
-      a.lam[ig] = lam;
-      a.d_actions[ig] = da;
+      finish_agent(e, a, ig, gj, ag.st[j], ag.sc[j]);
     }
     __syncthreads();
   }
+  // the last CTA out leaves the work counter and the exit tally at zero for
+  // the next launch (every CTA has made its last claim before it counts out)
+  __syncthreads();
+  if (tid == 0 && atomicAdd(a.counter + 1, 1u) == gridDim.x - 1) {
+    a.counter[0] = 0u;
+    a.counter[1] = 0u;
+  }
+}
+
+// ---- split form ----------------------------------------------------------------
+
+// Part 1: persistent warps claim agents one at a time from ADJ_STRIPES
+// striped counters (warp g draws agents c, c + ADJ_STRIPES, ... from counter
+// c = g mod ADJ_STRIPES; the counters are zero at launch) and, for an agent
+// in the scene after the step, re-select its row from global memory (the
+// world's agents and road block through L1/L2) and write its observer-side
+// gradient g_obs[i] (times m_i), its heading's (cos, sin) and its slot row:
+// slot[i][j] = the slot of local partner j, 0xff for every other agent.  A
+// done agent's row is all 0xff.  Dynamic shared memory: WARPS x
+// (ObsWarpSmem + 128 B).  Registers capped for 32 warps per SM.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv e, AdjArgs a) {
+  extern __shared__ __align__(16) unsigned char adj_smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(adj_smem_raw)[wid];
+  uint8_t* srow = adj_smem_raw + WARPS * sizeof(ObsWarpSmem) + wid * GD_MAX_AGENTS_PER_WORLD;
+  static_assert(GD_MAX_AGENTS_PER_WORLD == 4 * WARP, "a slot row is one 32-bit word per lane");
+  const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % ADJ_STRIPES;
+  for (;;) {
+    unsigned k = 0;
+    if (lane == 0) k = atomicAdd(a.ocounter + c, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    const unsigned i = c + ADJ_STRIPES * k;
+    if (i >= (unsigned)e.A) break;
+    unsigned* grow = reinterpret_cast<unsigned*>(a.slot + (size_t)i * GD_MAX_AGENTS_PER_WORLD);
+    if (a.fpost[i] & GD_FLAG_DONE) {
+      grow[lane] = 0xffffffffu;
+      continue;
+    }
+    reinterpret_cast<unsigned*>(srow)[lane] = 0xffffffffu;
+    __syncwarp();
+    const float4 st = a.post[i], sc = e.stat[i];
+    const int w = e.agent_world[i];
+    const int a0 = e.agent_off[w];
+    WorldView v;
+    v.state = a.post + a0;
+    v.stat = e.stat + a0;
+    v.cs = nullptr;
+    v.flags = a.fpost + a0;
+    v.n = e.agent_off[w + 1] - a0;
+    road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
+    v.g = e.rgrid[w];
+    float sn, cn;
+    sincosf(st.z, &sn, &cn);
+    float Rs, Rs2;
+    reselect_radius(e, a, (int)i, Rs, Rs2);
+    const float4 gr = observer_gradient(e, v, (int)i - a0, st, sc, cn, sn, a.obs_w + (size_t)i * a.obs_w_stride, Rs,
+                                        Rs2, sm, lane, [&](int r, int j) { srow[j] = (uint8_t)r; });
+    __syncwarp();
+    grow[lane] = reinterpret_cast<const unsigned*>(srow)[lane];
+    if (lane == 0) {
+      const float m = a.row_scale ? a.row_scale[i] : 1.f;
+      a.g_obs[i] = make_float4(m * gr.x, m * gr.y, m * gr.z, m * gr.w);
+      a.cs_obs[i] = make_float2(cn, sn);
+    }
+    __syncwarp();
+  }
+}
+
+// Part 2: thread per agent j (flat over all agents): its own observer-side
+// gradient, then the partner side from every observer i of its world that
+// holds it (ascending i, the fused form's order), the reward term and the
+// dynamics adjoint.  Block 0 leaves part 1's claim counters at zero for the
+// next part-1 launch.
+__global__ void __launch_bounds__(256) k_adj_dynamics(DevEnv e, AdjArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x < ADJ_STRIPES) a.ocounter[threadIdx.x] = 0u;
+  const int ig = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ig >= e.A) return;
+  const float4 st = a.post[ig], sc = e.stat[ig];
+  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (a.obs_w) {
+    const int w = e.agent_world[ig];
+    const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0, j = ig - a0;
+    if (!(a.fpost[ig] & GD_FLAG_DONE)) g = a.g_obs[ig];
+    float2 cj;
+    sincosf(st.z, &cj.y, &cj.x);
+    const uint8_t* col = a.slot + (size_t)a0 * GD_MAX_AGENTS_PER_WORLD + j;
+    for (int i = 0; i < n; ++i) {
+      const int r = col[(size_t)i * GD_MAX_AGENTS_PER_WORLD];
+      if (r == 0xff) continue;
+      const float2 ci = a.cs_obs[a0 + i];
+      partner_term(g, ci.x, ci.y, cj, a.obs_w + (size_t)(a0 + i) * a.obs_w_stride, r,
+                   a.row_scale ? a.row_scale[a0 + i] : 1.f);
+    }
+  }
+  finish_agent(e, a, ig, g, st, sc);
 }
 
 }  // namespace gd

@@ -34,6 +34,10 @@ struct NvtxRange {
 constexpr int kObsWarpsDefault = 8;
 constexpr int kWorldWarps = 8;    // default CTA size of k_world (warps); 4 and 16 also built
 constexpr int kAdjWarps = 8;
+// Split adjoint's observer kernel: CTA size and shared memory (the
+// observation scratch and one slot row per warp).
+constexpr int kAdjObsWarps = 8;
+constexpr size_t kAdjObsSmem = kAdjObsWarps * (sizeof(ObsWarpSmem) + GD_MAX_AGENTS_PER_WORLD);
 constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
 
@@ -64,6 +68,7 @@ constexpr size_t kAdjFixedSmem = 128 + sizeof(AdjAgents) + kAdjWarps * sizeof(Ob
 constexpr size_t kSmemPerSM = 228 * 1024, kSmemPerCta = 1024;
 static_assert((32 / kSplitWarps) * (kSplitSmem + kSmemPerCta) <= kSmemPerSM, "k_observe_split: 32 warps per SM");
 static_assert(3 * (kAdjFixedSmem + 16 + kSmemPerCta) <= kSmemPerSM, "k_adjoint without the tile: 3 CTAs per SM");
+static_assert((32 / kAdjObsWarps) * (kAdjObsSmem + kSmemPerCta) <= kSmemPerSM, "k_adj_observer: 32 warps per SM");
 // Fixed shared memory of the fused LiDAR kernel besides the road tile.
 inline size_t lidar_fixed_smem(int warps, int n) {
   return 128 + sizeof(FusedAgents) + warps * lidar_warp_bytes(n) + lidar_dirs_bytes(n);
@@ -127,8 +132,21 @@ struct gd_env {
   int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
   size_t adj_smem = 0;
   int adj_grid = 0;
+  int adj_split = 1;            // 1: k_adj_observer + k_adj_dynamics; 0: one fused k_adjoint per step
+  int ao_grid = 0;              // persistent CTAs of k_adj_observer
+  float4* adj_g = nullptr;      // [A] split adjoint: observer-side gradients
+  float2* adj_cs = nullptr;     // [A] split adjoint: observers' (cos, sin)
+  uint8_t* adj_slot = nullptr;  // [A][GD_MAX_AGENTS_PER_WORLD] split adjoint: partner slot rows
+  unsigned* adj_oc = nullptr;   // [ADJ_STRIPES] k_adj_observer's claim counters (zero between launches)
   const float* diff_actions = nullptr;   // actions of the last objective rollout
   int diff_steps = 0;
+  // captured differentiable rollouts (batched form) and their arguments
+  cudaGraphExec_t ograph = nullptr;      // gd_rollout_objective
+  const void* og_key[6] = {};
+  int og_steps = -1;
+  cudaGraphExec_t bgraph = nullptr;      // gd_rollout_backward
+  const void* bg_key[7] = {};
+  int bg_steps = -1;
   // LiDAR / view cone
   int lidar_n = 0;              // rays per agent (0 = not enabled)
   LidarFan fan{};
@@ -323,8 +341,24 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, afn, kAdjWarps * 32, env->adj_smem);
     if (e != cudaSuccess) return e;
     env->adj_grid = std::max(1, std::min(env->W, std::max(per_sm, 1) * nsm));
+    const void* ofn = reinterpret_cast<const void*>(k_adj_observer<kAdjObsWarps>);
+    e = allow_max_smem(ofn);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ofn, kAdjObsWarps * 32, kAdjObsSmem);
+    if (e != cudaSuccess) return e;
+    env->ao_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (env->A + kAdjObsWarps - 1) / kAdjObsWarps));
   }
   return cudaSuccess;
+}
+
+// Captured graphs hold kernel shapes and device pointers by value: any
+// change of shape or arena drops them (they are captured again on the next
+// call).
+static void drop_graphs(gd_env* env) {
+  for (cudaGraphExec_t* g : {&env->graph, &env->lgraph, &env->hgraph, &env->ograph, &env->bgraph}) {
+    if (*g) cudaGraphExecDestroy(*g);
+    *g = nullptr;
+  }
 }
 
 // Road arena for grid cell `cell` (m): per world one 16-byte aligned block of
@@ -427,18 +461,7 @@ static cudaError_t build_road(gd_env* env, float cell) {
   env->road_cell = cell;
   env->max_block = max_block;
   if ((e = shape_kernels(env, max_block)) != cudaSuccess) return e;
-  if (env->graph) {
-    cudaGraphExecDestroy(env->graph);
-    env->graph = nullptr;
-  }
-  if (env->lgraph) {
-    cudaGraphExecDestroy(env->lgraph);
-    env->lgraph = nullptr;
-  }
-  if (env->hgraph) {
-    cudaGraphExecDestroy(env->hgraph);
-    env->hgraph = nullptr;
-  }
+  drop_graphs(env);
   return cudaStreamSynchronize(env->stream);
 }
 
@@ -469,6 +492,7 @@ void gd_default_config(gd_config* c) {
   c->dynamics = GD_DYN_BICYCLE;
   c->nontrivial_dist = 2.f;
   c->obs_split = 1;
+  c->adjoint_split = 1;
 }
 
 const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
@@ -476,9 +500,7 @@ const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g
 gd_status gd_destroy(gd_env* env) {
   if (!env) return GD_OK;
   cudaStreamSynchronize(env->stream);
-  if (env->graph) cudaGraphExecDestroy(env->graph);
-  if (env->lgraph) cudaGraphExecDestroy(env->lgraph);
-  if (env->hgraph) cudaGraphExecDestroy(env->hgraph);
+  drop_graphs(env);
   for (void* p : env->allocs) cudaFree(p);
   if (env->h_err) cudaFreeHost(env->h_err);
   delete env;
@@ -507,6 +529,8 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
     return fail(nullptr, GD_ERR_INVALID_ARG, "block_size must be 0, 128, 256 or 512");
   if (c->topk_strategy < 0 || c->topk_strategy > 2) return fail(nullptr, GD_ERR_INVALID_ARG, "topk_strategy must be 0..2");
   if (c->obs_split != 0 && c->obs_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "obs_split must be 0 or 1");
+  if (c->adjoint_split != 0 && c->adjoint_split != 1)
+    return fail(nullptr, GD_ERR_INVALID_ARG, "adjoint_split must be 0 or 1");
   if (c->lidar_rays < 0 || c->lidar_rays > GD_MAX_LIDAR_RAYS)
     return fail(nullptr, GD_ERR_CAPACITY, "lidar_rays outside 0..GD_MAX_LIDAR_RAYS");
   if (!(c->lidar_fov >= 1e-3f) || !(c->lidar_fov <= 6.2831855f))
@@ -702,7 +726,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     // k_world's work counter and exit tally (each launch leaves them at zero), the adjoint's counter
     GD_TRY(dev_alloc(env, &env->counter, 2));
     GD_TRY(cudaMemsetAsync(env->counter, 0, 2 * sizeof(unsigned), env->stream));
-    GD_TRY(dev_alloc(env, &env->acounter, 1));
+    GD_TRY(dev_alloc(env, &env->acounter, 2));
+    GD_TRY(cudaMemsetAsync(env->acounter, 0, 2 * sizeof(unsigned), env->stream));
     GD_TRY(dev_alloc(env, &env->ocounter, OBS_STRIPES));
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
@@ -717,6 +742,11 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
     GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
+    GD_TRY(dev_alloc(env, &env->adj_g, (size_t)A));
+    GD_TRY(dev_alloc(env, &env->adj_cs, (size_t)A));
+    GD_TRY(dev_alloc(env, &env->adj_slot, (size_t)A * GD_MAX_AGENTS_PER_WORLD));
+    GD_TRY(dev_alloc(env, &env->adj_oc, ADJ_STRIPES));
+    GD_TRY(cudaMemsetAsync(env->adj_oc, 0, ADJ_STRIPES * sizeof(unsigned), env->stream));
     // K-th road distances of the objective rollout; 0x7f7f7f7f (3.4e38) = no bound
     GD_TRY(dev_alloc(env, &env->rk_hist, (size_t)cfg->episode_len * A));
     GD_TRY(cudaMemsetAsync(env->rk_hist, 0x7f, sizeof(float) * (size_t)cfg->episode_len * A, env->stream));
@@ -725,6 +755,7 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
   env->split = cfg->obs_split;
   env->notile = cfg->road_no_tile;
   env->adj_notile = cfg->road_no_tile;
+  env->adj_split = cfg->adjoint_split ? 1 : 0;
   env->d.topk = cfg->topk_strategy == 2 ? 2 : 1;
   if (cfg->lidar_rays > 0) {
     const int n = cfg->lidar_rays;
@@ -795,6 +826,8 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->lidar_road_tile = env->lw_notile ? 0 : 1;
   info->lidar_split = env->lw_split;
   info->obs_split = env->split;
+  info->adjoint_split = env->adj_split;
+  info->adjoint_road_tile = env->adj_notile ? 0 : 1;
   return GD_OK;
 }
 
@@ -847,7 +880,8 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          float* obs, int32_t* road_idx, int32_t* partner_idx, int do_step,
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
-                         unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES) {
+                         unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES, float4* state_out = nullptr,
+                         uint8_t* flags_out = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
@@ -887,6 +921,8 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.rk_out = (ell && obs) ? rk_out : nullptr;
   a.clear = clear;
   a.clear_n = clear ? clear_n : 0;
+  a.state_out = state_out;
+  a.flags_out = flags_out;
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
   const size_t smem = step_only ? env->step_smem : env->world_smem;
@@ -1365,14 +1401,94 @@ static gd_status need_diff(gd_env* env, const char* what) {
   return GD_OK;
 }
 
-// Copy (state, flags, t, episode-end status) between the env and a slot.
+// Optional instrumentation of a host-issued sequence of launches: CUDA
+// events around each launch, tagged with the launch's kind.
+struct LaunchTimer {
+  cudaStream_t stream = nullptr;
+  std::vector<int> kind;
+  std::vector<cudaEvent_t> ev;     // two per launch
+  cudaError_t err = cudaSuccess;
+  void begin(int k) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (err == cudaSuccess) err = cudaEventCreate(&a);
+    if (err == cudaSuccess) err = cudaEventCreate(&b);
+    if (err != cudaSuccess) return;
+    kind.push_back(k);
+    ev.push_back(a);
+    ev.push_back(b);
+    cudaEventRecord(a, stream);
+  }
+  void end() {
+    if (err == cudaSuccess && !ev.empty()) cudaEventRecord(ev.back(), stream);
+  }
+  ~LaunchTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+static void tbegin(LaunchTimer* tm, int k) { if (tm) tm->begin(k); }
+static void tend(LaunchTimer* tm) { if (tm) tm->end(); }
+
+// Copy (state, flags, t, episode-end status) between the env and a slot: one
+// launch of k_copy_snapshot.
 static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t* dWD, const float4* sS,
-                          const uint8_t* sF, const int* sT, const uint8_t* sWD) {
+                          const uint8_t* sF, const int* sT, const uint8_t* sWD, cudaStream_t stream = nullptr) {
+  if (!stream) stream = env->stream;
+  const Snapshot dst{dS, dF, dT, dWD};
+  const Snapshot src{const_cast<float4*>(sS), const_cast<uint8_t*>(sF), const_cast<int*>(sT),
+                     const_cast<uint8_t*>(sWD)};
+  const int n = std::max(env->A, env->W);
+  k_copy_snapshot<<<std::min(blocks_for(n, 256), 1184u), 256, 0, stream>>>(dst, src, env->A, env->W);
+}
+
+// Capture what `issue(stream)` launches on a private stream into *out (an
+// existing graph is replaced).
+extern "C++" {
+namespace {
+template <typename Fn>
+gd_status capture_graph(gd_env* env, cudaGraphExec_t* out, const char* what, Fn&& issue) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(env, e, what);
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return cuda_fail(env, e, what);
+  }
+  issue(cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return cuda_fail(env, e, what);
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return cuda_fail(env, e, what);
+  }
+  return GD_OK;
+}
+}  // namespace
+}  // extern "C++"
+
+// The objective rollout's launches: a checkpoint every C steps (one copy
+// launch), then the step (+ observation and objective) launches.
+static void issue_objective(gd_env* env, int steps, const float* actions, const float* obs_weight,
+                            float reward_weight, float* ell, float* obs, cudaStream_t stream) {
   const size_t A = (size_t)env->A, W = (size_t)env->W;
-  cudaMemcpyAsync(dS, sS, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
-  cudaMemcpyAsync(dF, sF, A, cudaMemcpyDeviceToDevice, env->stream);
-  if (dT) cudaMemcpyAsync(dT, sT, sizeof(int) * W, cudaMemcpyDeviceToDevice, env->stream);
-  if (dWD) cudaMemcpyAsync(dWD, sWD, W, cudaMemcpyDeviceToDevice, env->stream);
+  const DevEnv& d = env->d;
+  for (int t = 0; t < steps; ++t) {
+    if (t % env->C == 0) {
+      const int c = t / env->C;
+      copy_snapshot(env, env->ckS + c * A, env->ckF + c * A, env->ckT + c * W, env->ckWD + c * W, d.state, d.flags, d.t,
+                    d.world_done, stream);
+    }
+    launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, stream, nullptr,
+                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A);
+  }
 }
 
 gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
@@ -1393,26 +1509,47 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
     }
     obs = env->obs_scratch;
   }
-  const size_t A = (size_t)env->A, W = (size_t)env->W;
-  const DevEnv& d = env->d;
-  for (int t = 0; t < steps; ++t) {
-    if (t % env->C == 0) {
-      const int c = t / env->C;
-      copy_snapshot(env, env->ckS + c * A, env->ckF + c * A, env->ckT + c * W, env->ckWD + c * W, d.state, d.flags, d.t,
-                    d.world_done);
+  if (env->A > 0) {
+    if (!batched(env)) {
+      // plain form: every launch issued from the host
+      issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, env->stream);
+    } else {
+      // batched form: one captured graph, re-used while the arguments are the same
+      uint32_t rw_bits;
+      std::memcpy(&rw_bits, &reward_weight, sizeof(rw_bits));
+      const void* key[6] = {actions, obs_weight, ell, obs, (const void*)(uintptr_t)rw_bits, nullptr};
+      bool same = env->ograph && env->og_steps == steps;
+      for (int k = 0; k < 6 && same; ++k) same = env->og_key[k] == key[k];
+      if (!same) {
+        env->og_steps = -1;
+        st = capture_graph(env, &env->ograph, "gd_rollout_objective: capture", [&](cudaStream_t cs) {
+          issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, cs);
+        });
+        if (st != GD_OK) return st;
+        for (int k = 0; k < 6; ++k) env->og_key[k] = key[k];
+        env->og_steps = steps;
+      }
+      cudaError_t e = cudaGraphLaunch(env->ograph, env->stream);
+      if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_objective: graph launch");
     }
-    launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, nullptr, nullptr,
-                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A);
   }
   env->diff_actions = actions;
   env->diff_steps = steps;
   return launch_check(env, "gd_rollout_objective");
 }
 
+// Adjoint of one step (pre -> post under `actions`): the split form's two
+// launches (observer side over agents, then a thread per agent) or the
+// fused per-world launch.  lam_zero: the incoming adjoint is zero;
+// lam_copy: also write the outgoing adjoint there.  Neither form needs a
+// memset: each leaves its claim counters at zero.
 static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, const float4* post, const uint8_t* fpost,
                            const float* actions, const float* obs_w, long long stride, const float* row_scale,
-                           const float* rew_w, float reward_w, float* d_actions, const float* rk = nullptr) {
-  AdjArgs a;
+                           const float* rew_w, float reward_w, float* d_actions, const float* rk = nullptr,
+                           cudaStream_t stream = nullptr, int lam_zero = 0, float* lam_copy = nullptr,
+                           LaunchTimer* tm = nullptr) {
+  if (!stream) stream = env->stream;
+  AdjArgs a{};
   a.pre = pre;
   a.fpre = fpre;
   a.post = post;
@@ -1429,28 +1566,71 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
   a.counter = env->acounter;
   a.order = env->order;
   a.tile_bytes = env->adj_tile;
-  cudaMemsetAsync(env->acounter, 0, sizeof(unsigned), env->stream);
-  if (env->adj_notile)
-    k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
-  else
-    k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, env->stream>>>(env->d, a);
+  a.lam_zero = lam_zero;
+  a.lam_copy = reinterpret_cast<float4*>(lam_copy);
+  a.g_obs = env->adj_g;
+  a.cs_obs = env->adj_cs;
+  a.slot = env->adj_slot;
+  a.ocounter = env->adj_oc;
+  if (env->adj_split) {
+    if (obs_w) {
+      tbegin(tm, 2);
+      k_adj_observer<kAdjObsWarps><<<env->ao_grid, kAdjObsWarps * 32, kAdjObsSmem, stream>>>(env->d, a);
+      tend(tm);
+    }
+    tbegin(tm, 3);
+    k_adj_dynamics<<<blocks_for(env->A, 256), 256, 0, stream>>>(env->d, a);
+    tend(tm);
+  } else {
+    tbegin(tm, 2);
+    if (env->adj_notile)
+      k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, a);
+    else
+      k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, a);
+    tend(tm);
+  }
 }
 
 // Recompute `len` steps of the segment starting from segS[0] / segF[0] /
-// segT / segWD, leaving the state after step k in segS[k+1] / segF[k+1].
-static void recompute_segment(gd_env* env, const float* actions0, int len) {
+// segT / segWD, leaving the state after step k in segS[k+1] / segF[k+1]:
+// each step reads slot k and writes slot k + 1 (no copy between steps).
+static void recompute_segment(gd_env* env, const float* actions0, int len, cudaStream_t stream = nullptr,
+                              LaunchTimer* tm = nullptr) {
   const size_t A = (size_t)env->A;
   DevEnv dv = env->d;
   dv.t = env->segT;
   dv.world_done = env->segWD;
   for (int k = 0; k < len; ++k) {
-    cudaMemcpyAsync(env->segS + (k + 1) * A, env->segS + k * A, sizeof(float4) * A, cudaMemcpyDeviceToDevice,
-                    env->stream);
-    cudaMemcpyAsync(env->segF + (k + 1) * A, env->segF + k * A, A, cudaMemcpyDeviceToDevice, env->stream);
-    dv.state = env->segS + (k + 1) * A;
-    dv.flags = env->segF + (k + 1) * A;
-    launch_world(env, actions0 + (size_t)k * A * 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, nullptr,
-                 &dv);
+    dv.state = env->segS + k * A;
+    dv.flags = env->segF + k * A;
+    tbegin(tm, 1);
+    launch_world(env, actions0 + (size_t)k * A * 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, stream, &dv,
+                 nullptr, 0.f, nullptr, nullptr, nullptr, 0, env->segS + (k + 1) * A, env->segF + (k + 1) * A);
+    tend(tm);
+  }
+}
+
+// The backward pass's launches: per checkpoint segment, last first, the
+// segment's start copied from its checkpoint, its steps recomputed, then the
+// adjoint of each of its steps in reverse.
+static void issue_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                           float* d_actions, float* d_state0, cudaStream_t stream, LaunchTimer* tm = nullptr) {
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  const int T = env->diff_steps, C = env->C;
+  for (int seg = (T - 1) / C; seg >= 0; --seg) {
+    const int t0 = seg * C, len = std::min(C, T - t0);
+    tbegin(tm, 0);
+    copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->ckS + seg * A, env->ckF + seg * A,
+                  env->ckT + seg * W, env->ckWD + seg * W, stream);
+    tend(tm);
+    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, stream, tm);
+    for (int k = len - 1; k >= 0; --k) {
+      const int t = t0 + k;
+      launch_adjoint(env, env->segS + k * A, env->segF + k * A, env->segS + (k + 1) * A, env->segF + (k + 1) * A,
+                     env->diff_actions + (size_t)t * A * 2, obs_weight, 0, d_ell ? d_ell + (size_t)t * A : nullptr,
+                     nullptr, reward_weight, d_actions + (size_t)t * A * 2, env->rk_hist + (size_t)t * A, stream,
+                     t == T - 1, t == 0 ? d_state0 : nullptr, tm);
+    }
   }
 }
 
@@ -1463,23 +1643,61 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
   if (env->diff_steps < 1) return fail(env, GD_ERR_STATE, "gd_rollout_backward: no gd_rollout_objective to differentiate");
   if (!obs_weight || !d_actions) return fail(env, GD_ERR_INVALID_ARG, "obs_weight and d_actions must not be NULL");
   if (!aligned16(obs_weight)) return fail(env, GD_ERR_INVALID_ARG, "obs_weight must be 16-byte aligned");
-  const size_t A = (size_t)env->A, W = (size_t)env->W;
-  const int T = env->diff_steps, C = env->C;
-  cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
-  for (int seg = (T - 1) / C; seg >= 0; --seg) {
-    const int t0 = seg * C, len = std::min(C, T - t0);
-    copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->ckS + seg * A, env->ckF + seg * A,
-                  env->ckT + seg * W, env->ckWD + seg * W);
-    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len);
-    for (int k = len - 1; k >= 0; --k) {
-      const int t = t0 + k;
-      launch_adjoint(env, env->segS + k * A, env->segF + k * A, env->segS + (k + 1) * A, env->segF + (k + 1) * A,
-                     env->diff_actions + (size_t)t * A * 2, obs_weight, 0, d_ell ? d_ell + (size_t)t * A : nullptr,
-                     nullptr, reward_weight, d_actions + (size_t)t * A * 2, env->rk_hist + (size_t)t * A);
-    }
+  if (env->A == 0) return GD_OK;
+  if (!batched(env)) {
+    // plain form: every launch issued from the host
+    issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, env->stream);
+    return launch_check(env, "gd_rollout_backward");
   }
-  if (d_state0) cudaMemcpyAsync(d_state0, env->lam, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+  uint32_t rw_bits;
+  std::memcpy(&rw_bits, &reward_weight, sizeof(rw_bits));
+  const void* key[7] = {obs_weight, d_ell, d_actions, d_state0, env->diff_actions, (const void*)(uintptr_t)rw_bits,
+                        nullptr};
+  bool same = env->bgraph && env->bg_steps == env->diff_steps;
+  for (int k = 0; k < 7 && same; ++k) same = env->bg_key[k] == key[k];
+  if (!same) {
+    env->bg_steps = -1;
+    st = capture_graph(env, &env->bgraph, "gd_rollout_backward: capture", [&](cudaStream_t cs) {
+      issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs);
+    });
+    if (st != GD_OK) return st;
+    for (int k = 0; k < 7; ++k) env->bg_key[k] = key[k];
+    env->bg_steps = env->diff_steps;
+  }
+  cudaError_t e = cudaGraphLaunch(env->bgraph, env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_rollout_backward: graph launch");
   return launch_check(env, "gd_rollout_backward");
+}
+
+gd_status gd_time_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                           float* d_actions, float* d_state0, float* ms, int32_t* launches) {
+  NvtxRange range_("gd_time_backward");
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_diff(env, "gd_time_backward");
+  if (st != GD_OK) return st;
+  if (env->diff_steps < 1) return fail(env, GD_ERR_STATE, "gd_time_backward: no gd_rollout_objective to differentiate");
+  if (!obs_weight || !d_actions || !ms || !launches)
+    return fail(env, GD_ERR_INVALID_ARG, "obs_weight, d_actions, ms and launches must not be NULL");
+  if (!aligned16(obs_weight)) return fail(env, GD_ERR_INVALID_ARG, "obs_weight must be 16-byte aligned");
+  for (int k = 0; k < GD_BWD_KINDS; ++k) {
+    ms[k] = 0.f;
+    launches[k] = 0;
+  }
+  if (env->A == 0) return GD_OK;
+  LaunchTimer tm;
+  tm.stream = env->stream;
+  issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, env->stream, &tm);
+  cudaError_t e = tm.err;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
+  if (e != cudaSuccess) return cuda_fail(env, e, "gd_time_backward");
+  for (size_t q = 0; q < tm.kind.size(); ++q) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, tm.ev[2 * q], tm.ev[2 * q + 1]);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_time_backward: events");
+    ms[tm.kind[q]] += t;
+    launches[tm.kind[q]] += 1;
+  }
+  return launch_check(env, "gd_time_backward");
 }
 
 gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,
@@ -1492,14 +1710,13 @@ gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_sta
   const float* w = d_obs ? d_obs : obs_weight;
   if (w && !aligned16(w)) return fail(env, GD_ERR_INVALID_ARG, "d_obs / obs_weight must be 16-byte aligned");
   const size_t A = (size_t)env->A;
+  if (A == 0) return GD_OK;
   copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->d.state, env->d.flags, env->d.t,
                 env->d.world_done);
   recompute_segment(env, actions, 1);
   if (d_state_next) cudaMemcpyAsync(env->lam, d_state_next, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
-  else cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
   launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, actions, w, d_obs ? env->F : 0, nullptr,
-                 d_reward_s, 0.f, d_actions);
-  cudaMemcpyAsync(d_state, env->lam, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
+                 d_reward_s, 0.f, d_actions, nullptr, nullptr, d_state_next ? 0 : 1, d_state);
   return launch_check(env, "gd_step_backward");
 }
 
@@ -1641,8 +1858,8 @@ gd_status gd_autotune(gd_env* env) {
     d.topk = best_st;
     e = build_road(env, best_cell);
   }
-  // adjoint kernel (differentiable envs): road tile or not, timed on one
-  // step's adjoint about the current state
+  // adjoint (differentiable envs): the split form, or the fused form with or
+  // without the road tile, timed on one step's adjoint about the current state
   if (e == cudaSuccess && (env->cfg.flags & GD_DIFFERENTIABLE)) {
     float* wts = nullptr;
     float* dact = nullptr;
@@ -1658,16 +1875,16 @@ gd_status gd_autotune(gd_env* env) {
       recompute_segment(env, act, 1);
     }
     float abest = INFINITY;
-    int abest_nt = env->adj_notile;
-    for (int nt = 0; nt < 2 && e == cudaSuccess; ++nt) {
-      env->adj_notile = nt;
+    int abest_nt = env->adj_notile, abest_sp = env->adj_split;
+    for (int form = 0; form < 3 && e == cudaSuccess; ++form) {
+      env->adj_split = form == 0;
+      env->adj_notile = form == 2;
       if ((e = shape_kernels(env, env->max_block)) != cudaSuccess) break;
       float ms = INFINITY;
       for (int rep = 0; rep < 3; ++rep) {
-        cudaMemsetAsync(env->lam, 0, sizeof(float4) * A, env->stream);
         cudaEventRecord(e0, env->stream);
         launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, act, wts, 0, nullptr, nullptr, 1.f,
-                       dact);
+                       dact, nullptr, nullptr, 1);
         cudaEventRecord(e1, env->stream);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float t = 0.f;
@@ -1676,13 +1893,15 @@ gd_status gd_autotune(gd_env* env) {
       }
       if (e == cudaSuccess && ms < abest) {
         abest = ms;
-        abest_nt = nt;
+        abest_nt = env->adj_notile;
+        abest_sp = env->adj_split;
       }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
     dev_free(env, wts);
     dev_free(env, dact);
     env->adj_notile = abest_nt;
+    env->adj_split = abest_sp;
     if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
   // fused LiDAR kernel: CTA size, on the chosen road grid
@@ -1721,6 +1940,7 @@ gd_status gd_autotune(gd_env* env) {
     if (e == cudaSuccess) e = shape_kernels(env, env->max_block);
   }
   restore(0);
+  drop_graphs(env);
   if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_autotune");

@@ -264,4 +264,25 @@ __global__ void k_mark_uncontrolled(DevEnv e, uint8_t* __restrict__ init_flags, 
   }
 }
 
+// Grid-stride copy of a state snapshot (state and flags per agent, episode
+// step and episode-end status per world) in one launch: the checkpoints of a
+// differentiable rollout and the start of each recomputed segment.
+struct Snapshot {
+  float4* state;
+  uint8_t* flags;
+  int* t;
+  uint8_t* world_done;
+};
+__global__ void k_copy_snapshot(Snapshot dst, Snapshot src, int A, int W) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += stride) {
+    dst.state[i] = src.state[i];
+    dst.flags[i] = src.flags[i];
+  }
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += stride) {
+    dst.t[w] = src.t[w];
+    dst.world_done[w] = src.world_done[w];
+  }
+}
+
 }  // namespace gd

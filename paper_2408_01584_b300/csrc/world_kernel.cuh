@@ -52,6 +52,12 @@ struct FusedArgs {
   float* rk_out;             // [A] with ell: each observed agent's K-th road distance (+inf: fewer), or nullptr
   unsigned* clear;           // cleared (clear_n words) by the launch, for the launch that follows; or nullptr
   int clear_n;
+  // step out of place: the post-step state and flags go here instead of
+  // over e.state / e.flags (which the launch then only reads); nullptr = in
+  // place.  The backward pass recomputes a checkpoint segment this way, each
+  // step's state in its own slot, without a copy per step.
+  float4* state_out;
+  uint8_t* flags_out;
   LidarArgs lidar;           // LiDAR observation (k_world<W, true>); lidar.depth == nullptr: none
 };
 
@@ -487,8 +493,8 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
           r = (first ? 1.f : 0.f) - (coll ? e.cpen : 0.f) - (offr ? e.opn : 0.f);
         }
         ag.fl[tid] = f;
-        e.state[i] = ag.st[tid];
-        e.flags[i] = f;
+        (a.state_out ? a.state_out : e.state)[i] = ag.st[tid];
+        (a.flags_out ? a.flags_out : e.flags)[i] = f;
         if (a.reward) a.reward[i] = r;
         if (a.done) a.done[i] = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) ? 1 : 0;
         dn = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) != 0;

@@ -33,7 +33,8 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_step_observe", "gd_rollout", "gd_rollout_backward", "gd_step_backward", "gd_get_state",
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
-           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats", "gd_rollout_host")
+           "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats", "gd_rollout_host",
+           "gd_time_backward")
 
 GD_STATS = 5   # in the scene, controlled in the scene, goal, collided, off-road
 
@@ -59,7 +60,8 @@ class gd_config(C.Structure):
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32),
-                ("nontrivial_dist", C.c_float), ("road_no_tile", C.c_int32), ("obs_split", C.c_int32)]
+                ("nontrivial_dist", C.c_float), ("road_no_tile", C.c_int32), ("obs_split", C.c_int32),
+                ("adjoint_split", C.c_int32)]
 
 
 class gd_scene_batch(C.Structure):
@@ -77,7 +79,8 @@ class gd_info(C.Structure):
                 ("block_size", C.c_int32), ("road_cell", C.c_float), ("topk_strategy", C.c_int32),
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_road_tile", C.c_int32), ("lidar_split", C.c_int32),
-                ("road_tile", C.c_int32), ("obs_split", C.c_int32)]
+                ("road_tile", C.c_int32), ("obs_split", C.c_int32), ("adjoint_split", C.c_int32),
+                ("adjoint_road_tile", C.c_int32)]
 
 
 _lib = None
@@ -120,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_decimate.argtypes = [i32, i32, vp, vp, vp, f32, vp, vp]
     lib.gd_episode_stats.argtypes = [vp, vp, vp]
     lib.gd_rollout_host.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.gd_time_backward.argtypes = [vp, vp, f32, vp, vp, vp, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -320,6 +324,22 @@ def gd_rollout_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_stat
                                              _ptr(d_actions), _ptr(d_state0)))
 
 
+GD_BWD_KINDS = 4
+BWD_KINDS = ("checkpoint copy", "recomputed step", "adjoint observer side (or fused adjoint)",
+             "adjoint per-agent part")
+
+
+def gd_time_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0=None):
+    """gd_rollout_backward launch by launch under CUDA events: returns
+    (ms [4], launches [4]) per kind (see BWD_KINDS); blocks."""
+    lib = load_library()
+    ms = (C.c_float * GD_BWD_KINDS)()
+    n = (C.c_int32 * GD_BWD_KINDS)()
+    _check(lib, env, lib.gd_time_backward(env, _ptr(obs_weight, align=16), float(reward_weight), _ptr(d_ell),
+                                          _ptr(d_actions), _ptr(d_state0), ms, n))
+    return list(ms), list(n)
+
+
 def gd_step_backward(env, actions, d_state_next, d_obs, obs_weight, d_reward_s, d_state, d_actions):
     lib = load_library()
     _check(lib, env, lib.gd_step_backward(env, _ptr(actions), _ptr(d_state_next), _ptr(d_obs), _ptr(obs_weight),
@@ -360,11 +380,17 @@ def gd_collide_noalloc(agent_off, state, extent, active, cell, collided, stream=
     """Allocation-free collision query: agent_off is a HOST int32 array
     [W+1]; state [A,4], extent [A,2], active [A] (or None) and collided [A]
     are CUDA tensors.  See include/gd.h for who needs it."""
+    import torch
     lib = load_library()
     off = np.ascontiguousarray(agent_off, np.int32)
-    st = lib.gd_collide_noalloc(len(off) - 1, off.ctypes.data_as(C.c_void_p), _ptr(state, align=16),
-                                _ptr(extent, align=8), _ptr(active), float(cell), _ptr(collided),
-                                C.c_void_p(stream or 0))
+    # the C entry point cannot see the size of a device buffer: a tensor of
+    # the wrong dtype or length is refused here, before anything launches
+    A = int(off[-1]) if len(off) else 0
+    st = lib.gd_collide_noalloc(len(off) - 1, off.ctypes.data_as(C.c_void_p),
+                                _ptr(state, dtype=torch.float32, numel=4 * A, align=16),
+                                _ptr(extent, dtype=torch.float32, numel=2 * A, align=8),
+                                _ptr(active, dtype=torch.uint8, numel=A), float(cell),
+                                _ptr(collided, dtype=torch.uint8, numel=A), C.c_void_p(stream or 0))
     _check(lib, None, st)
 
 

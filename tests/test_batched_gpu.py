@@ -250,3 +250,24 @@ def test_envs_with_different_shared_memory_coexist():
         np.testing.assert_array_equal(x, y)
     big.close()
     small.close()
+
+
+def test_batched_teacher_forced_fwdbwd_subset_tuned():
+    # the forward step at the 8,192-world forward+backward workload's largest
+    # shapes (128 agents and 10,000 road points down to 32 and 5,000; K = 200,
+    # P = 63), autotuned, teacher-forced against the oracle for 5 steps on a
+    # sample of agents
+    from paper_2408_01584_b300 import gd
+    from paper_2408_01584_b300.gd import Env
+    wl = scenes.WORKLOADS["fwdbwd_8192"]
+    sc = scenes.make_scene(np.array([128, 96, 64, 32]), np.array([10000, 8300, 6700, 5000]), 2, n_poly=wl["n_poly"])
+    ocfg = workload_config("fwdbwd_8192")
+    acts = scenes.make_actions(5, sc.num_agents, 2)
+    env = Env(sc, **_batched(ocfg))
+    gd.gd_autotune(env.h)
+    info = gd.gd_get_info(env.h)
+    rng = np.random.default_rng(2)
+    agents = np.sort(rng.choice(sc.num_agents, 160, replace=False))
+    _, ex = teacher_forced(sc, ocfg, 5, acts, env=env, obs_agents=agents)
+    print(f"fwdbwd subset forward: split {info.obs_split}, block {info.block_size}, cell {info.road_cell}, "
+          f"exceptions {len(ex)}")

@@ -186,3 +186,45 @@ def test_road_edges_under_long_boxes(form):
     assert 0 < n_off < sc.num_agents, n_off    # both outcomes occur
     print("offroad:", n_off, "exceptions:", ex.items)
     env.close()
+
+
+def test_free_running_drift_91_steps():
+    # the per-step comparisons above are teacher-forced; this one lets the
+    # float32 GPU rollout and the float64 oracle each run on their own for a
+    # whole 91-step episode of 16 worlds of the 1,024 x 64 workload (same
+    # actions) and reports how far the states drift apart, per step, over
+    # the agents whose flags have agreed so far (a decision that flips near
+    # its cutoff sends an agent on another path, and its world's partners
+    # with it, so the world is dropped from that step on)
+    from paper_2408_01584_b300.gd import Env
+    sc = scenes.workload_scene("plain_1024x64", 0).subset(0, 16)
+    ocfg = workload_config("plain_1024x64", auto_reset=False)
+    T = 91
+    acts = scenes.make_actions(T, sc.num_agents, 0)
+    env = Env(sc, **gd_kwargs(ocfg))
+    ora = Oracle(sc, ocfg)
+    world = np.repeat(np.arange(sc.num_worlds), np.diff(sc.agent_off))
+    agree = np.ones(sc.num_worlds, bool)
+    pos_err, head_err, kept = [], [], []
+    for t in range(T):
+        env.step(torch.from_numpy(acts[t]).cuda())
+        env.sync()
+        ora.step(acts[t])
+        gs, gf, _ = [_np(x) for x in env.get_state()]
+        os_, of = ora.get_state()[:2]
+        bad = np.zeros(sc.num_worlds, bool)
+        np.logical_or.at(bad, world, gf != of)
+        agree &= ~bad
+        m = agree[world] & ((gf & 1) == 0)
+        d = np.abs(gs.astype(np.float64) - os_.astype(np.float64))
+        pos_err.append(float(np.hypot(d[m, 0], d[m, 1]).max()) if m.any() else 0.0)
+        head_err.append(float(d[m, 2].max()) if m.any() else 0.0)
+        kept.append(int(agree.sum()))
+    print("free-running drift, max position error (m) at steps 1, 10, 30, 60, 91:",
+          [f"{pos_err[k]:.2e}" for k in (0, 9, 29, 59, 90)],
+          "heading (rad):", [f"{head_err[k]:.2e}" for k in (0, 9, 29, 59, 90)],
+          "worlds still agreeing:", [kept[k] for k in (0, 9, 29, 59, 90)])
+    assert kept[9] >= 8
+    # rounding, not a modelling difference: far below a metre after a whole episode
+    assert max(pos_err) < 1e-2 and max(head_err) < 1e-3
+    env.close()

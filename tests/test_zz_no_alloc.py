@@ -69,20 +69,71 @@ def test_null_active_means_all_agents():
 
 
 def test_rejects_sizes_beyond_the_working_array():
+    # the capacity checks of the C entry point itself (called through ctypes
+    # directly: the binding would refuse these small tensors first)
+    import ctypes
     from paper_2408_01584_b300 import gd
+    lib = gd.load_library()
     state = torch.zeros(4, 4, device="cuda")
     extent = torch.ones(4, 2, device="cuda")
     out = torch.zeros(4, dtype=torch.uint8, device="cuda")
-    too_many_agents = np.concatenate([[0], np.full(2049, 128)]).cumsum().astype(np.int32)
-    with pytest.raises(gd.GdError) as e:
-        gd.gd_collide_noalloc(too_many_agents, state, extent, None, 5.0, out)
-    assert e.value.status == 4 and "GD_NOALLOC_MAX_AGENTS" in gd.gd_last_error(None)
-    with pytest.raises(gd.GdError) as e:
-        gd.gd_collide_noalloc(np.zeros(16386, np.int32), state, extent, None, 5.0, out)
-    assert e.value.status == 4 and "GD_NOALLOC_MAX_WORLDS" in gd.gd_last_error(None)
-    with pytest.raises(gd.GdError) as e:
-        gd.gd_collide_noalloc(np.array([0, 129], np.int32), state, extent, None, 5.0, out)
-    assert e.value.status == 4
-    with pytest.raises(gd.GdError) as e:
-        gd.gd_collide_noalloc(np.array([0, 4], np.int32), state, extent, None, 0.0, out)
-    assert e.value.status == 1
+
+    def call(off, cell=5.0):
+        off = np.ascontiguousarray(off, np.int32)
+        return lib.gd_collide_noalloc(len(off) - 1, off.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.c_void_p(state.data_ptr()), ctypes.c_void_p(extent.data_ptr()), None,
+                                      ctypes.c_float(cell), ctypes.c_void_p(out.data_ptr()), None)
+
+    too_many_agents = np.concatenate([[0], np.full(2049, 128)]).cumsum()
+    assert call(too_many_agents) == 4 and "GD_NOALLOC_MAX_AGENTS" in gd.gd_last_error(None)
+    assert call(np.zeros(16386)) == 4 and "GD_NOALLOC_MAX_WORLDS" in gd.gd_last_error(None)
+    assert call([0, 129]) == 4
+    assert call([0, 4], cell=0.0) == 1
+    torch.cuda.synchronize()
+    assert (out.cpu().numpy() == 0).all()          # nothing was launched
+
+
+def test_later_calls_allocate_nothing():
+    # after a first call (which loads the module and its array), further
+    # calls change neither the device's free memory nor the caching
+    # allocator's counts
+    gd, sc, env, extent = _setup()
+    env.step(torch.zeros(sc.num_agents, 2, device="cuda"))
+    state, _, _ = env.get_state()
+    out = torch.empty(sc.num_agents, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    gd.gd_collide_noalloc(sc.agent_off, state, extent, None, 5.0, out, stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(5):
+        gd.gd_collide_noalloc(sc.agent_off, state, extent, None, 5.0, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    stats1 = torch.cuda.memory_stats()
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert stats1.get(k, 0) == stats0.get(k, 0), k
+    env.close()
+
+
+def test_binding_refuses_wrong_sized_buffers():
+    # the C entry point cannot see device buffer sizes; the binding checks
+    # dtype and length against agent_off[-1] before anything launches
+    from paper_2408_01584_b300 import gd
+    off = np.array([0, 3, 4], np.int32)
+    state = torch.zeros(4, 4, device="cuda")
+    extent = torch.ones(4, 2, device="cuda")
+    out = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    gd.gd_collide_noalloc(off, state, extent, None, 5.0, out)      # the right sizes pass
+    torch.cuda.synchronize()
+    bad = [dict(collided=torch.zeros(3, dtype=torch.uint8, device="cuda")),
+           dict(state=torch.zeros(4, 4, dtype=torch.float64, device="cuda")),
+           dict(state=torch.zeros(3, 4, device="cuda")),
+           dict(extent=torch.ones(4, 3, device="cuda")),
+           dict(active=torch.ones(5, dtype=torch.uint8, device="cuda")),
+           dict(collided=torch.zeros(4, dtype=torch.int32, device="cuda"))]
+    for b in bad:
+        args = dict(state=state, extent=extent, active=None, collided=out)
+        args.update(b)
+        with pytest.raises(ValueError):
+            gd.gd_collide_noalloc(off, args["state"], args["extent"], args["active"], 5.0, args["collided"])
