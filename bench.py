@@ -52,17 +52,22 @@ def _kernel_source_hash(kernel="k_world"):
     return h.hexdigest()[:16]
 
 
-def _measured_traffic(workload, kernel="k_world"):
+def _measured_traffic(workload, kernel="k_world", shape=None):
     """DRAM bytes per launch of `kernel` from the committed ncu capture of
-    this workload, or None when the kernel sources changed since the
-    capture."""
+    this workload, or None when the kernel sources changed since the capture
+    or the capture's kernel shape (CTA size, road cell, tile, split) is not
+    the one in use."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("source_hash") == _kernel_source_hash(kernel) else None
+    if rec.get("source_hash") != _kernel_source_hash(kernel):
+        return None
+    if shape is not None and rec.get("shape") != shape:
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
 def _peaks():
@@ -185,6 +190,26 @@ def workload_cfg(name):
 # Observation launch of the split form, per agent besides the row (4F) and
 # the road: the agent's state (16 B), extents and goal (16 B) and flags (1 B).
 OBS_AGENT_BYTES = 33.0
+# Step launch per agent: reads state 16, extents and goal 16, flags 1, type 1,
+# action 8; writes state 16, flags 1, reward 4, done 1.  The road-edge
+# segments the off-road test reads are not counted (they are not in the
+# algorithmic byte formula; the step's DRAM traffic is about 3.6x this).
+STEP_AGENT_BYTES = 64.0
+# Checkpoint copy per agent: state and flags read and written.
+SNAPSHOT_AGENT_BYTES = 34.0
+
+
+def kernel_record(name, launches, total_ms, bytes_per_launch, peak, note=None):
+    """One kernel's roofline line: average launch duration (CUDA events) and
+    algorithmic bytes per launch against the HBM peak."""
+    us = total_ms * 1e3 / max(launches, 1)
+    gbs = bytes_per_launch / (us * 1e-6) / 1e9 if us > 0 else None
+    rec = {"kernel": name, "launches": int(launches), "avg_launch_us": us,
+           "algorithmic_bytes_per_launch": bytes_per_launch, "achieved_gbs": gbs,
+           "frac": gbs / peak if gbs else None, "bound": "hbm"}
+    if note:
+        rec["note"] = note
+    return rec
 
 
 def per_kernel_launch_us(env, actions, T, stream, flush):
@@ -209,16 +234,40 @@ def per_kernel_launch_us(env, actions, T, stream, flush):
     return {"step": step, "observe": obs}
 
 
-def algorithmic_bytes_per_agent_step(scene, F, radius=50.0):
+def forward_kernels(env, info, actions, T, stream, flush, ms_episode, road_bytes, peak):
+    """Roofline lines of the forward launches of a batched env: the step and
+    the observation launch of the split form (CUDA events around each launch
+    of one extra episode issued call by call), or the fused launch (episode
+    time / T).  Returns (kernels, dominant)."""
+    A, F = env.A, env.F
+    if info.obs_split:
+        us = per_kernel_launch_us(env, actions, T, stream, flush)
+        step = kernel_record("k_world (step only)", T, us["step"] * T / 1e3, STEP_AGENT_BYTES * A, peak,
+                             "road-edge segments read by the off-road test are not in the algorithmic bytes")
+        obs = kernel_record("k_observe_split (radial observation of every agent)", T, us["observe"] * T / 1e3,
+                            (4.0 * F + OBS_AGENT_BYTES + road_bytes) * A, peak)
+        obs["timing"] = step["timing"] = ("CUDA events around each launch of one extra episode issued call by call "
+                                          "(gd_step, then gd_observe)")
+        return [step, obs], obs
+    fused = kernel_record("k_world (fused step + observation)", T, ms_episode,
+                          (4.0 * F + 70.0 + road_bytes) * A, peak)
+    fused["timing"] = "episode time of the timed graph replays / steps"
+    return [fused], fused
+
+
+def algorithmic_bytes_per_agent_step(scene, F, radius=50.0, max_worlds=None):
     """Observation write 4F + state/action/flags ~70 B, and the road: 12 B
     (x, y, type/index) for every distinct road point of a world within the
     observation radius of at least one of its agents, per agent.  The road
     set is taken at the initial state, with every agent in the scene, so it
-    bounds the set of any later step from above."""
+    bounds the set of any later step from above.  max_worlds: count the road
+    over the first max_worlds worlds only and scale by their agents (for
+    the largest workloads)."""
     import numpy as np
     from scipy.spatial import cKDTree
     pts = 0
-    for w in range(scene.num_worlds):
+    nw = scene.num_worlds if max_worlds is None else min(scene.num_worlds, max_worlds)
+    for w in range(nw):
         a0, a1 = scene.agent_off[w], scene.agent_off[w + 1]
         r0, r1 = scene.road_off[w], scene.road_off[w + 1]
         if a1 == a0 or r1 == r0:
@@ -226,25 +275,27 @@ def algorithmic_bytes_per_agent_step(scene, F, radius=50.0):
         tree = cKDTree(np.stack([scene.road_x[r0:r1], scene.road_y[r0:r1]], 1).astype(np.float64))
         near = tree.query_ball_point(np.stack([scene.x[a0:a1], scene.y[a0:a1]], 1).astype(np.float64), radius)
         pts += len(set().union(*near))
-    road = 12.0 * pts / max(scene.num_agents, 1)
+    road = 12.0 * pts / max(int(scene.agent_off[nw]), 1)
     return 4.0 * F + 70.0, road
 
 
-def cpu_baseline(workload, seed, budget_s=12.0):
+def cpu_baseline(workload, seed, budget_s=12.0, scene=None, dynamics=0, actions=None):
     """The oracle as it stands, on a bounded sample of the same workload: the
     first 64 worlds, stepped (step + observe, episodes repeating the same
-    action sequence) until budget_s of wall-clock has passed."""
+    action sequence) until budget_s of wall-clock has passed.  scene: the
+    workload's scene when the caller has it already."""
     import numpy as np
     from oracle import Oracle, OracleConfig
     from oracle.oracle import num_threads
     from paper_2408_01584_b300 import scenes
     wl = scenes.WORKLOADS[workload]
-    sc = scenes.workload_scene(workload, seed).subset(0, min(64, wl["worlds"]))
+    sc = (scene if scene is not None else scenes.workload_scene(workload, seed)).subset(0, min(64, wl["worlds"]))
     cfg = OracleConfig(k_road=wl["k_road"], n_partners=wl["n_partners"], episode_len=wl["steps"],
                        term_collision=wl["term_collision"], term_offroad=wl["term_offroad"],
-                       auto_reset=wl["auto_reset"])
+                       auto_reset=wl["auto_reset"], nontrivial_init=bool(wl.get("nontrivial_init", False)),
+                       dynamics=dynamics)
     o = Oracle(sc, cfg)
-    acts = scenes.make_actions(wl["steps"], sc.num_agents, seed)
+    acts = scenes.make_actions(wl["steps"], sc.num_agents, seed) if actions is None else actions[:, :sc.num_agents]
     t0 = time.perf_counter()
     steps = 0
     while (time.perf_counter() - t0) < budget_s:
@@ -255,6 +306,30 @@ def cpu_baseline(workload, seed, budget_s=12.0):
     return {"value": steps * sc.num_agents / dt, "unit": METRIC, "cores": num_threads(), "kind": "oracle",
             "sample": f"first {sc.num_worlds} worlds ({sc.num_agents} agents) of {workload}, {steps} steps of "
                       f"step+observe, float64 brute force, OpenMP over worlds, {dt:.1f} s"}
+
+
+def cpu_baseline_fwdbwd(workload, scene, worlds, steps, seed=0):
+    """The oracle's forward + backward as it stands (oracle/gradient.py: the
+    float64 C++ oracle rollout, then float64 autograd along its decisions)
+    on the first `worlds` worlds of the workload for `steps` steps."""
+    import numpy as np
+    from oracle import OracleConfig
+    from oracle.gradient import objective_gradient
+    from oracle.oracle import num_threads
+    from paper_2408_01584_b300 import scenes
+    wl = scenes.WORKLOADS[workload]
+    sc = scene.subset(0, worlds)
+    cfg = OracleConfig(k_road=wl["k_road"], n_partners=wl["n_partners"], episode_len=wl["steps"],
+                       term_collision=wl["term_collision"], term_offroad=wl["term_offroad"],
+                       auto_reset=wl["auto_reset"])
+    acts = scenes.make_actions(steps, sc.num_agents, seed)
+    w = np.random.default_rng(seed).uniform(0, 1, cfg.feat)
+    t0 = time.perf_counter()
+    objective_gradient(sc, cfg, acts, w, 1.0)
+    dt = time.perf_counter() - t0
+    return {"value": steps * sc.num_agents / dt, "unit": METRIC + " (forward+backward)", "cores": num_threads(),
+            "kind": "oracle", "sample": f"first {worlds} worlds ({sc.num_agents} agents) of {workload}, {steps} steps: "
+                                        f"float64 brute-force rollout + float64 autograd gradient, {dt:.1f} s"}
 
 
 def whole_job_rate(units_per_rank, local_ms, world, device):
@@ -334,14 +409,17 @@ def controlled_agent_steps(done, static, agent_off):
     return total
 
 
-def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
-    """Batched rollouts (fused kernel, CUDA graph) of another workload."""
+def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0, road_worlds=256, cpu_s=8.0):
+    """Batched rollouts (persistent kernels, CUDA graph) of another
+    workload, with each forward kernel's roofline line and the oracle on
+    its first 64 worlds."""
     import torch
     from paper_2408_01584_b300 import gd, scenes
     wl = scenes.WORKLOADS[workload]
     T = wl["steps"]
     sc = scenes.workload_scene(workload, seed)
     cfg = workload_cfg(workload)
+    hbm, peak_kind = _peaks()
     with torch.cuda.stream(stream):
         env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_BATCHED))
         gd.gd_autotune(env.h)
@@ -360,22 +438,35 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0):
             run()
         ms = _time_rollouts(run, steps, stream, flush)
         gd.gd_sync(env.h)
-    act = active_agent_steps(done.cpu().numpy(), sc.agent_off)
-    ctl = controlled_agent_steps(done.cpu().numpy(), static, sc.agent_off)
+        done_h = done.cpu().numpy()
+        _, road = algorithmic_bytes_per_agent_step(sc, env.F, float(env.cfg.obs_radius), road_worlds)
+        kernels, dom = forward_kernels(env, info, actions, T, stream, flush, statistics.mean(ms), road, hbm)
+        gd.gd_sync(env.h)
+    act = active_agent_steps(done_h, sc.agent_off)
+    ctl = controlled_agent_steps(done_h, static, sc.agent_off)
     out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
            "active_agent_steps_per_s": act * steps / (sum(ms) / 1e3),
            "controlled_agent_steps_per_s": ctl * steps / (sum(ms) / 1e3),
            "uncontrolled_agents": int(static.sum()),
            "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile, "obs_split": info.obs_split}}
+                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile, "obs_split": info.obs_split},
+           "roofline": dict(dom, peak=hbm, peak_kind=peak_kind, unit="GB/s",
+                            road_bytes_per_agent=road,
+                            road_bytes_sample=f"road points within R of the agents of the first "
+                                              f"{min(road_worlds, sc.num_worlds)} worlds"),
+           "kernels": kernels}
     env.close()
+    out["cpu_baseline"] = cpu_baseline(workload, seed, budget_s=cpu_s, scene=sc)
     return out
 
 
-def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
+def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_worlds=256, cpu_worlds=8, cpu_steps=91):
     """Differentiable rollouts: objective forward (checkpoints every 10
-    steps) + adjoint backward over the whole episode."""
+    steps) + adjoint backward over the whole episode, each a captured CUDA
+    graph (batched form), against the same kernels issued from the host
+    (plain form); each kernel's roofline line from a launch-by-launch pass
+    under CUDA events; the oracle's forward + backward on a sample."""
     import numpy as np
     import torch
     from paper_2408_01584_b300 import gd, scenes
@@ -383,37 +474,97 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0):
     T = wl["steps"]
     sc = scenes.workload_scene(workload, seed)
     cfg = workload_cfg(workload)
+    hbm, peak_kind = _peaks()
+    res = {}
     with torch.cuda.stream(stream):
-        env = gd.Env(sc, stream=stream, **dict(cfg, flags=cfg["flags"] | gd.GD_DIFFERENTIABLE))
-        gd.gd_autotune(env.h)
-        info = gd.gd_get_info(env.h)
-        A, F = env.A, env.F
-        actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
-        w = torch.from_numpy(np.random.default_rng(seed).uniform(0, 1, F).astype(np.float32)).to(dev)
-        ell = torch.empty(T, A, device=dev)
-        d_act = torch.empty(T, A, 2, device=dev)
-        d_s0 = torch.empty(A, 4, device=dev)
+        for form in ("batched", "plain"):
+            fl = cfg["flags"] | gd.GD_DIFFERENTIABLE | (gd.GD_BATCHED if form == "batched" else 0)
+            env = gd.Env(sc, stream=stream, **dict(cfg, flags=fl))
+            gd.gd_autotune(env.h)
+            info = gd.gd_get_info(env.h)
+            A, F = env.A, env.F
+            actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
+            w = torch.from_numpy(np.random.default_rng(seed).uniform(0, 1, F).astype(np.float32)).to(dev)
+            ell = torch.empty(T, A, device=dev)
+            d_act = torch.empty(T, A, 2, device=dev)
+            d_s0 = torch.empty(A, 4, device=dev)
 
-        def fwd():
-            gd.gd_reset(env.h, None)
-            gd.gd_rollout_objective(env.h, T, actions, w, 1.0, ell, env.obs)
+            def fwd():
+                gd.gd_reset(env.h, None)
+                gd.gd_rollout_objective(env.h, T, actions, w, 1.0, ell, env.obs)
 
-        def fwdbwd():
-            fwd()
-            gd.gd_rollout_backward(env.h, w, 1.0, None, d_act, d_s0)
+            def fwdbwd():
+                fwd()
+                gd.gd_rollout_backward(env.h, w, 1.0, None, d_act, d_s0)
 
-        for _ in range(warmup):
-            fwdbwd()
-        ms_f = _time_rollouts(fwd, steps, stream, flush)
-        ms = _time_rollouts(fwdbwd, steps, stream, flush)
-        gd.gd_sync(env.h)
+            for _ in range(warmup):
+                fwdbwd()
+            ms_f = _time_rollouts(fwd, steps, stream, flush)
+            ms = _time_rollouts(fwdbwd, steps, stream, flush)
+            gd.gd_sync(env.h)
+            res[form] = {"value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC + " (forward+backward)",
+                         "ms_per_episode": statistics.mean(ms), "forward_only_ms_per_episode": statistics.mean(ms_f),
+                         "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
+                                       "topk_strategy": info.topk_strategy, "road_tile": info.road_tile,
+                                       "obs_split": info.obs_split, "adjoint_split": info.adjoint_split,
+                                       "adjoint_road_tile": info.adjoint_road_tile}}
+            if form == "batched":
+                # launch by launch under events: one objective rollout, one backward pass
+                flush_l2(flush)
+                gd.gd_reset(env.h, None)
+                ms_o, n_o = gd.gd_time_objective(env.h, T, actions, w, 1.0, ell, env.obs)
+                flush_l2(flush)
+                ms_b, n_b = gd.gd_time_backward(env.h, w, 1.0, None, d_act, d_s0)
+                _, road = algorithmic_bytes_per_agent_step(sc, F, float(env.cfg.obs_radius), road_worlds)
+                n_w = float((np.diff(sc.agent_off) ** 2).sum()) / A          # agents of an agent's world, averaged
+                kern = []
+                if n_o[0]:
+                    kern.append(kernel_record("k_copy_snapshot (checkpoint)", n_o[0], ms_o[0], SNAPSHOT_AGENT_BYTES * A,
+                                              hbm))
+                if info.obs_split:
+                    kern.append(kernel_record("k_world (step only, writes r_s)", n_o[1], ms_o[1],
+                                              (STEP_AGENT_BYTES + 4) * A, hbm))
+                    kern.append(kernel_record("k_observe_split<LOSS> (observation + objective term)", n_o[2], ms_o[2],
+                                              (4.0 * F + OBS_AGENT_BYTES + 12 + road) * A, hbm,
+                                              "row 4F, own state 33 B, ell read+write 8 B, K-th distance 4 B, road"))
+                else:
+                    kern.append(kernel_record("k_world (fused step + observation + objective)", n_o[2], ms_o[2],
+                                              (4.0 * F + 70.0 + 8 + road) * A, hbm))
+                kern.append(kernel_record("k_copy_snapshot (segment start)", n_b[0], ms_b[0], SNAPSHOT_AGENT_BYTES * A,
+                                          hbm))
+                kern.append(kernel_record("k_world (recomputed step, out of place)", n_b[1], ms_b[1],
+                                          STEP_AGENT_BYTES * A, hbm))
+                if info.adjoint_split:
+                    kern.append(kernel_record(
+                        "k_adj_observer (re-selection, observer-side gradient, slot rows)", n_b[2], ms_b[2],
+                        (16 + 16 + 1 + 4 + 16 + 8 + 128 + road) * A, hbm,
+                        "reads post state, extents, flags, K-th distance and the road; writes gradient, (cos, sin), "
+                        "128-byte slot row"))
+                    kern.append(kernel_record(
+                        "k_adj_dynamics (partner side, reward, dynamics adjoint)", n_b[3], ms_b[3],
+                        (16 + 16 + 16 + 1 + 16 + 1 + 8 + 16 + 8 + n_w + 16 + 8) * A, hbm,
+                        "reads gradient, post and pre state, extents, flags, action, adjoint, (cos, sin), its slot "
+                        "column; writes adjoint and action gradient"))
+                else:
+                    kern.append(kernel_record("k_adjoint (fused)", n_b[2], ms_b[2],
+                                              (16 + 16 + 1 + 16 + 1 + 8 + 16 + 4 + 16 + 8 + road) * A, hbm))
+                res[form]["kernels"] = kern
+                res[form]["road_bytes_per_agent"] = road
+                # dominant backward kernel
+                bwd = [k for k in kern if k["kernel"].startswith(("k_adj", "k_adjoint"))]
+                top = max(bwd, key=lambda k: k["avg_launch_us"] * k["launches"])
+                res[form]["roofline"] = dict(top, peak=hbm, peak_kind=peak_kind, unit="GB/s")
+            env.close()
+            del env
     out = {"workload": workload, "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road,
-           "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC + " (forward+backward)",
-           "ms_per_episode": statistics.mean(ms), "forward_only_ms_per_episode": statistics.mean(ms_f),
-           "ckpt_every": 10,
-           "autotuned": {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
-                         "topk_strategy": info.topk_strategy, "road_tile": info.road_tile, "obs_split": info.obs_split}}
-    env.close()
+           "value": res["batched"]["value"], "unit": METRIC + " (forward+backward)",
+           "ms_per_episode": res["batched"]["ms_per_episode"],
+           "forward_only_ms_per_episode": res["batched"]["forward_only_ms_per_episode"], "ckpt_every": 10,
+           "form": "batched: objective rollout and backward pass each one captured CUDA graph",
+           "autotuned": res["batched"]["autotuned"], "roofline": res["batched"]["roofline"],
+           "kernels": res["batched"]["kernels"],
+           "plain": dict(res["plain"], form="plain: the same kernels issued from the host launch by launch, no graph")}
+    out["cpu_baseline"] = cpu_baseline_fwdbwd(workload, sc, cpu_worlds, cpu_steps, seed)
     return out
 
 
@@ -469,8 +620,10 @@ def bench_lidar(workload, n_rays, fov, head, steps, warmup, dev, stream, flush, 
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
            "autotuned": {"lidar_block_size": info.lidar_block_size, "road_tile": info.lidar_road_tile,
                          "split": info.lidar_split, "road_cell_m": round(float(info.road_cell), 3)},
-           "hbm": {"achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                   "frac": achieved / hbm, "algorithmic_bytes_per_agent_step": algo},
+           "roofline": {"kernel": "k_lidar (split form) or k_world<LIDAR> (fused), as tuned", "bound": "hbm",
+                        "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": achieved / hbm, "algorithmic_bytes_per_agent_step": algo,
+                        "timing": "episode time of the timed graph replays / steps (both launches of a step)"},
            "cpu_baseline": {"value": reps * na / cpu_dt, "unit": "agent-scans/s", "cores": num_threads(),
                             "kind": "oracle", "sample": f"{na} agents of world 0, {reps} scans, {cpu_dt:.1f} s"}}
     env.close()
@@ -505,6 +658,10 @@ def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
         for _ in range(warmup):
             run()
         ms = _time_rollouts(run, steps, stream, flush)
+        hbm, peak_kind = _peaks()
+        _, road = algorithmic_bytes_per_agent_step(sc, env.F, float(env.cfg.obs_radius), 256)
+        kernels, _ = forward_kernels(env, gd.gd_get_info(env.h), actions, T, stream, flush, statistics.mean(ms), road,
+                                     hbm)
         # a trajectory of every agent (no agent leaves: per-stage steps without termination)
         envt = gd.Env(sc, stream=stream, goal_radius=0.0, dynamics=gd.GD_DYN_INVERTIBLE, k_road=0, n_partners=0)
         states = torch.empty(T + 1, A, 4, device=dev)
@@ -528,19 +685,34 @@ def bench_invertible(workload, steps, warmup, dev, stream, flush, seed=0):
     moving = np.abs(states[:-1, :, 3].cpu().numpy() * float(envt.cfg.dt)) > 0.05
     d = np.abs(rec.cpu().numpy() - acts_h)
     err = [float(d[..., 0].max()), float(d[..., 1][moving].max())]
-    hbm, peak_kind = _peaks()
     inv_s = statistics.median(ms_inv) / 1e3
     algo = (T + 1) * A * 16 + A * 16 + T * A * 8
+    inv_rec = kernel_record("k_invert (expert-action inversion, 91 steps of every agent)", 1, statistics.median(ms_inv),
+                            algo, hbm)
+    kernels.append(inv_rec)
+    # the oracle's inversion of the first 4,096 agents' trajectories (float64)
+    from oracle import OracleConfig
+    from oracle.oracle import invert as oracle_invert, num_threads
+    n_cpu = min(A, 4096)
+    st_h = states[:, :n_cpu].cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    oracle_invert(OracleConfig(dynamics=1), st_h, sc.length[:n_cpu])
+    cpu_inv_s = time.perf_counter() - t0
     out = {"workload": workload, "dynamics": "simplified invertible model", "agents": A,
+           "roofline": dict(inv_rec, peak=hbm, peak_kind=peak_kind, unit="GB/s"), "kernels": kernels,
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
            "inversion": {"value": T * A / inv_s, "unit": "agent-steps/s", "ms": statistics.median(ms_inv),
                          "timing": f"median of {len(ms_inv)} launches, each after an L2 flush",
                          "max_abs_error_accel_curvature": err,
                          "note": "curvature error over steps that moved more than 5 cm",
                          "hbm": {"achieved": algo / inv_s / 1e9, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                                 "frac": algo / inv_s / 1e9 / hbm, "algorithmic_bytes": algo}}}
+                                 "frac": algo / inv_s / 1e9 / hbm, "algorithmic_bytes": algo},
+                         "cpu_baseline": {"value": T * n_cpu / cpu_inv_s, "unit": "agent-steps/s",
+                                          "cores": num_threads(), "kind": "oracle",
+                                          "sample": f"{n_cpu} agents x {T} steps, float64, {cpu_inv_s:.2f} s"}}}
     env.close()
     envt.close()
+    out["cpu_baseline"] = cpu_baseline(workload, seed, budget_s=6.0, scene=sc, dynamics=1, actions=acts_h)
     return out
 
 
@@ -548,6 +720,7 @@ def bench_decimation(workload, steps, warmup, dev, stream, flush, seed=0):
     """Scene-load decimation (Sec. 3.1): gd_decimate over every polyline of
     the 0.1 m-sampled workload, and batched rollouts on the raw and on the
     decimated roads (the paper's claim: 10-15x fewer points, faster steps)."""
+    import numpy as np
     import torch
     from paper_2408_01584_b300 import gd, scenes
     wl = scenes.WORKLOADS[workload]
@@ -586,12 +759,28 @@ def bench_decimation(workload, steps, warmup, dev, stream, flush, seed=0):
                            "ms_per_episode": statistics.mean(ms), "road_points": scene.num_road,
                            "device_bytes": int(gd.gd_get_info(env.h).device_bytes)}
             env.close()
+    hbm, peak_kind = _peaks()
+    # the oracle's decimation of the first 32 worlds' polylines (float32, OpenMP over polylines)
+    from oracle.oracle import decimate as oracle_decimate, num_threads
+    n_poly_cpu = int(np.searchsorted(off, sc.road_off[min(32, sc.num_worlds)]))
+    t0 = time.perf_counter()
+    oracle_decimate(off[:n_poly_cpu + 1], sc.road_x[:off[n_poly_cpu]], sc.road_y[:off[n_poly_cpu]], gd.DECIMATE_AREA)
+    cpu_dec_s = time.perf_counter() - t0
+    # k_vw reads each point's x, y once and writes its keep byte, plus the offsets
+    vw = kernel_record("k_vw (Visvalingam-Whyatt, thread per polyline)", len(ms_dec), sum(ms_dec),
+                       9.0 * sc.num_road + 4.0 * len(off), hbm,
+                       "bound by the latency of one thread's sequential eliminations, not by HBM")
     return {"workload": workload, "decimation": {"points_in": sc.num_road, "points_kept": int(k.sum()),
                                                  "reduction": sc.num_road / max(int(k.sum()), 1),
                                                  "polylines": len(off) - 1, "area_tol_m2": gd.DECIMATE_AREA,
                                                  "ms": statistics.mean(ms_dec),
-                                                 "points_per_s": sc.num_road / (statistics.mean(ms_dec) / 1e3)},
-            "value": rates["decimated"]["value"], "unit": METRIC, "rollout": rates}
+                                                 "points_per_s": sc.num_road / (statistics.mean(ms_dec) / 1e3),
+                                                 "roofline": dict(vw, peak=hbm, peak_kind=peak_kind, unit="GB/s")},
+            "value": rates["decimated"]["value"], "unit": METRIC, "rollout": rates,
+            "roofline": dict(vw, peak=hbm, peak_kind=peak_kind, unit="GB/s"),
+            "cpu_baseline": {"value": int(off[n_poly_cpu]) / cpu_dec_s, "unit": "points/s (decimation)", "cores": num_threads(),
+                             "kind": "oracle", "sample": f"{n_poly_cpu} polylines ({int(off[n_poly_cpu])} points) of the "
+                                                         f"first 32 worlds, {cpu_dec_s:.2f} s"}}
 
 
 def run_profile(args):
@@ -721,32 +910,22 @@ def run_ours(args, rank, world):
         gd.gd_sync(env_b.h)
         e2e_ms = _time_rollouts(e2e_rollout, max(2, min(args.steps, 5)), stream, flush)
         gd.gd_sync(env_b.h)
-        kernel_us = per_kernel_launch_us(env_b, actions, T, stream, flush) if info.obs_split else None
+        bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F, float(env_b.cfg.obs_radius))
+        hbm, peak_kind = _peaks()
+        kernels, dom = forward_kernels(env_b, info, actions, T, stream, flush, statistics.mean(ms), bytes_road, hbm)
+        gd.gd_sync(env_b.h)
     agent_steps = T * A * world
     value = agent_steps * args.steps / (total_ms / 1e3)
-    bytes_obs, bytes_road = algorithmic_bytes_per_agent_step(sc, F, float(env_b.cfg.obs_radius))
-    hbm, peak_kind = _peaks()
-    if kernel_us:
-        # split form: the observation launch dominates (row write, agent state, road once per world)
-        kernel = "k_observe_split (radial observation of every agent)"
-        launch_s = kernel_us["observe"] / 1e6
-        roof_bytes = 4.0 * F + OBS_AGENT_BYTES + bytes_road
-        launches = 2 * args.steps * T
-        step_kernel = {"kernel": "k_world (step only)", "avg_launch_us": kernel_us["step"]}
-    else:
-        kernel = "k_world (fused step + observation)"
-        launch_s = statistics.mean(ms) / T / 1e3      # one fused launch = one simulator step of every world
-        roof_bytes = bytes_obs + bytes_road
-        launches = args.steps * T
-        step_kernel = None
-    achieved = roof_bytes * A / launch_s / 1e9
+    launches = (2 if info.obs_split else 1) * args.steps * T
+    shape = {"block_size": info.block_size, "road_cell_m": round(float(info.road_cell), 3),
+             "road_tile": info.road_tile, "obs_split": info.obs_split}
     out = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload,
                    "form": ("batched, split: per step a persistent step kernel over worlds and a persistent "
-                            "observation kernel over agents; 91-step CUDA graph") if kernel_us else
+                            "observation kernel over agents; 91-step CUDA graph") if info.obs_split else
                            "batched, fused: one persistent kernel per simulator step; 91-step CUDA graph",
                    "autotuned": tuned,
                    "worlds": sc.num_worlds, "agents": A, "road_points": sc.num_road, "k_road": cfg["k_road"],
@@ -756,17 +935,16 @@ def run_ours(args, rank, world):
                          f"{A * F * 4 / 1e6:.0f} MB per simulator step > 126 MB L2",
                    "parallelism": f"independent worlds, {world} GPU(s), no collective"},
         "e2e": {"value": agent_steps / world * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": METRIC,
-                "h2d_bytes_per_step": int(T * A * 8), "d2h_bytes_per_step": int(T * A * 5)},
+                "h2d_bytes_per_step": int(T * A * 8), "d2h_bytes_per_step": int(T * A * 5),
+                "note": "gd_rollout_host: actions in from pinned host memory, reward and done out, copies inside the "
+                        "timed region; the observations stay on the device (the C ABI's design: a learner on the "
+                        "same GPU reads them there)"},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved,
-                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": _measured_traffic(args.workload, "k_observe_split" if kernel_us else "k_world"),
-                     "algorithmic_bytes_per_agent_step": roof_bytes,
-                     "avg_launch_us": launch_s * 1e6,
-                     "timing": ("CUDA events around each launch of one extra episode issued call by call "
-                                "(gd_step, then gd_observe)") if kernel_us else
-                               "episode time of the timed graph replays / 91",
-                     **({"step_kernel": step_kernel} if step_kernel else {})},
+        "roofline": dict(dom, peak=hbm, peak_kind=peak_kind, unit="GB/s",
+                         traffic=_measured_traffic(args.workload, "k_observe_split" if info.obs_split else "k_world",
+                                                   shape),
+                         road_bytes_per_agent=bytes_road),
+        "kernels": kernels,
         "active_agent_steps_per_s": active_agent_steps(done_d.cpu().numpy(), sc.agent_off) * args.steps
         / (total_ms / 1e3),
         "plain": {"value": T * A * len(plain_ms) / (sum(plain_ms) / 1e3), "unit": METRIC,
@@ -782,8 +960,8 @@ def run_ours(args, rank, world):
         import math
         out["workloads"] = [bench_batched_forward("uneven_4096", 3, 1, dev, stream, flush),
                             bench_batched_forward("nontrivial_1024x64", 3, 1, dev, stream, flush),
-                            bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush),
-                            bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush),
+                            bench_fwdbwd("diff_512x32", 3, 1, dev, stream, flush, cpu_worlds=8),
+                            bench_fwdbwd("fwdbwd_8192", 2, 1, dev, stream, flush, cpu_worlds=4),
                             bench_lidar(args.workload, 3000, 2 * math.pi, False, 3, 1, dev, stream, flush),
                             bench_lidar(args.workload, 3000, 2 * math.pi / 3, True, 3, 1, dev, stream, flush),
                             bench_invertible(args.workload, 3, 1, dev, stream, flush),

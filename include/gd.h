@@ -371,6 +371,17 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
 gd_status gd_time_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
                            float* d_actions, float* d_state0, float* ms, int32_t* launches);
 
+/* Instrumentation, as gd_time_backward: gd_rollout_objective (same arguments
+ * and results; obs must not be NULL) with every launch issued from the host
+ * under CUDA events.  Blocks.  Kinds (GD_OBJ_KINDS):
+ *   0 checkpoint copies (k_copy_snapshot);
+ *   1 step launches of the split form (the step kernel, writing r_s);
+ *   2 observation launches of the split form (completing the objective
+ *     terms), or the fused step + observation launches. */
+#define GD_OBJ_KINDS 3
+gd_status gd_time_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
+                            float reward_weight, float* ell, float* obs, float* ms, int32_t* launches);
+
 /* Adjoint of one step about the CURRENT state and the given actions
  * (the step is not applied; requires GD_DIFFERENTIABLE): given
  * d_state_next [A,4] = dL/d(state after the step) (NULL = zero), the

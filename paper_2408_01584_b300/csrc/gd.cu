@@ -873,6 +873,48 @@ static void launch_observe(gd_env* env, float* obs, int32_t* road_idx, int32_t* 
       d, obs, road_idx, partner_idx);
 }
 
+// Optional instrumentation of a host-issued sequence of launches: CUDA
+// events around each launch, tagged with the launch's kind.
+struct LaunchTimer {
+  cudaStream_t stream = nullptr;
+  std::vector<int> kind;
+  std::vector<cudaEvent_t> ev;     // two per launch
+  cudaError_t err = cudaSuccess;
+  void begin(int k) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (err == cudaSuccess) err = cudaEventCreate(&a);
+    if (err == cudaSuccess) err = cudaEventCreate(&b);
+    if (err != cudaSuccess) return;
+    kind.push_back(k);
+    ev.push_back(a);
+    ev.push_back(b);
+    cudaEventRecord(a, stream);
+  }
+  void end() {
+    if (err == cudaSuccess && !ev.empty()) cudaEventRecord(ev.back(), stream);
+  }
+  // Wait for the stream, then add each launch's time to ms[kind] and count
+  // it in n[kind] (kinds below nk).
+  cudaError_t collect(float* ms, int32_t* n, int nk) {
+    cudaError_t e = err;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    for (size_t q = 0; q < kind.size() && e == cudaSuccess; ++q) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]);
+      if (e == cudaSuccess && kind[q] < nk) {
+        ms[kind[q]] += t;
+        n[kind[q]] += 1;
+      }
+    }
+    return e;
+  }
+  ~LaunchTimer() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+static void tbegin(LaunchTimer* tm, int k) { if (tm) tm->begin(k); }
+static void tend(LaunchTimer* tm) { if (tm) tm->end(); }
+
 // Batched form: one persistent launch (its work counter was left at zero by the previous one).
 // With env->split, an observation without the objective is the step launch
 // (nothing observed) followed by k_observe_split over all agents.
@@ -881,7 +923,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
                          unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES, float4* state_out = nullptr,
-                         uint8_t* flags_out = nullptr) {
+                         uint8_t* flags_out = nullptr, LaunchTimer* tm = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
@@ -891,16 +933,18 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
     // the step launch clears the observation counters; without a step, a memset does
     if (do_step)
       launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv, nullptr, 0.f, ell,
-                   nullptr, env->ocounter);
+                   nullptr, env->ocounter, (int)OBS_STRIPES, nullptr, nullptr, tm);
     else
       cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
     const SplitLoss loss{obs_w, reward_w, ell, rk_out};
+    tbegin(tm, 2);
     if (ell)
       k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
           *dv, obs, road_idx, partner_idx, env->ocounter, loss);
     else
       k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
           *dv, obs, road_idx, partner_idx, env->ocounter, loss);
+    tend(tm);
     return;
   }
   FusedArgs a{};
@@ -926,6 +970,11 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
   const size_t smem = step_only ? env->step_smem : env->world_smem;
+  tbegin(tm, step_only ? 1 : 2);
+  struct EndTimer {
+    LaunchTimer* t;
+    ~EndTimer() { tend(t); }
+  } end_timer_{tm};
   if (env->notile || step_only) {
     switch (env->warps) {
       case 4: k_world<4, false, true><<<grid, 4 * 32, smem, stream>>>(*dv, a); break;
@@ -1401,33 +1450,6 @@ static gd_status need_diff(gd_env* env, const char* what) {
   return GD_OK;
 }
 
-// Optional instrumentation of a host-issued sequence of launches: CUDA
-// events around each launch, tagged with the launch's kind.
-struct LaunchTimer {
-  cudaStream_t stream = nullptr;
-  std::vector<int> kind;
-  std::vector<cudaEvent_t> ev;     // two per launch
-  cudaError_t err = cudaSuccess;
-  void begin(int k) {
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (err == cudaSuccess) err = cudaEventCreate(&a);
-    if (err == cudaSuccess) err = cudaEventCreate(&b);
-    if (err != cudaSuccess) return;
-    kind.push_back(k);
-    ev.push_back(a);
-    ev.push_back(b);
-    cudaEventRecord(a, stream);
-  }
-  void end() {
-    if (err == cudaSuccess && !ev.empty()) cudaEventRecord(ev.back(), stream);
-  }
-  ~LaunchTimer() {
-    for (cudaEvent_t e : ev) cudaEventDestroy(e);
-  }
-};
-static void tbegin(LaunchTimer* tm, int k) { if (tm) tm->begin(k); }
-static void tend(LaunchTimer* tm) { if (tm) tm->end(); }
-
 // Copy (state, flags, t, episode-end status) between the env and a slot: one
 // launch of k_copy_snapshot.
 static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t* dWD, const float4* sS,
@@ -1477,17 +1499,21 @@ gd_status capture_graph(gd_env* env, cudaGraphExec_t* out, const char* what, Fn&
 // The objective rollout's launches: a checkpoint every C steps (one copy
 // launch), then the step (+ observation and objective) launches.
 static void issue_objective(gd_env* env, int steps, const float* actions, const float* obs_weight,
-                            float reward_weight, float* ell, float* obs, cudaStream_t stream) {
+                            float reward_weight, float* ell, float* obs, cudaStream_t stream,
+                            LaunchTimer* tm = nullptr) {
   const size_t A = (size_t)env->A, W = (size_t)env->W;
   const DevEnv& d = env->d;
   for (int t = 0; t < steps; ++t) {
     if (t % env->C == 0) {
       const int c = t / env->C;
+      tbegin(tm, 0);
       copy_snapshot(env, env->ckS + c * A, env->ckF + c * A, env->ckT + c * W, env->ckWD + c * W, d.state, d.flags, d.t,
                     d.world_done, stream);
+      tend(tm);
     }
     launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, stream, nullptr,
-                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A);
+                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A, nullptr,
+                 (int)OBS_STRIPES, nullptr, nullptr, tm);
   }
 }
 
@@ -1603,10 +1629,8 @@ static void recompute_segment(gd_env* env, const float* actions0, int len, cudaS
   for (int k = 0; k < len; ++k) {
     dv.state = env->segS + k * A;
     dv.flags = env->segF + k * A;
-    tbegin(tm, 1);
     launch_world(env, actions0 + (size_t)k * A * 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, stream, &dv,
-                 nullptr, 0.f, nullptr, nullptr, nullptr, 0, env->segS + (k + 1) * A, env->segF + (k + 1) * A);
-    tend(tm);
+                 nullptr, 0.f, nullptr, nullptr, nullptr, 0, env->segS + (k + 1) * A, env->segF + (k + 1) * A, tm);
   }
 }
 
@@ -1687,17 +1711,37 @@ gd_status gd_time_backward(gd_env* env, const float* obs_weight, float reward_we
   LaunchTimer tm;
   tm.stream = env->stream;
   issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, env->stream, &tm);
-  cudaError_t e = tm.err;
-  if (e == cudaSuccess) e = cudaStreamSynchronize(env->stream);
+  cudaError_t e = tm.collect(ms, launches, GD_BWD_KINDS);
   if (e != cudaSuccess) return cuda_fail(env, e, "gd_time_backward");
-  for (size_t q = 0; q < tm.kind.size(); ++q) {
-    float t = 0.f;
-    e = cudaEventElapsedTime(&t, tm.ev[2 * q], tm.ev[2 * q + 1]);
-    if (e != cudaSuccess) return cuda_fail(env, e, "gd_time_backward: events");
-    ms[tm.kind[q]] += t;
-    launches[tm.kind[q]] += 1;
-  }
   return launch_check(env, "gd_time_backward");
+}
+
+gd_status gd_time_objective(gd_env* env, int32_t steps, const float* actions, const float* obs_weight,
+                            float reward_weight, float* ell, float* obs, float* ms, int32_t* launches) {
+  NvtxRange range_("gd_time_objective");
+  if (!env) return GD_ERR_INVALID_ARG;
+  gd_status st = need_diff(env, "gd_time_objective");
+  if (st != GD_OK) return st;
+  if (steps < 1 || steps > env->n_ckpt * env->C)
+    return fail(env, GD_ERR_INVALID_ARG, "steps must be in 1..episode_len");
+  if (!actions || !obs_weight || !ell || !obs || !ms || !launches)
+    return fail(env, GD_ERR_INVALID_ARG, "actions, obs_weight, ell, obs, ms and launches must not be NULL");
+  if (!aligned16(obs_weight) || !aligned16(obs))
+    return fail(env, GD_ERR_INVALID_ARG, "obs_weight and obs must be 16-byte aligned");
+  for (int k = 0; k < GD_OBJ_KINDS; ++k) {
+    ms[k] = 0.f;
+    launches[k] = 0;
+  }
+  if (env->A > 0) {
+    LaunchTimer tm;
+    tm.stream = env->stream;
+    issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, env->stream, &tm);
+    cudaError_t e = tm.collect(ms, launches, GD_OBJ_KINDS);
+    if (e != cudaSuccess) return cuda_fail(env, e, "gd_time_objective");
+  }
+  env->diff_actions = actions;
+  env->diff_steps = steps;
+  return launch_check(env, "gd_time_objective");
 }
 
 gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_state_next, const float* d_obs,

@@ -34,7 +34,7 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
            "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats", "gd_rollout_host",
-           "gd_time_backward")
+           "gd_time_backward", "gd_time_objective")
 
 GD_STATS = 5   # in the scene, controlled in the scene, goal, collided, off-road
 
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_episode_stats.argtypes = [vp, vp, vp]
     lib.gd_rollout_host.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.gd_time_backward.argtypes = [vp, vp, f32, vp, vp, vp, vp, vp]
+    lib.gd_time_objective.argtypes = [vp, i32, vp, vp, f32, vp, vp, vp, vp]
     for name in SYMBOLS:
         fn = getattr(lib, name)
         if name not in ("gd_default_config", "gd_last_error"):
@@ -337,6 +338,21 @@ def gd_time_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0=
     n = (C.c_int32 * GD_BWD_KINDS)()
     _check(lib, env, lib.gd_time_backward(env, _ptr(obs_weight, align=16), float(reward_weight), _ptr(d_ell),
                                           _ptr(d_actions), _ptr(d_state0), ms, n))
+    return list(ms), list(n)
+
+
+GD_OBJ_KINDS = 3
+OBJ_KINDS = ("checkpoint copy", "step launch (split form)", "observation launch (or fused step + observation)")
+
+
+def gd_time_objective(env, steps, actions, obs_weight, reward_weight, ell, obs):
+    """gd_rollout_objective launch by launch under CUDA events: returns
+    (ms [3], launches [3]) per kind (see OBJ_KINDS); blocks."""
+    lib = load_library()
+    ms = (C.c_float * GD_OBJ_KINDS)()
+    n = (C.c_int32 * GD_OBJ_KINDS)()
+    _check(lib, env, lib.gd_time_objective(env, int(steps), _ptr(actions), _ptr(obs_weight, align=16),
+                                           float(reward_weight), _ptr(ell), _ptr(obs, align=16), ms, n))
     return list(ms), list(n)
 
 

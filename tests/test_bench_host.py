@@ -32,3 +32,27 @@ def test_controlled_agent_steps_excludes_uncontrolled_agents():
 def test_whole_job_rate_single_rank():
     t, rate = bench.whole_job_rate(1000, 250.0, 1, None)
     assert t == 250.0 and rate == 1000 / 0.25
+
+
+def test_kernel_record_arithmetic():
+    # 1 GB per launch in 1 ms is 1,000 GB/s: half of a 2,000 GB/s peak
+    r = bench.kernel_record("k", 4, 4.0, 1e9, 2000.0, "n")
+    assert r["launches"] == 4 and abs(r["avg_launch_us"] - 1000.0) < 1e-9
+    assert abs(r["achieved_gbs"] - 1000.0) < 1e-6 and abs(r["frac"] - 0.5) < 1e-9 and r["note"] == "n"
+
+
+def test_measured_traffic_keyed_on_sources_and_shape(tmp_path, monkeypatch):
+    import json
+    import os
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    h = bench._kernel_source_hash("k_observe_split")
+    shape = {"block_size": 128, "road_cell_m": 8.0, "road_tile": 0, "obs_split": 1}
+    with open(prof / "k_observe_split_w.traffic.json", "w") as f:
+        json.dump({"dram_bytes_per_launch": 5.0, "source_hash": h, "shape": shape}, f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda k: h)
+    assert bench._measured_traffic("w", "k_observe_split", shape) == 5.0
+    assert bench._measured_traffic("w", "k_observe_split", dict(shape, road_cell_m=12.0)) is None
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda k: "other")
+    assert bench._measured_traffic("w", "k_observe_split", shape) is None
