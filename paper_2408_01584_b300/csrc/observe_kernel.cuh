@@ -416,16 +416,21 @@ __device__ __forceinline__ int select_partners(const WorldView& v, int li, int P
   if (P == 0) return 0;
   int n = 0;
   const unsigned lt = (1u << lane) - 1u;
-  // two candidates per lane per round: both loads go out before either test
+  // two candidates per lane per round: the flags and states of both go out
+  // together, before any test (a done candidate's state is read for
+  // nothing, but no load waits for another)
   for (int j0 = 0; j0 < v.n; j0 += 2 * WARP) {
     bool live[2];
     float4 q[2];
+    uint8_t fj[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int j = j0 + u * WARP + lane;
-      live[u] = j < v.n && j != li && !(v.flags[j] & GD_FLAG_DONE);
-      q[u] = live[u] ? v.state[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+      fj[u] = j < v.n ? v.flags[j] : (uint8_t)GD_FLAG_DONE;
+      q[u] = j < v.n ? v.state[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) live[u] = j0 + u * WARP + lane != li && !(fj[u] & GD_FLAG_DONE);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const float d2 = dist2(q[u].x - ex, q[u].y - ey);
