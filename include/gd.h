@@ -454,6 +454,27 @@ const char* gd_last_error(const gd_env* env);
 gd_status gd_decimate(int32_t num_polylines, int32_t num_points, const int32_t* poly_off, const float* x,
                       const float* y, float area_tol, uint8_t* keep, void* cuda_stream);
 
+/* The same decimation over a whole scene batch at load, before gd_create.
+ * The polylines are the maximal runs of consecutive road points of one world
+ * with one road_poly id (lane centre lines and road edges alike).  The road
+ * arrays of `scene` (HOST memory, as for gd_create) are decimated on the
+ * device and the kept points written, in their order, world by world, to the
+ * caller's HOST arrays:
+ *   keep           uint8 [N] (1 = kept; N = road_off[num_worlds]) or NULL
+ *   road_off_out   int32 [num_worlds + 1], CSR offsets of the kept points
+ *   road_x_out, road_y_out  float [N]; road_type_out uint8 [N];
+ *   road_poly_out  int32 [N]  (the first *num_kept entries are written)
+ *   num_kept       int32: points kept
+ * The agent arrays are not read; a caller passes them on unchanged with the
+ * new road arrays to gd_create (road indices then count the kept points).
+ * Blocks until done (device buffers of about 13 bytes per point are taken
+ * from the stream-ordered allocator for the call).  Errors:
+ * GD_ERR_INVALID_ARG (NULL, bad offsets, bad tolerance), GD_ERR_OOM,
+ * GD_ERR_CUDA; message in gd_last_error(NULL). */
+gd_status gd_decimate_scene(const gd_scene_batch* scene, float area_tol, void* cuda_stream, uint8_t* keep,
+                            int32_t* road_off_out, float* road_x_out, float* road_y_out, uint8_t* road_type_out,
+                            int32_t* road_poly_out, int32_t* num_kept);
+
 /* ---- allocation-free collision query ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: a program whose GPU memory is owned by

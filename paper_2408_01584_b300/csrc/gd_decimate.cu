@@ -13,7 +13,9 @@
 // are float32 with the rounding spelled out (no contraction), so every
 // elimination decision is reproducible.
 #include <cstdint>
+#include <cstring>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -162,5 +164,86 @@ extern "C" gd_status gd_decimate(int32_t num_polylines, int32_t num_points, cons
     gd_set_thread_error(std::string("gd_decimate: launch: ") + cudaGetErrorString(e));
     return GD_ERR_CUDA;
   }
+  return GD_OK;
+}
+
+// Scene-level decimation: the polylines of a host scene batch (maximal runs
+// of consecutive road points of one world with one polyline id) decimated on
+// the device, then the kept points compacted on the host, world by world.
+extern "C" gd_status gd_decimate_scene(const gd_scene_batch* scene, float area_tol, void* cuda_stream, uint8_t* keep,
+                                       int32_t* road_off_out, float* road_x_out, float* road_y_out,
+                                       uint8_t* road_type_out, int32_t* road_poly_out, int32_t* num_kept) {
+  auto bad = [](const char* m) {
+    gd_set_thread_error(std::string("gd_decimate_scene: ") + m);
+    return GD_ERR_INVALID_ARG;
+  };
+  if (!scene || !road_off_out || !num_kept) return bad("scene, road_off_out and num_kept must not be NULL");
+  const int W = scene->num_worlds;
+  if (W < 0) return bad("num_worlds must be >= 0");
+  if (W > 0 && !scene->road_off) return bad("road_off must not be NULL");
+  if (!(area_tol >= 0.f) || !(area_tol < 3.0e38f)) return bad("area_tol must be finite and >= 0");
+  if (W > 0 && scene->road_off[0] != 0) return bad("road_off[0] must be 0");
+  for (int w = 0; w < W; ++w)
+    if (scene->road_off[w + 1] < scene->road_off[w]) return bad("road_off must be non-decreasing");
+  const int N = W > 0 ? scene->road_off[W] : 0;
+  if (N > 0 && (!scene->road_x || !scene->road_y || !scene->road_type || !scene->road_poly))
+    return bad("road_x, road_y, road_type and road_poly must not be NULL");
+  if (N > 0 && (!road_x_out || !road_y_out || !road_type_out || !road_poly_out))
+    return bad("road_x_out, road_y_out, road_type_out and road_poly_out must not be NULL");
+  // polylines: a new one starts at each world's first point and wherever the id changes
+  std::vector<int32_t> off;
+  off.reserve(1024);
+  for (int w = 0; w < W; ++w)
+    for (int p = scene->road_off[w]; p < scene->road_off[w + 1]; ++p)
+      if (p == scene->road_off[w] || scene->road_poly[p] != scene->road_poly[p - 1]) off.push_back(p);
+  off.push_back(N);
+  const int P = (int)off.size() - 1;
+  std::vector<uint8_t> k((size_t)N, 1);
+  if (N > 0) {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n = (size_t)N;
+    // one device block: polyline offsets, x, y, keep (each part 16-byte aligned)
+    const size_t b_off = ((size_t)(P + 1) * 4 + 15) & ~(size_t)15, b_xy = (n * 4 + 15) & ~(size_t)15;
+    void* dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&dev, b_off + 2 * b_xy + n, s);
+    if (e != cudaSuccess) {
+      gd_set_thread_error(std::string("gd_decimate_scene: device buffers: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA;
+    }
+    char* base = static_cast<char*>(dev);
+    int32_t* d_off = reinterpret_cast<int32_t*>(base);
+    float* d_x = reinterpret_cast<float*>(base + b_off);
+    float* d_y = reinterpret_cast<float*>(base + b_off + b_xy);
+    uint8_t* d_keep = reinterpret_cast<uint8_t*>(base + b_off + 2 * b_xy);
+    e = cudaMemcpyAsync(d_off, off.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_x, scene->road_x, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_y, scene->road_y, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    gd_status st = GD_OK;
+    if (e == cudaSuccess) st = gd_decimate(P, N, d_off, d_x, d_y, area_tol, d_keep, cuda_stream);
+    if (e == cudaSuccess && st == GD_OK) e = cudaMemcpyAsync(k.data(), d_keep, n, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dev, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (st != GD_OK) return st;
+    if (e != cudaSuccess) {
+      gd_set_thread_error(std::string("gd_decimate_scene: ") + cudaGetErrorString(e));
+      return GD_ERR_CUDA;
+    }
+  }
+  // compaction, world by world (kept points keep their order)
+  int m = 0;
+  road_off_out[0] = 0;
+  for (int w = 0; w < W; ++w) {
+    for (int p = scene->road_off[w]; p < scene->road_off[w + 1]; ++p) {
+      if (!k[(size_t)p]) continue;
+      road_x_out[m] = scene->road_x[p];
+      road_y_out[m] = scene->road_y[p];
+      road_type_out[m] = scene->road_type[p];
+      road_poly_out[m] = scene->road_poly[p];
+      ++m;
+    }
+    road_off_out[w + 1] = m;
+  }
+  if (keep && N > 0) std::memcpy(keep, k.data(), (size_t)N);
+  *num_kept = m;
   return GD_OK;
 }

@@ -34,7 +34,7 @@ SYMBOLS = ("gd_default_config", "gd_create", "gd_destroy", "gd_get_info", "gd_re
            "gd_set_state", "gd_autotune", "gd_sync", "gd_last_error", "gd_collide_noalloc",
            "gd_rollout_objective", "gd_selftest_timeout", "gd_observe_lidar", "gd_step_observe_lidar",
            "gd_rollout_lidar", "gd_invert_actions", "gd_decimate", "gd_episode_stats", "gd_rollout_host",
-           "gd_time_backward", "gd_time_objective")
+           "gd_time_backward", "gd_time_objective", "gd_decimate_scene")
 
 GD_STATS = 5   # in the scene, controlled in the scene, goal, collided, off-road
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
     lib.gd_rollout_lidar.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp]
     lib.gd_invert_actions.argtypes = [vp, i32, vp, vp]
     lib.gd_decimate.argtypes = [i32, i32, vp, vp, vp, f32, vp, vp]
+    lib.gd_decimate_scene.argtypes = [C.POINTER(gd_scene_batch), f32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.gd_episode_stats.argtypes = [vp, vp, vp]
     lib.gd_rollout_host.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.gd_time_backward.argtypes = [vp, vp, f32, vp, vp, vp, vp, vp]
@@ -169,13 +170,7 @@ def gd_default_config(**over) -> gd_config:
 def gd_create(cfg: gd_config, scene, stream=None):
     """Upload a ``scenes.Scene`` (host numpy arrays); returns the env handle."""
     lib = load_library()
-    arrs = dict(agent_off=np.ascontiguousarray(scene.agent_off, np.int32),
-                road_off=np.ascontiguousarray(scene.road_off, np.int32))
-    for k in ("x", "y", "theta", "v", "length", "width", "goal_x", "goal_y", "road_x", "road_y"):
-        arrs[k] = np.ascontiguousarray(getattr(scene, k), np.float32)
-    arrs["agent_type"] = np.ascontiguousarray(scene.agent_type, np.uint8)
-    arrs["road_type"] = np.ascontiguousarray(scene.road_type, np.uint8)
-    arrs["road_poly"] = np.ascontiguousarray(scene.road_poly, np.int32)
+    arrs = _scene_arrays(scene)
     sb = gd_scene_batch(num_worlds=scene.num_worlds, **{k: a.ctypes.data for k, a in arrs.items()})
     env = C.c_void_p()
     st = lib.gd_create(C.byref(cfg), C.byref(sb), C.c_void_p(stream or 0), C.byref(env))
@@ -290,27 +285,40 @@ def polylines(scene):
     return np.append(np.nonzero(brk)[0], N).astype(np.int32)
 
 
+def _scene_arrays(scene):
+    """Contiguous host arrays of a ``scenes.Scene`` in the C ABI's types."""
+    arrs = dict(agent_off=np.ascontiguousarray(scene.agent_off, np.int32),
+                road_off=np.ascontiguousarray(scene.road_off, np.int32))
+    for k in ("x", "y", "theta", "v", "length", "width", "goal_x", "goal_y", "road_x", "road_y"):
+        arrs[k] = np.ascontiguousarray(getattr(scene, k), np.float32)
+    arrs["agent_type"] = np.ascontiguousarray(scene.agent_type, np.uint8)
+    arrs["road_type"] = np.ascontiguousarray(scene.road_type, np.uint8)
+    arrs["road_poly"] = np.ascontiguousarray(scene.road_poly, np.int32)
+    return arrs
+
+
 def decimate_scene(scene, area_tol=DECIMATE_AREA, stream=None):
-    """The scene with its road polylines decimated on the GPU (gd_decimate);
+    """The scene with its road polylines decimated (gd_decimate_scene);
     returns (decimated scene, keep mask uint8 [N] over the original points).
     Road indices of the decimated scene count the kept points in order."""
     import dataclasses
-    import torch
-    off = polylines(scene)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    t_off = torch.from_numpy(off).to(dev)
-    tx = torch.from_numpy(np.ascontiguousarray(scene.road_x, np.float32)).to(dev)
-    ty = torch.from_numpy(np.ascontiguousarray(scene.road_y, np.float32)).to(dev)
-    keep = torch.empty(scene.num_road, dtype=torch.uint8, device=dev)
-    gd_decimate(t_off, tx, ty, area_tol, keep, stream)
-    k = keep.cpu().numpy()
-    m = k.astype(bool)
-    world = np.repeat(np.arange(scene.num_worlds), np.diff(scene.road_off))
-    road_off = np.zeros(scene.num_worlds + 1, np.int32)
-    road_off[1:] = np.cumsum(np.bincount(world[m], minlength=scene.num_worlds))
-    out = dataclasses.replace(scene, road_x=scene.road_x[m], road_y=scene.road_y[m], road_type=scene.road_type[m],
-                              road_poly=scene.road_poly[m], road_off=road_off)
-    return out, k
+    lib = load_library()
+    arrs = _scene_arrays(scene)
+    sb = gd_scene_batch(num_worlds=scene.num_worlds, **{k: a.ctypes.data for k, a in arrs.items()})
+    N = scene.num_road
+    keep = np.zeros(N, np.uint8)
+    off = np.zeros(scene.num_worlds + 1, np.int32)
+    rx, ry = np.zeros(N, np.float32), np.zeros(N, np.float32)
+    rt, rp = np.zeros(N, np.uint8), np.zeros(N, np.int32)
+    kept = C.c_int32(0)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    st = lib.gd_decimate_scene(C.byref(sb), float(area_tol), C.c_void_p(stream or 0), p(keep), p(off), p(rx), p(ry),
+                               p(rt), p(rp), C.byref(kept))
+    _check(lib, None, st)
+    m = kept.value
+    out = dataclasses.replace(scene, road_x=rx[:m].copy(), road_y=ry[:m].copy(), road_type=rt[:m].copy(),
+                              road_poly=rp[:m].copy(), road_off=off)
+    return out, keep
 
 
 def gd_rollout_objective(env, steps, actions, obs_weight, reward_weight, ell, obs=None):

@@ -120,6 +120,26 @@ def test_rejects_bad_arguments_before_any_launch(lib):
     assert lib.gd_decimate(1, 10, None, None, None, C.c_float(1e-3), None, None) == INV
     assert lib.gd_decimate(0, 0, None, None, None, C.c_float(1e-3), None, None) == 0
     assert "NULL" in gd.gd_last_error(None) or "must" in gd.gd_last_error(None)
+    # scene-level decimation: validated before any CUDA call
+    arrs = gd._scene_arrays(sc)
+    sb = gd.gd_scene_batch(num_worlds=sc.num_worlds, **{k: a.ctypes.data for k, a in arrs.items()})
+    off = np.zeros(sc.num_worlds + 1, np.int32)
+    kept = C.c_int32(0)
+    pv = lambda a: a.ctypes.data_as(C.c_void_p)
+    assert lib.gd_decimate_scene(None, C.c_float(1e-3), None, None, pv(off), None, None, None, None,
+                                 C.byref(kept)) == INV
+    assert lib.gd_decimate_scene(C.byref(sb), C.c_float(-1.0), None, None, pv(off), None, None, None, None,
+                                 C.byref(kept)) == INV
+    assert lib.gd_decimate_scene(C.byref(sb), C.c_float(1e-3), None, None, pv(off), None, None, None, None,
+                                 C.byref(kept)) == INV                     # output arrays missing
+    assert "road_x_out" in gd.gd_last_error(None)
+    bad_off = arrs["road_off"].copy()
+    bad_off[2] = bad_off[1] - 1
+    sb2 = gd.gd_scene_batch(num_worlds=sc.num_worlds, **dict({k: a.ctypes.data for k, a in arrs.items()},
+                                                              road_off=bad_off.ctypes.data))
+    assert lib.gd_decimate_scene(C.byref(sb2), C.c_float(1e-3), None, None, pv(off), None, None, None, None,
+                                 C.byref(kept)) == INV
+    assert "non-decreasing" in gd.gd_last_error(None)
     # NULL out pointer
     cfg = gd.gd_default_config()
     assert lib.gd_create(C.byref(cfg), None, None, None) == INV

@@ -67,3 +67,28 @@ def test_decimated_scene_runs_and_matches_oracle():
     acts = scenes.make_actions(15, dsc.num_agents, 4)
     _, ex = teacher_forced(dsc, ocfg, 15, acts, obs_every=3)
     print("exceptions:", ex.items)
+
+
+def test_decimate_scene_c_abi_full_size():
+    # gd_decimate_scene: the polylines split (maximal runs of one world's
+    # points with one id), decimated and compacted behind the C ABI, on the
+    # full 256 x 64 dense-road workload; keep mask bitwise against the
+    # oracle's on polylines split here independently, compaction against
+    # numpy masking
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("dense_roads_256x64", 0)
+    starts = [p for w in range(sc.num_worlds) for p in range(sc.road_off[w], sc.road_off[w + 1])
+              if p == sc.road_off[w] or sc.road_poly[p] != sc.road_poly[p - 1]]
+    off = np.array(starts + [sc.num_road], np.int32)
+    ref = decimate(off, sc.road_x, sc.road_y, gd.DECIMATE_AREA)
+    dsc, keep = gd.decimate_scene(sc)
+    np.testing.assert_array_equal(keep, ref)
+    m = ref.astype(bool)
+    np.testing.assert_array_equal(dsc.road_x, sc.road_x[m])
+    np.testing.assert_array_equal(dsc.road_y, sc.road_y[m])
+    np.testing.assert_array_equal(dsc.road_type, sc.road_type[m])
+    np.testing.assert_array_equal(dsc.road_poly, sc.road_poly[m])
+    world = np.repeat(np.arange(sc.num_worlds), np.diff(sc.road_off))
+    np.testing.assert_array_equal(np.diff(dsc.road_off), np.bincount(world[m], minlength=sc.num_worlds))
+    np.testing.assert_array_equal(dsc.x, sc.x)          # agents untouched
+    print(f"gd_decimate_scene: {sc.num_road} -> {dsc.num_road} points over {len(off) - 1} polylines")
