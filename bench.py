@@ -515,6 +515,9 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
                 ms_o, n_o = gd.gd_time_objective(env.h, T, actions, w, 1.0, ell, env.obs)
                 flush_l2(flush)
                 ms_b, n_b = gd.gd_time_backward(env.h, w, 1.0, None, d_act, d_s0)
+                # a split adjoint launch covers a whole segment: bytes per
+                # launch are the agent-step bytes of all T steps over the launches
+                seg = lambda per_agent_step, n: per_agent_step * A * T / max(n, 1)
                 _, road = algorithmic_bytes_per_agent_step(sc, F, float(env.cfg.obs_radius), road_worlds)
                 n_w = float((np.diff(sc.agent_off) ** 2).sum()) / A          # agents of an agent's world, averaged
                 kern = []
@@ -536,15 +539,15 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
                                           STEP_AGENT_BYTES * A, hbm))
                 if info.adjoint_split:
                     kern.append(kernel_record(
-                        "k_adj_observer (re-selection, observer-side gradient, slot rows)", n_b[2], ms_b[2],
-                        (16 + 16 + 1 + 4 + 16 + 8 + 128 + road) * A, hbm,
-                        "reads post state, extents, flags, K-th distance and the road; writes gradient, (cos, sin), "
-                        "128-byte slot row"))
+                        "k_adj_observer (a segment's re-selections, observer-side gradients, slot rows)", n_b[2],
+                        ms_b[2], seg(16 + 16 + 1 + 4 + 16 + 8 + 128 + road, n_b[2]), hbm,
+                        "per agent-step: reads post state, extents, flags, K-th distance and the road; writes "
+                        "gradient, (cos, sin), 128-byte slot row"))
                     kern.append(kernel_record(
-                        "k_adj_dynamics (partner side, reward, dynamics adjoint)", n_b[3], ms_b[3],
-                        (16 + 16 + 16 + 1 + 16 + 1 + 8 + 16 + 8 + n_w + 16 + 8) * A, hbm,
-                        "reads gradient, post and pre state, extents, flags, action, adjoint, (cos, sin), its slot "
-                        "column; writes adjoint and action gradient"))
+                        "k_adj_dynamics (a segment's partner sides, rewards, dynamics adjoints)", n_b[3], ms_b[3],
+                        seg(16 + 16 + 16 + 1 + 1 + 8 + 8 + n_w + 8, n_b[3]) + 2 * 16 * A, hbm,
+                        "per agent-step: reads gradient, post and pre state, flags, action, (cos, sin), its slot "
+                        "column; writes the action gradient; the adjoint is read and written once per segment"))
                 else:
                     kern.append(kernel_record("k_adjoint (fused)", n_b[2], ms_b[2],
                                               (16 + 16 + 1 + 16 + 1 + 8 + 16 + 4 + 16 + 8 + road) * A, hbm))

@@ -364,8 +364,10 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
  * of kind k (GD_BWD_KINDS entries each, host memory):
  *   0 checkpoint copies (k_copy_snapshot), one per segment;
  *   1 recomputed steps (the step kernel, out of place), one per step;
- *   2 the adjoint's observer side (split form) or the whole fused adjoint;
- *   3 the split adjoint's per-agent part (partner side and dynamics).
+ *   2 the adjoint's observer side (split form: one launch per checkpoint
+ *     segment, all its steps) or the whole fused adjoint (one per step);
+ *   3 the split adjoint's per-agent part (partner side and dynamics of all
+ *     the segment's steps, one launch per segment).
  * Per-launch averages are ms[k] / launches[k]. */
 #define GD_BWD_KINDS 4
 gd_status gd_time_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,

@@ -16,17 +16,20 @@
 //
 // Two forms compute the same sums in the same order, so their gradients are
 // bit-identical:
-//   split (default): k_adj_observer, persistent warps that claim agents one
-//     at a time (no per-world barrier): re-run the forward selection from
-//     global memory (same code, same state, so the same sets), accumulate the
-//     gradient on the observer's own state (lanes over slots, shuffle-tree
-//     reduction) and record which slot each partner sits in; then
-//     k_adj_dynamics, a thread per agent: gather the gradient it receives as
-//     somebody's partner in ascending order of the observer (a fixed order,
-//     so the sums are deterministic), add the reward term, apply the
-//     dynamics adjoint;
-//   fused: k_adjoint, one CTA per world (persistent, work list as in the
-//     forward kernel), both parts with the world in shared memory.
+//   split (default), one launch pair per checkpoint segment: k_adj_observer,
+//     persistent warps that claim (step, agent) tasks of the whole segment
+//     one at a time (no per-world barrier, and every step of the segment in
+//     one launch): re-run the forward selection from global memory (same
+//     code, same state, so the same sets), accumulate the gradient on the
+//     observer's own state (lanes over slots, shuffle-tree reduction) and
+//     record which slot each partner sits in; then k_adj_dynamics, a thread
+//     per agent that walks the segment's steps backwards with the adjoint in
+//     registers: gather the gradient the agent receives as somebody's
+//     partner in ascending order of the observer (a fixed order, so the sums
+//     are deterministic), add the reward term, apply the dynamics adjoint;
+//   fused: k_adjoint, one step per launch, one CTA per world (persistent,
+//     work list as in the forward kernel), both parts with the world in
+//     shared memory.
 #pragma once
 #include "gd_device.cuh"
 #include "observe_kernel.cuh"
@@ -34,31 +37,34 @@
 
 namespace gd {
 
+// Adjoint of `steps` consecutive steps (a segment; the fused form takes one
+// step, steps = 1).  Step k of the segment goes from S[k] to S[k + 1];
+// every per-step array holds one [A] slice per step.
 struct AdjArgs {
-  const float4* pre;        // [A] state before the step
-  const uint8_t* fpre;      // [A] flags before the step
-  const float4* post;       // [A] state after the step
-  const uint8_t* fpost;     // [A] flags after the step
-  const float2* actions;    // [A] actions of the step
+  const float4* S;          // [steps + 1][A] states: S[k] before step k, S[k + 1] after it
+  const uint8_t* F;         // [steps + 1][A] flags, likewise
+  const float2* actions;    // [steps][A] actions of the steps
   const float* obs_w;       // weight rows (obs_w + i * obs_w_stride), 16-byte aligned; nullptr = no obs term
   long long obs_w_stride;   // 0 = one row for every agent, F = one row per agent
-  const float* row_scale;   // [A] per-agent multiplier m_i, or nullptr (1)
-  const float* rew_w;       // [A] per-agent reward weight, or nullptr (reward_w)
+  const float* row_scale;   // [steps][A] per-agent multiplier m_i, or nullptr (1)
+  const float* rew_w;       // [A] per-agent reward weight (steps = 1 only), or nullptr (reward_w)
   float reward_w;
-  float4* lam;              // [A] in: dL/d post-step state; out: dL/d pre-step state
-  float2* d_actions;        // [A] out: dL/d (accel, steer)
-  const float* rk;          // [A] each agent's K-th road distance at this step in the forward rollout
-                            // (bounds the re-selection's disk), or nullptr: the full radius
-  unsigned* counter;         // fused form: [2] work counter and exit tally, left at zero by each launch
+  float4* lam;              // [A] in: dL/d state after the last step; out: dL/d state before the first
+  float2* d_actions;        // [steps][A] out: dL/d (accel, steer)
+  const float* rk;          // [steps][A] each agent's K-th road distance at the step in the forward
+                            // rollout (bounds the re-selection's disk), or nullptr: the full radius
+  unsigned* counter;        // fused form: [2] work counter and exit tally, left at zero by each launch
   const int* order;
   int tile_bytes;
-  int lam_zero;              // 1: the incoming lam is zero (the last step of a rollout); lam is not read
-  float4* lam_copy;          // [A] or nullptr: a second copy of the outgoing lam (d_state0 of the first step)
-  // split form
-  float4* g_obs;             // [A] observer-side gradient on each agent's own state (agents in the scene)
-  float2* cs_obs;            // [A] (cos, sin) of each observer's post-step heading (agents in the scene)
-  uint8_t* slot;             // [A][GD_MAX_AGENTS_PER_WORLD] slot of local partner j in observer i's row, 0xff = none
-  unsigned* ocounter;        // [ADJ_STRIPES] agent claims of k_adj_observer; k_adj_dynamics leaves them at zero
+  int lam_zero;             // 1: the incoming lam is zero (the last step of a rollout); lam is not read
+  float4* lam_copy;         // [A] or nullptr: a second copy of the outgoing lam (d_state0 of the first step)
+  int steps;
+  // split form, one slice per step of the segment
+  float4* g_obs;            // [steps][A] observer-side gradient on each agent's own state (agents in the scene)
+  float2* cs_obs;           // [steps][A] (cos, sin) of each observer's post-step heading (agents in the scene)
+  uint8_t* slot;            // [steps][A][GD_MAX_AGENTS_PER_WORLD] slot of local partner j in observer i's row,
+                            // 0xff = none
+  unsigned* ocounter;       // [ADJ_STRIPES] task claims of k_adj_observer; k_adj_dynamics leaves them at zero
 };
 
 constexpr unsigned ADJ_STRIPES = 32;
@@ -179,13 +185,14 @@ __device__ __forceinline__ float4 observer_gradient(const DevEnv& e, const World
   return make_float4(gx, gy, gt, gv);
 }
 
-// Radius of the re-selection of agent i: the forward step's K-th road
-// distance + 1e-3 m when it is below R, else R.
-__device__ __forceinline__ void reselect_radius(const DevEnv& e, const AdjArgs& a, int i, float& Rs, float& Rs2) {
+// Radius of the re-selection of agent i at step k: the forward step's K-th
+// road distance + 1e-3 m when it is below R, else R.
+__device__ __forceinline__ void reselect_radius(const DevEnv& e, const AdjArgs& a, int k, int i, float& Rs,
+                                                float& Rs2) {
   Rs = e.R;
   Rs2 = e.R2;
   if (a.rk) {
-    const float r = a.rk[i] + 1e-3f;
+    const float r = a.rk[(size_t)k * e.A + i] + 1e-3f;
     if (r < e.R) {
       Rs = r;
       Rs2 = r * r;
@@ -207,34 +214,33 @@ __device__ __forceinline__ void partner_term(float4& g, float ci, float si, floa
   g.w += m * we;
 }
 
-// Last part for agent ig: the smooth goal reward term (a controlled agent in
-// the scene before the step), lam += g, then the dynamics adjoint; writes
-// lam (and lam_copy) and d_actions.  st, sc: post-step state and extents/goal.
-__device__ __forceinline__ void finish_agent(const DevEnv& e, const AdjArgs& a, int ig, float4 g, float4 st,
-                                             float4 sc) {
-  const uint8_t f0 = a.fpre[ig];
+// Last part of step k for agent ig: the smooth goal reward term (a
+// controlled agent in the scene before the step), lam += g, then the
+// dynamics adjoint, which takes lam back to the state before the step;
+// writes d_actions of the step.  st, sc: post-step state and extents/goal.
+__device__ __forceinline__ void finish_step(const DevEnv& e, const AdjArgs& a, int k, int ig, float4 g, float4 st,
+                                            float4 sc, float4& lam) {
+  const size_t ik = (size_t)k * e.A + ig;
+  const uint8_t f0 = a.F[ik];
   if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
-    const float m = a.row_scale ? a.row_scale[ig] : 1.f;
+    const float m = a.row_scale ? a.row_scale[ik] : 1.f;
     const float rw = (a.rew_w ? a.rew_w[ig] : a.reward_w) * m;
     const float dx = st.x - sc.z, dy = st.y - sc.w, c = e.smooth_c;
     const float qn = sqrtf(fmaf(dx, dx, fmaf(dy, dy, __fmul_rn(c, c))));
     g.x -= rw * dx / qn;
     g.y -= rw * dy / qn;
   }
-  float4 lam = a.lam_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : a.lam[ig];
   lam.x += g.x;
   lam.y += g.y;
   lam.z += g.z;
   lam.w += g.w;
   float2 da = make_float2(0.f, 0.f);
   if (!(f0 & (GD_FLAG_DONE | GD_FLAG_STATIC))) {      // done and uncontrolled agents do not move
-    const float2 u = a.actions[ig];
-    if (e.dyn == 1) invertible_adjoint(a.pre[ig], u.x, u.y, e.dt, lam, da);
-    else bicycle_adjoint(a.pre[ig], u.x, u.y, sc.x, e.dt, e.vmax, lam, da);
+    const float2 u = a.actions[ik];
+    if (e.dyn == 1) invertible_adjoint(a.S[ik], u.x, u.y, e.dt, lam, da);
+    else bicycle_adjoint(a.S[ik], u.x, u.y, sc.x, e.dt, e.vmax, lam, da);
   }
-  a.lam[ig] = lam;
-  if (a.lam_copy) a.lam_copy[ig] = lam;
-  a.d_actions[ig] = da;
+  a.d_actions[ik] = da;
 }
 
 // ---- fused form --------------------------------------------------------------
@@ -280,13 +286,13 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
     }
     if (tid == 0) s_next = WARPS;
     if (tid < n) {
-      const float4 s = a.post[a0 + tid];
+      const float4 s = a.S[(size_t)e.A + a0 + tid];
       ag.st[tid] = s;
       float sn, cn;
       sincosf(s.z, &sn, &cn);
       ag.cs[tid] = make_float2(cn, sn);
       ag.sc[tid] = e.stat[a0 + tid];
-      ag.fl[tid] = a.fpost[a0 + tid];
+      ag.fl[tid] = a.F[(size_t)e.A + a0 + tid];
       ag.g[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int q = tid; q < n * n; q += WARPS * 32) ag.slot_of[q / n][q % n] = 0xff;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
         if (!(ag.fl[li] & GD_FLAG_DONE)) {
           const int i = a0 + li;
           float Rs, Rs2;
-          reselect_radius(e, a, i, Rs, Rs2);
+          reselect_radius(e, a, 0, i, Rs, Rs2);
           const float4 gr = observer_gradient(e, v, li, ag.st[li], ag.sc[li], ag.cs[li].x, ag.cs[li].y,
                                               a.obs_w + (size_t)i * a.obs_w_stride, Rs, Rs2, sm, lane,
                                               [&](int r, int j) { ag.slot_of[li][j] = (uint8_t)r; });
@@ -348,7 +354,10 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
                        a.row_scale ? a.row_scale[a0 + i] : 1.f);
         }
       }
-      finish_agent(e, a, ig, gj, ag.st[j], ag.sc[j]);
+      float4 lam = a.lam_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : a.lam[ig];
+      finish_step(e, a, 0, ig, gj, ag.st[j], ag.sc[j], lam);
+      a.lam[ig] = lam;
+      if (a.lam_copy) a.lam_copy[ig] = lam;
     }
     __syncthreads();
   }
@@ -363,15 +372,16 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_adjoint(D
 
 // ---- split form ----------------------------------------------------------------
 
-// Part 1: persistent warps claim agents one at a time from ADJ_STRIPES
-// striped counters (warp g draws agents c, c + ADJ_STRIPES, ... from counter
-// c = g mod ADJ_STRIPES; the counters are zero at launch) and, for an agent
-// in the scene after the step, re-select its row from global memory (the
-// world's agents and road block through L1/L2) and write its observer-side
-// gradient g_obs[i] (times m_i), its heading's (cos, sin) and its slot row:
-// slot[i][j] = the slot of local partner j, 0xff for every other agent.  A
-// done agent's row is all 0xff.  Dynamic shared memory: WARPS x
-// (ObsWarpSmem + 128 B).  Registers capped for 32 warps per SM.
+// Part 1: persistent warps claim (step, agent) tasks of the segment, step
+// major, one at a time from ADJ_STRIPES striped counters (warp g draws tasks
+// c, c + ADJ_STRIPES, ... from counter c = g mod ADJ_STRIPES; the counters
+// are zero at launch) and, for an agent in the scene after the step,
+// re-select its row from global memory (the world's agents and road block
+// through L1/L2) and write its observer-side gradient g_obs (times m_i), its
+// heading's (cos, sin) and its slot row: slot[i][j] = the slot of local
+// partner j, 0xff for every other agent.  A done agent's row is all 0xff.
+// Dynamic shared memory: WARPS x (ObsWarpSmem + 128 B).  Registers capped
+// for 32 warps per SM.
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv e, AdjArgs a) {
   extern __shared__ __align__(16) unsigned char adj_smem_raw[];
@@ -380,74 +390,95 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv 
   uint8_t* srow = adj_smem_raw + WARPS * sizeof(ObsWarpSmem) + wid * GD_MAX_AGENTS_PER_WORLD;
   static_assert(GD_MAX_AGENTS_PER_WORLD == 4 * WARP, "a slot row is one 32-bit word per lane");
   const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % ADJ_STRIPES;
+  const unsigned tasks = (unsigned)a.steps * (unsigned)e.A;
   for (;;) {
-    unsigned k = 0;
-    if (lane == 0) k = atomicAdd(a.ocounter + c, 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    const unsigned i = c + ADJ_STRIPES * k;
-    if (i >= (unsigned)e.A) break;
-    unsigned* grow = reinterpret_cast<unsigned*>(a.slot + (size_t)i * GD_MAX_AGENTS_PER_WORLD);
-    if (a.fpost[i] & GD_FLAG_DONE) {
+    unsigned kk = 0;
+    if (lane == 0) kk = atomicAdd(a.ocounter + c, 1u);
+    kk = __shfl_sync(0xffffffffu, kk, 0);
+    const unsigned q = c + ADJ_STRIPES * kk;
+    if (q >= tasks) break;
+    const int k = (int)(q / (unsigned)e.A), i = (int)(q - (unsigned)k * (unsigned)e.A);
+    const size_t ik = (size_t)k * e.A + i;
+    const float4* post = a.S + (size_t)(k + 1) * e.A;
+    const uint8_t* fpost = a.F + (size_t)(k + 1) * e.A;
+    unsigned* grow = reinterpret_cast<unsigned*>(a.slot + ik * GD_MAX_AGENTS_PER_WORLD);
+    if (fpost[i] & GD_FLAG_DONE) {
       grow[lane] = 0xffffffffu;
       continue;
     }
     reinterpret_cast<unsigned*>(srow)[lane] = 0xffffffffu;
     __syncwarp();
-    const float4 st = a.post[i], sc = e.stat[i];
+    const float4 st = post[i], sc = e.stat[i];
     const int w = e.agent_world[i];
     const int a0 = e.agent_off[w];
     WorldView v;
-    v.state = a.post + a0;
+    v.state = post + a0;
     v.stat = e.stat + a0;
     v.cs = nullptr;
-    v.flags = a.fpost + a0;
+    v.flags = fpost + a0;
     v.n = e.agent_off[w + 1] - a0;
     road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
     v.g = e.rgrid[w];
     float sn, cn;
     sincosf(st.z, &sn, &cn);
     float Rs, Rs2;
-    reselect_radius(e, a, (int)i, Rs, Rs2);
-    const float4 gr = observer_gradient(e, v, (int)i - a0, st, sc, cn, sn, a.obs_w + (size_t)i * a.obs_w_stride, Rs,
+    reselect_radius(e, a, k, i, Rs, Rs2);
+    const float4 gr = observer_gradient(e, v, i - a0, st, sc, cn, sn, a.obs_w + (size_t)i * a.obs_w_stride, Rs,
                                         Rs2, sm, lane, [&](int r, int j) { srow[j] = (uint8_t)r; });
     __syncwarp();
     grow[lane] = reinterpret_cast<const unsigned*>(srow)[lane];
     if (lane == 0) {
-      const float m = a.row_scale ? a.row_scale[i] : 1.f;
-      a.g_obs[i] = make_float4(m * gr.x, m * gr.y, m * gr.z, m * gr.w);
-      a.cs_obs[i] = make_float2(cn, sn);
+      const float m = a.row_scale ? a.row_scale[ik] : 1.f;
+      a.g_obs[ik] = make_float4(m * gr.x, m * gr.y, m * gr.z, m * gr.w);
+      a.cs_obs[ik] = make_float2(cn, sn);
     }
     __syncwarp();
   }
 }
 
-// Part 2: thread per agent j (flat over all agents): its own observer-side
-// gradient, then the partner side from every observer i of its world that
-// holds it (ascending i, the fused form's order), the reward term and the
-// dynamics adjoint.  Block 0 leaves part 1's claim counters at zero for the
-// next part-1 launch.
+// Part 2: thread per agent j (flat over all agents), the segment's steps
+// last to first with the adjoint in registers: per step its own
+// observer-side gradient, the partner side from every observer i of its
+// world that holds it (ascending i, the fused form's order), the reward term
+// and the dynamics adjoint.  Block 0 leaves part 1's claim counters at zero
+// for the next part-1 launch.
 __global__ void __launch_bounds__(256) k_adj_dynamics(DevEnv e, AdjArgs a) {
   if (blockIdx.x == 0 && threadIdx.x < ADJ_STRIPES) a.ocounter[threadIdx.x] = 0u;
   const int ig = blockIdx.x * blockDim.x + threadIdx.x;
   if (ig >= e.A) return;
-  const float4 st = a.post[ig], sc = e.stat[ig];
-  float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (a.obs_w) {
-    const int w = e.agent_world[ig];
-    const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0, j = ig - a0;
-    if (!(a.fpost[ig] & GD_FLAG_DONE)) g = a.g_obs[ig];
-    float2 cj;
-    sincosf(st.z, &cj.y, &cj.x);
-    const uint8_t* col = a.slot + (size_t)a0 * GD_MAX_AGENTS_PER_WORLD + j;
-    for (int i = 0; i < n; ++i) {
-      const int r = col[(size_t)i * GD_MAX_AGENTS_PER_WORLD];
-      if (r == 0xff) continue;
-      const float2 ci = a.cs_obs[a0 + i];
-      partner_term(g, ci.x, ci.y, cj, a.obs_w + (size_t)(a0 + i) * a.obs_w_stride, r,
-                   a.row_scale ? a.row_scale[a0 + i] : 1.f);
+  const float4 sc = e.stat[ig];
+  const int w = e.agent_world[ig];
+  const int a0 = e.agent_off[w], n = e.agent_off[w + 1] - a0, j = ig - a0;
+  float4 lam = a.lam_zero ? make_float4(0.f, 0.f, 0.f, 0.f) : a.lam[ig];
+  for (int k = a.steps - 1; k >= 0; --k) {
+    const size_t ik = (size_t)k * e.A + ig;
+    const float4 st = a.S[ik + e.A];
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.obs_w) {
+      if (!(a.F[ik + e.A] & GD_FLAG_DONE)) g = a.g_obs[ik];
+      float2 cj;
+      sincosf(st.z, &cj.y, &cj.x);
+      const size_t ko = (size_t)k * e.A + a0;       // the world's first agent at step k
+      const uint8_t* col = a.slot + ko * GD_MAX_AGENTS_PER_WORLD + j;
+      // the column's bytes are read eight at a time, so their loads overlap
+      for (int i0 = 0; i0 < n; i0 += 8) {
+        uint8_t rr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rr[u] = i0 + u < n ? col[(size_t)(i0 + u) * GD_MAX_AGENTS_PER_WORLD] : (uint8_t)0xff;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (rr[u] == 0xff) continue;
+          const int i = i0 + u;
+          const float2 ci = a.cs_obs[ko + i];
+          partner_term(g, ci.x, ci.y, cj, a.obs_w + (size_t)(a0 + i) * a.obs_w_stride, rr[u],
+                       a.row_scale ? a.row_scale[ko + i] : 1.f);
+        }
+      }
     }
+    finish_step(e, a, k, ig, g, st, sc, lam);
   }
-  finish_agent(e, a, ig, g, st, sc);
+  a.lam[ig] = lam;
+  if (a.lam_copy) a.lam_copy[ig] = lam;
 }
 
 }  // namespace gd

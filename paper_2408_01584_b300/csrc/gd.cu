@@ -134,9 +134,9 @@ struct gd_env {
   int adj_grid = 0;
   int adj_split = 1;            // 1: k_adj_observer + k_adj_dynamics; 0: one fused k_adjoint per step
   int ao_grid = 0;              // persistent CTAs of k_adj_observer
-  float4* adj_g = nullptr;      // [A] split adjoint: observer-side gradients
-  float2* adj_cs = nullptr;     // [A] split adjoint: observers' (cos, sin)
-  uint8_t* adj_slot = nullptr;  // [A][GD_MAX_AGENTS_PER_WORLD] split adjoint: partner slot rows
+  float4* adj_g = nullptr;      // [C][A] split adjoint: observer-side gradients, one slice per segment step
+  float2* adj_cs = nullptr;     // [C][A] split adjoint: observers' (cos, sin)
+  uint8_t* adj_slot = nullptr;  // [C][A][GD_MAX_AGENTS_PER_WORLD] split adjoint: partner slot rows
   unsigned* adj_oc = nullptr;   // [ADJ_STRIPES] k_adj_observer's claim counters (zero between launches)
   const float* diff_actions = nullptr;   // actions of the last objective rollout
   int diff_steps = 0;
@@ -346,7 +346,8 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ofn, kAdjObsWarps * 32, kAdjObsSmem);
     if (e != cudaSuccess) return e;
-    env->ao_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (env->A + kAdjObsWarps - 1) / kAdjObsWarps));
+    env->ao_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm,
+                                        (env->C * env->A + kAdjObsWarps - 1) / kAdjObsWarps));
   }
   return cudaSuccess;
 }
@@ -742,9 +743,9 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
     GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
-    GD_TRY(dev_alloc(env, &env->adj_g, (size_t)A));
-    GD_TRY(dev_alloc(env, &env->adj_cs, (size_t)A));
-    GD_TRY(dev_alloc(env, &env->adj_slot, (size_t)A * GD_MAX_AGENTS_PER_WORLD));
+    GD_TRY(dev_alloc(env, &env->adj_g, (size_t)env->C * A));
+    GD_TRY(dev_alloc(env, &env->adj_cs, (size_t)env->C * A));
+    GD_TRY(dev_alloc(env, &env->adj_slot, (size_t)env->C * A * GD_MAX_AGENTS_PER_WORLD));
     GD_TRY(dev_alloc(env, &env->adj_oc, ADJ_STRIPES));
     GD_TRY(cudaMemsetAsync(env->adj_oc, 0, ADJ_STRIPES * sizeof(unsigned), env->stream));
     // K-th road distances of the objective rollout; 0x7f7f7f7f (3.4e38) = no bound
@@ -1564,22 +1565,23 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
   return launch_check(env, "gd_rollout_objective");
 }
 
-// Adjoint of one step (pre -> post under `actions`): the split form's two
-// launches (observer side over agents, then a thread per agent) or the
-// fused per-world launch.  lam_zero: the incoming adjoint is zero;
-// lam_copy: also write the outgoing adjoint there.  Neither form needs a
-// memset: each leaves its claim counters at zero.
-static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, const float4* post, const uint8_t* fpost,
-                           const float* actions, const float* obs_w, long long stride, const float* row_scale,
-                           const float* rew_w, float reward_w, float* d_actions, const float* rk = nullptr,
-                           cudaStream_t stream = nullptr, int lam_zero = 0, float* lam_copy = nullptr,
-                           LaunchTimer* tm = nullptr) {
+// Adjoint of `steps` consecutive steps, S[k] -> S[k + 1] under actions[k]
+// (S, F: steps + 1 slices of A states / flags; the per-step arrays: steps
+// slices of A): the split form's launch pair for the whole segment
+// (observer side over (step, agent) tasks, then a thread per agent over the
+// steps), or one fused per-world launch per step, last step first.
+// lam_zero: the adjoint after the last step is zero; lam_copy: also write
+// the adjoint before the first step there.  Neither form needs a memset:
+// each leaves its claim counters at zero.
+static void launch_adjoint(gd_env* env, const float4* S, const uint8_t* F, const float* actions, int steps,
+                           const float* obs_w, long long stride, const float* row_scale, const float* rew_w,
+                           float reward_w, float* d_actions, const float* rk = nullptr, cudaStream_t stream = nullptr,
+                           int lam_zero = 0, float* lam_copy = nullptr, LaunchTimer* tm = nullptr) {
   if (!stream) stream = env->stream;
+  const size_t A = (size_t)env->A;
   AdjArgs a{};
-  a.pre = pre;
-  a.fpre = fpre;
-  a.post = post;
-  a.fpost = fpost;
+  a.S = S;
+  a.F = F;
   a.actions = reinterpret_cast<const float2*>(actions);
   a.obs_w = obs_w;
   a.obs_w_stride = stride;
@@ -1594,6 +1596,7 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
   a.tile_bytes = env->adj_tile;
   a.lam_zero = lam_zero;
   a.lam_copy = reinterpret_cast<float4*>(lam_copy);
+  a.steps = steps;
   a.g_obs = env->adj_g;
   a.cs_obs = env->adj_cs;
   a.slot = env->adj_slot;
@@ -1607,12 +1610,24 @@ static void launch_adjoint(gd_env* env, const float4* pre, const uint8_t* fpre, 
     tbegin(tm, 3);
     k_adj_dynamics<<<blocks_for(env->A, 256), 256, 0, stream>>>(env->d, a);
     tend(tm);
-  } else {
+    return;
+  }
+  for (int k = steps - 1; k >= 0; --k) {
+    AdjArgs ak = a;
+    ak.S = S + (size_t)k * A;
+    ak.F = F + (size_t)k * A;
+    ak.actions = a.actions + (size_t)k * A;
+    ak.row_scale = row_scale ? row_scale + (size_t)k * A : nullptr;
+    ak.rk = rk ? rk + (size_t)k * A : nullptr;
+    ak.d_actions = a.d_actions + (size_t)k * A;
+    ak.steps = 1;
+    ak.lam_zero = lam_zero && k == steps - 1;
+    ak.lam_copy = k == 0 ? a.lam_copy : nullptr;
     tbegin(tm, 2);
     if (env->adj_notile)
-      k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, a);
+      k_adjoint<kAdjWarps, true><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, ak);
     else
-      k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, a);
+      k_adjoint<kAdjWarps><<<env->adj_grid, kAdjWarps * 32, env->adj_smem, stream>>>(env->d, ak);
     tend(tm);
   }
 }
@@ -1648,13 +1663,9 @@ static void issue_backward(gd_env* env, const float* obs_weight, float reward_we
                   env->ckT + seg * W, env->ckWD + seg * W, stream);
     tend(tm);
     recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, stream, tm);
-    for (int k = len - 1; k >= 0; --k) {
-      const int t = t0 + k;
-      launch_adjoint(env, env->segS + k * A, env->segF + k * A, env->segS + (k + 1) * A, env->segF + (k + 1) * A,
-                     env->diff_actions + (size_t)t * A * 2, obs_weight, 0, d_ell ? d_ell + (size_t)t * A : nullptr,
-                     nullptr, reward_weight, d_actions + (size_t)t * A * 2, env->rk_hist + (size_t)t * A, stream,
-                     t == T - 1, t == 0 ? d_state0 : nullptr, tm);
-    }
+    launch_adjoint(env, env->segS, env->segF, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
+                   d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
+                   env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm);
   }
 }
 
@@ -1759,8 +1770,8 @@ gd_status gd_step_backward(gd_env* env, const float* actions, const float* d_sta
                 env->d.world_done);
   recompute_segment(env, actions, 1);
   if (d_state_next) cudaMemcpyAsync(env->lam, d_state_next, sizeof(float4) * A, cudaMemcpyDeviceToDevice, env->stream);
-  launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, actions, w, d_obs ? env->F : 0, nullptr,
-                 d_reward_s, 0.f, d_actions, nullptr, nullptr, d_state_next ? 0 : 1, d_state);
+  launch_adjoint(env, env->segS, env->segF, actions, 1, w, d_obs ? env->F : 0, nullptr, d_reward_s, 0.f, d_actions,
+                 nullptr, nullptr, d_state_next ? 0 : 1, d_state);
   return launch_check(env, "gd_step_backward");
 }
 
@@ -1927,8 +1938,7 @@ gd_status gd_autotune(gd_env* env) {
       float ms = INFINITY;
       for (int rep = 0; rep < 3; ++rep) {
         cudaEventRecord(e0, env->stream);
-        launch_adjoint(env, env->segS, env->segF, env->segS + A, env->segF + A, act, wts, 0, nullptr, nullptr, 1.f,
-                       dact, nullptr, nullptr, 1);
+        launch_adjoint(env, env->segS, env->segF, act, 1, wts, 0, nullptr, nullptr, 1.f, dact, nullptr, nullptr, 1);
         cudaEventRecord(e1, env->stream);
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float t = 0.f;
