@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv 
 // world that holds it (ascending i, the fused form's order), the reward term
 // and the dynamics adjoint.  Block 0 leaves part 1's claim counters at zero
 // for the next part-1 launch.
-__global__ void __launch_bounds__(256) k_adj_dynamics(DevEnv e, AdjArgs a) {
+__global__ void __launch_bounds__(64) k_adj_dynamics(DevEnv e, AdjArgs a) {
   if (blockIdx.x == 0 && threadIdx.x < ADJ_STRIPES) a.ocounter[threadIdx.x] = 0u;
   const int ig = blockIdx.x * blockDim.x + threadIdx.x;
   if (ig >= e.A) return;

@@ -1607,8 +1607,10 @@ static void launch_adjoint(gd_env* env, const float4* S, const uint8_t* F, const
       k_adj_observer<kAdjObsWarps><<<env->ao_grid, kAdjObsWarps * 32, kAdjObsSmem, stream>>>(env->d, a);
       tend(tm);
     }
+    // 64-thread blocks: a thread's loop is latency-bound, so the blocks are
+    // spread over every SM even when there are few agents
     tbegin(tm, 3);
-    k_adj_dynamics<<<blocks_for(env->A, 256), 256, 0, stream>>>(env->d, a);
+    k_adj_dynamics<<<blocks_for(env->A, 64), 64, 0, stream>>>(env->d, a);
     tend(tm);
     return;
   }
