@@ -191,6 +191,10 @@ typedef struct gd_info {
   int32_t adjoint_split;                            /* 1: the step's adjoint is two launches (split form) */
   int32_t adjoint_road_tile;                        /* 1: the fused adjoint copies each world's road into
                                                        shared memory */
+  int32_t objective_graph_kernels, objective_graph_other;  /* nodes of the captured gd_rollout_objective graph:
+                                                              kernel launches, other nodes (copies, memsets);
+                                                              0 while none is captured */
+  int32_t backward_graph_kernels, backward_graph_other;    /* the same for gd_rollout_backward */
 } gd_info;
 
 typedef struct gd_env gd_env;

@@ -147,6 +147,8 @@ struct gd_env {
   cudaGraphExec_t bgraph = nullptr;      // gd_rollout_backward
   const void* bg_key[7] = {};
   int bg_steps = -1;
+  int og_nodes[2] = {0, 0};              // node counts of the captured objective graph: kernels, others
+  int bg_nodes[2] = {0, 0};              // and of the backward graph
   // LiDAR / view cone
   int lidar_n = 0;              // rays per agent (0 = not enabled)
   LidarFan fan{};
@@ -829,6 +831,10 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->obs_split = env->split;
   info->adjoint_split = env->adj_split;
   info->adjoint_road_tile = env->adj_notile ? 0 : 1;
+  info->objective_graph_kernels = env->ograph ? env->og_nodes[0] : 0;
+  info->objective_graph_other = env->ograph ? env->og_nodes[1] : 0;
+  info->backward_graph_kernels = env->bgraph ? env->bg_nodes[0] : 0;
+  info->backward_graph_other = env->bgraph ? env->bg_nodes[1] : 0;
   return GD_OK;
 }
 
@@ -1467,8 +1473,10 @@ static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t
 // existing graph is replaced).
 extern "C++" {
 namespace {
+// Capture what `issue(stream)` launches; nodes[0] / nodes[1] receive the
+// graph's kernel nodes / other nodes (copies, memsets, ...) when given.
 template <typename Fn>
-gd_status capture_graph(gd_env* env, cudaGraphExec_t* out, const char* what, Fn&& issue) {
+gd_status capture_graph(gd_env* env, cudaGraphExec_t* out, const char* what, Fn&& issue, int* nodes = nullptr) {
   if (*out) {
     cudaGraphExecDestroy(*out);
     *out = nullptr;
@@ -1486,6 +1494,19 @@ gd_status capture_graph(gd_env* env, cudaGraphExec_t* out, const char* what, Fn&
   e = cudaStreamEndCapture(cap, &g);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return cuda_fail(env, e, what);
+  if (nodes) {
+    size_t n = 0;
+    nodes[0] = nodes[1] = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess && n > 0) {
+      std::vector<cudaGraphNode_t> v(n);
+      if (cudaGraphGetNodes(g, v.data(), &n) == cudaSuccess) {
+        for (size_t q = 0; q < n; ++q) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(v[q], &t) == cudaSuccess) ++nodes[t == cudaGraphNodeTypeKernel ? 0 : 1];
+        }
+      }
+    }
+  }
   e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -1549,9 +1570,10 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
       for (int k = 0; k < 6 && same; ++k) same = env->og_key[k] == key[k];
       if (!same) {
         env->og_steps = -1;
-        st = capture_graph(env, &env->ograph, "gd_rollout_objective: capture", [&](cudaStream_t cs) {
-          issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, cs);
-        });
+        st = capture_graph(
+            env, &env->ograph, "gd_rollout_objective: capture",
+            [&](cudaStream_t cs) { issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, cs); },
+            env->og_nodes);
         if (st != GD_OK) return st;
         for (int k = 0; k < 6; ++k) env->og_key[k] = key[k];
         env->og_steps = steps;
@@ -1694,9 +1716,10 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
   for (int k = 0; k < 7 && same; ++k) same = env->bg_key[k] == key[k];
   if (!same) {
     env->bg_steps = -1;
-    st = capture_graph(env, &env->bgraph, "gd_rollout_backward: capture", [&](cudaStream_t cs) {
-      issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs);
-    });
+    st = capture_graph(
+        env, &env->bgraph, "gd_rollout_backward: capture",
+        [&](cudaStream_t cs) { issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs); },
+        env->bg_nodes);
     if (st != GD_OK) return st;
     for (int k = 0; k < 7; ++k) env->bg_key[k] = key[k];
     env->bg_steps = env->diff_steps;

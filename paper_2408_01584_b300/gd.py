@@ -80,7 +80,9 @@ class gd_info(C.Structure):
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_road_tile", C.c_int32), ("lidar_split", C.c_int32),
                 ("road_tile", C.c_int32), ("obs_split", C.c_int32), ("adjoint_split", C.c_int32),
-                ("adjoint_road_tile", C.c_int32)]
+                ("adjoint_road_tile", C.c_int32), ("objective_graph_kernels", C.c_int32),
+                ("objective_graph_other", C.c_int32), ("backward_graph_kernels", C.c_int32),
+                ("backward_graph_other", C.c_int32)]
 
 
 _lib = None

@@ -288,12 +288,22 @@ def test_graph_pair_equals_host_issued_launches():
     rng = np.random.default_rng(12)
     w = rng.uniform(0, 1, ocfg.feat)
     d_ell = rng.uniform(0.5, 1.5, (T, sc.num_agents))
-    host, _ = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell)
-    graph, _ = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell, reps=3, flags=_kw(ocfg)["flags"] | gd.GD_BATCHED)
+    host, info_h = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell)
+    graph, info = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell, reps=3, flags=_kw(ocfg)["flags"] | gd.GD_BATCHED)
     for rep in graph:
         for a, b in zip(host[0], rep):
             np.testing.assert_array_equal(a, b)
     assert np.isfinite(host[0][1]).all() and np.isfinite(host[0][2]).all()
+    # the graphs hold kernel launches only, no copy or memset node: the
+    # objective one launch pair per step (split form) plus a checkpoint copy
+    # kernel per segment, the backward per segment a checkpoint copy, the
+    # recomputed steps and the adjoint launch pair (split form)
+    segs = (T + 9) // 10
+    assert info_h.objective_graph_kernels == 0 and info_h.backward_graph_kernels == 0     # nothing captured
+    assert info.objective_graph_other == 0 and info.backward_graph_other == 0
+    per_step = 2 if info.obs_split else 1
+    assert info.objective_graph_kernels == per_step * T + segs
+    assert info.backward_graph_kernels == segs + T + (2 * segs if info.adjoint_split else T)
 
 
 @pytest.mark.parametrize("form", [dict(adjoint_split=0, road_no_tile=0), dict(adjoint_split=0, road_no_tile=1)])
