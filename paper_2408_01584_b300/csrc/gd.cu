@@ -102,7 +102,9 @@ struct gd_env {
   int warps = kWorldWarps;     // CTA size of k_world (4, 8 or 16 warps)
   int split = 1;               // radial observation: 1 = k_world step, then k_observe_split over agents
   int so_grid = 0;             // persistent CTAs of k_observe_split
-  unsigned* ocounter = nullptr;  // its agent counters (OBS_STRIPES)
+  unsigned* ocounter = nullptr;  // its agent counters (2 x OBS_STRIPES: the overlapped rollout alternates sets)
+  float4* alt_state = nullptr;   // [A] the overlapped rollout's second state buffer
+  uint8_t* alt_flags = nullptr;  // [A] and flag buffer
   float road_cell = 8.f;       // road grid cell (m)
   size_t max_block = 16;       // largest road block (bytes)
   // host copy of the road, to rebuild the road blocks for another cell size
@@ -731,7 +733,11 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaMemsetAsync(env->counter, 0, 2 * sizeof(unsigned), env->stream));
     GD_TRY(dev_alloc(env, &env->acounter, 2));
     GD_TRY(cudaMemsetAsync(env->acounter, 0, 2 * sizeof(unsigned), env->stream));
-    GD_TRY(dev_alloc(env, &env->ocounter, OBS_STRIPES));
+    GD_TRY(dev_alloc(env, &env->ocounter, 2 * OBS_STRIPES));
+    if (cfg->flags & GD_BATCHED) {
+      GD_TRY(dev_alloc(env, &env->alt_state, (size_t)A));
+      GD_TRY(dev_alloc(env, &env->alt_flags, (size_t)A));
+    }
   }
   if (cfg->flags & GD_DIFFERENTIABLE) {
     env->C = cfg->ckpt_every;
@@ -1103,6 +1109,75 @@ gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint
   return gd_observe(env, obs, nullptr, nullptr);
 }
 
+#ifndef GD_ROLLOUT_OVERLAP
+#define GD_ROLLOUT_OVERLAP 1
+#endif
+
+// The step launch of the split form (no observation) on explicit state
+// buffers, optionally as a programmatic dependent of the launch before it.
+static cudaError_t launch_step_ex(gd_env* env, const DevEnv& dv, const FusedArgs& a, cudaStream_t stream, bool pdl) {
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(env->step_grid);
+  lc.blockDim = dim3(env->warps * 32);
+  lc.dynamicSmemBytes = env->step_smem;
+  lc.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = pdl ? 1 : 0;
+  switch (env->warps) {
+    case 4: return cudaLaunchKernelEx(&lc, k_world<4, false, true>, dv, a);
+    case 16: return cudaLaunchKernelEx(&lc, k_world<16, false, true>, dv, a);
+    default: return cudaLaunchKernelEx(&lc, k_world<8, false, true>, dv, a);
+  }
+}
+
+// Overlapped split rollout: the state and flags alternate between the env's
+// buffers and a second pair, so that step t + 1 (which reads step t's
+// output and writes the other pair) may run beside observation t (which
+// reads step t's output); step t + 1 is a programmatic dependent of
+// observation t and finishes only after it, and the observation counters
+// alternate between two sets.  The last of the rollout's `steps` steps
+// writes the env's own buffers.  Issues steps [t0, t1) (t1 <= steps); the
+// first of them is an ordinary launch (it may follow other work).
+static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, const float* actions, float* obs,
+                                     int obs_per_step, float* reward, uint8_t* done, cudaStream_t stream) {
+  const size_t A = (size_t)env->A;
+  float4* sbuf[2] = {env->d.state, env->alt_state};
+  uint8_t* fbuf[2] = {env->d.flags, env->alt_flags};
+  // the buffer step t reads: the env's own before the first step, else the
+  // one step t - 1 wrote
+  int in = t0 == 0 ? 0 : (((steps - t0) & 1) ? 1 : 0);
+  for (int t = t0; t < t1; ++t) {
+    const int out = ((steps - 1 - t) & 1) ? 1 : 0;
+    unsigned* oc = env->ocounter + (size_t)(t & 1) * OBS_STRIPES;
+    DevEnv dv = env->d;
+    dv.state = sbuf[in];
+    dv.flags = fbuf[in];
+    FusedArgs a{};
+    a.actions = reinterpret_cast<const float2*>(actions + (size_t)t * A * 2);
+    a.reward = reward ? reward + (size_t)t * A : nullptr;
+    a.done = done ? done + (size_t)t * A : nullptr;
+    a.counter = env->counter;
+    a.order = env->order;
+    a.tile_bytes = env->tile_cap;
+    a.do_step = 1;
+    a.clear = oc;
+    a.clear_n = (int)OBS_STRIPES;
+    a.state_out = out == in ? nullptr : sbuf[out];
+    a.flags_out = out == in ? nullptr : fbuf[out];
+    launch_step_ex(env, dv, a, stream, t > t0);
+    DevEnv dvo = env->d;
+    dvo.state = sbuf[out];
+    dvo.flags = fbuf[out];
+    const SplitLoss loss{nullptr, 0.f, nullptr, nullptr};
+    k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+        dvo, obs + (obs_per_step ? (size_t)t * A * env->F : 0), nullptr, nullptr, oc, loss);
+    in = out;
+  }
+}
+
 gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step, float* reward,
                      uint8_t* done) {
   NvtxRange range_("gd_rollout");
@@ -1141,10 +1216,13 @@ gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* ob
       cudaStreamDestroy(cap);
       return cuda_fail(env, e, "gd_rollout: begin capture");
     }
-    for (int t = 0; t < steps; ++t)
-      launch_world(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
-                   done ? done + (size_t)t * A : nullptr, nullptr, obs + (obs_per_step ? (size_t)t * A * env->F : 0),
-                   nullptr, nullptr, 1, cap);
+    if (GD_ROLLOUT_OVERLAP && env->split)
+      issue_rollout_overlapped(env, steps, 0, steps, actions, obs, obs_per_step, reward, done, cap);
+    else
+      for (int t = 0; t < steps; ++t)
+        launch_world(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                     done ? done + (size_t)t * A : nullptr, nullptr,
+                     obs + (obs_per_step ? (size_t)t * A * env->F : 0), nullptr, nullptr, 1, cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
@@ -1249,9 +1327,12 @@ gd_status gd_rollout_host(gd_env* env, int32_t steps, const float* actions_host,
       for (int t0 = 0; t0 < steps; t0 += kHostChunk, ++c) {
         const int n = std::min(kHostChunk, steps - t0);
         cudaStreamWaitEvent(cs, in_done[(size_t)c], 0);
-        for (int t = t0; t < t0 + n; ++t)
-          launch_world(env, env->hs_act + (size_t)t * A * 2, env->hs_rew + (size_t)t * A, env->hs_done + (size_t)t * A,
-                       nullptr, obs, nullptr, nullptr, 1, cs);
+        if (GD_ROLLOUT_OVERLAP && env->split)
+          issue_rollout_overlapped(env, steps, t0, t0 + n, env->hs_act, obs, 0, env->hs_rew, env->hs_done, cs);
+        else
+          for (int t = t0; t < t0 + n; ++t)
+            launch_world(env, env->hs_act + (size_t)t * A * 2, env->hs_rew + (size_t)t * A,
+                         env->hs_done + (size_t)t * A, nullptr, obs, nullptr, nullptr, 1, cs);
         cudaEvent_t out = event();
         cudaEventRecord(out, cs);
         cudaStreamWaitEvent(co, out, 0);

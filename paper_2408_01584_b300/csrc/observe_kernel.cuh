@@ -688,6 +688,9 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
   const int lane = threadIdx.x & 31;
   ObsWarpSmem& sm = reinterpret_cast<ObsWarpSmem*>(obs_smem_raw)[threadIdx.x >> 5];
   const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % OBS_STRIPES;
+  // a step launch queued behind this one as a programmatic dependent (the
+  // overlapped rollout) may start as SMs free up at this launch's tail
+  asm volatile("griddepcontrol.launch_dependents;");
   for (;;) {
     unsigned k = 0;
     if (lane == 0) k = atomicAdd(counters + c, 1u);

@@ -584,6 +584,12 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
     a.counter[0] = 0u;
     a.counter[1] = 0u;
   }
+  // A step launched as a programmatic dependent of the previous observation
+  // launch (the overlapped rollout: it reads and writes other state buffers
+  // than that launch) ends only once that launch has, so the observation
+  // launch after it never overlaps the one before.  Without such a launch
+  // this returns at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 }  // namespace gd

@@ -427,3 +427,42 @@ def test_gradient_91_steps_every_segment():
     assert max(seg) <= GRAD_RTOL and err_s <= GRAD_RTOL
     # the gradient of the last segment is not trivially zero
     assert np.abs(ga_o[81:]).max() > 1e-3 * ref
+
+
+def test_timed_passes_equal_the_rollout_calls():
+    # gd_time_objective / gd_time_backward (launch by launch under events)
+    # compute what gd_rollout_objective / gd_rollout_backward compute, and
+    # count their launches per kind
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([6, 9, 17]), np.array([700, 800, 1500]), 14)
+    ocfg = OracleConfig(k_road=48, n_partners=7, episode_len=91, term_collision=True, term_offroad=True)
+    T = 23
+    acts = scenes.make_actions(T, sc.num_agents, 14)
+    rng = np.random.default_rng(14)
+    w = torch.from_numpy(rng.uniform(0, 1, ocfg.feat).astype(np.float32)).cuda()
+    env = gd.Env(sc, **dict(_kw(ocfg), flags=_kw(ocfg)["flags"] | gd.GD_BATCHED))
+    a = torch.from_numpy(acts).cuda().contiguous()
+    A = sc.num_agents
+    outs = []
+    for timed in (False, True):
+        ell = torch.empty(T, A, device="cuda")
+        da = torch.empty(T, A, 2, device="cuda")
+        ds = torch.empty(A, 4, device="cuda")
+        gd.gd_reset(env.h)
+        if timed:
+            ms_o, n_o = gd.gd_time_objective(env.h, T, a, w, 0.7, ell, env.obs)
+            ms_b, n_b = gd.gd_time_backward(env.h, w, 0.7, None, da, ds)
+        else:
+            gd.gd_rollout_objective(env.h, T, a, w, 0.7, ell, env.obs)
+            gd.gd_rollout_backward(env.h, w, 0.7, None, da, ds)
+        env.sync()
+        outs.append([x.cpu().numpy() for x in (ell, da, ds)])
+    for x, y in zip(*outs):
+        np.testing.assert_array_equal(x, y)
+    info = gd.gd_get_info(env.h)
+    segs = (T + 9) // 10
+    assert n_o[0] == segs and n_o[2] == T and n_o[1] == (T if info.obs_split else 0)
+    assert n_b[0] == segs and n_b[1] == T
+    assert n_b[2] == (segs if info.adjoint_split else T) and n_b[3] == (segs if info.adjoint_split else 0)
+    assert all(m >= 0 for m in ms_o + ms_b) and sum(ms_b) > 0
+    env.close()
