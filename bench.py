@@ -80,7 +80,7 @@ def _peaks():
 
 
 class Clocks:
-    """SM clock and throttle-reason sampling (NVML, every 20 ms) during a
+    """SM clock and throttle-reason sampling (NVML, every 5 ms) during a
     timed region; the device is matched to the CUDA device by PCI bus id."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
@@ -111,10 +111,10 @@ class Clocks:
                                      nv.nvmlDeviceGetPowerUsage(h) / 1000.0))
             except Exception as e:  # keep timing even if one read fails
                 self.err = repr(e)
-            self.stop.wait(0.02)
+            self.stop.wait(0.005)
 
     def _smi(self):
-        """Fallback: nvidia-smi every 50 ms for the same PCI bus id."""
+        """Fallback: nvidia-smi every 20 ms for the same PCI bus id."""
         import subprocess
         import torch
         p = torch.cuda.get_device_properties(self.dev)
@@ -123,7 +123,7 @@ class Clocks:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         self.proc = subprocess.Popen(["nvidia-smi", f"--id={bus}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                      "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                      "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
 
     def __enter__(self):
         import threading
@@ -163,10 +163,13 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [f"no samples ({self.err})"]}
         sm = [x[0] for x in self.samples]
         reasons = sorted({name for x in self.samples for bit, name in self.REASONS.items() if x[2] & bit})
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
-                "reasons": reasons, "samples": len(self.samples),
-                "power_w_max": max(x[3] for x in self.samples),
-                "source": "nvml 20 ms" if self.proc is None else "nvidia-smi 50 ms"}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+               "reasons": reasons, "samples": len(self.samples),
+               "power_w_max": max(x[3] for x in self.samples),
+               "source": "nvml 5 ms" if self.proc is None else "nvidia-smi 20 ms"}
+        if self.proc is not None and self.err:
+            out["nvml_error"] = self.err[:200]
+        return out
 
 
 def workload_description(name, seed=0):

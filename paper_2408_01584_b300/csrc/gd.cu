@@ -1109,6 +1109,18 @@ gd_status gd_step_observe(gd_env* env, const float* actions, float* reward, uint
   return gd_observe(env, obs, nullptr, nullptr);
 }
 
+// Copy (state, flags, t, episode-end status) between the env and a slot: one
+// launch of k_copy_snapshot.
+static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t* dWD, const float4* sS,
+                          const uint8_t* sF, const int* sT, const uint8_t* sWD, cudaStream_t stream = nullptr) {
+  if (!stream) stream = env->stream;
+  const Snapshot dst{dS, dF, dT, dWD};
+  const Snapshot src{const_cast<float4*>(sS), const_cast<uint8_t*>(sF), const_cast<int*>(sT),
+                     const_cast<uint8_t*>(sWD)};
+  const int n = std::max(env->A, env->W);
+  k_copy_snapshot<<<std::min(blocks_for(n, 256), 1184u), 256, 0, stream>>>(dst, src, env->A, env->W);
+}
+
 #ifndef GD_ROLLOUT_OVERLAP
 #define GD_ROLLOUT_OVERLAP 1
 #endif
@@ -1141,9 +1153,14 @@ static cudaError_t launch_step_ex(gd_env* env, const DevEnv& dv, const FusedArgs
 // alternate between two sets.  The last of the rollout's `steps` steps
 // writes the env's own buffers.  Issues steps [t0, t1) (t1 <= steps); the
 // first of them is an ordinary launch (it may follow other work).
+// With obs_w, the objective rollout: step t writes each agent's smooth
+// reward into ell[t], observation t completes it and records the K-th road
+// distances, and every ckpt_every steps a copy launch saves the state step
+// t reads as a checkpoint (the step after a copy is an ordinary launch).
 static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, const float* actions, float* obs,
-                                     int obs_per_step, float* reward, uint8_t* done, cudaStream_t stream) {
-  const size_t A = (size_t)env->A;
+                                     int obs_per_step, float* reward, uint8_t* done, cudaStream_t stream,
+                                     const float* obs_w = nullptr, float reward_w = 0.f, float* ell = nullptr) {
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
   float4* sbuf[2] = {env->d.state, env->alt_state};
   uint8_t* fbuf[2] = {env->d.flags, env->alt_flags};
   // the buffer step t reads: the env's own before the first step, else the
@@ -1152,6 +1169,12 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
   for (int t = t0; t < t1; ++t) {
     const int out = ((steps - 1 - t) & 1) ? 1 : 0;
     unsigned* oc = env->ocounter + (size_t)(t & 1) * OBS_STRIPES;
+    const bool ckpt = ell && t % env->C == 0;
+    if (ckpt) {
+      const int c = t / env->C;
+      copy_snapshot(env, env->ckS + c * A, env->ckF + c * A, env->ckT + c * W, env->ckWD + c * W, sbuf[in], fbuf[in],
+                    env->d.t, env->d.world_done, stream);
+    }
     DevEnv dv = env->d;
     dv.state = sbuf[in];
     dv.flags = fbuf[in];
@@ -1167,13 +1190,21 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
     a.clear_n = (int)OBS_STRIPES;
     a.state_out = out == in ? nullptr : sbuf[out];
     a.flags_out = out == in ? nullptr : fbuf[out];
-    launch_step_ex(env, dv, a, stream, t > t0);
+    a.ell = ell ? ell + (size_t)t * A : nullptr;
+    launch_step_ex(env, dv, a, stream, t > t0 && !ckpt);
     DevEnv dvo = env->d;
     dvo.state = sbuf[out];
     dvo.flags = fbuf[out];
-    const SplitLoss loss{nullptr, 0.f, nullptr, nullptr};
-    k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
-        dvo, obs + (obs_per_step ? (size_t)t * A * env->F : 0), nullptr, nullptr, oc, loss);
+    float* orow = obs + (obs_per_step ? (size_t)t * A * env->F : 0);
+    if (ell) {
+      const SplitLoss loss{obs_w, reward_w, ell + (size_t)t * A, env->rk_hist + (size_t)t * A};
+      k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+          dvo, orow, nullptr, nullptr, oc, loss);
+    } else {
+      const SplitLoss loss{nullptr, 0.f, nullptr, nullptr};
+      k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(dvo, orow, nullptr, nullptr,
+                                                                                           oc, loss);
+    }
     in = out;
   }
 }
@@ -1538,17 +1569,6 @@ static gd_status need_diff(gd_env* env, const char* what) {
   return GD_OK;
 }
 
-// Copy (state, flags, t, episode-end status) between the env and a slot: one
-// launch of k_copy_snapshot.
-static void copy_snapshot(gd_env* env, float4* dS, uint8_t* dF, int* dT, uint8_t* dWD, const float4* sS,
-                          const uint8_t* sF, const int* sT, const uint8_t* sWD, cudaStream_t stream = nullptr) {
-  if (!stream) stream = env->stream;
-  const Snapshot dst{dS, dF, dT, dWD};
-  const Snapshot src{const_cast<float4*>(sS), const_cast<uint8_t*>(sF), const_cast<int*>(sT),
-                     const_cast<uint8_t*>(sWD)};
-  const int n = std::max(env->A, env->W);
-  k_copy_snapshot<<<std::min(blocks_for(n, 256), 1184u), 256, 0, stream>>>(dst, src, env->A, env->W);
-}
 
 // Capture what `issue(stream)` launches on a private stream into *out (an
 // existing graph is replaced).
@@ -1653,7 +1673,13 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
         env->og_steps = -1;
         st = capture_graph(
             env, &env->ograph, "gd_rollout_objective: capture",
-            [&](cudaStream_t cs) { issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, cs); },
+            [&](cudaStream_t cs) {
+              if (GD_ROLLOUT_OVERLAP && env->split)
+                issue_rollout_overlapped(env, steps, 0, steps, actions, obs, 0, nullptr, nullptr, cs, obs_weight,
+                                         reward_weight, ell);
+              else
+                issue_objective(env, steps, actions, obs_weight, reward_weight, ell, obs, cs);
+            },
             env->og_nodes);
         if (st != GD_OK) return st;
         for (int k = 0; k < 6; ++k) env->og_key[k] = key[k];
