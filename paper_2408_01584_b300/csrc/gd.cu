@@ -127,6 +127,10 @@ struct gd_env {
   uint8_t* segF = nullptr;      // [C+1][A]
   int* segT = nullptr;          // [W]
   uint8_t* segWD = nullptr;     // [W]
+  float4* segS2 = nullptr;      // a second segment buffer set: the captured backward recomputes one segment
+  uint8_t* segF2 = nullptr;     // while the adjoint of the one after it runs
+  int* segT2 = nullptr;
+  uint8_t* segWD2 = nullptr;
   float4* lam = nullptr;        // [A] adjoint of the state
   float* rk_hist = nullptr;     // [episode_len][A] K-th road distance of each agent at each objective step
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
@@ -750,6 +754,12 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(dev_alloc(env, &env->segF, (size_t)(env->C + 1) * A));
     GD_TRY(dev_alloc(env, &env->segT, (size_t)W));
     GD_TRY(dev_alloc(env, &env->segWD, (size_t)W));
+    if (cfg->flags & GD_BATCHED) {
+      GD_TRY(dev_alloc(env, &env->segS2, (size_t)(env->C + 1) * A));
+      GD_TRY(dev_alloc(env, &env->segF2, (size_t)(env->C + 1) * A));
+      GD_TRY(dev_alloc(env, &env->segT2, (size_t)W));
+      GD_TRY(dev_alloc(env, &env->segWD2, (size_t)W));
+    }
     GD_TRY(dev_alloc(env, &env->lam, (size_t)A));
     GD_TRY(dev_alloc(env, &env->adj_g, (size_t)env->C * A));
     GD_TRY(dev_alloc(env, &env->adj_cs, (size_t)env->C * A));
@@ -1766,17 +1776,31 @@ static void launch_adjoint(gd_env* env, const float4* S, const uint8_t* F, const
 // Recompute `len` steps of the segment starting from segS[0] / segF[0] /
 // segT / segWD, leaving the state after step k in segS[k+1] / segF[k+1]:
 // each step reads slot k and writes slot k + 1 (no copy between steps).
+// A segment's buffers: states and flags before / after each step, its
+// worlds' episode steps and episode-end status.
+struct SegBuf {
+  float4* S;
+  uint8_t* F;
+  int* T;
+  uint8_t* WD;
+};
+static SegBuf seg_buf(gd_env* env, int which) {
+  return which ? SegBuf{env->segS2, env->segF2, env->segT2, env->segWD2}
+               : SegBuf{env->segS, env->segF, env->segT, env->segWD};
+}
+
 static void recompute_segment(gd_env* env, const float* actions0, int len, cudaStream_t stream = nullptr,
-                              LaunchTimer* tm = nullptr) {
+                              LaunchTimer* tm = nullptr, int which = 0) {
   const size_t A = (size_t)env->A;
+  const SegBuf b = seg_buf(env, which);
   DevEnv dv = env->d;
-  dv.t = env->segT;
-  dv.world_done = env->segWD;
+  dv.t = b.T;
+  dv.world_done = b.WD;
   for (int k = 0; k < len; ++k) {
-    dv.state = env->segS + k * A;
-    dv.flags = env->segF + k * A;
+    dv.state = b.S + k * A;
+    dv.flags = b.F + k * A;
     launch_world(env, actions0 + (size_t)k * A * 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, stream, &dv,
-                 nullptr, 0.f, nullptr, nullptr, nullptr, 0, env->segS + (k + 1) * A, env->segF + (k + 1) * A, tm);
+                 nullptr, 0.f, nullptr, nullptr, nullptr, 0, b.S + (k + 1) * A, b.F + (k + 1) * A, tm);
   }
 }
 
@@ -1798,6 +1822,45 @@ static void issue_backward(gd_env* env, const float* obs_weight, float reward_we
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
                    env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm);
   }
+}
+
+// The captured backward pass, pipelined over two segment buffers: on a
+// second stream each segment's checkpoint copy and recomputed steps, on the
+// capturing stream its adjoint once they are done, so that the recompute of
+// a segment runs beside the adjoint of the segment after it; a buffer is
+// refilled only after the adjoint that read it.
+static void issue_backward_pipelined(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
+                                     float* d_actions, float* d_state0, cudaStream_t cap, cudaStream_t sr,
+                                     std::vector<cudaEvent_t>& evs) {
+  const size_t A = (size_t)env->A, W = (size_t)env->W;
+  const int T = env->diff_steps, C = env->C, nseg = (T - 1) / C + 1;
+  auto event = [&]() {
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    evs.push_back(e);
+    return e;
+  };
+  cudaEvent_t fork = event();
+  cudaEventRecord(fork, cap);
+  cudaStreamWaitEvent(sr, fork, 0);
+  std::vector<cudaEvent_t> done_adj((size_t)nseg, nullptr);
+  for (int j = 0; j < nseg; ++j) {
+    const int seg = nseg - 1 - j, t0 = seg * C, len = std::min(C, T - t0), which = j & 1;
+    const SegBuf b = seg_buf(env, which);
+    if (j >= 2) cudaStreamWaitEvent(sr, done_adj[(size_t)(j - 2)], 0);
+    copy_snapshot(env, b.S, b.F, b.T, b.WD, env->ckS + seg * A, env->ckF + seg * A, env->ckT + seg * W,
+                  env->ckWD + seg * W, sr);
+    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, sr, nullptr, which);
+    cudaEvent_t rec = event();
+    cudaEventRecord(rec, sr);
+    cudaStreamWaitEvent(cap, rec, 0);
+    launch_adjoint(env, b.S, b.F, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
+                   d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
+                   env->rk_hist + (size_t)t0 * A, cap, t0 + len == T, t0 == 0 ? d_state0 : nullptr);
+    done_adj[(size_t)j] = event();
+    cudaEventRecord(done_adj[(size_t)j], cap);
+  }
+  // the second stream's last work (segment 0's recompute) is already joined
 }
 
 gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward_weight, const float* d_ell,
@@ -1823,10 +1886,20 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
   for (int k = 0; k < 7 && same; ++k) same = env->bg_key[k] == key[k];
   if (!same) {
     env->bg_steps = -1;
+    cudaStream_t sr = nullptr;
+    std::vector<cudaEvent_t> evs;
+    const bool pipe = cudaStreamCreateWithFlags(&sr, cudaStreamNonBlocking) == cudaSuccess;
     st = capture_graph(
         env, &env->bgraph, "gd_rollout_backward: capture",
-        [&](cudaStream_t cs) { issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs); },
+        [&](cudaStream_t cs) {
+          if (pipe)
+            issue_backward_pipelined(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs, sr, evs);
+          else
+            issue_backward(env, obs_weight, reward_weight, d_ell, d_actions, d_state0, cs);
+        },
         env->bg_nodes);
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    if (sr) cudaStreamDestroy(sr);
     if (st != GD_OK) return st;
     for (int k = 0; k < 7; ++k) env->bg_key[k] = key[k];
     env->bg_steps = env->diff_steps;
