@@ -5,13 +5,18 @@
 // triangle it spans with its two current neighbours; ties: lower index) is
 // eliminated while that area is below the tolerance; its neighbours' areas
 // are recomputed with their new neighbours and raised to the eliminated
-// area if smaller.  End points stay.  The elimination is sequential within
-// a polyline, so one thread runs one polyline with a binary min-heap of
-// 64-bit keys (area bits << 32 | local index: areas are >= 0, so the bits
-// order like the values and the index breaks ties) and neighbour links, all
-// in a scratch buffer of 20 bytes per point allocated on the stream.  Areas
-// are float32 with the rounding spelled out (no contraction), so every
-// elimination decision is reproducible.
+// area if smaller.  End points stay.  Points carry 64-bit keys (area bits
+// << 32 | local index: areas are >= 0, so the bits order like the values and
+// the index breaks ties); the elimination is sequential within a polyline.
+// A polyline of up to VW_WARP_CAP points is run by one warp with its keys
+// and neighbour links in shared memory: each lane keeps the minimum of its
+// own chunk of keys, a shuffle reduction gives the polyline's minimum, and
+// after an elimination only the lanes whose chunks changed rescan them.  A
+// longer polyline is run by one thread with a binary min-heap of the keys
+// and neighbour links in a scratch buffer of 20 bytes per point allocated on
+// the stream.  Both take the same decisions.  Areas are float32 with the
+// rounding spelled out (no contraction), so every elimination decision is
+// reproducible.
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -75,13 +80,94 @@ struct VwHeap {
   }
 };
 
-// One thread per polyline (grid-stride).  Scratch arrays are indexed by the
-// global point index.
+constexpr int VW_WARP_CAP = 1024;     // points of a polyline the warp form holds in shared memory
+constexpr int VW_WARPS = 8;            // warps per CTA of the warp form
+constexpr size_t VW_WARP_SMEM = (size_t)VW_WARP_CAP * (8 + 2 + 2);   // keys + two 16-bit links per point
+
+// Warp form: one warp per polyline of at most VW_WARP_CAP points (longer
+// ones are left to k_vw).  Dynamic shared memory: VW_WARPS x VW_WARP_SMEM.
+__global__ void __launch_bounds__(VW_WARPS * 32) k_vw_warp(int num_polylines, const int* __restrict__ poly_off,
+                                                         const float* __restrict__ x, const float* __restrict__ y,
+                                                         float tol, uint8_t* __restrict__ keep) {
+  extern __shared__ __align__(16) unsigned char vw_smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(vw_smem + (size_t)wid * VW_WARP_SMEM);
+  unsigned short* prv = reinterpret_cast<unsigned short*>(keys + VW_WARP_CAP);
+  unsigned short* nxt = prv + VW_WARP_CAP;
+  const unsigned long long NONE = ~0ull;     // end points and eliminated points
+  for (int p = blockIdx.x * VW_WARPS + wid; p < num_polylines; p += gridDim.x * VW_WARPS) {
+    const int o = poly_off[p], n = poly_off[p + 1] - o;
+    if (n > VW_WARP_CAP) continue;
+    for (int i = lane; i < n; i += 32) keep[o + i] = 1;
+    if (n < 3) continue;
+    const float* px = x + o;
+    const float* py = y + o;
+    for (int i = lane; i < n; i += 32) {
+      prv[i] = (unsigned short)(i - 1);
+      nxt[i] = (unsigned short)(i + 1);
+      keys[i] = (i == 0 || i == n - 1) ? NONE
+                                       : vw_key(vw_area(px[i - 1], py[i - 1], px[i], py[i], px[i + 1], py[i + 1]), i);
+    }
+    __syncwarp();
+    // lane l owns points [l ch, l ch + ch)
+    const int ch = (n + 31) / 32, lo = min(lane * ch, n), hi = min(lo + ch, n);
+    // four independent minima, so the chunk's loads overlap
+    auto chunk_min = [&]() {
+      unsigned long long m0 = NONE, m1 = NONE, m2 = NONE, m3 = NONE;
+      int i = lo;
+      for (; i + 3 < hi; i += 4) {
+        m0 = min(m0, keys[i]);
+        m1 = min(m1, keys[i + 1]);
+        m2 = min(m2, keys[i + 2]);
+        m3 = min(m3, keys[i + 3]);
+      }
+      for (; i < hi; ++i) m0 = min(m0, keys[i]);
+      return min(min(m0, m1), min(m2, m3));
+    };
+    unsigned long long mine = chunk_min();
+    for (;;) {
+      unsigned long long m = mine;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, off));
+      const float am = __uint_as_float((unsigned)(m >> 32));
+      if (m == NONE || !(am < tol)) break;
+      const int i = (int)(m & 0xffffffffu);
+      int a = 0, c = 0;
+      if (lane == 0) {
+        keep[o + i] = 0;
+        keys[i] = NONE;
+        a = prv[i];
+        c = nxt[i];
+        nxt[a] = (unsigned short)c;
+        prv[c] = (unsigned short)a;
+        const int nb[2] = {a, c};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int j = nb[q];
+          if (j <= 0 || j >= n - 1) continue;
+          const int pj = prv[j], nj = nxt[j];
+          const float na = fmaxf(vw_area(px[pj], py[pj], px[j], py[j], px[nj], py[nj]), am);
+          keys[j] = vw_key(na, j);
+        }
+      }
+      a = __shfl_sync(0xffffffffu, a, 0);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      __syncwarp();
+      if (lane == i / ch || lane == a / ch || lane == c / ch) mine = chunk_min();
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+}
+
+// Heap form: one thread per polyline longer than min_len points (grid-
+// stride).  Scratch arrays are indexed by the global point index.
 __global__ void k_vw(int num_polylines, const int* __restrict__ poly_off, const float* __restrict__ x,
                      const float* __restrict__ y, float tol, uint8_t* __restrict__ keep, unsigned long long* heap,
-                     int* hpos, int* prv, int* nxt) {
+                     int* hpos, int* prv, int* nxt, int min_len) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < num_polylines; p += gridDim.x * blockDim.x) {
     const int o = poly_off[p], n = poly_off[p + 1] - o;
+    if (n <= min_len) continue;
     const float* px = x + o;
     const float* py = y + o;
     for (int i = 0; i < n; ++i) keep[o + i] = 1;
@@ -155,10 +241,16 @@ extern "C" gd_status gd_decimate(int32_t num_polylines, int32_t num_points, cons
   int* hpos = reinterpret_cast<int*>(heap + n);
   int* prv = hpos + n;
   int* nxt = prv + n;
-  const int block = 128;
-  const int grid = (num_polylines + block - 1) / block;
-  k_vw<<<grid, block, 0, s>>>(num_polylines, poly_off, x, y, area_tol, keep, heap, hpos, prv, nxt);
-  e = cudaGetLastError();
+  // polylines of up to VW_WARP_CAP points: a warp each; longer ones: the heap form
+  e = cudaFuncSetAttribute(k_vw_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(VW_WARPS * VW_WARP_SMEM));
+  if (e == cudaSuccess) {
+    const int wgrid = (num_polylines + VW_WARPS - 1) / VW_WARPS;
+    k_vw_warp<<<wgrid, VW_WARPS * 32, VW_WARPS * VW_WARP_SMEM, s>>>(num_polylines, poly_off, x, y, area_tol, keep);
+    const int block = 128;
+    const int grid = (num_polylines + block - 1) / block;
+    k_vw<<<grid, block, 0, s>>>(num_polylines, poly_off, x, y, area_tol, keep, heap, hpos, prv, nxt, VW_WARP_CAP);
+    e = cudaGetLastError();
+  }
   cudaFreeAsync(scratch, s);
   if (e != cudaSuccess) {
     gd_set_thread_error(std::string("gd_decimate: launch: ") + cudaGetErrorString(e));

@@ -26,7 +26,9 @@ def _gpu(off, x, y, tol):
 
 def test_random_polylines_bitwise():
     rng = np.random.default_rng(1)
-    lens = np.concatenate([[0, 1, 2, 3, 3], rng.integers(3, 400, 300)])
+    # short ones (a warp each, shared memory) and ones past 1,024 points (a
+    # thread each, heap in global scratch), both forms in one call
+    lens = np.concatenate([[0, 1, 2, 3, 3], rng.integers(3, 400, 300), [1023, 1024, 1025, 2500]])
     off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
     pts = []
     for k, n in enumerate(lens):
