@@ -126,9 +126,11 @@ __global__ void __launch_bounds__(VW_WARPS * 32) k_vw_warp(int num_polylines, co
     };
     unsigned long long mine = chunk_min();
     for (;;) {
-      unsigned long long m = mine;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, off));
+      // the warp's minimum key: the least area bits, then the least index
+      // among the lanes that hold them
+      const unsigned hb = __reduce_min_sync(0xffffffffu, (unsigned)(mine >> 32));
+      const unsigned lb = __reduce_min_sync(0xffffffffu, (unsigned)(mine >> 32) == hb ? (unsigned)mine : 0xffffffffu);
+      const unsigned long long m = ((unsigned long long)hb << 32) | lb;
       const float am = __uint_as_float((unsigned)(m >> 32));
       if (m == NONE || !(am < tol)) break;
       const int i = (int)(m & 0xffffffffu);
