@@ -773,9 +773,9 @@ def bench_decimation(workload, steps, warmup, dev, stream, flush, seed=0):
     oracle_decimate(off[:n_poly_cpu + 1], sc.road_x[:off[n_poly_cpu]], sc.road_y[:off[n_poly_cpu]], gd.DECIMATE_AREA)
     cpu_dec_s = time.perf_counter() - t0
     # k_vw reads each point's x, y once and writes its keep byte, plus the offsets
-    vw = kernel_record("k_vw (Visvalingam-Whyatt, thread per polyline)", len(ms_dec), sum(ms_dec),
+    vw = kernel_record("k_vw_warp (Visvalingam-Whyatt, a warp per polyline)", len(ms_dec), sum(ms_dec),
                        9.0 * sc.num_road + 4.0 * len(off), hbm,
-                       "bound by the latency of one thread's sequential eliminations, not by HBM")
+                       "bound by instruction issue over each polyline's sequential eliminations, not by HBM")
     return {"workload": workload, "decimation": {"points_in": sc.num_road, "points_kept": int(k.sum()),
                                                  "reduction": sc.num_road / max(int(k.sum()), 1),
                                                  "polylines": len(off) - 1, "area_tol_m2": gd.DECIMATE_AREA,

@@ -271,3 +271,31 @@ def test_batched_teacher_forced_fwdbwd_subset_tuned():
     _, ex = teacher_forced(sc, ocfg, 5, acts, env=env, obs_agents=agents)
     print(f"fwdbwd subset forward: split {info.obs_split}, block {info.block_size}, cell {info.road_cell}, "
           f"exceptions {len(ex)}")
+
+
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_overlapped_graph_short_rollouts(T):
+    # the captured split rollout alternates two state buffers (the last step
+    # writes the env's own): one, two and three steps, against the
+    # per-stage form, and a step taken after the rollout starts from its
+    # final state
+    sc = small_scene(seed=17)
+    ocfg = OracleConfig(k_road=64, n_partners=16, episode_len=9, term_collision=True, term_offroad=True,
+                        auto_reset=True)
+    acts = scenes.make_actions(T + 1, sc.num_agents, 17)
+    plain = _rollout(sc, gd_kwargs(ocfg), acts, "stepwise")
+    from paper_2408_01584_b300 import gd
+    env = gd.Env(sc, **_batched(ocfg))
+    a = torch.from_numpy(acts).cuda().contiguous()
+    obs = torch.zeros(T, env.A, env.F, device="cuda")
+    rew = torch.zeros(T, env.A, device="cuda")
+    gd.gd_rollout(env.h, T, a[:T], obs, True, rew, None)
+    env.step(a[T])
+    env.observe()
+    env.sync()
+    np.testing.assert_array_equal(_np(obs), plain["obs"][:T])
+    np.testing.assert_array_equal(_np(rew), plain["reward"][:T])
+    np.testing.assert_array_equal(_np(env.obs), plain["obs"][T])
+    s, f, _ = env.get_state()
+    np.testing.assert_array_equal(_np(s), plain["state"])
+    env.close()
