@@ -532,7 +532,8 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
                                               (STEP_AGENT_BYTES + 4) * A, hbm))
                     kern.append(kernel_record("k_observe_split<LOSS> (observation + objective term)", n_o[2], ms_o[2],
                                               (4.0 * F + OBS_AGENT_BYTES + 12 + road) * A, hbm,
-                                              "row 4F, own state 33 B, ell read+write 8 B, K-th distance 4 B, road"))
+                                              "row 4F, own state 33 B, ell read+write 8 B, K-th distance 4 B, road; "
+                                              "the selection record (2K B per agent in the scene) is not counted"))
                 else:
                     kern.append(kernel_record("k_world (fused step + observation + objective)", n_o[2], ms_o[2],
                                               (4.0 * F + 70.0 + 8 + road) * A, hbm))
@@ -542,10 +543,11 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
                                           STEP_AGENT_BYTES * A, hbm))
                 if info.adjoint_split:
                     kern.append(kernel_record(
-                        "k_adj_observer (a segment's re-selections, observer-side gradients, slot rows)", n_b[2],
-                        ms_b[2], seg(16 + 16 + 1 + 4 + 16 + 8 + 128 + road, n_b[2]), hbm,
-                        "per agent-step: reads post state, extents, flags, K-th distance and the road; writes "
-                        "gradient, (cos, sin), 128-byte slot row"))
+                        "k_adj_observer (a segment's recorded selections, observer-side gradients, slot rows)",
+                        n_b[2], ms_b[2], seg(16 + 16 + 1 + 2 * env.K + 16 + 8 + 128 + road * 8 / 12, n_b[2]), hbm,
+                        "per agent-step: reads post state, extents, flags, the forward's selection record (2K B) and "
+                        "the selected points' coordinates (bounded by 8 B per road point within R of the world's "
+                        "agents); writes gradient, (cos, sin), 128-byte slot row"))
                     kern.append(kernel_record(
                         "k_adj_dynamics (a segment's partner sides, rewards, dynamics adjoints)", n_b[3], ms_b[3],
                         seg(16 + 16 + 16 + 1 + 1 + 8 + 8 + n_w + 8, n_b[3]) + 2 * 16 * A, hbm,

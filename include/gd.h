@@ -82,9 +82,11 @@ typedef enum gd_status {
 #define GD_AUTO_RESET 0x4u       /* gd_step first resets worlds whose episode ended */
 #define GD_BATCHED 0x8u          /* persistent kernels: the step over a world work list, the observation
                                     over an agent counter (or fused with the step, obs_split = 0) */
-#define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward, and each agent's K-th road
+#define GD_DIFFERENTIABLE 0x10u  /* keep checkpoints for gd_rollout_backward, each agent's K-th road
                                     distance at every step of gd_rollout_objective (4 B x A x
-                                    episode_len), which bounds the backward's re-selection */
+                                    episode_len) and its road selection (2 B x K x A x episode_len,
+                                    taken at gd_create when it fits; the backward pass reads it instead
+                                    of selecting again, else re-selects within the K-th distance) */
 #define GD_NONTRIVIAL_INIT 0x20u /* "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges"):
                                     agents within nontrivial_dist of their goal at the start are not
                                     controlled (GD_FLAG_STATIC) */

@@ -53,6 +53,8 @@ struct AdjArgs {
   float2* d_actions;        // [steps][A] out: dL/d (accel, steer)
   const float* rk;          // [steps][A] each agent's K-th road distance at the step in the forward
                             // rollout (bounds the re-selection's disk), or nullptr: the full radius
+  const uint16_t* sel;      // [steps][A][K] the forward rollout's road selections (split form), or
+                            // nullptr: re-selected
   unsigned* counter;        // fused form: [2] work counter and exit tally, left at zero by each launch
   const int* order;
   int tile_bytes;
@@ -131,10 +133,14 @@ __device__ __forceinline__ void invertible_adjoint(const float4 s, float accel, 
 // ego features, the partner slots and the road slots (lanes over slots, then
 // a shuffle tree), returned to every lane.  on_partner(r, j) is called once
 // per selected partner (slot r, local index j) by the lane that handles it.
+// The road selection is re-run (over the disk of radius Rs), or, given
+// selrow, read from the forward rollout's record of the same step: the same
+// positions in the same slots, so the sums are the same.
 template <typename OnPartner>
 __device__ __forceinline__ float4 observer_gradient(const DevEnv& e, const WorldView& v, int li, float4 st, float4 sc,
                                                     float c, float s, const float* __restrict__ wrow, float Rs,
-                                                    float Rs2, ObsWarpSmem& sm, int lane, OnPartner&& on_partner) {
+                                                    float Rs2, ObsWarpSmem& sm, int lane, OnPartner&& on_partner,
+                                                    const uint16_t* __restrict__ selrow = nullptr) {
   float gx = 0.f, gy = 0.f, gt = 0.f, gv = 0.f;
   if (lane == 0) {
     // ego: speed and goal offset in the ego frame
@@ -162,19 +168,37 @@ __device__ __forceinline__ float4 observer_gradient(const DevEnv& e, const World
     gy += fmaf(-s, wa.x, -__fmul_rn(c, wa.y));
     gt += fmaf(wa.x, yp, -__fmul_rn(wa.y, xp)) + fmaf(wa.z, sd, -__fmul_rn(wa.w, cd));
   }
-  // road points: the forward selection's K-th distance bounds the disk that
-  // holds the same K points (the full radius when it had fewer than K)
-  int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
-  if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
   const float* wroad = wrow + 8 + 8 * e.P;
-  for (int r = lane; r < nroad; r += WARP) {
-    const float2 q = v.xy[sel_pos(sm.sel[r])];
+  auto road_term = [&](int r, unsigned pos) {
+    const float2 q = v.xy[pos];
     const float dx = q.x - st.x, dy = q.y - st.y;
     const float xp = rot_x(c, s, dx, dy), yp = rot_y(c, s, dx, dy);
     const float wa = __ldg(wroad + 4 * r), wb = __ldg(wroad + 4 * r + 1);
     gx += fmaf(-c, wa, __fmul_rn(s, wb));
     gy += fmaf(-s, wa, -__fmul_rn(c, wb));
     gt += fmaf(wa, yp, -__fmul_rn(wb, xp));
+  };
+  if (selrow) {
+    // the recorded selection: a lane's slots r = lane, lane + 32, ... in
+    // order, their positions loaded four at a time
+    constexpr int U = 4;
+    for (int r0 = 0; r0 < e.K; r0 += U * WARP) {
+      unsigned pos[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u * WARP + lane;
+        pos[u] = r < e.K ? (unsigned)selrow[r] : (unsigned)OBS_SEL_NONE;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (pos[u] != OBS_SEL_NONE) road_term(r0 + u * WARP + lane, pos[u]);
+    }
+  } else {
+    // road points: the forward selection's K-th distance bounds the disk
+    // that holds the same K points (the full radius when it had fewer than K)
+    int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
+    if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+    for (int r = lane; r < nroad; r += WARP) road_term(r, sel_pos(sm.sel[r]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -424,7 +448,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv 
     float Rs, Rs2;
     reselect_radius(e, a, k, i, Rs, Rs2);
     const float4 gr = observer_gradient(e, v, i - a0, st, sc, cn, sn, a.obs_w + (size_t)i * a.obs_w_stride, Rs,
-                                        Rs2, sm, lane, [&](int r, int j) { srow[j] = (uint8_t)r; });
+                                        Rs2, sm, lane, [&](int r, int j) { srow[j] = (uint8_t)r; },
+                                        a.sel ? a.sel + ik * e.K : nullptr);
     __syncwarp();
     grow[lane] = reinterpret_cast<const unsigned*>(srow)[lane];
     if (lane == 0) {

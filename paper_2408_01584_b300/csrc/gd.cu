@@ -133,6 +133,8 @@ struct gd_env {
   uint8_t* segWD2 = nullptr;
   float4* lam = nullptr;        // [A] adjoint of the state
   float* rk_hist = nullptr;     // [episode_len][A] K-th road distance of each agent at each objective step
+  uint16_t* sel_hist = nullptr; // [episode_len][A][K] road selection of each agent at each objective step, or
+                                // nullptr (no room: the backward pass re-selects)
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
   int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
@@ -769,6 +771,15 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     // K-th road distances of the objective rollout; 0x7f7f7f7f (3.4e38) = no bound
     GD_TRY(dev_alloc(env, &env->rk_hist, (size_t)cfg->episode_len * A));
     GD_TRY(cudaMemsetAsync(env->rk_hist, 0x7f, sizeof(float) * (size_t)cfg->episode_len * A, env->stream));
+    // the objective rollout's road selections, so that the backward pass
+    // reads them instead of selecting again; without room for them it
+    // re-selects (the same sets, so the same gradients)
+    if (cfg->k_road > 0 && A > 0) {
+      if (dev_alloc(env, &env->sel_hist, (size_t)cfg->episode_len * A * cfg->k_road) != cudaSuccess) {
+        cudaGetLastError();
+        env->sel_hist = nullptr;
+      }
+    }
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
   env->split = cfg->obs_split;
@@ -946,7 +957,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
                          unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES, float4* state_out = nullptr,
-                         uint8_t* flags_out = nullptr, LaunchTimer* tm = nullptr) {
+                         uint8_t* flags_out = nullptr, LaunchTimer* tm = nullptr, uint16_t* sel_out = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
@@ -959,7 +970,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                    nullptr, env->ocounter, (int)OBS_STRIPES, nullptr, nullptr, tm);
     else
       cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
-    const SplitLoss loss{obs_w, reward_w, ell, rk_out};
+    const SplitLoss loss{obs_w, reward_w, ell, rk_out, sel_out};
     tbegin(tm, 2);
     if (ell)
       k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
@@ -986,6 +997,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.reward_w = reward_w;
   a.ell = ell;
   a.rk_out = (ell && obs) ? rk_out : nullptr;
+  a.sel_out = (ell && obs) ? sel_out : nullptr;
   a.clear = clear;
   a.clear_n = clear ? clear_n : 0;
   a.state_out = state_out;
@@ -1207,11 +1219,12 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
     dvo.flags = fbuf[out];
     float* orow = obs + (obs_per_step ? (size_t)t * A * env->F : 0);
     if (ell) {
-      const SplitLoss loss{obs_w, reward_w, ell + (size_t)t * A, env->rk_hist + (size_t)t * A};
+      const SplitLoss loss{obs_w, reward_w, ell + (size_t)t * A, env->rk_hist + (size_t)t * A,
+                           env->sel_hist ? env->sel_hist + (size_t)t * A * env->d.K : nullptr};
       k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
           dvo, orow, nullptr, nullptr, oc, loss);
     } else {
-      const SplitLoss loss{nullptr, 0.f, nullptr, nullptr};
+      const SplitLoss loss{nullptr, 0.f, nullptr, nullptr, nullptr};
       k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(dvo, orow, nullptr, nullptr,
                                                                                            oc, loss);
     }
@@ -1646,7 +1659,8 @@ static void issue_objective(gd_env* env, int steps, const float* actions, const 
     }
     launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, stream, nullptr,
                  obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A, nullptr,
-                 (int)OBS_STRIPES, nullptr, nullptr, tm);
+                 (int)OBS_STRIPES, nullptr, nullptr, tm,
+                 env->sel_hist ? env->sel_hist + (size_t)t * A * env->d.K : nullptr);
   }
 }
 
@@ -1715,7 +1729,8 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
 static void launch_adjoint(gd_env* env, const float4* S, const uint8_t* F, const float* actions, int steps,
                            const float* obs_w, long long stride, const float* row_scale, const float* rew_w,
                            float reward_w, float* d_actions, const float* rk = nullptr, cudaStream_t stream = nullptr,
-                           int lam_zero = 0, float* lam_copy = nullptr, LaunchTimer* tm = nullptr) {
+                           int lam_zero = 0, float* lam_copy = nullptr, LaunchTimer* tm = nullptr,
+                           const uint16_t* sel = nullptr) {
   if (!stream) stream = env->stream;
   const size_t A = (size_t)env->A;
   AdjArgs a{};
@@ -1730,6 +1745,7 @@ static void launch_adjoint(gd_env* env, const float4* S, const uint8_t* F, const
   a.lam = env->lam;
   a.d_actions = reinterpret_cast<float2*>(d_actions);
   a.rk = rk;
+  a.sel = sel;
   a.counter = env->acounter;
   a.order = env->order;
   a.tile_bytes = env->adj_tile;
@@ -1820,7 +1836,8 @@ static void issue_backward(gd_env* env, const float* obs_weight, float reward_we
     recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, stream, tm);
     launch_adjoint(env, env->segS, env->segF, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
-                   env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm);
+                   env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm,
+                   env->sel_hist ? env->sel_hist + (size_t)t0 * A * env->d.K : nullptr);
   }
 }
 
@@ -1856,7 +1873,8 @@ static void issue_backward_pipelined(gd_env* env, const float* obs_weight, float
     cudaStreamWaitEvent(cap, rec, 0);
     launch_adjoint(env, b.S, b.F, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
-                   env->rk_hist + (size_t)t0 * A, cap, t0 + len == T, t0 == 0 ? d_state0 : nullptr);
+                   env->rk_hist + (size_t)t0 * A, cap, t0 + len == T, t0 == 0 ? d_state0 : nullptr, nullptr,
+                   env->sel_hist ? env->sel_hist + (size_t)t0 * A * env->d.K : nullptr);
     done_adj[(size_t)j] = event();
     cudaEventRecord(done_adj[(size_t)j], cap);
   }

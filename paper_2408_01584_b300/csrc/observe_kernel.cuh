@@ -504,6 +504,10 @@ __device__ __forceinline__ float write_done_row(const DevEnv& e, uint8_t f, floa
   return acc;
 }
 
+// Recorded selection (objective rollouts): a slot past the points in range.
+constexpr uint16_t OBS_SEL_NONE = 0xffff;
+static_assert(GD_MAX_ROAD_PER_WORLD <= 0xffff, "block positions must fit a recorded slot below OBS_SEL_NONE");
+
 // One full observation row of local agent li of the world in view v.
 // With LOSS, returns (to every lane) w . row for the weight row w (F
 // floats); otherwise returns 0.
@@ -512,7 +516,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
                                                ObsWarpSmem& sm, int lane, float4* anchor,
                                                const float* __restrict__ w = nullptr, float* rk_slot = nullptr,
-                                               const float4* own = nullptr) {
+                                               const float4* own = nullptr, uint16_t* sel_slot = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
@@ -568,6 +572,10 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
       if (anchor) *anchor = make_float4(st.x, st.y, rk, 0.f);
       if (rk_slot) *rk_slot = rk;
     }
+    // the selection itself, for the backward pass: block positions in rank
+    // order, OBS_SEL_NONE past the points in range
+    if (sel_slot)
+      for (int r = lane; r < e.K; r += WARP) sel_slot[r] = r < nroad ? (uint16_t)sel_pos(sm.sel[r]) : OBS_SEL_NONE;
     write_road<LOSS>(v, e.K, nroad, st.x, st.y, c, s, sm, lane, row + 2 + 2 * e.P, ridx,
                      LOSS ? w + 8 + 8 * e.P : nullptr, acc);
   }
@@ -625,7 +633,7 @@ template <bool LOSS = false>
 __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* __restrict__ obs,
                                                 int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
                                                 ObsWarpSmem& sm, int lane, const float* __restrict__ wrow = nullptr,
-                                                float* rk_slot = nullptr) {
+                                                float* rk_slot = nullptr, uint16_t* sel_slot = nullptr) {
   // the agent's own state first: it does not wait for the world's loads
   const float4 own[2] = {e.state[i], e.stat[i]};
   const int w = e.agent_world[i];
@@ -640,7 +648,7 @@ __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* _
   v.g = e.rgrid[w];
   return observe_agent<LOSS>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
                              partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
-                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own);
+                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own, sel_slot);
 }
 
 // Per-stage form: one warp per agent over the whole batch.  Dynamic shared
@@ -666,6 +674,7 @@ struct SplitLoss {
   float reward_w;
   float* ell;          // [A]
   float* rk;           // [A] or nullptr
+  uint16_t* sel;       // [A][K] each observed agent's road selection (block positions), or nullptr
 };
 
 // Batched split form, after the step (k_world without observation):
@@ -707,7 +716,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
       dot = write_done_row<LOSS>(e, f, orow, ridx, pidx, loss.w, lane);
     } else {
       dot = observe_global<LOSS>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
-                                 LOSS && loss.rk ? loss.rk + i : nullptr);
+                                 LOSS && loss.rk ? loss.rk + i : nullptr,
+                                 LOSS && loss.sel ? loss.sel + (size_t)i * e.K : nullptr);
     }
     if (LOSS && lane == 0) loss.ell[i] = fmaf(loss.reward_w, loss.ell[i], dot);
   }

@@ -50,6 +50,7 @@ struct FusedArgs {
   float reward_w;
   float* ell;                // [A] or nullptr
   float* rk_out;             // [A] with ell: each observed agent's K-th road distance (+inf: fewer), or nullptr
+  uint16_t* sel_out;         // [A][K] with ell: each observed agent's road selection (block positions), or nullptr
   unsigned* clear;           // cleared (clear_n words) by the launch, for the launch that follows; or nullptr
   int clear_n;
   // step out of place: the post-step state and flags go here instead of
@@ -553,8 +554,11 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         if (a.ell) {
           float4* anc = e.anchor ? e.anchor + i : nullptr;
           float* rks = a.rk_out ? a.rk_out + i : nullptr;
-          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks)
-                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks);
+          uint16_t* sels = a.sel_out ? a.sel_out + (size_t)i * e.K : nullptr;
+          const float dot = use_tile ? observe_agent<true>(e, vt, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks,
+                                                           nullptr, sels)
+                                     : observe_agent<true>(e, vg, li, orow, ridx, pidx, osm, lane, anc, a.obs_w, rks,
+                                                           nullptr, sels);
           if (lane == 0) {
             float rs = 0.f;
             if (a.do_step && ag.act0[li] && !(ag.fl[li] & GD_FLAG_STATIC)) {
