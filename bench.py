@@ -628,7 +628,7 @@ def bench_lidar(workload, n_rays, fov, head, steps, warmup, dev, stream, flush, 
            "value": T * A * steps / (sum(ms) / 1e3), "unit": METRIC, "ms_per_episode": statistics.mean(ms),
            "autotuned": {"lidar_block_size": info.lidar_block_size, "road_tile": info.lidar_road_tile,
                          "split": info.lidar_split, "road_cell_m": round(float(info.road_cell), 3)},
-           "roofline": {"kernel": "k_lidar (split form) or k_world<LIDAR> (fused), as tuned", "bound": "hbm",
+           "roofline": {"kernel": "k_lidar_group (split form) or k_world<LIDAR> (fused), as tuned", "bound": "hbm",
                         "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                         "frac": achieved / hbm, "algorithmic_bytes_per_agent_step": algo,
                         "timing": "episode time of the timed graph replays / steps (both launches of a step)"},
@@ -796,7 +796,7 @@ def run_profile(args):
     sees warm-up + timed k_world launches and nothing else.  --shape
     B,C,T: CTA size B, road cell C m, road tile T (0/1) instead of the
     library's default shape; --lidar N: the LiDAR rollout (N rays over --fov
-    degrees, split form: k_world step + k_lidar scan per simulator step)
+    degrees, split form: k_world step + k_lidar_group scan per simulator step)
     instead of the radial one; --worlds W: the first W worlds of the
     workload only."""
     import math

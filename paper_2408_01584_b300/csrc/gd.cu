@@ -32,6 +32,7 @@ struct NvtxRange {
 };
 
 constexpr int kObsWarpsDefault = 8;
+constexpr int kLidarGroup = 2;    // warps per agent of the stand-alone LiDAR scan (2, 3 or 4 built)
 constexpr int kWorldWarps = 8;    // default CTA size of k_world (warps); 4 and 16 also built
 constexpr int kAdjWarps = 8;
 // Split adjoint's observer kernel: CTA size and shared memory (the
@@ -161,10 +162,10 @@ struct gd_env {
   int lidar_n = 0;              // rays per agent (0 = not enabled)
   LidarFan fan{};
   float2* ray_dirs = nullptr;   // [n] (cos, sin) of the ray angles in the sensor frame
-  int lidar_obs_warps = 12;     // stand-alone k_lidar CTA size (warps: 12, 8 or 4)
+  int lidar_groups = 1;         // stand-alone scan: warp groups per CTA of k_lidar_group
   int lo_grid = 0;              // its persistent CTAs
   unsigned* lcounter = nullptr; // its agent counters (LIDAR_STRIPES)
-  int lw_split = 0;             // batched form: 1 = k_world step + k_lidar, 0 = one fused k_world
+  int lw_split = 0;             // batched form: 1 = k_world step + k_lidar_group, 0 = one fused k_world
   int lw_warps = 8;             // fused LiDAR kernel CTA size (4, 8 or 12 warps)
   int lw_notile = 0;            // 1: no shared-memory road tile (more warps per SM)
   int lw_tile = 0;              // its road tile (bytes)
@@ -805,28 +806,21 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     env->lw_split = cfg->lidar_split;
     GD_TRY(dev_alloc(env, &env->lcounter, LIDAR_STRIPES));
-    // stand-alone scan: the most warps whose shared memory fits one CTA
-    int wp = 12;
-    while (wp > 4 && wp * lidar_warp_bytes(n) + lidar_dirs_bytes(n) + 1024 > (size_t)smem_blk) wp -= 4;
-    env->lidar_obs_warps = wp;
-    const size_t ls = wp * lidar_warp_bytes(n) + lidar_dirs_bytes(n);
+    // stand-alone scan: groups of kLidarGroup warps, as many as fit one CTA
+    constexpr int G = kLidarGroup;
+    int groups = std::min(LIDAR_MAX_GROUPS, LidarGroupShape<G>::max_warps / G);
+    while (groups > 1 && lidar_groups_smem(G, groups, n) + 1024 > (size_t)smem_blk) --groups;
+    if (lidar_groups_smem(G, groups, n) + 1024 > (size_t)smem_blk) {
+      gd_destroy(env);
+      return fail(nullptr, GD_ERR_INVALID_ARG, "lidar_rays: the scan's keys and ray table do not fit shared memory");
+    }
+    env->lidar_groups = groups;
     int per_sm = 0, nsm = 0;
     GD_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    switch (wp) {
-      case 12:
-        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<12>)));
-        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<12>, 12 * 32, ls));
-        break;
-      case 8:
-        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<8>)));
-        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<8>, 8 * 32, ls));
-        break;
-      default:
-        GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar<4>)));
-        GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar<4>, 4 * 32, ls));
-        break;
-    }
-    env->lo_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (A + wp - 1) / wp));
+    GD_TRY(allow_max_smem(reinterpret_cast<const void*>(k_lidar_group<G>)));
+    GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar_group<G>, groups * G * 32,
+                                                         lidar_groups_smem(G, groups, n)));
+    env->lo_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (A + groups - 1) / groups));
   }
   GD_TRY(build_road(env, rcell));
   GD_TRY(cudaStreamSynchronize(env->stream));
@@ -1046,14 +1040,10 @@ static void launch_lidar(gd_env* env, const float* head, float* depth, uint8_t* 
                          bool cleared = false) {
   if (!stream) stream = env->stream;
   const LidarArgs la = lidar_args(env, head, depth, cls);
-  const int wp = env->lidar_obs_warps;
-  const size_t smem = wp * (size_t)la.warp_bytes + lidar_dirs_bytes(env->lidar_n);
+  const int groups = env->lidar_groups;
   if (!cleared) cudaMemsetAsync(env->lcounter, 0, LIDAR_STRIPES * sizeof(unsigned), stream);
-  switch (wp) {
-    case 12: k_lidar<12><<<env->lo_grid, 12 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
-    case 8: k_lidar<8><<<env->lo_grid, 8 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
-    default: k_lidar<4><<<env->lo_grid, 4 * 32, smem, stream>>>(env->d, la, env->lcounter); break;
-  }
+  k_lidar_group<kLidarGroup><<<env->lo_grid, groups * kLidarGroup * 32,
+                               lidar_groups_smem(kLidarGroup, groups, env->lidar_n), stream>>>(env->d, la, env->lcounter);
 }
 
 // Fused LiDAR form: one persistent launch of the step (if do_step) and the

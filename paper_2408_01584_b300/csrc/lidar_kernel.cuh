@@ -10,7 +10,8 @@
 // or road edge (agent first at equal t); depth R, class none when it meets
 // nothing.  An agent that is done observes nothing (all zero).
 //
-// One warp per agent, obstacle-major.  Seen from the ray origin, an obstacle
+// Obstacle-major, one warp per agent in the fused kernel and a pair of
+// warps per agent in the stand-alone scan.  Seen from the ray origin, an obstacle
 // that keeps at least LIDAR_NEAR_FULL away subtends an arc shorter than pi:
 // the arc between the extreme corner (box) or end point (segment)
 // directions.  It maps to one contiguous range of ray indices (two when it
@@ -24,7 +25,7 @@
 // lengths, so a near box (hundreds of rays) and a far segment (a few) cost
 // the same per ray.
 //
-// Every warp keeps one 32-bit key per ray in shared memory: the depth's
+// Every agent being scanned has one 32-bit key per ray in shared memory: the depth's
 // bits with the lowest bit replaced by the class (0 agent, 1 road edge),
 // folded with atomicMin.  Depths are >= 0, so the bits order like the
 // values; the replaced bit moves the depth by at most one unit in the last
@@ -310,13 +311,14 @@ __device__ __forceinline__ void lidar_decode(unsigned key, float R, float& d, ui
   }
 }
 
-// Write one agent's row from the keys (zeros if `done`).
+// Write one agent's row from the keys (zeros if `done`): thread `lane` of
+// the `nt` that share the row (a warp, or a warp pair).
 __device__ __forceinline__ void lidar_write(const unsigned* keys, int n, float R, bool done, float* __restrict__ drow,
-                                            uint8_t* __restrict__ crow, int lane) {
+                                            uint8_t* __restrict__ crow, int lane, int nt = WARP) {
   const bool vec = (n & 3) == 0 && ((uintptr_t)drow & 15u) == 0 && (!crow || ((uintptr_t)crow & 3u) == 0);
   if (vec) {
     const uint4* k4 = reinterpret_cast<const uint4*>(keys);
-    for (int q = lane; q < (n >> 2); q += WARP) {
+    for (int q = lane; q < (n >> 2); q += nt) {
       float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
       uint8_t c[4] = {0, 0, 0, 0};
       if (!done) {
@@ -332,7 +334,7 @@ __device__ __forceinline__ void lidar_write(const unsigned* keys, int n, float R
                                                ((uint32_t)c[3] << 24);
     }
   } else {
-    for (int k = lane; k < n; k += WARP) {
+    for (int k = lane; k < n; k += nt) {
       float d = 0.f;
       uint8_t c = 0;
       if (!done) lidar_decode(keys[k], R, d, c);
@@ -340,6 +342,152 @@ __device__ __forceinline__ void lidar_write(const unsigned* keys, int n, float R
       if (crow) crow[k] = c;
     }
   }
+}
+
+// Queue item(s) of the box of agent j (in the scene, not the observer) seen
+// from (ex, ey) with sensor axis (cs, ss): returns the number of ray ranges
+// (0..2, in r0 / r1) and sets the item geometry ga, gb.
+__device__ __forceinline__ int lidar_box_item(const WorldView& v, int j, float ex, float ey, float cs, float ss,
+                                              float R, const LidarFan& fan, unsigned& r0, unsigned& r1, float4& ga,
+                                              float2& gb) {
+  const float4 sj = v.state[j];
+  const float4 tj = v.stat[j];
+  float cj, sjn;
+  if (v.cs) {
+    cj = v.cs[j].x;
+    sjn = v.cs[j].y;
+  } else {
+    sincosf(sj.z, &sjn, &cj);
+  }
+  const float hl = 0.5f * tj.x, hw = 0.5f * tj.y;
+  const float qx = ex - sj.x, qy = ey - sj.y;               // ray origin relative to the box centre
+  const float dc = sqrtf(dist2(qx, qy));
+  if (!(dc <= R + sqrtf(dist2(hl, hw)) + 1e-3f)) return 0;
+  const float ox = rot_x(cj, sjn, qx, qy), oy = rot_y(cj, sjn, qx, qy);
+  const float cp = fmaf(cs, cj, __fmul_rn(ss, sjn)), sp = fmaf(ss, cj, -__fmul_rn(cs, sjn));
+  ga = make_float4(ox, oy, cp, sp);
+  gb = make_float2(hl, hw);
+  bool full = fabsf(ox) <= hl + LIDAR_NEAR_FULL && fabsf(oy) <= hw + LIDAR_NEAR_FULL;
+  float lo = 0.f, hi = 0.f;
+  if (!full) {
+    // corner directions in the sensor frame; the box subtends less than pi,
+    // so offsets from corner 0 need no wrap beyond one turn
+    const float c1 = rot_x(cs, ss, -qx, -qy), c2 = rot_y(cs, ss, -qx, -qy);
+    float g0 = 0.f, dmin = 0.f, dmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float u = (k & 1) ? hl : -hl, w = (k & 2) ? hw : -hw;
+      const float p1 = c1 + fmaf(u, cp, __fmul_rn(w, sp)), p2 = c2 + fmaf(w, cp, -__fmul_rn(u, sp));
+      const float gk = atan2f(p2, p1);
+      if (k == 0) {
+        g0 = gk;
+      } else {
+        float dl = gk - g0;
+        dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
+        dmin = fminf(dmin, dl);
+        dmax = fmaxf(dmax, dl);
+      }
+    }
+    lo = g0 + dmin;
+    hi = g0 + dmax;
+    full = hi - lo >= LIDAR_PI - 0.01f;
+  }
+  return arc_ranges(fan, lo, hi, full, r0, r1);
+}
+
+// Queue item(s) of the road-edge segment sg = (a, b) seen from (ex, ey)
+// with sensor axis (cs, ss); as lidar_box_item.
+__device__ __forceinline__ int lidar_seg_item(float4 sg, float ex, float ey, float cs, float ss, float R,
+                                              const LidarFan& fan, unsigned& r0, unsigned& r1, float4& ga,
+                                              float2& gb) {
+  const float wx = sg.x - ex, wy = sg.y - ey, dx = sg.z - sg.x, dy = sg.w - sg.y;
+  const float dd = dist2(dx, dy);
+  const float tp = dd > 0.f ? clampf(__fdividef(-fmaf(wx, dx, __fmul_rn(wy, dy)), dd), 0.f, 1.f) : 0.f;
+  const float dist = sqrtf(dist2(fmaf(tp, dx, wx), fmaf(tp, dy, wy)));
+  if (!(dist <= R + 1e-3f)) return 0;
+  const float w1 = rot_x(cs, ss, wx, wy), w2 = rot_y(cs, ss, wx, wy);
+  const float d1 = rot_x(cs, ss, dx, dy), d2 = rot_y(cs, ss, dx, dy);
+  ga = make_float4(w1, w2, d1, d2);
+  gb = make_float2(fmaf(w1, d2, -__fmul_rn(w2, d1)), 0.f);
+  bool full = dist < LIDAR_NEAR_FULL;
+  float lo = 0.f, hi = 0.f;
+  if (!full) {
+    // end point directions; the short way between them is the arc
+    const float ga0 = atan2f(w2, w1), gb0 = atan2f(w2 + d2, w1 + d1);
+    float dl = gb0 - ga0;
+    dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
+    lo = dl >= 0.f ? ga0 : gb0;
+    hi = lo + fabsf(dl);
+    full = hi - lo >= LIDAR_PI - 0.01f;
+  }
+  return arc_ranges(fan, lo, hi, full, r0, r1);
+}
+
+// Sensor axis of an agent with heading state z (or (cos, sin) from cs) and
+// head rotation `head`: the heading turned by the head angle.
+__device__ __forceinline__ void lidar_axis(const WorldView& v, int li, float z, float head, float& cs, float& ss) {
+  float ct, st;
+  if (v.cs) {
+    ct = v.cs[li].x;
+    st = v.cs[li].y;
+  } else {
+    sincosf(z, &st, &ct);
+  }
+  float sh, ch;
+  sincosf(head, &sh, &ch);
+  cs = fmaf(ct, ch, -__fmul_rn(st, sh));
+  ss = fmaf(st, ch, __fmul_rn(ct, sh));
+}
+
+// Fold one warp's share of agent li's obstacles into the keys: of the
+// rounds of 32 boxes, then of 32 road-edge candidates, those with index
+// part, part + parts, ... (all of them when parts = 1).  The warp's queue is
+// empty at entry and at exit.
+__device__ __forceinline__ void lidar_fold(const WorldView& v, int li, float R, float ex, float ey, float cs, float ss,
+                                           const LidarArgs& la, LidarWarpHead& h, unsigned* keys, int lane, int part,
+                                           int parts) {
+  // ---- other agents' boxes ------------------------------------------------
+  int nq = 0;
+  for (int j0 = part * WARP; j0 < v.n; j0 += parts * WARP) {
+    const int j = j0 + lane;
+    int m = 0;
+    unsigned r0 = 0, r1 = 0;
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 gb = make_float2(0.f, 0.f);
+    if (j < v.n && j != li && !(v.flags[j] & GD_FLAG_DONE))
+      m = lidar_box_item(v, j, ex, ey, cs, ss, R, la.fan, r0, r1, ga, gb);
+    nq = lidar_push(h, nq, m, r0, r1, ga, gb, lane);
+    if (nq >= WARP) {
+      lidar_drain<false>(h, keys, nq, la.dirs, R, lane);
+      nq = 0;
+    }
+  }
+  if (nq) lidar_drain<false>(h, keys, nq, la.dirs, R, lane);
+  nq = 0;
+
+  // ---- road-edge segments: first points within R + longest segment -------
+  const float Rr = R + v.g.seg_max + 1e-3f;
+  int rows_total = 1;
+  for (int row0 = 0; row0 < rows_total; row0 += MAX_ROWS) {
+    int nrows = 0;
+    const int total = lidar_rows(v, la.lcell, Rr, ex, ey, row0, h, lane, nrows, rows_total);
+    walk_rows(
+        h, nrows, total, lane,
+        [&](unsigned p, bool valid) {
+          int m = 0;
+          unsigned r0 = 0, r1 = 0;
+          float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+          float2 gb = make_float2(0.f, 0.f);
+          if (valid) m = lidar_seg_item(la.lsegs[p], ex, ey, cs, ss, R, la.fan, r0, r1, ga, gb);
+          nq = lidar_push(h, nq, m, r0, r1, ga, gb, lane);
+          if (nq >= WARP) {
+            lidar_drain<true>(h, keys, nq, la.dirs, R, lane);
+            nq = 0;
+          }
+        },
+        part * WARP, parts * WARP);
+  }
+  if (nq) lidar_drain<true>(h, keys, nq, la.dirs, R, lane);
 }
 
 // LiDAR scan of agent li of the world in view v by one warp.
@@ -358,162 +506,90 @@ __device__ __forceinline__ void lidar_agent(const WorldView& v, int li, float R,
   }
   __syncwarp();
   const float4 s = v.state[li];
-  const float ex = s.x, ey = s.y;
-  float ct, st;
-  if (v.cs) {
-    ct = v.cs[li].x;
-    st = v.cs[li].y;
-  } else {
-    sincosf(s.z, &st, &ct);
-  }
-  float sh, ch;
-  sincosf(head, &sh, &ch);
-  // sensor axis: heading turned by the head angle
-  const float cs = fmaf(ct, ch, -__fmul_rn(st, sh)), ss = fmaf(st, ch, __fmul_rn(ct, sh));
-
-  // ---- other agents' boxes ------------------------------------------------
-  int nq = 0;
-  for (int j0 = 0; j0 < v.n; j0 += WARP) {
-    const int j = j0 + lane;
-    int m = 0;
-    unsigned r0 = 0, r1 = 0;
-    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 gb = make_float2(0.f, 0.f);
-    if (j < v.n && j != li && !(v.flags[j] & GD_FLAG_DONE)) {
-      const float4 sj = v.state[j];
-      const float4 tj = v.stat[j];
-      float cj, sjn;
-      if (v.cs) {
-        cj = v.cs[j].x;
-        sjn = v.cs[j].y;
-      } else {
-        sincosf(sj.z, &sjn, &cj);
-      }
-      const float hl = 0.5f * tj.x, hw = 0.5f * tj.y;
-      const float qx = ex - sj.x, qy = ey - sj.y;               // ray origin relative to the box centre
-      const float dc = sqrtf(dist2(qx, qy));
-      if (dc <= R + sqrtf(dist2(hl, hw)) + 1e-3f) {
-        const float ox = rot_x(cj, sjn, qx, qy), oy = rot_y(cj, sjn, qx, qy);
-        const float cp = fmaf(cs, cj, __fmul_rn(ss, sjn)), sp = fmaf(ss, cj, -__fmul_rn(cs, sjn));
-        ga = make_float4(ox, oy, cp, sp);
-        gb = make_float2(hl, hw);
-        bool full = fabsf(ox) <= hl + LIDAR_NEAR_FULL && fabsf(oy) <= hw + LIDAR_NEAR_FULL;
-        float lo = 0.f, hi = 0.f;
-        if (!full) {
-          // corner directions in the sensor frame; the box subtends less
-          // than pi, so offsets from corner 0 need no wrap beyond one turn
-          const float c1 = rot_x(cs, ss, -qx, -qy), c2 = rot_y(cs, ss, -qx, -qy);
-          float g0 = 0.f, dmin = 0.f, dmax = 0.f;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float u = (k & 1) ? hl : -hl, w = (k & 2) ? hw : -hw;
-            const float p1 = c1 + fmaf(u, cp, __fmul_rn(w, sp)), p2 = c2 + fmaf(w, cp, -__fmul_rn(u, sp));
-            const float gk = atan2f(p2, p1);
-            if (k == 0) {
-              g0 = gk;
-            } else {
-              float dl = gk - g0;
-              dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
-              dmin = fminf(dmin, dl);
-              dmax = fmaxf(dmax, dl);
-            }
-          }
-          lo = g0 + dmin;
-          hi = g0 + dmax;
-          full = hi - lo >= LIDAR_PI - 0.01f;
-        }
-        m = arc_ranges(la.fan, lo, hi, full, r0, r1);
-      }
-    }
-    nq = lidar_push(h, nq, m, r0, r1, ga, gb, lane);
-    if (nq >= WARP) {
-      lidar_drain<false>(h, keys, nq, la.dirs, R, lane);
-      nq = 0;
-    }
-  }
-  if (nq) lidar_drain<false>(h, keys, nq, la.dirs, R, lane);
-  nq = 0;
-
-  // ---- road-edge segments: first points within R + longest segment -------
-  const float Rr = R + v.g.seg_max + 1e-3f;
-  int rows_total = 1;
-  for (int row0 = 0; row0 < rows_total; row0 += MAX_ROWS) {
-    int nrows = 0;
-    const int total = lidar_rows(v, la.lcell, Rr, ex, ey, row0, h, lane, nrows, rows_total);
-    walk_rows(h, nrows, total, lane, [&](unsigned p, bool valid) {
-      int m = 0;
-      unsigned r0 = 0, r1 = 0;
-      float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
-      float2 gb = make_float2(0.f, 0.f);
-      if (valid) {
-        const float4 sg = la.lsegs[p];
-        const float wx = sg.x - ex, wy = sg.y - ey, dx = sg.z - sg.x, dy = sg.w - sg.y;
-        const float dd = dist2(dx, dy);
-        const float tp = dd > 0.f ? clampf(__fdividef(-fmaf(wx, dx, __fmul_rn(wy, dy)), dd), 0.f, 1.f) : 0.f;
-        const float dist = sqrtf(dist2(fmaf(tp, dx, wx), fmaf(tp, dy, wy)));
-        if (dist <= R + 1e-3f) {
-          const float w1 = rot_x(cs, ss, wx, wy), w2 = rot_y(cs, ss, wx, wy);
-          const float d1 = rot_x(cs, ss, dx, dy), d2 = rot_y(cs, ss, dx, dy);
-          ga = make_float4(w1, w2, d1, d2);
-          gb = make_float2(fmaf(w1, d2, -__fmul_rn(w2, d1)), 0.f);
-          bool full = dist < LIDAR_NEAR_FULL;
-          float lo = 0.f, hi = 0.f;
-          if (!full) {
-            // end point directions; the short way between them is the arc
-            const float ga0 = atan2f(w2, w1), gb0 = atan2f(w2 + d2, w1 + d1);
-            float dl = gb0 - ga0;
-            dl = dl > LIDAR_PI ? dl - 2.f * LIDAR_PI : (dl < -LIDAR_PI ? dl + 2.f * LIDAR_PI : dl);
-            lo = dl >= 0.f ? ga0 : gb0;
-            hi = lo + fabsf(dl);
-            full = hi - lo >= LIDAR_PI - 0.01f;
-          }
-          m = arc_ranges(la.fan, lo, hi, full, r0, r1);
-        }
-      }
-      nq = lidar_push(h, nq, m, r0, r1, ga, gb, lane);
-      if (nq >= WARP) {
-        lidar_drain<true>(h, keys, nq, la.dirs, R, lane);
-        nq = 0;
-      }
-    });
-  }
-  if (nq) lidar_drain<true>(h, keys, nq, la.dirs, R, lane);
+  float cs, ss;
+  lidar_axis(v, li, s.z, head, cs, ss);
+  lidar_fold(v, li, R, s.x, s.y, cs, ss, la, h, keys, lane, 0, 1);
   lidar_write(keys, n, R, false, drow, crow, lane);
 }
 
-// Stand-alone scan of every agent (the per-stage form, and the second
-// launch of the split batched form): persistent CTAs, each warp takes the
-// next agent from one of LIDAR_STRIPES counters, so no warp waits for another.  The
-// scene is read from global memory.  Dynamic shared memory: WARPS *
-// warp_bytes, then the ray directions.
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_lidar(DevEnv e, LidarArgs la, unsigned* counter) {
+// ---- a group of warps per agent ---------------------------------------------
+// The stand-alone scan with G warps on each agent: one key array per group
+// (the warps fold into it with atomicMin), one item queue per warp.  The
+// warps take rounds of 32 boxes and of 32 road-edge candidates in turn, so
+// each has its own queue and drains as in the one-warp form; a named
+// barrier of the group's 32 G threads (id 1 + group) orders the keys'
+// initialisation before the folds and the folds before the row is written.
+// A 3000-ray scan's keys then hold more warps per SM than the 12 of one
+// warp per agent.  The keys are the same folds of the same tests: the scan
+// is bit-identical to the one-warp form.
+__device__ __forceinline__ void group_sync(unsigned id, unsigned threads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Shared memory of one group: G warp heads, then the keys.
+__host__ __device__ __forceinline__ size_t lidar_group_bytes(int G, int n) {
+  return (size_t)G * sizeof(LidarWarpHead) + 16 * (size_t)((n + 3) / 4);
+}
+constexpr int LIDAR_MAX_GROUPS = 15;   // named barriers 1..15
+// Shared memory of a CTA of `groups` groups: the groups, the claim slots
+// (two per group), the ray directions.
+__host__ __device__ __forceinline__ size_t lidar_groups_smem(int G, int groups, int n) {
+  return (size_t)groups * lidar_group_bytes(G, n) + 16 * (size_t)((2 * LIDAR_MAX_GROUPS + 3) / 4) +
+         lidar_dirs_bytes(n);
+}
+// CTA size of the group form: at most this many warps.  Measured on the
+// 1,024 x 64 workload (3000 rays, 360 degrees, ms per episode): pairs
+// with 18, 20 and 22 warps per SM 49.2, 47.0 and 45.7; groups of three
+// (24 warps) 48.6 and of four (32 warps, 64 registers) 49.9; one warp per
+// agent (12 warps) 59.0.  22 warps of pairs is what shared memory holds
+// (11 x 18.2 KB + 23.4 KB of ray directions).
+template <int G>
+struct LidarGroupShape {
+  static constexpr int max_warps = G == 2 ? 22 : (G == 3 ? 24 : 32);
+};
+
+// Persistent CTAs of blockDim.x / (32 G) groups; group g of the grid draws
+// agents c, c + LIDAR_STRIPES, ... from counter c = g mod LIDAR_STRIPES.  The
+// group's first warp claims and publishes the claim in one of two slots,
+// alternating, so that a slot is rewritten only after the other warps have
+// passed the next barrier (and so read the slot).
+template <int G>
+__global__ void __launch_bounds__(LidarGroupShape<G>::max_warps * 32, 1)
+    k_lidar_group(DevEnv e, LidarArgs la, unsigned* counter) {
   extern __shared__ __align__(16) unsigned char lidar_smem_raw[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  float2* sdirs = reinterpret_cast<float2*>(lidar_smem_raw + (size_t)WARPS * la.warp_bytes);
-  lidar_stage_dirs(sdirs, la.dirs, la.fan.n);
+  const int n = la.fan.n;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, grp = wib / G, part = wib - grp * G;
+  const int groups = (int)(blockDim.x / (32 * G));
+  unsigned char* gbase = lidar_smem_raw + (size_t)grp * lidar_group_bytes(G, n);
+  LidarWarpHead& h = *reinterpret_cast<LidarWarpHead*>(gbase + part * sizeof(LidarWarpHead));
+  unsigned* keys = reinterpret_cast<unsigned*>(gbase + G * sizeof(LidarWarpHead));
+  unsigned* claim = reinterpret_cast<unsigned*>(lidar_smem_raw + (size_t)groups * lidar_group_bytes(G, n));
+  float2* sdirs = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(claim) +
+                                            16 * (size_t)((2 * LIDAR_MAX_GROUPS + 3) / 4));
+  lidar_stage_dirs(sdirs, la.dirs, n);
   __syncthreads();
   la.dirs = sdirs;
-  unsigned char* base = lidar_smem_raw + (size_t)wib * la.warp_bytes;
-  LidarWarpHead& h = *reinterpret_cast<LidarWarpHead*>(base);
-  unsigned* keys = reinterpret_cast<unsigned*>(base + sizeof(LidarWarpHead));
-  // claims striped over LIDAR_STRIPES counters (warp g draws agents c,
-  // c + LIDAR_STRIPES, ... from counter c = g mod LIDAR_STRIPES), so they do
-  // not all queue on one address
-  const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % LIDAR_STRIPES;
-  for (;;) {
-    unsigned k = 0;
-    if (lane == 0) k = atomicAdd(counter + c, 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    const unsigned iu = c + LIDAR_STRIPES * k;
+  const unsigned id = 1u + (unsigned)grp, nthr = 32u * G;
+  const int t = part * WARP + lane;     // thread of the group
+  const unsigned c = (unsigned)(blockIdx.x * groups + grp) % LIDAR_STRIPES;
+  for (int it = 0;; ++it) {
+    unsigned* slot = claim + 2 * grp + (it & 1);
+    if (t == 0) *slot = atomicAdd(counter + c, 1u);
+    group_sync(id, nthr);   // the claim published; the previous agent's row written by every warp
+    const unsigned iu = c + LIDAR_STRIPES * *slot;
     if (iu >= (unsigned)e.A) break;
     const int i = (int)iu;
+    float* drow = la.depth + (size_t)i * n;
+    uint8_t* crow = la.cls ? la.cls + (size_t)i * n : nullptr;
     if (e.flags[i] & GD_FLAG_DONE) {
       // removed from the scene: an all-zero row, no world loads
-      lidar_write(keys, la.fan.n, e.R, true, la.depth + (size_t)i * la.fan.n,
-                  la.cls ? la.cls + (size_t)i * la.fan.n : nullptr, lane);
+      lidar_write(keys, n, e.R, true, drow, crow, t, 32 * G);
       continue;
+    }
+    {
+      uint4* k4 = reinterpret_cast<uint4*>(keys);
+      const uint4 e4 = make_uint4(LIDAR_EMPTY, LIDAR_EMPTY, LIDAR_EMPTY, LIDAR_EMPTY);
+      for (int q = t; q < (n + 3) >> 2; q += 32 * G) k4[q] = e4;
     }
     const int w = e.agent_world[i];
     const int a0 = e.agent_off[w];
@@ -525,8 +601,13 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_lidar(DevEnv e, LidarArgs la,
     v.n = e.agent_off[w + 1] - a0;
     road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
     v.g = e.rgrid[w];
-    lidar_agent(v, i - a0, e.R, la.head ? la.head[i] : 0.f, la, la.depth + (size_t)i * la.fan.n,
-                la.cls ? la.cls + (size_t)i * la.fan.n : nullptr, h, keys, lane);
+    const float4 s = v.state[i - a0];
+    float cs, ss;
+    lidar_axis(v, i - a0, s.z, la.head ? la.head[i] : 0.f, cs, ss);
+    group_sync(id, nthr);   // keys initialised
+    lidar_fold(v, i - a0, e.R, s.x, s.y, cs, ss, la, h, keys, lane, part, G);
+    group_sync(id, nthr);   // every hit folded
+    lidar_write(keys, n, e.R, false, drow, crow, t, 32 * G);
   }
 }
 

@@ -136,11 +136,14 @@ __device__ __forceinline__ int road_rows(const WorldView& v, float R, float R2, 
 // sm.row_start / sm.row_excl: fn(pos, valid) is called by every lane in
 // every round (valid = this lane has a candidate), so fn may use warp
 // collectives.
+// Rounds start at entry `first` and step by `stride` (a multiple of 32):
+// two warps sharing a list walk alternate rounds.
 template <typename SM, typename Fn>
-__device__ __forceinline__ void walk_rows(const SM& sm, int nrows, int total, int lane, Fn&& fn) {
+__device__ __forceinline__ void walk_rows(const SM& sm, int nrows, int total, int lane, Fn&& fn, int first = 0,
+                                          int stride = WARP) {
   int r = 0;
   unsigned rs = sm.row_start[0], re = nrows > 1 ? sm.row_excl[1] : 0xffffffffu, rx = 0;
-  for (int f0 = 0; f0 < total; f0 += WARP) {
+  for (int f0 = first; f0 < total; f0 += stride) {
     const int f = f0 + lane;
     const bool valid = f < total;
     if (valid) {
