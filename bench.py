@@ -464,12 +464,15 @@ def bench_batched_forward(workload, steps, warmup, dev, stream, flush, seed=0, r
     return out
 
 
-def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_worlds=256, cpu_worlds=8, cpu_steps=91):
+def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_worlds=256, cpu_worlds=8, cpu_steps=91,
+                 shape=None):
     """Differentiable rollouts: objective forward (checkpoints every 10
     steps) + adjoint backward over the whole episode, each a captured CUDA
     graph (batched form), against the same kernels issued from the host
     (plain form); each kernel's roofline line from a launch-by-launch pass
-    under CUDA events; the oracle's forward + backward on a sample."""
+    under CUDA events; the oracle's forward + backward on a sample.
+    `shape`: gd_config fields that replace the autotuner (profiling runs,
+    where the tuner's trials are timed under the profiler)."""
     import numpy as np
     import torch
     from paper_2408_01584_b300 import gd, scenes
@@ -482,8 +485,9 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
     with torch.cuda.stream(stream):
         for form in ("batched", "plain"):
             fl = cfg["flags"] | gd.GD_DIFFERENTIABLE | (gd.GD_BATCHED if form == "batched" else 0)
-            env = gd.Env(sc, stream=stream, **dict(cfg, flags=fl))
-            gd.gd_autotune(env.h)
+            env = gd.Env(sc, stream=stream, **dict(cfg, flags=fl), **(shape or {}))
+            if not shape:
+                gd.gd_autotune(env.h)
             info = gd.gd_get_info(env.h)
             A, F = env.A, env.F
             actions = torch.from_numpy(scenes.make_actions(T, A, seed)).to(dev)
@@ -572,7 +576,8 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
            "autotuned": res["batched"]["autotuned"], "roofline": res["batched"]["roofline"],
            "kernels": res["batched"]["kernels"],
            "plain": dict(res["plain"], form="plain: the same kernels issued from the host launch by launch, no graph")}
-    out["cpu_baseline"] = cpu_baseline_fwdbwd(workload, sc, cpu_worlds, cpu_steps, seed)
+    if cpu_worlds:
+        out["cpu_baseline"] = cpu_baseline_fwdbwd(workload, sc, cpu_worlds, cpu_steps, seed)
     return out
 
 
@@ -808,7 +813,13 @@ def run_profile(args):
     if args.fwdbwd:
         stream = torch.cuda.Stream(dev)
         flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # see flush_l2
-        return dict(bench_fwdbwd(args.workload, args.steps, args.warmup, dev, stream, flush), profile=args.workload)
+        shape = None
+        if args.shape:
+            b, c, t = args.shape.split(",")
+            shape = dict(block_size=int(b), road_cell=float(c), road_no_tile=0 if int(t) else 1, obs_split=1,
+                         adjoint_split=1)
+        return dict(bench_fwdbwd(args.workload, args.steps, args.warmup, dev, stream, flush, shape=shape,
+                                 cpu_worlds=0 if shape else 8), profile=args.workload)
     wl = scenes.WORKLOADS[args.workload]
     T = wl["steps"]
     sc = scenes.workload_scene(args.workload, 0)
