@@ -39,7 +39,9 @@ constexpr int kAdjWarps = 8;
 // observation scratch and one slot row per warp).
 constexpr int kAdjObsWarps = 8;
 constexpr size_t kAdjObsSmem = kAdjObsWarps * (sizeof(ObsWarpSmem) + GD_MAX_AGENTS_PER_WORLD);
-constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window
+constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window (at least)
+constexpr float kTuneTrialMs = 1.5f;   // a trial's windows together last about this long (longer windows for
+                                       // small batches)
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
 
 // Split form's observation kernel: CTA size and shared memory.
@@ -2063,8 +2065,9 @@ gd_status gd_autotune(gd_env* env) {
       launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1);
     save(p);
   }
-  // time `launch` (kTuneSteps steps) at every phase: best of three sums
-  // after a warm-up
+  // time `launch` (win steps) at every phase: best of three sums after a
+  // warm-up
+  int win = kTuneSteps;
   auto time_phases = [&](auto&& launch, float& best) -> cudaError_t {
     best = INFINITY;
     for (int rep = 0; rep < 4; ++rep) {
@@ -2072,7 +2075,7 @@ gd_status gd_autotune(gd_env* env) {
       for (int p = 0; p < P; ++p) {
         restore(p);
         cudaEventRecord(e0, env->stream);
-        for (int k = 0; k < kTuneSteps; ++k) launch();
+        for (int k = 0; k < win; ++k) launch();
         cudaEventRecord(e1, env->stream);
         cudaError_t err = cudaEventSynchronize(e1);
         if (err != cudaSuccess) return err;
@@ -2084,12 +2087,24 @@ gd_status gd_autotune(gd_env* env) {
     }
     return cudaSuccess;
   };
+  // windows long enough to time: a small batch's steps take tens of
+  // microseconds, so its windows grow (up to the stride between the points)
+  // until the default shape's trial lasts about kTuneTrialMs
+  {
+    float probe = INFINITY;
+    e = time_phases([&] { launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1); },
+                    probe);
+    if (e == cudaSuccess && probe > 0.f && probe < kTuneTrialMs)
+      win = std::min(std::max(kTuneSteps, stride),
+                     std::max(kTuneSteps, (int)std::ceil(kTuneSteps * kTuneTrialMs / probe)));
+  }
   const float min_cell = (2.f * env->cfg.obs_radius + 0.01f) / (float)(MAX_ROWS - 2);
   const float cells[] = {6.f, 8.f, 12.f};
   const int warps[] = {4, 8, 16};
   float best_ms = INFINITY, best_cell = env->road_cell;
   int best_w = env->warps, best_st = d.topk, best_nt = env->notile, best_sp = env->split;
   for (float c : cells) {
+    if (e != cudaSuccess) break;
     const float cell = std::max(c, min_cell);
     if ((e = build_road(env, cell)) != cudaSuccess) break;
     for (int sp = 0; sp <= 1 && e == cudaSuccess; ++sp) {
