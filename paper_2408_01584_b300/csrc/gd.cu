@@ -166,7 +166,8 @@ struct gd_env {
   float2* ray_dirs = nullptr;   // [n] (cos, sin) of the ray angles in the sensor frame
   int lidar_groups = 1;         // stand-alone scan: warp groups per CTA of k_lidar_group
   int lo_grid = 0;              // its persistent CTAs
-  unsigned* lcounter = nullptr; // its agent counters (LIDAR_STRIPES)
+  unsigned* lcounter = nullptr; // its agent counters (two sets of LIDAR_STRIPES, alternating in the
+                                // overlapped rollout)
   int lw_split = 0;             // batched form: 1 = k_world step + k_lidar_group, 0 = one fused k_world
   int lw_warps = 8;             // fused LiDAR kernel CTA size (4, 8 or 12 warps)
   int lw_notile = 0;            // 1: no shared-memory road tile (more warps per SM)
@@ -807,7 +808,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaGetDevice(&dev));
     GD_TRY(cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     env->lw_split = cfg->lidar_split;
-    GD_TRY(dev_alloc(env, &env->lcounter, LIDAR_STRIPES));
+    GD_TRY(dev_alloc(env, &env->lcounter, 2 * LIDAR_STRIPES));
+    GD_TRY(cudaMemsetAsync(env->lcounter, 0, 2 * LIDAR_STRIPES * sizeof(unsigned), env->stream));
     // stand-alone scan: groups of kLidarGroup warps, as many as fit one CTA
     constexpr int G = kLidarGroup;
     int groups = std::min(LIDAR_MAX_GROUPS, LidarGroupShape<G>::max_warps / G);
@@ -1224,6 +1226,49 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
   }
 }
 
+// The split LiDAR rollout overlapped like issue_rollout_overlapped: the
+// state and flags alternate between two buffers (the last step leaves them
+// in the env's own), the step launch of t + 1 is a programmatic dependent of
+// scan t (it starts in that launch's tail and ends only after it), and the
+// scan's claim counters alternate between two sets.
+static void issue_lidar_overlapped(gd_env* env, int steps, const float* actions, const float* head, float* depth,
+                                   uint8_t* cls, int obs_per_step, float* reward, uint8_t* done, cudaStream_t stream) {
+  const size_t A = (size_t)env->A, n = (size_t)env->lidar_n;
+  float4* sbuf[2] = {env->d.state, env->alt_state};
+  uint8_t* fbuf[2] = {env->d.flags, env->alt_flags};
+  const int groups = env->lidar_groups;
+  int in = 0;
+  for (int t = 0; t < steps; ++t) {
+    const int out = ((steps - 1 - t) & 1) ? 1 : 0;
+    unsigned* lc = env->lcounter + (size_t)(t & 1) * LIDAR_STRIPES;
+    DevEnv dv = env->d;
+    dv.state = sbuf[in];
+    dv.flags = fbuf[in];
+    FusedArgs a{};
+    a.actions = reinterpret_cast<const float2*>(actions + (size_t)t * A * 2);
+    a.reward = reward ? reward + (size_t)t * A : nullptr;
+    a.done = done ? done + (size_t)t * A : nullptr;
+    a.counter = env->counter;
+    a.order = env->order;
+    a.tile_bytes = env->tile_cap;
+    a.do_step = 1;
+    a.clear = lc;
+    a.clear_n = (int)LIDAR_STRIPES;
+    a.state_out = out == in ? nullptr : sbuf[out];
+    a.flags_out = out == in ? nullptr : fbuf[out];
+    launch_step_ex(env, dv, a, stream, t > 0);
+    DevEnv dvo = env->d;
+    dvo.state = sbuf[out];
+    dvo.flags = fbuf[out];
+    const LidarArgs la = lidar_args(env, head ? head + (size_t)t * A : nullptr,
+                                    depth + (obs_per_step ? (size_t)t * A * n : 0),
+                                    cls ? cls + (obs_per_step ? (size_t)t * A * n : 0) : nullptr);
+    k_lidar_group<kLidarGroup><<<env->lo_grid, groups * kLidarGroup * 32,
+                                 lidar_groups_smem(kLidarGroup, groups, env->lidar_n), stream>>>(dvo, la, lc);
+    in = out;
+  }
+}
+
 gd_status gd_rollout(gd_env* env, int32_t steps, const float* actions, float* obs, int32_t obs_per_step, float* reward,
                      uint8_t* done) {
   NvtxRange range_("gd_rollout");
@@ -1501,9 +1546,12 @@ gd_status gd_rollout_lidar(gd_env* env, int32_t steps, const float* actions, con
       cudaStreamDestroy(cap);
       return cuda_fail(env, e, "gd_rollout_lidar: begin capture");
     }
-    for (int t = 0; t < steps; ++t)
-      launch_world_lidar(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
-                         done ? done + (size_t)t * A : nullptr, nullptr, hstep(t), dstep(t), cstep(t), 1, cap);
+    if (GD_ROLLOUT_OVERLAP && env->lw_split)
+      issue_lidar_overlapped(env, steps, actions, head, depth, cls, obs_per_step, reward, done, cap);
+    else
+      for (int t = 0; t < steps; ++t)
+        launch_world_lidar(env, actions + (size_t)t * A * 2, reward ? reward + (size_t)t * A : nullptr,
+                           done ? done + (size_t)t * A : nullptr, nullptr, hstep(t), dstep(t), cstep(t), 1, cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);

@@ -590,6 +590,9 @@ __global__ void __launch_bounds__(LidarGroupShape<G>::max_warps * 32, 1)
   unsigned* claim = reinterpret_cast<unsigned*>(lidar_smem_raw + (size_t)groups * lidar_group_bytes(G, n));
   float2* sdirs = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(claim) +
                                             16 * (size_t)((2 * LIDAR_MAX_GROUPS + 3) / 4));
+  // a step launch queued behind this one as a programmatic dependent (the
+  // overlapped rollout) may start as SMs free up at this launch's tail
+  asm volatile("griddepcontrol.launch_dependents;");
   lidar_stage_dirs(sdirs, la.dirs, n);
   __syncthreads();
   la.dirs = sdirs;

@@ -156,13 +156,16 @@ def test_lidar_fused_equals_per_stage_and_graph_equals_step_loop():
         assert torch.equal(a, b)
 
 
-def test_lidar_every_tuning_choice_gives_the_same_scan():
+@pytest.mark.parametrize("T", [3, 4])
+def test_lidar_every_tuning_choice_gives_the_same_scan(T):
     """CTA sizes 128 / 256 / 384 with and without the road tile, and the
-    split form (step, then a scan over all agents), on road grids of 6 and
-    12 m cells, produce bit-identical depths and classes."""
+    split form (step, then a scan over all agents; its rollout alternates
+    two state buffers, so odd and even step counts are both run), on road
+    grids of 6 and 12 m cells, produce bit-identical depths and classes and
+    leave the same state."""
     from paper_2408_01584_b300 import gd
     sc = small_scene(seed=8)
-    A, n, T = sc.num_agents, 1000, 3
+    A, n = sc.num_agents, 1000
     acts = torch.from_numpy(scenes.make_actions(T, A, 8)).cuda().contiguous()
     ref = None
     choices = [(b, t, 0) for b in (128, 256, 384) for t in (0, 1)] + [(256, 0, 1)]
@@ -176,10 +179,10 @@ def test_lidar_every_tuning_choice_gives_the_same_scan():
         cls = torch.empty(T, A, n, dtype=torch.uint8, device="cuda")
         gd.gd_rollout_lidar(env.h, T, acts, None, depth, cls, True)
         env.sync()
-        out = (depth.cpu(), cls.cpu())
+        out = (depth.cpu(), cls.cpu()) + tuple(x.cpu() for x in env.get_state())
         if ref is None:
             ref = out
-        assert torch.equal(out[0], ref[0]) and torch.equal(out[1], ref[1]), (block, no_tile, split, cell)
+        assert all(torch.equal(a, b) for a, b in zip(out, ref)), (block, no_tile, split, cell)
         env.close()
 
 
