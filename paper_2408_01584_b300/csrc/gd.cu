@@ -40,7 +40,7 @@ constexpr int kAdjWarps = 8;
 constexpr int kAdjObsWarps = 8;
 constexpr size_t kAdjObsSmem = kAdjObsWarps * (sizeof(ObsWarpSmem) + GD_MAX_AGENTS_PER_WORLD);
 constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window (at least)
-constexpr float kTuneTrialMs = 1.5f;   // a trial's windows together last about this long (longer windows for
+constexpr float kTuneTrialMs = 4.f;     // a trial's windows together last about this long (longer windows for
                                        // small batches)
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
 
