@@ -138,6 +138,8 @@ struct gd_env {
   float* rk_hist = nullptr;     // [episode_len][A] K-th road distance of each agent at each objective step
   uint16_t* sel_hist = nullptr; // [episode_len][A][K] road selection of each agent at each objective step, or
                                 // nullptr (no room: the backward pass re-selects)
+  bool sel_valid = false;       // sel_hist holds the last objective rollout's selections in the current road
+                                // layout (block positions; a rebuilt road grid invalidates them)
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
   int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
@@ -475,6 +477,7 @@ static cudaError_t build_road(gd_env* env, float cell) {
   env->d.lcell = p_lc;
   env->road_cell = cell;
   env->max_block = max_block;
+  env->sel_valid = false;    // recorded selections name positions in the old blocks
   if ((e = shape_kernels(env, max_block)) != cudaSuccess) return e;
   drop_graphs(env);
   return cudaStreamSynchronize(env->stream);
@@ -1755,6 +1758,7 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
   }
   env->diff_actions = actions;
   env->diff_steps = steps;
+  env->sel_valid = env->sel_hist != nullptr;
   return launch_check(env, "gd_rollout_objective");
 }
 
@@ -1860,6 +1864,9 @@ static void recompute_segment(gd_env* env, const float* actions0, int len, cudaS
   }
 }
 
+// The recorded selections the backward pass reads, or nullptr (re-select).
+static const uint16_t* rec_sel(const gd_env* env) { return env->sel_valid ? env->sel_hist : nullptr; }
+
 // The backward pass's launches: per checkpoint segment, last first, the
 // segment's start copied from its checkpoint, its steps recomputed, then the
 // adjoint of each of its steps in reverse.
@@ -1877,7 +1884,7 @@ static void issue_backward(gd_env* env, const float* obs_weight, float reward_we
     launch_adjoint(env, env->segS, env->segF, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
                    env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm,
-                   env->sel_hist ? env->sel_hist + (size_t)t0 * A * env->d.K : nullptr);
+                   rec_sel(env) ? rec_sel(env) + (size_t)t0 * A * env->d.K : nullptr);
   }
 }
 
@@ -1914,7 +1921,7 @@ static void issue_backward_pipelined(gd_env* env, const float* obs_weight, float
     launch_adjoint(env, b.S, b.F, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
                    env->rk_hist + (size_t)t0 * A, cap, t0 + len == T, t0 == 0 ? d_state0 : nullptr, nullptr,
-                   env->sel_hist ? env->sel_hist + (size_t)t0 * A * env->d.K : nullptr);
+                   rec_sel(env) ? rec_sel(env) + (size_t)t0 * A * env->d.K : nullptr);
     done_adj[(size_t)j] = event();
     cudaEventRecord(done_adj[(size_t)j], cap);
   }
@@ -1939,7 +1946,7 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
   uint32_t rw_bits;
   std::memcpy(&rw_bits, &reward_weight, sizeof(rw_bits));
   const void* key[7] = {obs_weight, d_ell, d_actions, d_state0, env->diff_actions, (const void*)(uintptr_t)rw_bits,
-                        nullptr};
+                        rec_sel(env)};
   bool same = env->bgraph && env->bg_steps == env->diff_steps;
   for (int k = 0; k < 7 && same; ++k) same = env->bg_key[k] == key[k];
   if (!same) {
@@ -2015,6 +2022,7 @@ gd_status gd_time_objective(gd_env* env, int32_t steps, const float* actions, co
   }
   env->diff_actions = actions;
   env->diff_steps = steps;
+  env->sel_valid = env->sel_hist != nullptr;
   return launch_check(env, "gd_time_objective");
 }
 

@@ -306,6 +306,55 @@ def test_graph_pair_equals_host_issued_launches():
     assert info.backward_graph_kernels == segs + T + (2 * segs if info.adjoint_split else T)
 
 
+def test_road_rebuild_between_objective_and_backward():
+    # The objective rollout records its road selections as positions in the
+    # world's road blocks, which the backward pass reads.  A retune between
+    # the two rebuilds the blocks (other cell sizes), so the backward pass
+    # must select again; it gives the same gradients, and so does the record
+    # of an objective rollout taken after the retune.
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.full(64, 24), np.full(64, 1500), 14)
+    ocfg = OracleConfig(k_road=48, n_partners=7, episode_len=12, term_collision=True, term_offroad=True)
+    T, A = 12, sc.num_agents
+    rng = np.random.default_rng(13)
+    a = torch.from_numpy(scenes.make_actions(T, A, 13)).cuda().contiguous()
+    wt = torch.from_numpy(rng.uniform(0, 1, ocfg.feat).astype(np.float32)).cuda()
+    ell = torch.empty(T, A, device="cuda")
+    # a 10 m road cell, which the tuner does not try, so that its final
+    # rebuild changes every block's layout
+    env = gd.Env(sc, **dict(_kw(ocfg), flags=_kw(ocfg)["flags"] | gd.GD_BATCHED), road_cell=10.0)
+
+    def objective():
+        gd.gd_reset(env.h)
+        gd.gd_rollout_objective(env.h, T, a, wt, 0.7, ell, env.obs)
+
+    def backward():
+        da = torch.full((T, A, 2), float("nan"), device="cuda")
+        ds = torch.full((A, 4), float("nan"), device="cuda")
+        gd.gd_rollout_backward(env.h, wt, 0.7, None, da, ds)
+        env.sync()
+        return da.cpu().numpy(), ds.cpu().numpy()
+
+    objective()
+    ref = backward()
+    objective()
+    # tuned from the initial state (the backward pass reads the objective's
+    # checkpoints, not the env's state): the split adjoint, which reads the
+    # records, and another cell size
+    gd.gd_reset(env.h)
+    gd.gd_autotune(env.h)
+    info = gd.gd_get_info(env.h)
+    assert abs(info.road_cell - 10.0) > 0.5 and info.adjoint_split == 1
+    retuned = backward()
+    objective()
+    again = backward()
+    env.close()
+    assert np.isfinite(ref[0]).all() and np.isfinite(ref[1]).all()
+    for got in (retuned, again):
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("form", [dict(adjoint_split=0, road_no_tile=0), dict(adjoint_split=0, road_no_tile=1)])
 def test_adjoint_forms_are_bit_identical(form):
     # the split adjoint (observer side over agents, then a thread per agent)
