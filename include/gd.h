@@ -89,7 +89,8 @@ typedef enum gd_status {
                                     of selecting again, else re-selects within the K-th distance) */
 #define GD_NONTRIVIAL_INIT 0x20u /* "all nontrivial" initialisation (Sec. 3.2 "Simulator sharp-edges"):
                                     agents within nontrivial_dist of their goal at the start are not
-                                    controlled (GD_FLAG_STATIC) */
+                                    controlled (GD_FLAG_STATIC); the observation keeps such parked
+                                    agents' road selections between steps (4 B x K x A) */
 
 /* per-agent status byte (gd_get_state / gd_set_state) */
 #define GD_FLAG_DONE 0x1u

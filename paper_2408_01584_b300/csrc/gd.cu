@@ -140,6 +140,7 @@ struct gd_env {
                                 // nullptr (no room: the backward pass re-selects)
   bool sel_valid = false;       // sel_hist holds the last objective rollout's selections in the current road
                                 // layout (block positions; a rebuilt road grid invalidates them)
+  unsigned road_epoch = 0;      // number of road layouts built so far (tags the parked agents' selections)
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
   int adj_notile = 0;           // 1: k_adjoint reads every road block from global memory
@@ -326,6 +327,8 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     int per_sm = 0;
     e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps>));
     if (e == cudaSuccess) e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps, true>));
+    if (e == cudaSuccess) e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps, false, true>));
+    if (e == cudaSuccess) e = allow_max_smem(reinterpret_cast<const void*>(k_observe_split<kSplitWarps, true, true>));
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_observe_split<kSplitWarps>, kSplitWarps * 32,
                                                         kSplitSmem);
@@ -478,6 +481,7 @@ static cudaError_t build_road(gd_env* env, float cell) {
   env->road_cell = cell;
   env->max_block = max_block;
   env->sel_valid = false;    // recorded selections name positions in the old blocks
+  env->d.road_epoch = ++env->road_epoch;   // and so do the parked agents' kept selections
   if ((e = shape_kernels(env, max_block)) != cudaSuccess) return e;
   drop_graphs(env);
   return cudaStreamSynchronize(env->stream);
@@ -719,6 +723,10 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(upload(env, &p_anc, anc.data(), (size_t)A));
     d.anchor = p_anc;
   }
+  // parked agents (the "all nontrivial" initialisation) keep their road
+  // selection between steps (K key low words each)
+  d.smemo = nullptr;
+  if ((cfg->flags & GD_NONTRIVIAL_INIT) && K > 0) GD_TRY(dev_alloc(env, &d.smemo, (size_t)A * K));
   GD_TRY(cudaMemsetAsync(d.err, 0, sizeof(unsigned), env->stream));
   GD_TRY(cudaMallocHost(&env->h_err, sizeof(unsigned)));
   d.agent_off = p_aoff; d.road_off = p_roff; d.agent_world = p_aw; d.state = p_state; d.init_state = p_init;
@@ -950,6 +958,22 @@ struct LaunchTimer {
 static void tbegin(LaunchTimer* tm, int k) { if (tm) tm->begin(k); }
 static void tend(LaunchTimer* tm) { if (tm) tm->end(); }
 
+// The split observation launch: the form that keeps the parked agents' road
+// selections between steps when the env has such agents (its own
+// instantiation, so that the other form's code is the same without them).
+extern "C++" {
+template <bool LOSS>
+static void launch_observe_split(gd_env* env, const DevEnv& dv, float* obs, int32_t* road_idx, int32_t* partner_idx,
+                                 unsigned* counters, const SplitLoss& loss, cudaStream_t stream) {
+  if (dv.smemo)
+    k_observe_split<kSplitWarps, LOSS, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+        dv, obs, road_idx, partner_idx, counters, loss);
+  else
+    k_observe_split<kSplitWarps, LOSS><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
+        dv, obs, road_idx, partner_idx, counters, loss);
+}
+}  // extern "C++"
+
 // Batched form: one persistent launch (its work counter was left at zero by the previous one).
 // With env->split, an observation without the objective is the step launch
 // (nothing observed) followed by k_observe_split over all agents.
@@ -974,11 +998,9 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
     const SplitLoss loss{obs_w, reward_w, ell, rk_out, sel_out};
     tbegin(tm, 2);
     if (ell)
-      k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
-          *dv, obs, road_idx, partner_idx, env->ocounter, loss);
+      launch_observe_split<true>(env, *dv, obs, road_idx, partner_idx, env->ocounter, loss, stream);
     else
-      k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
-          *dv, obs, road_idx, partner_idx, env->ocounter, loss);
+      launch_observe_split<false>(env, *dv, obs, road_idx, partner_idx, env->ocounter, loss, stream);
     tend(tm);
     return;
   }
@@ -1218,12 +1240,10 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
     if (ell) {
       const SplitLoss loss{obs_w, reward_w, ell + (size_t)t * A, env->rk_hist + (size_t)t * A,
                            env->sel_hist ? env->sel_hist + (size_t)t * A * env->d.K : nullptr};
-      k_observe_split<kSplitWarps, true><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(
-          dvo, orow, nullptr, nullptr, oc, loss);
+      launch_observe_split<true>(env, dvo, orow, nullptr, nullptr, oc, loss, stream);
     } else {
       const SplitLoss loss{nullptr, 0.f, nullptr, nullptr, nullptr};
-      k_observe_split<kSplitWarps><<<env->so_grid, kSplitWarps * 32, kSplitSmem, stream>>>(dvo, orow, nullptr, nullptr,
-                                                                                           oc, loss);
+      launch_observe_split<false>(env, dvo, orow, nullptr, nullptr, oc, loss, stream);
     }
     in = out;
   }

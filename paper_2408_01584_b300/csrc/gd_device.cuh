@@ -58,6 +58,8 @@ struct DevEnv {
   int W, A, N, K, P, F, T;
   float R, R2, goal_r, dt, vmax, cpen, opn, smooth_c, agent_cell;
   int topk;              // road top-K: 1 = bucket rank, 2 = bitonic sort when <= 256 points are in range
+  unsigned* smemo;       // [A][K] the last road selection (key low words) of each parked agent, or nullptr
+  unsigned road_epoch;   // layout number of the road blocks (a rebuild changes it): tags the memo in the anchor
   int dyn;               // 0: kinematic bicycle (App. B); 1: simplified invertible model (Sec. 3.2)
   uint32_t cflags;
   const int* agent_off;

@@ -509,17 +509,23 @@ __device__ __forceinline__ float write_done_row(const DevEnv& e, uint8_t f, floa
 
 // Recorded selection (objective rollouts): a slot past the points in range.
 constexpr uint16_t OBS_SEL_NONE = 0xffff;
+// A parked agent's kept selection: a slot past the points in range (no key
+// low word is all ones: a block position is below GD_MAX_ROAD_PER_WORLD).
+constexpr unsigned OBS_MEMO_NONE = 0xffffffffu;
 static_assert(GD_MAX_ROAD_PER_WORLD <= 0xffff, "block positions must fit a recorded slot below OBS_SEL_NONE");
 
 // One full observation row of local agent li of the world in view v.
 // With LOSS, returns (to every lane) w . row for the weight row w (F
 // floats); otherwise returns 0.
-template <bool LOSS>
+// MEMO: the form for envs with parked agents, which keeps their road
+// selections (memo_row) between steps.
+template <bool LOSS, bool MEMO = false>
 __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView& v, int li, float* __restrict__ obs_row,
                                                int32_t* __restrict__ ridx, int32_t* __restrict__ pidx,
                                                ObsWarpSmem& sm, int lane, float4* anchor,
                                                const float* __restrict__ w = nullptr, float* rk_slot = nullptr,
-                                               const float4* own = nullptr, uint16_t* sel_slot = nullptr) {
+                                               const float4* own = nullptr, uint16_t* sel_slot = nullptr,
+                                               unsigned* memo_row = nullptr) {
   float4* row = reinterpret_cast<float4*>(obs_row);
   const uint8_t f = v.flags[li];
   const float fc = (f & GD_FLAG_COLLIDED) ? 1.f : 0.f, fo = (f & GD_FLAG_OFFROAD) ? 1.f : 0.f,
@@ -564,15 +570,34 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
         Rs2 = r * r;
       }
     }
-    int nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
-    if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+    // A parked agent (GD_FLAG_STATIC) keeps its last selection in memo_row,
+    // tagged in its anchor by the road layout: while it is where the anchor
+    // says (bit for bit) and the layout is the same, the road and the agent
+    // have not moved, so the selection is the same and is read back.
+    const bool memo = MEMO && memo_row && anchor && (f & GD_FLAG_STATIC);
+    int nroad = 0;
+    if (MEMO && memo && __float_as_uint(an.w) == e.road_epoch && __float_as_uint(an.x) == __float_as_uint(st.x) &&
+        __float_as_uint(an.y) == __float_as_uint(st.y)) {
+      for (int r0 = 0; r0 < e.K; r0 += WARP) {
+        const int r = r0 + lane;
+        const unsigned wv = r < e.K ? memo_row[r] : OBS_MEMO_NONE;
+        if (r < e.K) sm.sel[r] = wv;
+        nroad += __popc(__ballot_sync(0xffffffffu, wv != OBS_MEMO_NONE));
+      }
+      __syncwarp();
+    } else {
+      nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
+      if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
+      if (MEMO && memo)
+        for (int r = lane; r < e.K; r += WARP) memo_row[r] = r < nroad ? sm.sel[r] : OBS_MEMO_NONE;
+    }
     if ((anchor || rk_slot) && lane == 0) {
       float rk = __int_as_float(0x7f800000);     // +inf: fewer than K in range
       if (nroad == e.K && e.K > 0) {
         const float2 q = v.xy[sel_pos(sm.sel[e.K - 1])];
         rk = sqrtf(dist2(q.x - st.x, q.y - st.y));
       }
-      if (anchor) *anchor = make_float4(st.x, st.y, rk, 0.f);
+      if (anchor) *anchor = make_float4(st.x, st.y, rk, (MEMO && memo) ? __uint_as_float(e.road_epoch) : 0.f);
       if (rk_slot) *rk_slot = rk;
     }
     // the selection itself, for the backward pass: block positions in rank
@@ -632,7 +657,7 @@ __device__ __forceinline__ bool offroad_from_block(const WorldView& v, float cx,
 // world's agents and road block through L1/L2).
 // With LOSS, returns (to every lane) wrow . row for the weight row wrow,
 // and writes the agent's K-th road distance to rk_slot if given.
-template <bool LOSS = false>
+template <bool LOSS = false, bool MEMO = false>
 __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* __restrict__ obs,
                                                 int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
                                                 ObsWarpSmem& sm, int lane, const float* __restrict__ wrow = nullptr,
@@ -649,9 +674,10 @@ __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* _
   v.n = e.agent_off[w + 1] - a0;
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
-  return observe_agent<LOSS>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
+  return observe_agent<LOSS, MEMO>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
                              partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
-                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own, sel_slot);
+                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own, sel_slot,
+                             MEMO && e.smemo ? e.smemo + (size_t)i * e.K : nullptr);
 }
 
 // Per-stage form: one warp per agent over the whole batch.  Dynamic shared
@@ -690,7 +716,7 @@ struct SplitLoss {
 // agents, and its road block in L1/L2, together.  Registers are capped for
 // 32 warps per SM (its shared memory allows them).
 constexpr unsigned OBS_STRIPES = 32;
-template <int WARPS, bool LOSS = false>
+template <int WARPS, bool LOSS = false, bool MEMO = false>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv e, float* __restrict__ obs,
                                                                            int32_t* __restrict__ road_idx,
                                                                            int32_t* __restrict__ partner_idx,
@@ -718,7 +744,7 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
     if (f & GD_FLAG_DONE) {
       dot = write_done_row<LOSS>(e, f, orow, ridx, pidx, loss.w, lane);
     } else {
-      dot = observe_global<LOSS>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
+      dot = observe_global<LOSS, MEMO>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
                                  LOSS && loss.rk ? loss.rk + i : nullptr,
                                  LOSS && loss.sel ? loss.sel + (size_t)i * e.K : nullptr);
     }

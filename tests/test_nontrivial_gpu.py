@@ -96,3 +96,35 @@ def test_episode_stats_count_the_flags():
         np.testing.assert_array_equal(tot.cpu().numpy(), exp.sum(0))
     assert exp[:, 0].sum() > exp[:, 1].sum()        # parked agents are in the scene but not controlled
     env.close()
+
+
+def test_parked_selections_after_a_retune():
+    # The split observation keeps each parked agent's road selection between
+    # steps, tagged in its anchor with the road layout.  A retune rebuilds
+    # the road blocks (another cell size than the 10 m the env starts with)
+    # and restores the anchors it saved before: the kept selections name
+    # positions of the old blocks and must not be read.  Rollouts before and
+    # after the retune equal the per-stage form's, bit for bit.
+    from paper_2408_01584_b300 import gd
+    sc = scenes.workload_scene("nontrivial_1024x64", 4, worlds=64)
+    ocfg = workload_config("nontrivial_1024x64", nontrivial_init=True)
+    T = 12
+    acts = torch.from_numpy(scenes.make_actions(T, sc.num_agents, 4)).cuda().contiguous()
+
+    def rollout(env):
+        gd.gd_reset(env.h)
+        obs = torch.empty(T, sc.num_agents, env.F, device="cuda")
+        gd.gd_rollout(env.h, T, acts, obs, True, None, None)
+        env.sync()
+        return obs.cpu()
+
+    plain = gd.Env(sc, **gd_kwargs(ocfg, flags=_flags(ocfg, False)))
+    ref = rollout(plain)
+    plain.close()
+    env = gd.Env(sc, **gd_kwargs(ocfg, flags=_flags(ocfg, True)), road_cell=10.0, obs_split=1)
+    assert torch.equal(rollout(env), ref)
+    gd.gd_autotune(env.h)
+    info = gd.gd_get_info(env.h)
+    assert abs(info.road_cell - 10.0) > 0.5 and info.obs_split == 1
+    assert torch.equal(rollout(env), ref)
+    env.close()
