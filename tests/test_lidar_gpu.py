@@ -74,7 +74,8 @@ def _teacher_forced(sc, form, n, fov, head_mode, steps, seed):
 
 @pytest.mark.parametrize("form", ["plain", "fused"])
 @pytest.mark.parametrize("n,fov,head", [(3000, 2 * math.pi, False), (1000, 2 * math.pi / 3, True),
-                                        (7, 2 * math.pi, False), (257, 0.5, True)])
+                                        (7, 2 * math.pi, False), (257, 0.5, True),
+                                        (8192, 2 * math.pi, False)])      # GD_MAX_LIDAR_RAYS: fewest warps per CTA
 def test_lidar_matches_oracle_small_ragged(form, n, fov, head):
     sc = small_scene(seed=11)
     fragile, seen = _teacher_forced(sc, form, n, fov, head, steps=3, seed=11)
