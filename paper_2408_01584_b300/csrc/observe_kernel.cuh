@@ -576,7 +576,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     // have not moved, so the selection is the same and is read back.
     const bool memo = MEMO && memo_row && anchor && (f & GD_FLAG_STATIC);
     int nroad = 0;
-    if (MEMO && memo && __float_as_uint(an.w) == e.road_epoch && __float_as_uint(an.x) == __float_as_uint(st.x) &&
+    if (memo && __float_as_uint(an.w) == e.road_epoch && __float_as_uint(an.x) == __float_as_uint(st.x) &&
         __float_as_uint(an.y) == __float_as_uint(st.y)) {
       for (int r0 = 0; r0 < e.K; r0 += WARP) {
         const int r = r0 + lane;
@@ -588,7 +588,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
     } else {
       nroad = select_road(v, e.K, Rs, Rs2, st.x, st.y, sm, lane, e.topk);
       if (nroad < e.K && Rs < e.R) nroad = select_road(v, e.K, e.R, e.R2, st.x, st.y, sm, lane, e.topk);
-      if (MEMO && memo)
+      if (memo)
         for (int r = lane; r < e.K; r += WARP) memo_row[r] = r < nroad ? sm.sel[r] : OBS_MEMO_NONE;
     }
     if ((anchor || rk_slot) && lane == 0) {
@@ -597,7 +597,7 @@ __device__ __forceinline__ float observe_agent(const DevEnv& e, const WorldView&
         const float2 q = v.xy[sel_pos(sm.sel[e.K - 1])];
         rk = sqrtf(dist2(q.x - st.x, q.y - st.y));
       }
-      if (anchor) *anchor = make_float4(st.x, st.y, rk, (MEMO && memo) ? __uint_as_float(e.road_epoch) : 0.f);
+      if (anchor) *anchor = make_float4(st.x, st.y, rk, memo ? __uint_as_float(e.road_epoch) : 0.f);
       if (rk_slot) *rk_slot = rk;
     }
     // the selection itself, for the backward pass: block positions in rank
@@ -656,7 +656,8 @@ __device__ __forceinline__ bool offroad_from_block(const WorldView& v, float cx,
 // Observation row of agent i with everything read from global memory (the
 // world's agents and road block through L1/L2).
 // With LOSS, returns (to every lane) wrow . row for the weight row wrow,
-// and writes the agent's K-th road distance to rk_slot if given.
+// and writes the agent's K-th road distance to rk_slot and its road
+// selection to sel_slot if given.  MEMO as in observe_agent.
 template <bool LOSS = false, bool MEMO = false>
 __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* __restrict__ obs,
                                                 int32_t* __restrict__ road_idx, int32_t* __restrict__ partner_idx,
@@ -674,10 +675,11 @@ __device__ __forceinline__ float observe_global(const DevEnv& e, int i, float* _
   v.n = e.agent_off[w + 1] - a0;
   road_block(e.arena + (size_t)e.arena_off[w] * 16, e.road_off[w + 1] - e.road_off[w], v);
   v.g = e.rgrid[w];
-  return observe_agent<LOSS, MEMO>(e, v, i - a0, obs + (size_t)i * e.F, road_idx ? road_idx + (size_t)i * e.K : nullptr,
-                             partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
-                             e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own, sel_slot,
-                             MEMO && e.smemo ? e.smemo + (size_t)i * e.K : nullptr);
+  return observe_agent<LOSS, MEMO>(e, v, i - a0, obs + (size_t)i * e.F,
+                                   road_idx ? road_idx + (size_t)i * e.K : nullptr,
+                                   partner_idx ? partner_idx + (size_t)i * e.P : nullptr, sm, lane,
+                                   e.anchor ? e.anchor + i : nullptr, wrow, rk_slot, own, sel_slot,
+                                   MEMO && e.smemo ? e.smemo + (size_t)i * e.K : nullptr);
 }
 
 // Per-stage form: one warp per agent over the whole batch.  Dynamic shared
@@ -745,8 +747,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv
       dot = write_done_row<LOSS>(e, f, orow, ridx, pidx, loss.w, lane);
     } else {
       dot = observe_global<LOSS, MEMO>(e, (int)i, obs, road_idx, partner_idx, sm, lane, loss.w,
-                                 LOSS && loss.rk ? loss.rk + i : nullptr,
-                                 LOSS && loss.sel ? loss.sel + (size_t)i * e.K : nullptr);
+                                       LOSS && loss.rk ? loss.rk + i : nullptr,
+                                       LOSS && loss.sel ? loss.sel + (size_t)i * e.K : nullptr);
     }
     if (LOSS && lane == 0) loss.ell[i] = fmaf(loss.reward_w, loss.ell[i], dot);
   }
