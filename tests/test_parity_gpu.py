@@ -148,6 +148,29 @@ def test_full_size_plain_1024x64_sampled_steps():
     print("exceptions:", len(ex))
 
 
+def test_full_size_uneven_4096_sampled_steps():
+    # the uneven batch at full size (4,096 worlds, 1 to 128 agents and 500 to
+    # 20,000 road points each) in the tuned batched form the bench times:
+    # every agent of the worlds with the most agents and with the most road
+    # points, and 4,096 agents at random, over three teacher-forced steps
+    from paper_2408_01584_b300 import gd
+    from paper_2408_01584_b300.gd import Env
+    sc = scenes.workload_scene("uneven_4096", 0)
+    ocfg = workload_config("uneven_4096")
+    acts = scenes.make_actions(3, sc.num_agents, 0)
+    env = Env(sc, **gd_kwargs(ocfg, flags=gd_kwargs(ocfg)["flags"] | gd.GD_BATCHED))
+    gd.gd_autotune(env.h)
+    apw, rpw = np.diff(sc.agent_off), np.diff(sc.road_off)
+    worlds = np.unique(np.concatenate([np.argsort(apw)[-8:], np.argsort(rpw)[-8:]]))
+    assert apw[worlds].max() == 128 and rpw[worlds].max() > 19000
+    big = np.concatenate([np.arange(sc.agent_off[w], sc.agent_off[w + 1]) for w in worlds])
+    rng = np.random.default_rng(0)
+    agents = np.unique(np.concatenate([big, rng.choice(sc.num_agents, 4096, replace=False)]))
+    _, ex = teacher_forced(sc, ocfg, 3, acts, obs_every=1, obs_agents=agents, env=env)
+    env.close()
+    print("exceptions:", len(ex))
+
+
 def _long_box_scene(seed):
     # one world: horizontal road edges 9 m apart and two vertical ones, each
     # its own polyline, 3 m between points; boxes 5 to 45 m long at headings
