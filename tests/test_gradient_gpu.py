@@ -306,6 +306,28 @@ def test_graph_pair_equals_host_issued_launches():
     assert info.backward_graph_kernels == segs + T + (2 * segs if info.adjoint_split else T)
 
 
+def test_parked_agents_graph_pair_equals_host_issued_launches():
+    # With parked agents (the "all nontrivial" initialisation) the batched
+    # objective keeps their road selections between steps (and records them
+    # for the backward pass); the host-issued plain form selects every step.
+    # Terms and gradients are bit-identical.
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([6, 9, 17, 12]), np.array([700, 800, 1500, 900]), 21, parked_frac=0.4)
+    ocfg = OracleConfig(k_road=48, n_partners=7, episode_len=23, term_collision=True, term_offroad=True,
+                        nontrivial_init=True)
+    T = 23
+    acts = scenes.make_actions(T, sc.num_agents, 21)
+    rng = np.random.default_rng(21)
+    w = rng.uniform(0, 1, ocfg.feat)
+    host, _ = _fwd_bwd(sc, ocfg, acts, w, 0.7)
+    graph, info = _fwd_bwd(sc, ocfg, acts, w, 0.7, reps=2, flags=_kw(ocfg)["flags"] | gd.GD_BATCHED, obs_split=1)
+    assert info.obs_split == 1
+    for rep in graph:
+        for a, b in zip(host[0], rep):
+            np.testing.assert_array_equal(a, b)
+    assert np.isfinite(host[0][1]).all()
+
+
 def test_road_rebuild_between_objective_and_backward():
     # The objective rollout records its road selections as positions in the
     # world's road blocks, which the backward pass reads.  A retune between
