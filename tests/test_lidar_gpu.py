@@ -50,8 +50,8 @@ def _env(sc, form, n, fov, **kw):
     return gd.Env(sc, lidar_rays=n, lidar_fov=fov, flags=flags, **kw)
 
 
-def _teacher_forced(sc, form, n, fov, head_mode, steps, seed):
-    env = _env(sc, form, n, fov)
+def _teacher_forced(sc, form, n, fov, head_mode, steps, seed, **kw):
+    env = _env(sc, form, n, fov, **kw)
     orc = Oracle(sc, OracleConfig(term_collision=True, term_offroad=True))
     acts = scenes.make_actions(steps, sc.num_agents, seed)
     rng = np.random.default_rng(seed)
@@ -125,6 +125,19 @@ def test_lidar_unaligned_output_and_null_class_match_the_vector_path():
     env.sync()
     assert torch.equal(d_al, d_un)
     env.close()
+
+
+@pytest.mark.parametrize("form", ["plain", "fused"])
+def test_lidar_with_parked_agents_and_mixed_types(form):
+    # the "all nontrivial" initialisation parks agents at their goals: they
+    # stay in the scene (boxes every other agent's rays can hit) but never
+    # move; pedestrians and cyclists among them
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([8, 14, 20]), np.array([900, 1200, 1600]), 31, parked_frac=0.5,
+                           type_mix=(0.7, 0.15, 0.15))
+    fragile, seen = _teacher_forced(sc, form, 1000, 2 * math.pi, False, steps=3, seed=31,
+                                    flags=FLAGS_TERM | gd.GD_NONTRIVIAL_INIT)
+    assert seen[1] > 0 and seen[2] > 0           # rays on agents and on road edges
 
 
 def test_lidar_fused_equals_per_stage_and_graph_equals_step_loop():
