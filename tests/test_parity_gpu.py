@@ -171,6 +171,24 @@ def test_full_size_uneven_4096_sampled_steps():
     print("exceptions:", len(ex))
 
 
+@pytest.mark.parametrize("batched", [False, True])
+def test_largest_world(batched):
+    # one world at both per-world limits, 128 agents and 32,767 road points:
+    # block positions up to 32,766 in the keys' 16-bit position field, a road
+    # block (393 KB) too large for a shared-memory tile
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([128]), np.array([32767]), 41)
+    ocfg = OracleConfig(k_road=200, n_partners=63, episode_len=91, term_collision=True, term_offroad=True)
+    acts = scenes.make_actions(3, sc.num_agents, 41)
+    over = dict(flags=gd_kwargs(ocfg)["flags"] | (gd.GD_BATCHED if batched else 0))
+    env, ex = teacher_forced(sc, ocfg, 3, acts, obs_every=1, gd_over=over)
+    if batched:
+        gd.gd_autotune(env.h)
+        env, ex2 = teacher_forced(sc, ocfg, 2, acts, obs_every=1, env=env)
+    env.close()
+    print("exceptions:", len(ex))
+
+
 def _long_box_scene(seed):
     # one world: horizontal road edges 9 m apart and two vertical ones, each
     # its own polyline, 3 m between points; boxes 5 to 45 m long at headings
