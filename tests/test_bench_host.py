@@ -56,3 +56,17 @@ def test_measured_traffic_keyed_on_sources_and_shape(tmp_path, monkeypatch):
     assert bench._measured_traffic("w", "k_observe_split", dict(shape, road_cell_m=12.0)) is None
     monkeypatch.setattr(bench, "_kernel_source_hash", lambda k: "other")
     assert bench._measured_traffic("w", "k_observe_split", shape) is None
+
+
+def test_observation_traffic_record_is_current():
+    # the bench's roofline line carries the DRAM traffic of the observation
+    # launch from the committed ncu capture only while that capture was taken
+    # of the current kernel sources at the tuned shape; a kernel edit must
+    # come with a new capture (profiles/k_observe_split_plain_1024x64.*)
+    import json
+    import os
+    path = os.path.join(bench.ROOT, "profiles", "k_observe_split_plain_1024x64.traffic.json")
+    rec = json.load(open(path))
+    assert rec["source_hash"] == bench._kernel_source_hash("k_observe_split")
+    got = bench._measured_traffic("plain_1024x64", "k_observe_split", rec["shape"])
+    assert got == rec["dram_bytes_per_launch"] > 0
