@@ -69,7 +69,7 @@ struct AdjArgs {
   unsigned* ocounter;       // [ADJ_STRIPES] task claims of k_adj_observer; k_adj_dynamics leaves them at zero
 };
 
-constexpr unsigned ADJ_STRIPES = 32;
+constexpr unsigned ADJ_STRIPES = 256;
 
 struct AdjAgents {
   float4 st[GD_MAX_AGENTS_PER_WORLD];   // post-step state
@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv 
 // and the dynamics adjoint.  Block 0 leaves part 1's claim counters at zero
 // for the next part-1 launch.
 __global__ void __launch_bounds__(64) k_adj_dynamics(DevEnv e, AdjArgs a) {
-  if (blockIdx.x == 0 && threadIdx.x < ADJ_STRIPES) a.ocounter[threadIdx.x] = 0u;
+  if (blockIdx.x == 0)
+    for (unsigned c = threadIdx.x; c < ADJ_STRIPES; c += blockDim.x) a.ocounter[c] = 0u;
   const int ig = blockIdx.x * blockDim.x + threadIdx.x;
   if (ig >= e.A) return;
   const float4 sc = e.stat[ig];

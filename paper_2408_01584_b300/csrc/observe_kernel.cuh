@@ -717,7 +717,7 @@ struct SplitLoss {
 // moves straight on; agents go out in index order, which keeps a world's
 // agents, and its road block in L1/L2, together.  Registers are capped for
 // 32 warps per SM (its shared memory allows them).
-constexpr unsigned OBS_STRIPES = 32;
+constexpr unsigned OBS_STRIPES = 128;
 template <int WARPS, bool LOSS = false, bool MEMO = false>
 __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_observe_split(DevEnv e, float* __restrict__ obs,
                                                                            int32_t* __restrict__ road_idx,

@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
     s_abort = 0;
   }
   // the counters of the observation launch that follows (split forms)
-  if (a.clear && blockIdx.x == 0 && tid < a.clear_n) a.clear[tid] = 0u;
+  if (a.clear && blockIdx.x == 0)
+    for (int i = tid; i < a.clear_n; i += WARPS * 32) a.clear[i] = 0u;
   __syncthreads();
   unsigned phase = 0;
   const bool observe = LIDAR ? a.lidar.depth != nullptr : a.obs != nullptr;
