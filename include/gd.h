@@ -513,7 +513,9 @@ gd_status gd_decimate_scene(const gd_scene_batch* scene, float area_tol, void* c
  * the driver then takes the array's memory (about 1.2 MB): make the first
  * call at initialisation, before a pool allocator reserves the GPU's
  * memory.  No later call allocates.  Each call copies agent_off from host
- * memory to the array on the given stream.  Every call reuses the same
+ * memory to the array on the given stream, so a call is not capturable: on
+ * a stream that is being captured into a CUDA graph it returns
+ * GD_ERR_INVALID_ARG and enqueues nothing.  Every call reuses the same
  * array (nothing in it needs to start at zero: each call writes what it
  * reads), so calls that overlap on the GPU, e.g. on two streams, race. */
 #define GD_NOALLOC_MAX_AGENTS 262144

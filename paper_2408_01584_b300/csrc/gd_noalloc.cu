@@ -187,10 +187,18 @@ extern "C" gd_status gd_collide_noalloc(int32_t num_worlds, const int32_t* agent
   if (A > 0 && (!state || !extent || !collided)) return na_fail(GD_ERR_INVALID_ARG, "state, extent and collided must not be NULL");
   if (((uintptr_t)state & 15u) || ((uintptr_t)extent & 7u))
     return na_fail(GD_ERR_INVALID_ARG, "state must be 16-byte and extent 8-byte aligned");
-  uint32_t* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
-  if (e != cudaSuccess) return na_fail(GD_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // a graph would keep the host address of agent_off and read it again at
+  // every replay, after the caller may have freed or changed it
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &capture);
+  if (e != cudaSuccess) return na_fail(GD_ERR_CUDA, std::string("capture status: ") + cudaGetErrorString(e));
+  if (capture != cudaStreamCaptureStatusNone)
+    return na_fail(GD_ERR_INVALID_ARG, "the stream is being captured into a CUDA graph; calls are not capturable "
+                                       "(each copies agent_off from host memory)");
+  uint32_t* scratch = nullptr;
+  e = scratch_for_current_device(&scratch);
+  if (e != cudaSuccess) return na_fail(GD_ERR_CUDA, std::string("scratch address: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(scratch + kOffOff, agent_off, sizeof(int32_t) * (num_worlds + 1), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return na_fail(GD_ERR_CUDA, std::string("offset copy: ") + cudaGetErrorString(e));
   if (A == 0) return GD_OK;

@@ -137,3 +137,32 @@ def test_binding_refuses_wrong_sized_buffers():
         args.update(b)
         with pytest.raises(ValueError):
             gd.gd_collide_noalloc(off, args["state"], args["extent"], args["active"], 5.0, args["collided"])
+
+
+def test_refuses_a_capturing_stream():
+    # a captured call would keep agent_off's host address and read it again
+    # at every replay: the entry point refuses and enqueues nothing, and the
+    # capture itself stays valid
+    from paper_2408_01584_b300 import gd
+    off = np.array([0, 3, 4], np.int32)
+    state = torch.zeros(4, 4, device="cuda")
+    extent = torch.ones(4, 2, device="cuda")
+    out = torch.full((4,), 7, dtype=torch.uint8, device="cuda")
+    x = torch.zeros(1, device="cuda")
+    gd.gd_collide_noalloc(off, state, extent, None, 5.0, out)      # first call before any capture
+    torch.cuda.synchronize()
+    out.fill_(7)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        x.add_(1.0)
+        with pytest.raises(gd.GdError) as err:
+            gd.gd_collide_noalloc(off, state, extent, None, 5.0, out, side.cuda_stream)
+        graph.capture_end()
+    assert err.value.status == 1 and "captured" in str(err.value)      # GD_ERR_INVALID_ARG
+    graph.replay()
+    torch.cuda.synchronize()
+    assert x.item() == 1.0
+    assert (out.cpu().numpy() == 7).all()
