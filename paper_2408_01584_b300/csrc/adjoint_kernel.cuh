@@ -415,12 +415,15 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_adj_observer(DevEnv 
   static_assert(GD_MAX_AGENTS_PER_WORLD == 4 * WARP, "a slot row is one 32-bit word per lane");
   const unsigned c = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) % ADJ_STRIPES;
   const unsigned tasks = (unsigned)a.steps * (unsigned)e.A;
+  // the next task is claimed as soon as the current one is known, so the
+  // claim's round trip overlaps the task's loads
+  unsigned kn = 0;
+  if (lane == 0) kn = atomicAdd(a.ocounter + c, 1u);
   for (;;) {
-    unsigned kk = 0;
-    if (lane == 0) kk = atomicAdd(a.ocounter + c, 1u);
-    kk = __shfl_sync(0xffffffffu, kk, 0);
+    const unsigned kk = __shfl_sync(0xffffffffu, kn, 0);
     const unsigned q = c + ADJ_STRIPES * kk;
     if (q >= tasks) break;
+    if (lane == 0) kn = atomicAdd(a.ocounter + c, 1u);
     const int k = (int)(q / (unsigned)e.A), i = (int)(q - (unsigned)k * (unsigned)e.A);
     const size_t ik = (size_t)k * e.A + i;
     const float4* post = a.S + (size_t)(k + 1) * e.A;
