@@ -43,6 +43,7 @@ constexpr int kTuneSteps = 4;     // consecutive steps timed per tuner window (a
 constexpr float kTuneTrialMs = 4.f;     // a trial's windows together last about this long (longer windows for
                                        // small batches)
 constexpr int kTunePhases = 3;    // points of an episode a tuner trial is timed at
+constexpr float kTuneCtaMargin = 0.03f;  // a step CTA of twice the warps must time this much faster to win
 
 // Split form's observation kernel: CTA size and shared memory.
 constexpr int kSplitWarps = 8;
@@ -2196,6 +2197,12 @@ gd_status gd_autotune(gd_env* env) {
           e = time_phases(
               [&] { launch_world(env, act, nullptr, nullptr, nullptr, env->obs_scratch, nullptr, nullptr, 1); }, ms);
           if (e != cudaSuccess) break;
+          // the trials issue the launches from the host; in the overlapped
+          // rollout the step launch of t + 1 shares the SMs with the tail of
+          // observation t, where a larger step CTA finds room later: near
+          // ties go to the smaller CTA (a larger one must win by
+          // kTuneCtaMargin per doubling of its warps)
+          ms *= 1.f + kTuneCtaMargin * (float)(wp == 4 ? 0 : (wp == 8 ? 1 : 2));
           if (ms < best_ms) {
             best_ms = ms;
             best_cell = cell;
