@@ -335,6 +335,9 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
                                                         kSplitSmem);
     if (e != cudaSuccess) return e;
     env->so_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (env->A + kSplitWarps - 1) / kSplitWarps));
+    // warp g draws from claim counter g mod OBS_STRIPES: every counter that
+    // holds an agent needs a warp
+    env->so_grid = std::max(env->so_grid, (std::min(env->A, (int)OBS_STRIPES) + kSplitWarps - 1) / kSplitWarps);
   }
   if (env->lidar_n > 0) {
     // the tile shrinks first; if even a 16-byte tile does not fit, fewer warps
@@ -368,6 +371,9 @@ static cudaError_t shape_kernels(gd_env* env, size_t max_block) {
     if (e != cudaSuccess) return e;
     env->ao_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm,
                                         (env->C * env->A + kAdjObsWarps - 1) / kAdjObsWarps));
+    // every claim counter that holds a task needs a warp (warp g draws from
+    // counter g mod ADJ_STRIPES)
+    env->ao_grid = std::max(env->ao_grid, (std::min(env->C * env->A, (int)ADJ_STRIPES) + kAdjObsWarps - 1) / kAdjObsWarps);
   }
   return cudaSuccess;
 }
@@ -837,6 +843,8 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
     GD_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lidar_group<G>, groups * G * 32,
                                                          lidar_groups_smem(G, groups, n)));
     env->lo_grid = std::max(1, std::min(std::max(per_sm, 1) * nsm, (A + groups - 1) / groups));
+    // every claim counter that holds an agent needs a warp group
+    env->lo_grid = std::max(env->lo_grid, (std::min(A, (int)LIDAR_STRIPES) + groups - 1) / groups);
   }
   GD_TRY(build_road(env, rcell));
   GD_TRY(cudaStreamSynchronize(env->stream));
