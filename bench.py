@@ -543,8 +543,15 @@ def bench_fwdbwd(workload, steps, warmup, dev, stream, flush, seed=0, road_world
                                               (4.0 * F + 70.0 + 8 + road) * A, hbm))
                 kern.append(kernel_record("k_copy_snapshot (segment start)", n_b[0], ms_b[0], SNAPSHOT_AGENT_BYTES * A,
                                           hbm))
-                kern.append(kernel_record("k_world (recomputed step, out of place)", n_b[1], ms_b[1],
-                                          STEP_AGENT_BYTES * A, hbm))
+                if info.adjoint_recompute:
+                    kern.append(kernel_record(
+                        "k_recompute (a segment's states from the forward's recorded decisions)", n_b[1], ms_b[1],
+                        seg(8 + 1 + 16 + 1, n_b[1]) + 17 * A, hbm,
+                        "per agent-step: reads the action and the recorded flags, writes state and flags; the "
+                        "segment's first state and flags once"))
+                else:
+                    kern.append(kernel_record("k_world (recomputed step, out of place)", n_b[1], ms_b[1],
+                                              STEP_AGENT_BYTES * A, hbm))
                 if info.adjoint_split:
                     kern.append(kernel_record(
                         "k_adj_observer (a segment's recorded selections, observer-side gradients, slot rows)",

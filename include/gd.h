@@ -160,6 +160,13 @@ typedef struct gd_config {
                                 observer side over agents (no per-world barriers) then a thread per
                                 agent for the partner side and the dynamics; 0 = one fused launch over
                                 worlds.  Both give bit-identical gradients. */
+  int32_t adjoint_recompute; /* states of a checkpoint segment recomputed by the backward pass
+                                (GD_DIFFERENTIABLE): 1 (default) = one thread-per-agent launch per
+                                segment from the objective rollout's record of its decisions (each
+                                step's post-step flags, A bytes per step of episode_len, allocated
+                                at create; without room for it, as 0);
+                                0 = the step kernel, one launch per step.  Both give bit-identical
+                                states, so bit-identical gradients. */
 } gd_config;
 
 typedef struct gd_scene_batch {
@@ -198,6 +205,9 @@ typedef struct gd_info {
                                                               kernel launches, other nodes (copies, memsets);
                                                               0 while none is captured */
   int32_t backward_graph_kernels, backward_graph_other;    /* the same for gd_rollout_backward */
+  int32_t adjoint_recompute;                                /* 1: the backward pass recomputes a segment in one
+                                                              launch from the recorded decisions; 0: the step
+                                                              kernel per step (see gd_config) */
 } gd_info;
 
 typedef struct gd_env gd_env;
@@ -370,7 +380,9 @@ gd_status gd_rollout_backward(gd_env* env, const float* obs_weight, float reward
  * ms[k] holds the total milliseconds and launches[k] the number of launches
  * of kind k (GD_BWD_KINDS entries each, host memory):
  *   0 checkpoint copies (k_copy_snapshot), one per segment;
- *   1 recomputed steps (the step kernel, out of place), one per step;
+ *   1 recomputed states: one k_recompute launch per segment from the
+ *     objective rollout's recorded decisions (gd_info.adjoint_recompute = 1),
+ *     else the step kernel, out of place, one per step;
  *   2 the adjoint's observer side (split form: one launch per checkpoint
  *     segment, all its steps) or the whole fused adjoint (one per step);
  *   3 the split adjoint's per-agent part (partner side and dynamics of all

@@ -141,6 +141,9 @@ struct gd_env {
                                 // nullptr (no room: the backward pass re-selects)
   bool sel_valid = false;       // sel_hist holds the last objective rollout's selections in the current road
                                 // layout (block positions; a rebuilt road grid invalidates them)
+  uint8_t* fl_hist = nullptr;   // [episode_len][A] post-step flags of each objective step, or nullptr (no room,
+                                // or adjoint_recompute = 0: the backward pass recomputes with the step kernel)
+  bool rec_valid = false;       // fl_hist holds the last objective rollout's decisions
   unsigned road_epoch = 0;      // number of road layouts built so far (tags the parked agents' selections)
   float* obs_scratch = nullptr; // [A,F] observation rows when the caller passes none
   int adj_tile = 0;
@@ -522,6 +525,7 @@ void gd_default_config(gd_config* c) {
   c->nontrivial_dist = 2.f;
   c->obs_split = 1;
   c->adjoint_split = 1;
+  c->adjoint_recompute = 1;
 }
 
 const char* gd_last_error(const gd_env* env) { return env ? env->err.c_str() : g_create_error.c_str(); }
@@ -560,6 +564,8 @@ static gd_status validate(const gd_config* c, const gd_scene_batch* s) {
   if (c->obs_split != 0 && c->obs_split != 1) return fail(nullptr, GD_ERR_INVALID_ARG, "obs_split must be 0 or 1");
   if (c->adjoint_split != 0 && c->adjoint_split != 1)
     return fail(nullptr, GD_ERR_INVALID_ARG, "adjoint_split must be 0 or 1");
+  if (c->adjoint_recompute != 0 && c->adjoint_recompute != 1)
+    return fail(nullptr, GD_ERR_INVALID_ARG, "adjoint_recompute must be 0 or 1");
   if (c->lidar_rays < 0 || c->lidar_rays > GD_MAX_LIDAR_RAYS)
     return fail(nullptr, GD_ERR_CAPACITY, "lidar_rays outside 0..GD_MAX_LIDAR_RAYS");
   if (!(c->lidar_fov >= 1e-3f) || !(c->lidar_fov <= 6.2831855f))
@@ -802,6 +808,15 @@ gd_status gd_create(const gd_config* cfg, const gd_scene_batch* s, void* cuda_st
         env->sel_hist = nullptr;
       }
     }
+    // the objective rollout's decisions (post-step flags), so that the
+    // backward pass recomputes a segment's states in one launch instead of a
+    // step launch per step; without room for them it runs the steps
+    if (A > 0 && cfg->adjoint_recompute) {
+      if (dev_alloc(env, &env->fl_hist, (size_t)cfg->episode_len * A) != cudaSuccess) {
+        cudaGetLastError();
+        env->fl_hist = nullptr;
+      }
+    }
   }
   if (cfg->block_size) env->warps = cfg->block_size / 32;
   env->split = cfg->obs_split;
@@ -876,6 +891,7 @@ gd_status gd_get_info(const gd_env* env, gd_info* info) {
   info->obs_split = env->split;
   info->adjoint_split = env->adj_split;
   info->adjoint_road_tile = env->adj_notile ? 0 : 1;
+  info->adjoint_recompute = env->fl_hist ? 1 : 0;
   info->objective_graph_kernels = env->ograph ? env->og_nodes[0] : 0;
   info->objective_graph_other = env->ograph ? env->og_nodes[1] : 0;
   info->backward_graph_kernels = env->bgraph ? env->bg_nodes[0] : 0;
@@ -991,7 +1007,8 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
                          cudaStream_t stream = nullptr, const DevEnv* dv = nullptr, const float* obs_w = nullptr,
                          float reward_w = 0.f, float* ell = nullptr, float* rk_out = nullptr,
                          unsigned* clear = nullptr, int clear_n = (int)OBS_STRIPES, float4* state_out = nullptr,
-                         uint8_t* flags_out = nullptr, LaunchTimer* tm = nullptr, uint16_t* sel_out = nullptr) {
+                         uint8_t* flags_out = nullptr, LaunchTimer* tm = nullptr, uint16_t* sel_out = nullptr,
+                         uint8_t* flags_rec = nullptr) {
   if (!stream) stream = env->stream;
   if (!dv) dv = &env->d;
   if (obs && env->split && (!ell || do_step)) {
@@ -1001,7 +1018,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
     // the step launch clears the observation counters; without a step, a memset does
     if (do_step)
       launch_world(env, actions, reward, done, world_done, nullptr, nullptr, nullptr, 1, stream, dv, nullptr, 0.f, ell,
-                   nullptr, env->ocounter, (int)OBS_STRIPES, nullptr, nullptr, tm);
+                   nullptr, env->ocounter, (int)OBS_STRIPES, nullptr, nullptr, tm, nullptr, flags_rec);
     else
       cudaMemsetAsync(env->ocounter, 0, OBS_STRIPES * sizeof(unsigned), stream);
     const SplitLoss loss{obs_w, reward_w, ell, rk_out, sel_out};
@@ -1034,6 +1051,7 @@ static void launch_world(gd_env* env, const float* actions, float* reward, uint8
   a.clear_n = clear ? clear_n : 0;
   a.state_out = state_out;
   a.flags_out = flags_out;
+  a.flags_rec = do_step ? flags_rec : nullptr;
   const bool step_only = obs == nullptr;
   const dim3 grid(step_only ? env->step_grid : env->world_grid);
   const size_t smem = step_only ? env->step_smem : env->world_smem;
@@ -1241,6 +1259,8 @@ static void issue_rollout_overlapped(gd_env* env, int steps, int t0, int t1, con
     a.state_out = out == in ? nullptr : sbuf[out];
     a.flags_out = out == in ? nullptr : fbuf[out];
     a.ell = ell ? ell + (size_t)t * A : nullptr;
+    // the objective rollout records its decisions for the backward pass
+    if (ell && env->fl_hist) a.flags_rec = env->fl_hist + (size_t)t * A;
     launch_step_ex(env, dv, a, stream, t > t0 && !ckpt);
     DevEnv dvo = env->d;
     dvo.state = sbuf[out];
@@ -1730,9 +1750,10 @@ static void issue_objective(gd_env* env, int steps, const float* actions, const 
       tend(tm);
     }
     launch_world(env, actions + (size_t)t * A * 2, nullptr, nullptr, nullptr, obs, nullptr, nullptr, 1, stream, nullptr,
-                 obs_weight, reward_weight, ell + (size_t)t * A, env->rk_hist + (size_t)t * A, nullptr,
-                 (int)OBS_STRIPES, nullptr, nullptr, tm,
-                 env->sel_hist ? env->sel_hist + (size_t)t * A * env->d.K : nullptr);
+                 obs_weight, reward_weight, ell + (size_t)t * A,
+                 env->rk_hist + (size_t)t * A, nullptr, (int)OBS_STRIPES, nullptr, nullptr, tm,
+                 env->sel_hist ? env->sel_hist + (size_t)t * A * env->d.K : nullptr,
+                 env->fl_hist ? env->fl_hist + (size_t)t * A : nullptr);
   }
 }
 
@@ -1742,7 +1763,8 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_diff(env, "gd_rollout_objective");
   if (st != GD_OK) return st;
-  if (steps < 1 || steps > env->n_ckpt * env->C)
+  // the per-step records (K-th distances, selections, decisions) hold episode_len steps
+  if (steps < 1 || steps > env->cfg.episode_len)
     return fail(env, GD_ERR_INVALID_ARG, "steps must be in 1..episode_len");
   if (!actions || !obs_weight || !ell) return fail(env, GD_ERR_INVALID_ARG, "actions, obs_weight and ell must not be NULL");
   if (!aligned16(obs_weight) || (obs && !aligned16(obs)))
@@ -1788,6 +1810,7 @@ gd_status gd_rollout_objective(gd_env* env, int32_t steps, const float* actions,
   env->diff_actions = actions;
   env->diff_steps = steps;
   env->sel_valid = env->sel_hist != nullptr;
+  env->rec_valid = env->fl_hist != nullptr;
   return launch_check(env, "gd_rollout_objective");
 }
 
@@ -1878,10 +1901,21 @@ static SegBuf seg_buf(gd_env* env, int which) {
                : SegBuf{env->segS, env->segF, env->segT, env->segWD};
 }
 
+// With t0 >= 0 (the segment's first step in the last objective rollout) and
+// that rollout's record of its decisions, one thread-per-agent launch
+// recomputes the states instead (the same states and flags, bit for bit).
 static void recompute_segment(gd_env* env, const float* actions0, int len, cudaStream_t stream = nullptr,
-                              LaunchTimer* tm = nullptr, int which = 0) {
+                              LaunchTimer* tm = nullptr, int which = 0, int t0 = -1) {
   const size_t A = (size_t)env->A;
   const SegBuf b = seg_buf(env, which);
+  if (!stream) stream = env->stream;
+  if (t0 >= 0 && env->rec_valid) {
+    tbegin(tm, 1);
+    k_recompute<<<blocks_for(env->A, 128), 128, 0, stream>>>(
+        env->d, reinterpret_cast<const float2*>(actions0), len, b.S, b.F, env->fl_hist + (size_t)t0 * A);
+    tend(tm);
+    return;
+  }
   DevEnv dv = env->d;
   dv.t = b.T;
   dv.world_done = b.WD;
@@ -1909,7 +1943,7 @@ static void issue_backward(gd_env* env, const float* obs_weight, float reward_we
     copy_snapshot(env, env->segS, env->segF, env->segT, env->segWD, env->ckS + seg * A, env->ckF + seg * A,
                   env->ckT + seg * W, env->ckWD + seg * W, stream);
     tend(tm);
-    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, stream, tm);
+    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, stream, tm, 0, t0);
     launch_adjoint(env, env->segS, env->segF, env->diff_actions + (size_t)t0 * A * 2, len, obs_weight, 0,
                    d_ell ? d_ell + (size_t)t0 * A : nullptr, nullptr, reward_weight, d_actions + (size_t)t0 * A * 2,
                    env->rk_hist + (size_t)t0 * A, stream, t0 + len == T, t0 == 0 ? d_state0 : nullptr, tm,
@@ -1943,7 +1977,7 @@ static void issue_backward_pipelined(gd_env* env, const float* obs_weight, float
     if (j >= 2) cudaStreamWaitEvent(sr, done_adj[(size_t)(j - 2)], 0);
     copy_snapshot(env, b.S, b.F, b.T, b.WD, env->ckS + seg * A, env->ckF + seg * A, env->ckT + seg * W,
                   env->ckWD + seg * W, sr);
-    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, sr, nullptr, which);
+    recompute_segment(env, env->diff_actions + (size_t)t0 * A * 2, len, sr, nullptr, which, t0);
     cudaEvent_t rec = event();
     cudaEventRecord(rec, sr);
     cudaStreamWaitEvent(cap, rec, 0);
@@ -2032,7 +2066,8 @@ gd_status gd_time_objective(gd_env* env, int32_t steps, const float* actions, co
   if (!env) return GD_ERR_INVALID_ARG;
   gd_status st = need_diff(env, "gd_time_objective");
   if (st != GD_OK) return st;
-  if (steps < 1 || steps > env->n_ckpt * env->C)
+  // the per-step records (K-th distances, selections, decisions) hold episode_len steps
+  if (steps < 1 || steps > env->cfg.episode_len)
     return fail(env, GD_ERR_INVALID_ARG, "steps must be in 1..episode_len");
   if (!actions || !obs_weight || !ell || !obs || !ms || !launches)
     return fail(env, GD_ERR_INVALID_ARG, "actions, obs_weight, ell, obs, ms and launches must not be NULL");
@@ -2052,6 +2087,7 @@ gd_status gd_time_objective(gd_env* env, int32_t steps, const float* actions, co
   env->diff_actions = actions;
   env->diff_steps = steps;
   env->sel_valid = env->sel_hist != nullptr;
+  env->rec_valid = env->fl_hist != nullptr;
   return launch_check(env, "gd_time_objective");
 }
 

@@ -50,6 +50,34 @@ __global__ void k_dynamics(DevEnv e, const float2* __restrict__ actions) {
   e.state[i] = s;
 }
 
+// The steps k = 0 .. len-1 of a checkpoint segment recomputed for the
+// backward pass from S[0] / F[0] (the segment's checkpoint), the steps'
+// actions and the forward rollout's record of its decisions, each step's
+// post-step flags fl_rec[k].  A thread per agent takes the step kernel's
+// state update (the dynamics of an agent neither done nor static, with the
+// same arithmetic; a differentiable env never restarts a world inside a
+// rollout), so S[k + 1] and F[k + 1] are bit for bit the step kernel's; the
+// collision, road-edge and goal decisions come from the record instead of
+// the grids.
+__global__ void k_recompute(DevEnv e, const float2* __restrict__ actions, int len, float4* __restrict__ S,
+                            uint8_t* __restrict__ F, const uint8_t* __restrict__ fl_rec) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e.A) return;
+  const float L = e.stat[i].x;
+  float4 s = S[i];
+  uint8_t f = F[i];
+  for (int k = 0; k < len; ++k) {
+    const size_t ik = (size_t)k * e.A + i;
+    if (!(f & (GD_FLAG_DONE | GD_FLAG_STATIC))) {
+      const float2 u = actions[ik];
+      if (!dynamics_step(e.dyn, s, u.x, u.y, L, e.dt, e.vmax)) atomicOr(e.err, ERR_ACTION);
+    }
+    f = fl_rec[ik];
+    S[ik + e.A] = s;
+    F[ik + e.A] = f;
+  }
+}
+
 // Cell coordinate clamped to the key's 12-bit range (clamping is monotone
 // and never separates two agents that are within one cell of each other).
 __device__ __forceinline__ int agent_cell(float v, float o, float inv) {

@@ -59,6 +59,8 @@ struct FusedArgs {
   // step's state in its own slot, without a copy per step.
   float4* state_out;
   uint8_t* flags_out;
+  uint8_t* flags_rec;        // [A] a second copy of the post-step flags (the objective rollout's record of
+                             // its decisions, for the backward pass's recompute), or nullptr
   LidarArgs lidar;           // LiDAR observation (k_world<W, true>); lidar.depth == nullptr: none
 };
 
@@ -497,6 +499,7 @@ __global__ void __launch_bounds__(WARPS * 32, LEAN ? 32 / WARPS : 1) k_world(Dev
         ag.fl[tid] = f;
         (a.state_out ? a.state_out : e.state)[i] = ag.st[tid];
         (a.flags_out ? a.flags_out : e.flags)[i] = f;
+        if (a.flags_rec) a.flags_rec[i] = f;
         if (a.reward) a.reward[i] = r;
         if (a.done) a.done[i] = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) ? 1 : 0;
         dn = (f & (GD_FLAG_DONE | GD_FLAG_STATIC)) != 0;

@@ -61,7 +61,7 @@ class gd_config(C.Structure):
                 ("lidar_rays", C.c_int32), ("lidar_fov", C.c_float), ("lidar_block_size", C.c_int32),
                 ("lidar_no_tile", C.c_int32), ("lidar_split", C.c_int32), ("dynamics", C.c_int32),
                 ("nontrivial_dist", C.c_float), ("road_no_tile", C.c_int32), ("obs_split", C.c_int32),
-                ("adjoint_split", C.c_int32)]
+                ("adjoint_split", C.c_int32), ("adjoint_recompute", C.c_int32)]
 
 
 class gd_scene_batch(C.Structure):
@@ -82,7 +82,7 @@ class gd_info(C.Structure):
                 ("road_tile", C.c_int32), ("obs_split", C.c_int32), ("adjoint_split", C.c_int32),
                 ("adjoint_road_tile", C.c_int32), ("objective_graph_kernels", C.c_int32),
                 ("objective_graph_other", C.c_int32), ("backward_graph_kernels", C.c_int32),
-                ("backward_graph_other", C.c_int32)]
+                ("backward_graph_other", C.c_int32), ("adjoint_recompute", C.c_int32)]
 
 
 _lib = None

@@ -303,7 +303,10 @@ def test_graph_pair_equals_host_issued_launches():
     assert info.objective_graph_other == 0 and info.backward_graph_other == 0
     per_step = 2 if info.obs_split else 1
     assert info.objective_graph_kernels == per_step * T + segs
-    assert info.backward_graph_kernels == segs + T + (2 * segs if info.adjoint_split else T)
+    # (the recomputed steps: one launch per segment from the recorded
+    # decisions, else a step launch per step)
+    recomputed = segs if info.adjoint_recompute else T
+    assert info.backward_graph_kernels == segs + recomputed + (2 * segs if info.adjoint_split else T)
 
 
 def test_parked_agents_graph_pair_equals_host_issued_launches():
@@ -533,7 +536,68 @@ def test_timed_passes_equal_the_rollout_calls():
     info = gd.gd_get_info(env.h)
     segs = (T + 9) // 10
     assert n_o[0] == segs and n_o[2] == T and n_o[1] == (T if info.obs_split else 0)
-    assert n_b[0] == segs and n_b[1] == T
+    assert n_b[0] == segs and n_b[1] == (segs if info.adjoint_recompute else T)
     assert n_b[2] == (segs if info.adjoint_split else T) and n_b[3] == (segs if info.adjoint_split else 0)
     assert all(m >= 0 for m in ms_o + ms_b) and sum(ms_b) > 0
+    env.close()
+
+
+@pytest.mark.parametrize("batched", [False, True])
+@pytest.mark.parametrize("parked", [False, True])
+def test_recompute_from_recorded_decisions_is_bit_identical(batched, parked):
+    # The backward pass recomputes a checkpoint segment's states in one
+    # thread-per-agent launch from the objective rollout's recorded
+    # decisions (each step's post-step flags) instead of a step launch per
+    # step.  Same states, so bit-identical terms and gradients, with agents
+    # that collide, leave the road or reach their goal inside the rollout,
+    # and with parked (static) agents.
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([6, 9, 17, 12]), np.array([700, 800, 1500, 900]), 31,
+                           parked_frac=0.4 if parked else 0.0)
+    ocfg = OracleConfig(k_road=48, n_partners=7, episode_len=23, term_collision=True, term_offroad=True,
+                        nontrivial_init=parked)
+    T = 23
+    acts = scenes.make_actions(T, sc.num_agents, 31)
+    rng = np.random.default_rng(31)
+    w = rng.uniform(0, 1, ocfg.feat)
+    d_ell = rng.uniform(0.5, 1.5, (T, sc.num_agents))
+    fl = _kw(ocfg)["flags"] | (gd.GD_BATCHED if batched else 0)
+    rec, info_r = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell, reps=2, flags=fl)
+    ref, info_s = _fwd_bwd(sc, ocfg, acts, w, 0.7, d_ell, flags=fl, adjoint_recompute=0)
+    assert info_r.adjoint_recompute == 1 and info_s.adjoint_recompute == 0
+    for rep in rec:
+        for a, b in zip(ref[0], rep):
+            np.testing.assert_array_equal(a, b)
+    assert np.isfinite(ref[0][1]).all() and np.isfinite(ref[0][2]).all()
+    # the decisions did change inside the rollout: some agents ended early
+    env = gd.Env(sc, **dict(_kw(ocfg), flags=fl))
+    a = torch.from_numpy(acts).cuda().contiguous()
+    done0 = None
+    for t in range(T):
+        env.step(a[t])
+        d = env.done.cpu().numpy().astype(bool)
+        if done0 is None:
+            done0 = d
+    env.close()
+    assert (d & ~done0).any()
+
+
+def test_objective_steps_are_bounded_by_the_episode():
+    # the per-step records hold episode_len steps: a longer objective rollout
+    # is refused before anything launches (episode_len 23 is not a multiple
+    # of the 10-step checkpoint interval)
+    from paper_2408_01584_b300 import gd
+    sc = scenes.make_scene(np.array([6, 9]), np.array([700, 800]), 3)
+    ocfg = OracleConfig(k_road=16, n_partners=7, episode_len=23)
+    env = gd.Env(sc, **_kw(ocfg))
+    T = 24
+    a = torch.zeros(T, sc.num_agents, 2, device="cuda")
+    wt = torch.ones(ocfg.feat, device="cuda")
+    ell = torch.empty(T, sc.num_agents, device="cuda")
+    with pytest.raises(gd.GdError) as err:
+        gd.gd_rollout_objective(env.h, T, a, wt, 1.0, ell, env.obs)
+    assert err.value.status == 1 and "episode_len" in str(err.value)      # GD_ERR_INVALID_ARG
+    gd.gd_rollout_objective(env.h, T - 1, a[: T - 1], wt, 1.0, ell[: T - 1], env.obs)
+    env.sync()
+    assert np.isfinite(ell[: T - 1].cpu().numpy()).all()
     env.close()
