@@ -601,3 +601,28 @@ def test_objective_steps_are_bounded_by_the_episode():
     env.sync()
     assert np.isfinite(ell[: T - 1].cpu().numpy()).all()
     env.close()
+
+
+def test_recompute_forms_identical_at_full_fwdbwd_8192():
+    # The whole 8,192-world forward+backward workload (658,227 agents,
+    # K = 200, P = 63, 91 steps) in the bench's batched form: the backward's
+    # one-launch recompute from the recorded flags and the step-kernel
+    # recompute give bit-identical objective terms and gradients.
+    import hashlib
+    from paper_2408_01584_b300 import gd
+    name = "fwdbwd_8192"
+    sc = scenes.workload_scene(name, 0)
+    ocfg = workload_config(name)
+    T = ocfg.episode_len
+    acts = scenes.make_actions(T, sc.num_agents, 0)
+    w = np.random.default_rng(0).uniform(0, 1, ocfg.feat)
+    fl = _kw(ocfg)["flags"] | gd.GD_BATCHED
+    digests = []
+    for rec in (1, 0):
+        outs, info = _fwd_bwd(sc, ocfg, acts, w, 1.0, flags=fl, adjoint_recompute=rec)
+        assert info.adjoint_recompute == rec
+        ell, da, ds = outs[0]
+        assert np.isfinite(da).all() and np.isfinite(ds).all() and np.abs(da).max() > 0
+        digests.append([hashlib.sha1(np.ascontiguousarray(x).tobytes()).hexdigest() for x in (ell, da, ds)])
+        del outs, ell, da, ds
+    assert digests[0] == digests[1]
